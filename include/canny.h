@@ -1,0 +1,175 @@
+/*
+ * canny.h -- C ABI of libcanny, a GB300 (sm_103a) Canny edge detector.
+ *
+ * The operation is the four-step pipeline of H. Mogale, "High Performance
+ * Canny Edge Detector using Parallel Patterns for Scalability on Modern
+ * Multicore Processors", Sec. 2.2.1 (Algorithm 1; Steps 1-4):
+ *   Step 1  Gaussian noise filter;
+ *   Step 2  Sobel gradient: strength and direction;
+ *   Step 3  non-maximum suppression;
+ *   Step 4  hysteresis: strength above the upper threshold is an edge, below
+ *           the lower one is not, in between is an edge only if connected to
+ *           an edge pixel above the upper threshold.
+ * The paper states the problem as: a grayscale image, a smoothing parameter
+ * and two thresholds in; an edge map out.
+ *
+ * Constants the paper leaves open are fixed as follows.
+ *   Integer path (CANNY_PATH_INT, bit-exact):
+ *     - 5x5 binomial Gaussian (1,4,6,4,1)^2 / 256, rounded half up;
+ *     - replicate (clamp-to-edge) border for the image and the smoothed image;
+ *     - Sobel Gx (x right), Gy (y down), strength Gx^2 + Gy^2;
+ *     - direction: 4 sectors with tan(22.5 deg) as 13573 / 2^15;
+ *     - suppression keeps a pixel that beats its negative-side neighbour
+ *       strictly and its positive-side neighbour or ties it; neighbours
+ *       outside the image count as 0;
+ *     - thresholds compared squared and strictly: weak if low^2 < G^2 <= high^2,
+ *       strong if G^2 > high^2; low and high must be integers in [0, 2^15);
+ *     - hysteresis through 8-connected weak/strong pixels.
+ *   Float path (CANNY_PATH_F32): sigma-parametrised separable Gaussian of odd
+ *     size ksize (taps exp(-k^2 / 2 sigma^2), normalised), float32 Sobel and
+ *     L2 strength, tan(22.5 deg) as 0.41421356f, thresholds low/high given as
+ *     fractions of the image's largest strength.
+ *
+ * Memory and ownership. All image pointers are device pointers (cudaMalloc,
+ * torch tensors) unless a function says "host". The caller owns every image
+ * buffer and the stream; the context owns its scratch (hysteresis tile state
+ * and worklists, the float path's strength buffer, the CUDA graph). The input
+ * is never written. The output must not overlap the input. Images are
+ * row-major uint8, row stride = pitch bytes (pitch >= width). Only the first
+ * `w` bytes of each output row are written; output values are 0 or 255.
+ *
+ * Errors. Functions return a canny_status and never abort. Argument errors
+ * are reported synchronously, before any work is queued. Launch failures
+ * return CANNY_ECUDA. Work is queued asynchronously on the given stream
+ * (a cudaStream_t passed as void*; NULL is the legacy default stream);
+ * an error raised while that work runs (including CANNY_ENOCONVERGE, the
+ * hysteresis pass cap) is reported by canny_get_stats(), which synchronises.
+ *
+ * Threads. A context serves one stream at a time: calls that share a context
+ * must be ordered on the same stream. Separate contexts are independent.
+ */
+#ifndef CANNY_H
+#define CANNY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CANNY_OK = 0,
+    CANNY_EINVAL = 1,          /* bad argument: null pointer, size, pitch, threshold */
+    CANNY_ENOMEM = 2,          /* device or pinned allocation failed */
+    CANNY_ECUDA = 3,           /* a CUDA call or kernel launch failed */
+    CANNY_ENOCONVERGE = 4,     /* hysteresis hit its pass cap before its fixpoint */
+    CANNY_EUNSUPPORTED = 5     /* request outside what this build supports */
+} canny_status;
+
+enum { CANNY_PATH_INT = 0, CANNY_PATH_F32 = 1 };
+
+typedef struct {
+    int path;          /* CANNY_PATH_INT or CANNY_PATH_F32 */
+    float sigma;       /* float path: Gaussian sigma (> 0); ignored by the integer path */
+    int ksize;         /* float path: odd kernel size in [3, 31]; the integer path uses 5 */
+    float low, high;   /* integer path: absolute strengths (integers, compared squared);
+                          float path: fractions of the largest strength; low <= high */
+    int max_passes;    /* cap on global hysteresis passes; 0 = automatic */
+} canny_params;
+
+/* One image of a pitched run or of a batch. */
+typedef struct {
+    const uint8_t *d_in;   /* device, h rows of in_pitch bytes */
+    uint8_t *d_out;        /* device, h rows of out_pitch bytes; not overlapping d_in */
+    int w, h;              /* pixels; w == 0 or h == 0 is an empty image (nothing written) */
+    int in_pitch, out_pitch;
+} canny_image;
+
+/* Counters of the most recent run on a context (read after synchronising). */
+typedef struct {
+    int64_t images;            /* images in the last run */
+    int64_t pixels;            /* pixels in the last run */
+    int64_t tiles;             /* 32x32 hysteresis tiles in the last run */
+    int64_t hyst_passes;       /* global hysteresis passes the last run took */
+    int64_t hyst_tiles_visited;/* tile visits summed over those passes */
+    int64_t pending_tiles;     /* tiles left with unresolved weak pixels after the local fill */
+    int32_t status;            /* canny_status of the last run's device work */
+    int32_t reserved;
+} canny_stats;
+
+typedef struct canny_ctx canny_ctx;
+
+/* Fill *p with the defaults: integer path, low 40, high 100, sigma 1.4, ksize 7. */
+canny_status canny_params_default(canny_params *p);
+
+/*
+ * Create a context for images of at most max_w x max_h pixels (the pixel
+ * budget max_w * max_h also bounds the total pixels of one canny_run_batch
+ * call). Allocates the scratch on the current device. Returns CANNY_EINVAL for
+ * non-positive sizes or invalid params, CANNY_ENOMEM if allocation fails.
+ */
+canny_status canny_create(int max_w, int max_h, const canny_params *p, canny_ctx **out);
+
+/* Free the context and its scratch. Synchronises the device first. NULL is a no-op. */
+void canny_destroy(canny_ctx *ctx);
+
+/*
+ * Edge map of one max_w x max_h image with tight rows (pitch = max_w): d_in and
+ * d_out are device buffers of max_w * max_h bytes. d_out doubles as the class
+ * map between the stencil and the hysteresis, so no other image-sized scratch
+ * is used on the integer path. Asynchronous on stream.
+ */
+canny_status canny_run(canny_ctx *ctx, const uint8_t *d_in, uint8_t *d_out, void *stream);
+
+/* Edge map of one image of any size up to the context's, with its own pitches. */
+canny_status canny_run_pitched(canny_ctx *ctx, const canny_image *img, void *stream);
+
+/*
+ * Edge maps of n images of any sizes (total pixels at most max_w * max_h, the
+ * context's pixel budget) in one launch sequence: every stage runs
+ * once over the tiles of all images. The image descriptors are read from host
+ * memory before the call returns. Outputs equal n separate canny_run_pitched
+ * calls byte for byte.
+ */
+canny_status canny_run_batch(canny_ctx *ctx, int n, const canny_image *imgs, void *stream);
+
+/*
+ * End-to-end call on host buffers: copies h_in (host, h rows of in_pitch bytes)
+ * to the device, runs the pipeline and copies the edge map back to h_out (host,
+ * h rows of out_pitch bytes); returns after the stream has been synchronised.
+ * Pinned (page-locked) host buffers give the fastest copies. Device buffers for
+ * the copies are owned by the context.
+ */
+canny_status canny_run_host(canny_ctx *ctx, const uint8_t *h_in, int in_pitch, uint8_t *h_out,
+                            int out_pitch, int w, int h, void *stream);
+
+/*
+ * Steps 1-3 and the double threshold only: the class map before hysteresis,
+ * 0 (none), 1 (weak) or 2 (strong) per pixel, into img->d_out.
+ */
+canny_status canny_classify(canny_ctx *ctx, const canny_image *img, void *stream);
+
+/*
+ * Step 4 only: img->d_in holds a class map (0 none, 1 weak, 2 strong; other
+ * values count as strong); the 0/255 edge map goes to img->d_out.
+ */
+canny_status canny_hysteresis(canny_ctx *ctx, const canny_image *img, void *stream);
+
+/*
+ * Float path, Steps 1-2 only: the gradient strength M (float32, row stride
+ * d_mag_pitch floats) of img into d_mag, and the image's largest strength into
+ * *d_max (device float). The context must use CANNY_PATH_F32.
+ */
+canny_status canny_magnitude_f32(canny_ctx *ctx, const canny_image *img, float *d_mag,
+                                 int d_mag_pitch, float *d_max, void *stream);
+
+/* Copy the counters of the last run into *out. Synchronises the context's last stream. */
+canny_status canny_get_stats(canny_ctx *ctx, canny_stats *out);
+
+/* Static, human-readable message for a status. */
+const char *canny_strerror(canny_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CANNY_H */

@@ -1,0 +1,226 @@
+"""Thin ctypes binding of libcanny's C ABI (``include/canny.h``).
+
+The functions keep the C names and argument order; only marshalling happens
+here (torch tensors and streams become raw pointers). Every step of the edge
+detector runs in the CUDA library. There is no CPU fallback: if the library
+is missing or no CUDA device is visible, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Sequence
+
+from . import build as _build
+
+CANNY_OK, CANNY_EINVAL, CANNY_ENOMEM, CANNY_ECUDA, CANNY_ENOCONVERGE, CANNY_EUNSUPPORTED = range(6)
+CANNY_PATH_INT, CANNY_PATH_F32 = 0, 1
+
+
+class CannyError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {strerror(status)} (status {status})")
+
+
+class canny_params(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int), ("sigma", ctypes.c_float), ("ksize", ctypes.c_int),
+                ("low", ctypes.c_float), ("high", ctypes.c_float), ("max_passes", ctypes.c_int)]
+
+
+class canny_image(ctypes.Structure):
+    _fields_ = [("d_in", ctypes.c_void_p), ("d_out", ctypes.c_void_p), ("w", ctypes.c_int),
+                ("h", ctypes.c_int), ("in_pitch", ctypes.c_int), ("out_pitch", ctypes.c_int)]
+
+
+class canny_stats(ctypes.Structure):
+    _fields_ = [("images", ctypes.c_int64), ("pixels", ctypes.c_int64), ("tiles", ctypes.c_int64),
+                ("hyst_passes", ctypes.c_int64), ("hyst_tiles_visited", ctypes.c_int64),
+                ("pending_tiles", ctypes.c_int64), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+_lib = None
+_lock = threading.Lock()
+
+# C name -> (argtypes, restype); every symbol include/canny.h declares
+_P = ctypes.c_void_p
+SIGNATURES = {
+    "canny_params_default": ([ctypes.POINTER(canny_params)], ctypes.c_int),
+    "canny_create": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(canny_params), ctypes.POINTER(_P)],
+                     ctypes.c_int),
+    "canny_destroy": ([_P], None),
+    "canny_run": ([_P, _P, _P, _P], ctypes.c_int),
+    "canny_run_pitched": ([_P, ctypes.POINTER(canny_image), _P], ctypes.c_int),
+    "canny_run_batch": ([_P, ctypes.c_int, ctypes.POINTER(canny_image), _P], ctypes.c_int),
+    "canny_run_host": ([_P, _P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P],
+                       ctypes.c_int),
+    "canny_classify": ([_P, ctypes.POINTER(canny_image), _P], ctypes.c_int),
+    "canny_hysteresis": ([_P, ctypes.POINTER(canny_image), _P], ctypes.c_int),
+    "canny_magnitude_f32": ([_P, ctypes.POINTER(canny_image), _P, ctypes.c_int, _P, _P],
+                            ctypes.c_int),
+    "canny_get_stats": ([_P, ctypes.POINTER(canny_stats)], ctypes.c_int),
+    "canny_strerror": ([ctypes.c_int], ctypes.c_char_p),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libcanny.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build_if_missing:
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError(f"libcanny.so not built ({_build.LIB}); run __graft_entry__.build()")
+            L = ctypes.CDLL(_build.LIB)
+            for name, (args, res) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+        return _lib
+
+
+def strerror(status: int) -> str:
+    return load().canny_strerror(status).decode()
+
+
+def _check(status: int, where: str) -> None:
+    if status != CANNY_OK:
+        raise CannyError(status, where)
+
+
+# ------------------------------------------------------------------ C-named calls
+def canny_params_default() -> canny_params:
+    p = canny_params()
+    _check(load().canny_params_default(ctypes.byref(p)), "canny_params_default")
+    return p
+
+
+def canny_create(max_w: int, max_h: int, params: canny_params) -> int:
+    ctx = _P()
+    _check(load().canny_create(max_w, max_h, ctypes.byref(params), ctypes.byref(ctx)), "canny_create")
+    return ctx.value
+
+
+def canny_destroy(ctx: int) -> None:
+    load().canny_destroy(ctx)
+
+
+def canny_run(ctx: int, d_in: int, d_out: int, stream: int = 0) -> None:
+    _check(load().canny_run(ctx, d_in, d_out, stream), "canny_run")
+
+
+def canny_run_pitched(ctx: int, img: canny_image, stream: int = 0) -> None:
+    _check(load().canny_run_pitched(ctx, ctypes.byref(img), stream), "canny_run_pitched")
+
+
+def canny_run_batch(ctx: int, imgs: Sequence[canny_image], stream: int = 0) -> None:
+    arr = (canny_image * len(imgs))(*imgs)
+    _check(load().canny_run_batch(ctx, len(imgs), arr, stream), "canny_run_batch")
+
+
+def canny_run_host(ctx: int, h_in: int, in_pitch: int, h_out: int, out_pitch: int, w: int, h: int,
+                   stream: int = 0) -> None:
+    _check(load().canny_run_host(ctx, h_in, in_pitch, h_out, out_pitch, w, h, stream), "canny_run_host")
+
+
+def canny_classify(ctx: int, img: canny_image, stream: int = 0) -> None:
+    _check(load().canny_classify(ctx, ctypes.byref(img), stream), "canny_classify")
+
+
+def canny_hysteresis(ctx: int, img: canny_image, stream: int = 0) -> None:
+    _check(load().canny_hysteresis(ctx, ctypes.byref(img), stream), "canny_hysteresis")
+
+
+def canny_magnitude_f32(ctx: int, img: canny_image, d_mag: int, d_mag_pitch: int, d_max: int,
+                        stream: int = 0) -> None:
+    _check(load().canny_magnitude_f32(ctx, ctypes.byref(img), d_mag, d_mag_pitch, d_max, stream),
+           "canny_magnitude_f32")
+
+
+def canny_get_stats(ctx: int) -> canny_stats:
+    st = canny_stats()
+    _check(load().canny_get_stats(ctx, ctypes.byref(st)), "canny_get_stats")
+    return st
+
+
+# ------------------------------------------------------------------ torch marshalling
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def image_of(t_in, t_out, w: int | None = None, h: int | None = None) -> canny_image:
+    """canny_image over two 2-D uint8 CUDA tensors (row stride = pitch)."""
+    for t in (t_in, t_out):
+        if not t.is_cuda or t.dtype.itemsize != 1 or t.dim() != 2 or t.stride(1) != 1:
+            raise ValueError("expected 2-D uint8 CUDA tensors with unit column stride")
+    hh = t_in.shape[0] if h is None else h
+    ww = t_in.shape[1] if w is None else w
+    return canny_image(t_in.data_ptr(), t_out.data_ptr(), ww, hh, t_in.stride(0), t_out.stride(0))
+
+
+class Canny:
+    """A context (``canny_create``) with torch-tensor convenience calls."""
+
+    def __init__(self, max_w: int, max_h: int, *, path: int = CANNY_PATH_INT, low: float = 40.0,
+                 high: float = 100.0, sigma: float = 1.4, ksize: int = 7, max_passes: int = 0):
+        p = canny_params_default()
+        p.path, p.low, p.high, p.sigma, p.ksize, p.max_passes = path, low, high, sigma, ksize, max_passes
+        self.max_w, self.max_h, self.params = max_w, max_h, p
+        self.ctx = canny_create(max_w, max_h, p)
+
+    def close(self) -> None:
+        if self.ctx:
+            canny_destroy(self.ctx)
+            self.ctx = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def run(self, t_in, t_out, stream=None) -> None:
+        """Tight max_w x max_h image: canny_run."""
+        canny_run(self.ctx, t_in.data_ptr(), t_out.data_ptr(), _stream_ptr(stream))
+
+    def run_pitched(self, t_in, t_out, stream=None) -> None:
+        canny_run_pitched(self.ctx, image_of(t_in, t_out), _stream_ptr(stream))
+
+    def run_batch(self, pairs, stream=None) -> None:
+        canny_run_batch(self.ctx, [image_of(a, b) for a, b in pairs], _stream_ptr(stream))
+
+    def classify(self, t_in, t_cls, stream=None) -> None:
+        canny_classify(self.ctx, image_of(t_in, t_cls), _stream_ptr(stream))
+
+    def hysteresis(self, t_cls, t_out, stream=None) -> None:
+        canny_hysteresis(self.ctx, image_of(t_cls, t_out), _stream_ptr(stream))
+
+    def magnitude(self, t_in, t_mag, t_max, stream=None) -> None:
+        img = canny_image(t_in.data_ptr(), 0, t_in.shape[1], t_in.shape[0], t_in.stride(0), 0)
+        canny_magnitude_f32(self.ctx, img, t_mag.data_ptr(), t_mag.stride(0), t_max.data_ptr(),
+                            _stream_ptr(stream))
+
+    def stats(self) -> dict:
+        return canny_get_stats(self.ctx).as_dict()

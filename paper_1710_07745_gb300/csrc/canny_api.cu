@@ -1,0 +1,476 @@
+// canny_api.cu -- the C ABI of libcanny (declared in include/canny.h): argument
+// checks, context scratch, and the launch sequence of the pipeline
+//   stencil (Steps 1-3 + thresholds) -> local fill -> global passes (Step 4).
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "canny_internal.cuh"
+
+using namespace canny;
+
+struct canny_ctx {
+    int max_w = 0, max_h = 0;
+    canny_params p = {};
+    IntThresholds it = {};
+    FloatParams fp = {};
+
+    HystScratch hs = {};
+    void *hyst_mem = nullptr;          // one allocation for the hysteresis scratch
+    float *mag = nullptr;              // float path: strength after suppression
+    float *d_max = nullptr;            // float path: the image's largest strength
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int use_graph = 1;                 // 0 after a graph could not be built: host-driven passes
+    uint32_t *h_state = nullptr;       // pinned copy of the device control block
+
+    uint8_t *d_host_in = nullptr, *d_host_out = nullptr;   // buffers of canny_run_host
+
+    HystImage *h_imgs = nullptr;       // pinned staging for batch descriptors
+    uint32_t h_imgs_cap = 0;
+    cudaEvent_t staging_free = nullptr;
+
+    cudaStream_t last_stream = nullptr;
+    canny_stats last = {};
+};
+
+namespace {
+
+canny_status from_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess) return CANNY_OK;
+    if (e == cudaErrorMemoryAllocation) return CANNY_ENOMEM;
+    return CANNY_ECUDA;
+}
+
+bool is_int_valued(float v) { return v == floorf(v); }
+
+canny_status check_params(const canny_params *p)
+{
+    if (!p) return CANNY_EINVAL;
+    if (p->path != CANNY_PATH_INT && p->path != CANNY_PATH_F32) return CANNY_EINVAL;
+    if (!(p->low >= 0.f) || !(p->high >= 0.f) || !(p->low <= p->high)) return CANNY_EINVAL;
+    if (p->max_passes < 0) return CANNY_EINVAL;
+    if (p->path == CANNY_PATH_INT) {
+        if (!is_int_valued(p->low) || !is_int_valued(p->high) || p->high >= 32768.f) return CANNY_EINVAL;
+    } else {
+        if (!(p->sigma > 0.f) || p->ksize < 3 || p->ksize > MAX_KSIZE || (p->ksize % 2) == 0)
+            return CANNY_EINVAL;
+    }
+    return CANNY_OK;
+}
+
+uint32_t tiles_of(int w, int h)
+{
+    if (w <= 0 || h <= 0) return 0;
+    return (uint32_t)((w + HT - 1) / HT) * (uint32_t)((h + HT - 1) / HT);
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+void free_hyst(canny_ctx *c)
+{
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->exec = nullptr;
+    c->graph = nullptr;
+    if (c->hyst_mem) cudaFree(c->hyst_mem);
+    c->hyst_mem = nullptr;
+    c->hs = HystScratch{};
+}
+
+// (Re)allocate the hysteresis scratch for at least max_tiles tiles and max_imgs images.
+canny_status ensure_hyst(canny_ctx *c, uint32_t max_tiles, uint32_t max_imgs)
+{
+    if (c->hyst_mem && c->hs.max_tiles >= max_tiles && c->hs.max_imgs >= max_imgs) return CANNY_OK;
+    if (c->hyst_mem) {
+        cudaDeviceSynchronize();
+        max_tiles = max_tiles > c->hs.max_tiles ? max_tiles : c->hs.max_tiles;
+        max_imgs = max_imgs > c->hs.max_imgs ? max_imgs : c->hs.max_imgs;
+        free_hyst(c);
+    }
+    if (max_tiles < 1) max_tiles = 1;
+    if (max_imgs < 1) max_imgs = 1;
+    size_t off_imgs = 0;
+    size_t off_masks = align_up(off_imgs + sizeof(HystImage) * max_imgs, 256);
+    size_t off_pend = align_up(off_masks + sizeof(TileMasks) * max_tiles, 256);
+    size_t off_stamp = align_up(off_pend + sizeof(uint32_t) * HT * (size_t)max_tiles, 256);
+    size_t off_lists = align_up(off_stamp + sizeof(uint32_t) * (size_t)max_tiles, 256);
+    size_t off_state = align_up(off_lists + sizeof(uint32_t) * 2 * (size_t)max_tiles, 256);
+    size_t total = align_up(off_state + sizeof(HystState), 256);
+    void *mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return CANNY_ENOMEM;
+    }
+    char *b = (char *)mem;
+    c->hyst_mem = mem;
+    c->hs.imgs = (HystImage *)(b + off_imgs);
+    c->hs.masks = (TileMasks *)(b + off_masks);
+    c->hs.pend_bits = (uint32_t *)(b + off_pend);
+    c->hs.stamp = (uint32_t *)(b + off_stamp);
+    c->hs.lists = (uint32_t *)(b + off_lists);
+    c->hs.state = (HystState *)(b + off_state);
+    c->hs.max_tiles = max_tiles;
+    c->hs.max_imgs = max_imgs;
+    if (cudaMemset(c->hs.state, 0, sizeof(HystState)) != cudaSuccess) return CANNY_ECUDA;
+    if (c->use_graph) {
+        if (hyst_build_graph(c->hs, &c->graph, &c->exec) != cudaSuccess) {
+            cudaGetLastError();
+            c->use_graph = 0;
+            c->graph = nullptr;
+            c->exec = nullptr;
+        }
+    }
+    return CANNY_OK;
+}
+
+uint32_t auto_max_passes(uint32_t ntiles)
+{
+    // Every pass that queues another promotes at least one pending border pixel
+    // (at most 4 * 32 - 4 per tile), so this bound is never reached by a correct run.
+    uint64_t cap = 64 + (uint64_t)(4 * HT - 4) * ntiles;
+    return cap > 0x7fffffffu ? 0x7fffffffu : (uint32_t)cap;
+}
+
+// Queue the global passes of the current run (after hyst_reset + local fill).
+canny_status run_global(canny_ctx *c, cudaStream_t s)
+{
+    if (c->use_graph && c->exec) return from_cuda(cudaGraphLaunch(c->exec, s));
+    // host-driven loop: one pass, read the control block, repeat
+    for (;;) {
+        cudaError_t e = launch_hyst_global_pass(c->hs, hyst_pass_grid(), false, 0, s);
+        if (e != cudaSuccess) return from_cuda(e);
+        e = cudaMemcpyAsync(c->h_state, c->hs.state, sizeof(HystState), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return from_cuda(e);
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return from_cuda(e);
+        const HystState *st = (const HystState *)c->h_state;
+        if (!st->keep_going) return CANNY_OK;
+    }
+}
+
+// per_dim: the image must fit max_w x max_h; otherwise only the pixel budget binds.
+canny_status check_image(const canny_ctx *c, const canny_image *im, bool per_dim = true)
+{
+    if (!im) return CANNY_EINVAL;
+    if (im->w < 0 || im->h < 0) return CANNY_EINVAL;
+    if (im->w == 0 || im->h == 0) return CANNY_OK;
+    if (per_dim && (im->w > c->max_w || im->h > c->max_h)) return CANNY_EINVAL;
+    if ((int64_t)im->w * im->h > (int64_t)c->max_w * c->max_h) return CANNY_EINVAL;
+    if (!im->d_in || !im->d_out) return CANNY_EINVAL;
+    if (im->in_pitch < im->w || im->out_pitch < im->w) return CANNY_EINVAL;
+    // the output must not overlap the input
+    const char *a0 = (const char *)im->d_in, *a1 = a0 + (int64_t)(im->h - 1) * im->in_pitch + im->w;
+    const char *b0 = (const char *)im->d_out, *b1 = b0 + (int64_t)(im->h - 1) * im->out_pitch + im->w;
+    if (a0 < b1 && b0 < a1) return CANNY_EINVAL;
+    return CANNY_OK;
+}
+
+// Steps 1-3 + thresholds into im->d_out as a class map.
+canny_status run_stencil(canny_ctx *c, const canny_image *im, cudaStream_t s)
+{
+    if (c->p.path == CANNY_PATH_INT)
+        return from_cuda(launch_k1_classify_u8(im->d_in, im->in_pitch, im->d_out, im->out_pitch,
+                                               im->w, im->h, c->it, s));
+    cudaError_t e = cudaMemsetAsync(c->d_max, 0, sizeof(float), s);
+    if (e == cudaSuccess)
+        e = launch_k1f_magnitude(im->d_in, im->in_pitch, c->mag, im->w, im->w, im->h, c->fp, true,
+                                 c->d_max, s);
+    if (e == cudaSuccess)
+        e = launch_k1f_classify(c->mag, im->w, im->d_out, im->out_pitch, im->w, im->h, c->d_max,
+                                c->fp.lo_frac, c->fp.hi_frac, s);
+    return from_cuda(e);
+}
+
+HystImage hyst_image(const canny_image *im, uint32_t base)
+{
+    HystImage h = {};
+    h.map = im->d_out;
+    h.w = im->w;
+    h.h = im->h;
+    h.pitch = im->out_pitch;
+    h.ntx = (im->w + HT - 1) / HT;
+    h.nty = (im->h + HT - 1) / HT;
+    h.tile_base = base;
+    return h;
+}
+
+uint32_t max_passes_for(const canny_ctx *c, uint32_t ntiles)
+{
+    return c->p.max_passes > 0 ? (uint32_t)c->p.max_passes : auto_max_passes(ntiles);
+}
+
+canny_status run_one(canny_ctx *c, const canny_image *im, cudaStream_t s, bool stencil = true)
+{
+    canny_status st = check_image(c, im);
+    if (st != CANNY_OK) return st;
+    c->last = canny_stats{};
+    c->last.images = 1;
+    c->last_stream = s;
+    if (im->w == 0 || im->h == 0) return CANNY_OK;
+    uint32_t ntiles = tiles_of(im->w, im->h);
+    st = ensure_hyst(c, ntiles, 1);
+    if (st != CANNY_OK) return st;
+    c->last.pixels = (int64_t)im->w * im->h;
+    c->last.tiles = ntiles;
+    if (stencil) {
+        st = run_stencil(c, im, s);
+    } else {
+        st = from_cuda(cudaMemcpy2DAsync(im->d_out, im->out_pitch, im->d_in, im->in_pitch, im->w, im->h,
+                                         cudaMemcpyDeviceToDevice, s));
+    }
+    if (st != CANNY_OK) return st;
+    st = from_cuda(hyst_reset(c->hs, ntiles, 1, max_passes_for(c, ntiles), s));
+    if (st != CANNY_OK) return st;
+    st = from_cuda(launch_hyst_local_single(c->hs, hyst_image(im, 0), s));
+    if (st != CANNY_OK) return st;
+    return run_global(c, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+canny_status canny_params_default(canny_params *p)
+{
+    if (!p) return CANNY_EINVAL;
+    p->path = CANNY_PATH_INT;
+    p->sigma = 1.4f;
+    p->ksize = 7;
+    p->low = 40.f;
+    p->high = 100.f;
+    p->max_passes = 0;
+    return CANNY_OK;
+}
+
+canny_status canny_create(int max_w, int max_h, const canny_params *p, canny_ctx **out)
+{
+    if (!out) return CANNY_EINVAL;
+    *out = nullptr;
+    if (max_w <= 0 || max_h <= 0) return CANNY_EINVAL;
+    if ((int64_t)max_w * max_h > ((int64_t)1 << 34)) return CANNY_EINVAL;
+    canny_status st = check_params(p);
+    if (st != CANNY_OK) return st;
+
+    canny_ctx *c = new (std::nothrow) canny_ctx();
+    if (!c) return CANNY_ENOMEM;
+    c->max_w = max_w;
+    c->max_h = max_h;
+    c->p = *p;
+    if (p->path == CANNY_PATH_INT) {
+        c->it.lo2 = (int)p->low * (int)p->low;
+        c->it.hi2 = (int)p->high * (int)p->high;
+    } else {
+        // Step 1 taps: exp(-k^2 / (2 sigma^2)), normalised in double, rounded to float
+        int r = p->ksize / 2;
+        double g[MAX_KSIZE], sum = 0.0, sd = (double)p->sigma;
+        for (int k = -r; k <= r; ++k) {
+            g[k + r] = exp(-(double)(k * k) / (2.0 * sd * sd));
+            sum += g[k + r];
+        }
+        for (int k = 0; k < p->ksize; ++k) c->fp.taps[k] = (float)(g[k] / sum);
+        c->fp.ksize = p->ksize;
+        c->fp.lo_frac = p->low;
+        c->fp.hi_frac = p->high;
+    }
+    if (getenv("CANNY_NO_GRAPH")) c->use_graph = 0;
+
+    cudaError_t e = cudaHostAlloc((void **)&c->h_state, sizeof(HystState), cudaHostAllocDefault);
+    if (e != cudaSuccess) { cudaGetLastError(); delete c; return CANNY_ENOMEM; }
+    e = cudaEventCreateWithFlags(&c->staging_free, cudaEventDisableTiming);
+    if (e != cudaSuccess) { cudaGetLastError(); canny_destroy(c); return from_cuda(e); }
+    st = ensure_hyst(c, tiles_of(max_w, max_h), 1);
+    if (st != CANNY_OK) { canny_destroy(c); return st; }
+    if (p->path == CANNY_PATH_F32) {
+        e = cudaMalloc((void **)&c->mag, sizeof(float) * (size_t)max_w * max_h);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_max, sizeof(float));
+        if (e != cudaSuccess) { cudaGetLastError(); canny_destroy(c); return CANNY_ENOMEM; }
+    }
+    *out = c;
+    return CANNY_OK;
+}
+
+void canny_destroy(canny_ctx *c)
+{
+    if (!c) return;
+    cudaDeviceSynchronize();
+    free_hyst(c);
+    if (c->mag) cudaFree(c->mag);
+    if (c->d_max) cudaFree(c->d_max);
+    if (c->d_host_in) cudaFree(c->d_host_in);
+    if (c->d_host_out) cudaFree(c->d_host_out);
+    if (c->h_state) cudaFreeHost(c->h_state);
+    if (c->h_imgs) cudaFreeHost(c->h_imgs);
+    if (c->staging_free) cudaEventDestroy(c->staging_free);
+    delete c;
+}
+
+canny_status canny_run(canny_ctx *c, const uint8_t *d_in, uint8_t *d_out, void *stream)
+{
+    if (!c) return CANNY_EINVAL;
+    canny_image im = {d_in, d_out, c->max_w, c->max_h, c->max_w, c->max_w};
+    return run_one(c, &im, (cudaStream_t)stream);
+}
+
+canny_status canny_run_pitched(canny_ctx *c, const canny_image *img, void *stream)
+{
+    if (!c) return CANNY_EINVAL;
+    return run_one(c, img, (cudaStream_t)stream);
+}
+
+canny_status canny_run_batch(canny_ctx *c, int n, const canny_image *imgs, void *stream)
+{
+    if (!c || n < 0 || (n > 0 && !imgs)) return CANNY_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t pixels = 0;
+    uint32_t ntiles = 0, nimg = 0;
+    for (int i = 0; i < n; ++i) {
+        canny_status st = check_image(c, &imgs[i], false);
+        if (st != CANNY_OK) return st;
+        pixels += (int64_t)imgs[i].w * imgs[i].h;
+        uint32_t t = tiles_of(imgs[i].w, imgs[i].h);
+        if (t) { ntiles += t; ++nimg; }
+    }
+    if (pixels > (int64_t)c->max_w * c->max_h) return CANNY_EINVAL;
+    c->last = canny_stats{};
+    c->last.images = n;
+    c->last.pixels = pixels;
+    c->last.tiles = ntiles;
+    c->last_stream = s;
+    if (nimg == 0) return CANNY_OK;
+    canny_status st = ensure_hyst(c, ntiles, nimg);
+    if (st != CANNY_OK) return st;
+    if (c->h_imgs_cap < nimg) {
+        cudaEventSynchronize(c->staging_free);
+        if (c->h_imgs) cudaFreeHost(c->h_imgs);
+        c->h_imgs = nullptr;
+        c->h_imgs_cap = 0;
+        if (cudaHostAlloc((void **)&c->h_imgs, sizeof(HystImage) * nimg, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return CANNY_ENOMEM;
+        }
+        c->h_imgs_cap = nimg;
+    }
+    // the staging buffer may still feed the previous batch's upload
+    cudaError_t e = cudaEventSynchronize(c->staging_free);
+    if (e != cudaSuccess) return from_cuda(e);
+    uint32_t base = 0, k = 0;
+    for (int i = 0; i < n; ++i) {
+        uint32_t t = tiles_of(imgs[i].w, imgs[i].h);
+        if (!t) continue;
+        c->h_imgs[k++] = hyst_image(&imgs[i], base);
+        base += t;
+    }
+    e = cudaMemcpyAsync(c->hs.imgs, c->h_imgs, sizeof(HystImage) * nimg, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(c->staging_free, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    for (int i = 0; i < n; ++i) {
+        if (imgs[i].w == 0 || imgs[i].h == 0) continue;
+        st = run_stencil(c, &imgs[i], s);
+        if (st != CANNY_OK) return st;
+    }
+    st = from_cuda(hyst_reset(c->hs, ntiles, nimg, max_passes_for(c, ntiles), s));
+    if (st != CANNY_OK) return st;
+    st = from_cuda(launch_hyst_local_batch(c->hs, ntiles, nimg, s));
+    if (st != CANNY_OK) return st;
+    return run_global(c, s);
+}
+
+canny_status canny_run_host(canny_ctx *c, const uint8_t *h_in, int in_pitch, uint8_t *h_out,
+                            int out_pitch, int w, int h, void *stream)
+{
+    if (!c || !h_in || !h_out || w < 0 || h < 0 || w > c->max_w || h > c->max_h) return CANNY_EINVAL;
+    if (in_pitch < w || out_pitch < w) return CANNY_EINVAL;
+    if (w == 0 || h == 0) return CANNY_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t cap = (size_t)c->max_w * c->max_h;
+    if (!c->d_host_in) {
+        if (cudaMalloc((void **)&c->d_host_in, cap) != cudaSuccess ||
+            cudaMalloc((void **)&c->d_host_out, cap) != cudaSuccess) {
+            cudaGetLastError();
+            return CANNY_ENOMEM;
+        }
+    }
+    cudaError_t e = cudaMemcpy2DAsync(c->d_host_in, w, h_in, in_pitch, w, h, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    canny_image im = {c->d_host_in, c->d_host_out, w, h, w, w};
+    canny_status st = run_one(c, &im, s);
+    if (st != CANNY_OK) return st;
+    e = cudaMemcpy2DAsync(h_out, out_pitch, c->d_host_out, w, w, h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_state, c->hs.state, sizeof(HystState), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return from_cuda(e);
+    const HystState *hst = (const HystState *)c->h_state;
+    return (hst->error & 1u) ? CANNY_ENOCONVERGE : CANNY_OK;
+}
+
+canny_status canny_hysteresis(canny_ctx *c, const canny_image *img, void *stream)
+{
+    if (!c) return CANNY_EINVAL;
+    return run_one(c, img, (cudaStream_t)stream, false);
+}
+
+canny_status canny_classify(canny_ctx *c, const canny_image *img, void *stream)
+{
+    if (!c) return CANNY_EINVAL;
+    canny_status st = check_image(c, img);
+    if (st != CANNY_OK) return st;
+    if (img->w == 0 || img->h == 0) return CANNY_OK;
+    return run_stencil(c, img, (cudaStream_t)stream);
+}
+
+canny_status canny_magnitude_f32(canny_ctx *c, const canny_image *img, float *d_mag, int d_mag_pitch,
+                                 float *d_max, void *stream)
+{
+    if (!c || !img || !d_mag || !d_max) return CANNY_EINVAL;
+    if (c->p.path != CANNY_PATH_F32) return CANNY_EUNSUPPORTED;
+    if (img->w < 0 || img->h < 0 || img->w > c->max_w || img->h > c->max_h) return CANNY_EINVAL;
+    if (img->w == 0 || img->h == 0) return CANNY_OK;
+    if (!img->d_in || img->in_pitch < img->w || d_mag_pitch < img->w) return CANNY_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(d_max, 0, sizeof(float), s);
+    if (e == cudaSuccess)
+        e = launch_k1f_magnitude(img->d_in, img->in_pitch, d_mag, d_mag_pitch, img->w, img->h, c->fp,
+                                 false, d_max, s);
+    return from_cuda(e);
+}
+
+canny_status canny_get_stats(canny_ctx *c, canny_stats *out)
+{
+    if (!c || !out) return CANNY_EINVAL;
+    *out = c->last;
+    if (c->last.tiles == 0) { out->status = CANNY_OK; return CANNY_OK; }
+    cudaError_t e = cudaStreamSynchronize(c->last_stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->h_state, c->hs.state, sizeof(HystState), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        out->status = from_cuda(e);
+        return (canny_status)out->status;
+    }
+    const HystState *st = (const HystState *)c->h_state;
+    out->hyst_passes = st->pass;
+    out->hyst_tiles_visited = st->visited;
+    out->pending_tiles = st->pending_tiles;
+    out->status = (st->error & 1u) ? CANNY_ENOCONVERGE : CANNY_OK;
+    return CANNY_OK;
+}
+
+const char *canny_strerror(canny_status s)
+{
+    switch (s) {
+    case CANNY_OK: return "ok";
+    case CANNY_EINVAL: return "invalid argument";
+    case CANNY_ENOMEM: return "out of memory";
+    case CANNY_ECUDA: return "CUDA error";
+    case CANNY_ENOCONVERGE: return "hysteresis did not converge within the pass cap";
+    case CANNY_EUNSUPPORTED: return "unsupported request";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,100 @@
+// canny_internal.cuh -- types shared by the kernels and the C ABI of libcanny.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "canny.h"
+
+namespace canny {
+
+// ---------------------------------------------------------------- hysteresis tiles
+// Hysteresis (Step 4 of the paper's Sec. 2.2.1) works on 32x32 pixel tiles: one
+// warp per tile, one lane per row, one 32-bit mask per row.
+constexpr int HT = 32;
+
+// One image as the hysteresis kernels see it: its edge map (written in place)
+// and where its tiles start in the global tile numbering.
+struct HystImage {
+    uint8_t *map;       // edge map (device), h rows of pitch bytes
+    int w, h, pitch;
+    int ntx, nty;       // tiles across and down
+    uint32_t tile_base; // global index of the image's tile (0, 0)
+    uint32_t pad;
+};
+
+// Per-tile border masks, written by the local fill and updated by global passes.
+// edge_*: which border pixels are edges; pend_*: which border pixels are weak
+// pixels not (yet) connected to an edge. Bit i of top/bottom is column i, bit i
+// of left/right is row i.
+struct TileMasks {
+    uint32_t edge_top, edge_bottom, edge_left, edge_right;
+    uint32_t pend_top, pend_bottom, pend_left, pend_right;
+};
+
+// Device-side control block of one run's hysteresis.
+struct HystState {
+    uint32_t list_count[2];   // sizes of the two worklists
+    uint32_t done_ctas;       // CTAs finished in the current global pass
+    uint32_t pass;            // global passes completed
+    uint32_t max_passes;      // cap
+    uint32_t error;           // bit 0: cap reached with work left
+    uint32_t visited;         // tile visits summed over passes
+    uint32_t pending_tiles;   // tiles with unresolved weak pixels after the local fill
+    uint32_t ntiles;          // tiles in this run
+    uint32_t nimg;            // images in this run
+    uint32_t keep_going;      // host-loop mode: 1 if another pass is needed
+    uint32_t pad[5];
+};
+
+struct HystScratch {
+    HystImage *imgs;          // [max_imgs]
+    TileMasks *masks;         // [max_tiles]
+    uint32_t *pend_bits;      // [max_tiles * 32]: weak-not-edge pixels, one word per tile row
+    uint32_t *stamp;          // [max_tiles]: last pass a tile was queued for
+    uint32_t *lists;          // [2 * max_tiles]
+    HystState *state;
+    uint32_t max_tiles;
+    uint32_t max_imgs;
+};
+
+// ---------------------------------------------------------------- stencil launch data
+// Integer-path thresholds, squared.
+struct IntThresholds {
+    int lo2, hi2;
+};
+
+constexpr int MAX_KSIZE = 31;
+struct FloatParams {
+    float taps[MAX_KSIZE];
+    int ksize;
+    float lo_frac, hi_frac;
+};
+
+// ---------------------------------------------------------------- launchers (k1_stencil.cu)
+cudaError_t launch_k1_classify_u8(const uint8_t *in, int in_pitch, uint8_t *cls, int cls_pitch,
+                                  int w, int h, IntThresholds t, cudaStream_t s);
+cudaError_t launch_k1f_magnitude(const uint8_t *in, int in_pitch, float *mag, int mag_pitch,
+                                 int w, int h, const FloatParams &fp, bool nms, float *d_max,
+                                 cudaStream_t s);
+cudaError_t launch_k1f_classify(const float *mag_nms, int mag_pitch, uint8_t *cls, int cls_pitch,
+                                int w, int h, const float *d_max, float lo_frac, float hi_frac,
+                                cudaStream_t s);
+
+// ---------------------------------------------------------------- launchers (hysteresis.cu)
+// Local fill over all tiles of one image whose class map is already in img.map.
+cudaError_t launch_hyst_local_single(const HystScratch &hs, HystImage img, cudaStream_t s);
+// Local fill over all tiles of the images already uploaded to hs.imgs.
+cudaError_t launch_hyst_local_batch(const HystScratch &hs, uint32_t ntiles, uint32_t nimg,
+                                    cudaStream_t s);
+// One global pass over the current worklist. graph_cond: conditional handle to set
+// (0 when not in a graph).
+cudaError_t launch_hyst_global_pass(const HystScratch &hs, int grid, bool in_graph,
+                                    unsigned long long cond_handle, cudaStream_t s);
+cudaError_t hyst_reset(const HystScratch &hs, uint32_t ntiles, uint32_t nimg,
+                       uint32_t max_passes, cudaStream_t s);
+int hyst_pass_grid();
+// Executable graph { while (cond) global pass } bound to this scratch.
+cudaError_t hyst_build_graph(const HystScratch &hs, cudaGraph_t *graph_out, cudaGraphExec_t *exec_out);
+
+}  // namespace canny

@@ -1,0 +1,410 @@
+// hysteresis.cu -- Step 4 of the paper's Sec. 2.2.1: a weak pixel (between the
+// thresholds) is an edge only if it is connected to a strong one. Read as
+// 8-connectivity through weak/strong pixels.
+//
+// Two stages, both on 32x32 tiles held as 32-bit row masks in one warp
+// (lane = row):
+//   local fill   each tile grows its strong pixels through its own weak pixels
+//                until stable, writes 255/0 into the map, and records which weak
+//                pixels are still unresolved ("pending") and which border pixels
+//                are edges or pending;
+//   global pass  a tile on the worklist takes the edges on its neighbours'
+//                borders as seeds for its pending border pixels, grows them, and
+//                queues any neighbour whose facing border gained edges while it
+//                still has pending pixels there. Passes repeat until the
+//                worklist is empty; a CUDA-graph while-node drives the loop, its
+//                condition set by the last CTA of each pass.
+// Pending pixels live only in a compact bitmap, so the map never holds a value
+// other than 0/255 and no clean-up sweep is needed.
+#include "canny_internal.cuh"
+
+namespace canny {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int WARPS = 8;             // tiles per CTA in the local fill and the global pass
+constexpr int THREADS = WARPS * 32;
+
+// Bits of c that lie in a run (of consecutive set bits) containing a bit of s;
+// s must be a subset of c. Upward: adding s to c carries from the lowest seed of
+// each run past its top, clearing exactly the bits from that seed up; downward:
+// the same on the bit-reversed words.
+__device__ __forceinline__ uint32_t fill_runs(uint32_t s, uint32_t c)
+{
+    uint32_t up = (c & ~(c + s)) | s;
+    uint32_t rs = __brev(s), rc = __brev(c);
+    uint32_t dn = __brev((rc & ~(rc + rs)) | rs);
+    return up | dn;
+}
+
+// Grow e (subset of c) through 8-connected pixels of c inside the tile until
+// stable. Every round that changes something adds at least one pixel, so at
+// most 1024 + 1 rounds run.
+__device__ __forceinline__ uint32_t flood_tile(uint32_t e, uint32_t c, int lane)
+{
+    for (int it = 0; it < HT * HT + 2; ++it) {
+        uint32_t f = fill_runs(e, c);
+        uint32_t d = f | (f << 1) | (f >> 1);
+        uint32_t up = __shfl_up_sync(FULL, d, 1);
+        uint32_t dn = __shfl_down_sync(FULL, d, 1);
+        if (lane == 0) up = 0;
+        if (lane == HT - 1) dn = 0;
+        uint32_t ne = f | (c & (up | dn));
+        bool changed = __any_sync(FULL, ne != e);
+        e = ne;
+        if (!changed) break;
+    }
+    return e;
+}
+
+// 4-bit mask of the nonzero bytes of w (bit k = byte k).
+__device__ __forceinline__ uint32_t nz_nibble(uint32_t w)
+{
+    uint32_t m = (((w & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | w) & 0x80808080u;
+    return ((m >> 7) * 0x10204080u) >> 28;
+}
+
+// 4 bytes 0xFF/0x00 from the low 4 bits of t.
+__device__ __forceinline__ uint32_t nibble_bytes(uint32_t t)
+{
+    return ((t * 0x00204081u) & 0x01010101u) * 0xFFu;
+}
+
+// Row `lane` of tile (tx, ty): cand = class >= 1, strong = class >= 2.
+__device__ __forceinline__ void load_row(const HystImage &im, int tx, int ty, int lane,
+                                         uint32_t &cand, uint32_t &strong)
+{
+    cand = strong = 0;
+    int y = ty * HT + lane, x0 = tx * HT;
+    if (y >= im.h) return;
+    const uint8_t *row = im.map + (int64_t)y * im.pitch + x0;
+    int n = min(HT, im.w - x0);
+    if (n == HT && (((uintptr_t)row) & 15) == 0) {
+        uint4 a = reinterpret_cast<const uint4 *>(row)[0];
+        uint4 b = reinterpret_cast<const uint4 *>(row)[1];
+        uint32_t wd[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            cand |= nz_nibble(wd[k]) << (4 * k);
+            strong |= nz_nibble(wd[k] & 0xFEFEFEFEu) << (4 * k);
+        }
+    } else {
+        for (int i = 0; i < n; ++i) {
+            uint8_t v = row[i];
+            if (v) cand |= 1u << i;
+            if (v >= 2) strong |= 1u << i;
+        }
+    }
+}
+
+// Write row `lane` of the tile as 255 where e is set, 0 elsewhere.
+__device__ __forceinline__ void store_row(const HystImage &im, int tx, int ty, int lane, uint32_t e)
+{
+    int y = ty * HT + lane, x0 = tx * HT;
+    if (y >= im.h) return;
+    uint8_t *row = im.map + (int64_t)y * im.pitch + x0;
+    int n = min(HT, im.w - x0);
+    if (n == HT && (((uintptr_t)row) & 15) == 0) {
+        uint4 a, b;
+        a.x = nibble_bytes(e); a.y = nibble_bytes(e >> 4); a.z = nibble_bytes(e >> 8); a.w = nibble_bytes(e >> 12);
+        b.x = nibble_bytes(e >> 16); b.y = nibble_bytes(e >> 20); b.z = nibble_bytes(e >> 24); b.w = nibble_bytes(e >> 28);
+        reinterpret_cast<uint4 *>(row)[0] = a;
+        reinterpret_cast<uint4 *>(row)[1] = b;
+    } else {
+        for (int i = 0; i < n; ++i) row[i] = ((e >> i) & 1) ? 255 : 0;
+    }
+}
+
+__device__ __forceinline__ int find_image(const HystImage *imgs, int nimg, uint32_t t)
+{
+    int lo = 0, hi = nimg - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (imgs[mid].tile_base <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void push(const HystScratch &hs, uint32_t list, uint32_t tile, uint32_t stamp)
+{
+    if (atomicMax(&hs.stamp[tile], stamp) < stamp) {
+        uint32_t idx = atomicAdd(&hs.state->list_count[list], 1u);
+        hs.lists[(size_t)list * hs.max_tiles + idx] = tile;
+    }
+}
+
+// ---------------------------------------------------------------- local fill
+template <bool SINGLE>
+__global__ void __launch_bounds__(THREADS)
+hyst_local_kernel(HystScratch hs, HystImage single, uint32_t ntiles, uint32_t nimg)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t t = (blockIdx.x * THREADS + threadIdx.x) >> 5;
+    if (SINGLE && blockIdx.x == 0 && threadIdx.x == 0) hs.imgs[0] = single;
+    if (t >= ntiles) return;
+    HystImage im = SINGLE ? single : hs.imgs[find_image(hs.imgs, (int)nimg, t)];
+    const uint32_t local = t - im.tile_base;
+    const int tx = (int)(local % (uint32_t)im.ntx), ty = (int)(local / (uint32_t)im.ntx);
+
+    uint32_t cand, strong;
+    load_row(im, tx, ty, lane, cand, strong);
+    const uint32_t e = flood_tile(strong, cand, lane);
+    store_row(im, tx, ty, lane, e);
+    const uint32_t pend = cand & ~e;
+
+    TileMasks m;
+    m.edge_top = __shfl_sync(FULL, e, 0);
+    m.edge_bottom = __shfl_sync(FULL, e, HT - 1);
+    m.edge_left = __ballot_sync(FULL, e & 1u);
+    m.edge_right = __ballot_sync(FULL, e >> 31);
+    m.pend_top = __shfl_sync(FULL, pend, 0);
+    m.pend_bottom = __shfl_sync(FULL, pend, HT - 1);
+    m.pend_left = __ballot_sync(FULL, pend & 1u);
+    m.pend_right = __ballot_sync(FULL, pend >> 31);
+    const bool any_pend = __any_sync(FULL, pend != 0);
+    if (any_pend) hs.pend_bits[(size_t)t * HT + lane] = pend;
+    if (lane == 0) {
+        hs.masks[t] = m;
+        if (any_pend) atomicAdd(&hs.state->pending_tiles, 1u);
+        // pending pixels on the border may be reached from a neighbour: queue for pass 0
+        if (m.pend_top | m.pend_bottom | m.pend_left | m.pend_right) push(hs, 0, t, 1);
+    }
+}
+
+// ---------------------------------------------------------------- global pass
+__device__ __forceinline__ void global_item(const HystScratch &hs, uint32_t t, uint32_t k, int lane,
+                                            int nimg)
+{
+    const TileMasks mu = hs.masks[t];
+    if ((mu.pend_top | mu.pend_bottom | mu.pend_left | mu.pend_right) == 0) return;
+    const HystImage im = hs.imgs[find_image(hs.imgs, nimg, t)];
+    const uint32_t local = t - im.tile_base;
+    const int tx = (int)(local % (uint32_t)im.ntx), ty = (int)(local / (uint32_t)im.ntx);
+    const bool hasL = tx > 0, hasR = tx < im.ntx - 1, hasU = ty > 0, hasD = ty < im.nty - 1;
+    const uint32_t ntx = (uint32_t)im.ntx;
+
+    // seeds: pending border pixels next to an edge pixel of a neighbouring tile
+    uint32_t s_top = 0, s_bot = 0, s_left = 0, s_right = 0;
+    if (hasU && mu.pend_top) {
+        uint32_t a = hs.masks[t - ntx].edge_bottom;
+        uint32_t ring = a | (a << 1) | (a >> 1);
+        if (hasL && (hs.masks[t - ntx - 1].edge_bottom >> 31)) ring |= 1u;
+        if (hasR && (hs.masks[t - ntx + 1].edge_bottom & 1u)) ring |= 1u << 31;
+        s_top = ring & mu.pend_top;
+    }
+    if (hasD && mu.pend_bottom) {
+        uint32_t a = hs.masks[t + ntx].edge_top;
+        uint32_t ring = a | (a << 1) | (a >> 1);
+        if (hasL && (hs.masks[t + ntx - 1].edge_top >> 31)) ring |= 1u;
+        if (hasR && (hs.masks[t + ntx + 1].edge_top & 1u)) ring |= 1u << 31;
+        s_bot = ring & mu.pend_bottom;
+    }
+    if (hasL && mu.pend_left) {
+        uint32_t a = hs.masks[t - 1].edge_right;
+        s_left = (a | (a << 1) | (a >> 1)) & mu.pend_left;
+    }
+    if (hasR && mu.pend_right) {
+        uint32_t a = hs.masks[t + 1].edge_left;
+        s_right = (a | (a << 1) | (a >> 1)) & mu.pend_right;
+    }
+    if ((s_top | s_bot | s_left | s_right) == 0) return;
+
+    uint32_t p = hs.pend_bits[(size_t)t * HT + lane];
+    uint32_t e0 = ((s_left >> lane) & 1u) | (((s_right >> lane) & 1u) << 31);
+    if (lane == 0) e0 |= s_top;
+    if (lane == HT - 1) e0 |= s_bot;
+    e0 &= p;
+    const uint32_t e = flood_tile(e0, p, lane);
+
+    // write the new edges (sparse byte stores) and the shrunken pending set
+    if (e) {
+        int y = ty * HT + lane;
+        uint8_t *row = im.map + (int64_t)y * im.pitch + tx * HT;
+        uint32_t bits = e;
+        while (bits) {
+            int b = __ffs(bits) - 1;
+            row[b] = 255;
+            bits &= bits - 1;
+        }
+    }
+    p &= ~e;
+    hs.pend_bits[(size_t)t * HT + lane] = p;
+
+    const uint32_t e_top = __shfl_sync(FULL, e, 0), e_bot = __shfl_sync(FULL, e, HT - 1);
+    const uint32_t e_left = __ballot_sync(FULL, e & 1u), e_right = __ballot_sync(FULL, e >> 31);
+    const uint32_t p_top = __shfl_sync(FULL, p, 0), p_bot = __shfl_sync(FULL, p, HT - 1);
+    const uint32_t p_left = __ballot_sync(FULL, p & 1u), p_right = __ballot_sync(FULL, p >> 31);
+    if (lane == 0) {
+        TileMasks *mt = &hs.masks[t];
+        if (e_top) atomicOr(&mt->edge_top, e_top);
+        if (e_bot) atomicOr(&mt->edge_bottom, e_bot);
+        if (e_left) atomicOr(&mt->edge_left, e_left);
+        if (e_right) atomicOr(&mt->edge_right, e_right);
+        atomicAnd(&mt->pend_top, p_top);
+        atomicAnd(&mt->pend_bottom, p_bot);
+        atomicAnd(&mt->pend_left, p_left);
+        atomicAnd(&mt->pend_right, p_right);
+        __threadfence();
+        // queue neighbours whose facing border has pending pixels next to a new edge
+        const uint32_t nl = (k + 1) & 1u, st = k + 2;
+        if (hasU && e_top) {
+            uint32_t d = e_top | (e_top << 1) | (e_top >> 1);
+            if (hs.masks[t - ntx].pend_bottom & d) push(hs, nl, t - ntx, st);
+            if (hasL && (e_top & 1u) && (hs.masks[t - ntx - 1].pend_bottom >> 31)) push(hs, nl, t - ntx - 1, st);
+            if (hasR && (e_top >> 31) && (hs.masks[t - ntx + 1].pend_bottom & 1u)) push(hs, nl, t - ntx + 1, st);
+        }
+        if (hasD && e_bot) {
+            uint32_t d = e_bot | (e_bot << 1) | (e_bot >> 1);
+            if (hs.masks[t + ntx].pend_top & d) push(hs, nl, t + ntx, st);
+            if (hasL && (e_bot & 1u) && (hs.masks[t + ntx - 1].pend_top >> 31)) push(hs, nl, t + ntx - 1, st);
+            if (hasR && (e_bot >> 31) && (hs.masks[t + ntx + 1].pend_top & 1u)) push(hs, nl, t + ntx + 1, st);
+        }
+        if (hasL && e_left) {
+            uint32_t d = e_left | (e_left << 1) | (e_left >> 1);
+            if (hs.masks[t - 1].pend_right & d) push(hs, nl, t - 1, st);
+        }
+        if (hasR && e_right) {
+            uint32_t d = e_right | (e_right << 1) | (e_right >> 1);
+            if (hs.masks[t + 1].pend_left & d) push(hs, nl, t + 1, st);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(THREADS)
+hyst_global_kernel(HystScratch hs, int in_graph, cudaGraphConditionalHandle cond)
+{
+    HystState *st = hs.state;
+    const uint32_t k = *(volatile uint32_t *)&st->pass;
+    const uint32_t cur = k & 1u, nxt = cur ^ 1u;
+    const uint32_t count = *(volatile uint32_t *)&st->list_count[cur];
+    const int nimg = (int)st->nimg;
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * THREADS + threadIdx.x) >> 5;
+    const uint32_t nwarps = gridDim.x * WARPS;
+    const uint32_t *list = hs.lists + (size_t)cur * hs.max_tiles;
+    for (uint32_t i = warp; i < count; i += nwarps) global_item(hs, list[i], k, lane, nimg);
+
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&st->done_ctas, 1u) == gridDim.x - 1) {
+            __threadfence();
+            const uint32_t next = atomicAdd(&st->list_count[nxt], 0u);
+            st->list_count[cur] = 0;
+            st->visited += count;
+            st->pass = k + 1;
+            st->done_ctas = 0;
+            bool more = next > 0;
+            if (more && k + 1 >= st->max_passes) {
+                st->error |= 1u;
+                more = false;
+            }
+            st->keep_going = more ? 1u : 0u;
+            __threadfence();
+            if (in_graph) cudaGraphSetConditional(cond, more ? 1u : 0u);
+        }
+    }
+}
+
+__global__ void hyst_init_kernel(HystState *st, uint32_t ntiles, uint32_t nimg, uint32_t max_passes)
+{
+    HystState s = {};
+    s.ntiles = ntiles;
+    s.nimg = nimg;
+    s.max_passes = max_passes;
+    s.keep_going = 1;
+    *st = s;
+}
+
+}  // namespace
+
+int hyst_pass_grid()
+{
+    static int grid = 0;
+    if (!grid) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 152;
+        grid = 2 * sms;
+    }
+    return grid;
+}
+
+cudaError_t hyst_reset(const HystScratch &hs, uint32_t ntiles, uint32_t nimg, uint32_t max_passes,
+                       cudaStream_t s)
+{
+    cudaError_t err = cudaMemsetAsync(hs.stamp, 0, sizeof(uint32_t) * (size_t)ntiles, s);
+    if (err != cudaSuccess) return err;
+    hyst_init_kernel<<<1, 1, 0, s>>>(hs.state, ntiles, nimg, max_passes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hyst_local_single(const HystScratch &hs, HystImage img, cudaStream_t s)
+{
+    uint32_t ntiles = (uint32_t)img.ntx * (uint32_t)img.nty;
+    if (ntiles == 0) return cudaSuccess;
+    int grid = (int)((ntiles + WARPS - 1) / WARPS);
+    hyst_local_kernel<true><<<grid, THREADS, 0, s>>>(hs, img, ntiles, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hyst_local_batch(const HystScratch &hs, uint32_t ntiles, uint32_t nimg, cudaStream_t s)
+{
+    if (ntiles == 0) return cudaSuccess;
+    int grid = (int)((ntiles + WARPS - 1) / WARPS);
+    HystImage none = {};
+    hyst_local_kernel<false><<<grid, THREADS, 0, s>>>(hs, none, ntiles, nimg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hyst_global_pass(const HystScratch &hs, int grid, bool in_graph,
+                                    unsigned long long cond_handle, cudaStream_t s)
+{
+    hyst_global_kernel<<<grid, THREADS, 0, s>>>(hs, in_graph ? 1 : 0,
+                                                (cudaGraphConditionalHandle)cond_handle);
+    return cudaGetLastError();
+}
+
+// Build the executable graph { while (cond) hyst_global_kernel } for this scratch.
+cudaError_t hyst_build_graph(const HystScratch &hs, cudaGraph_t *graph_out, cudaGraphExec_t *exec_out)
+{
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    cudaError_t err = cudaGraphCreate(&g, 0);
+    if (err != cudaSuccess) return err;
+    cudaGraphConditionalHandle cond;
+    err = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+    if (err != cudaSuccess) { cudaGraphDestroy(g); return err; }
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    err = cudaGraphAddNode(&cnode, g, nullptr, nullptr, 0, &cp);
+    if (err != cudaSuccess) { cudaGraphDestroy(g); return err; }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+
+    HystScratch hs_copy = hs;
+    int in_graph = 1;
+    void *args[] = {&hs_copy, &in_graph, &cond};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void *)hyst_global_kernel;
+    kp.gridDim = dim3(hyst_pass_grid());
+    kp.blockDim = dim3(THREADS);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    cudaGraphNode_t knode;
+    err = cudaGraphAddKernelNode(&knode, body, nullptr, 0, &kp);
+    if (err != cudaSuccess) { cudaGraphDestroy(g); return err; }
+    err = cudaGraphInstantiate(&ex, g, 0);
+    if (err != cudaSuccess) { cudaGraphDestroy(g); return err; }
+    *graph_out = g;
+    *exec_out = ex;
+    return cudaSuccess;
+}
+
+}  // namespace canny

@@ -1,0 +1,85 @@
+"""The C-ABI library builds, loads and exports every symbol include/canny.h declares;
+host-side argument checks reject bad input before any CUDA call (no GPU needed)."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+pytestmark = pytest.mark.skipif(shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"),
+                                reason="CUDA toolkit not present")
+
+
+def _declared_symbols(header):
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(canny_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1710_07745_gb300 import canny
+    return canny.load()
+
+
+def test_header_declares_the_boundary():
+    syms = _declared_symbols(os.path.join(ROOT, "include", "canny.h"))
+    for s in ("canny_create", "canny_run", "canny_run_batch", "canny_run_pitched", "canny_destroy",
+              "canny_strerror", "canny_get_stats"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_1710_07745_gb300 import canny
+    for header in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if header.endswith(".h"):
+            for sym in _declared_symbols(os.path.join(ROOT, "include", header)):
+                assert hasattr(lib, sym), f"{sym} declared in {header} but not exported"
+    # and the binding knows every one of them
+    for sym in _declared_symbols(os.path.join(ROOT, "include", "canny.h")):
+        assert sym in canny.SIGNATURES, sym
+
+
+def test_strerror_and_defaults(lib):
+    from paper_1710_07745_gb300 import canny
+    assert canny.strerror(canny.CANNY_OK) == "ok"
+    assert "converge" in canny.strerror(canny.CANNY_ENOCONVERGE)
+    p = canny.canny_params_default()
+    assert (p.path, p.low, p.high, p.ksize, p.max_passes) == (0, 40.0, 100.0, 7, 0)
+    assert abs(p.sigma - 1.4) < 1e-6
+
+
+@pytest.mark.parametrize("field,value", [("path", 7), ("low", 120.0), ("low", -1.0), ("high", 40.5),
+                                         ("high", 40000.0), ("max_passes", -3)])
+def test_create_rejects_bad_params_without_cuda(lib, field, value):
+    from paper_1710_07745_gb300 import canny
+    p = canny.canny_params_default()
+    setattr(p, field, value)
+    ctx = ctypes.c_void_p()
+    assert lib.canny_create(64, 64, ctypes.byref(p), ctypes.byref(ctx)) == canny.CANNY_EINVAL
+    assert not ctx.value
+
+
+@pytest.mark.parametrize("sigma,ksize", [(0.0, 7), (1.4, 6), (1.4, 1), (1.4, 33)])
+def test_create_rejects_bad_float_params(lib, sigma, ksize):
+    from paper_1710_07745_gb300 import canny
+    p = canny.canny_params_default()
+    p.path, p.sigma, p.ksize, p.low, p.high = canny.CANNY_PATH_F32, sigma, ksize, 0.1, 0.3
+    ctx = ctypes.c_void_p()
+    assert lib.canny_create(64, 64, ctypes.byref(p), ctypes.byref(ctx)) == canny.CANNY_EINVAL
+
+
+def test_create_rejects_bad_sizes_and_nulls(lib):
+    from paper_1710_07745_gb300 import canny
+    p = canny.canny_params_default()
+    ctx = ctypes.c_void_p()
+    for w, h in [(0, 10), (10, 0), (-1, 5)]:
+        assert lib.canny_create(w, h, ctypes.byref(p), ctypes.byref(ctx)) == canny.CANNY_EINVAL
+    assert lib.canny_create(8, 8, None, ctypes.byref(ctx)) == canny.CANNY_EINVAL
+    assert lib.canny_create(8, 8, ctypes.byref(p), None) == canny.CANNY_EINVAL
+    assert lib.canny_run(None, None, None, None) == canny.CANNY_EINVAL
+    assert lib.canny_get_stats(None, None) == canny.CANNY_EINVAL
+    lib.canny_destroy(None)

@@ -1,0 +1,328 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Integer path: bit-exact edge maps and class maps on every case. Float path:
+strength within 1e-5 relative, edge maps equal except where the oracle's own
+decision is within 1e-3 of a threshold or neighbour (and what is connected to
+such a pixel).
+"""
+import numpy as np
+import pytest
+import scipy.ndimage as ndi
+
+import oracle
+from paper_1710_07745_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1710_07745_gb300 import canny  # noqa: E402
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run_int(img, low=40, high=100, ctx=None, stage="edges"):
+    h, w = img.shape
+    c = ctx or canny.Canny(max(w, 1), max(h, 1), low=low, high=high)
+    d_in = dev(img)
+    d_out = torch.full((h, w), 7, dtype=torch.uint8, device="cuda")
+    if stage == "edges":
+        c.run_pitched(d_in, d_out)
+    else:
+        c.classify(d_in, d_out)
+    torch.cuda.synchronize()
+    st = c.stats()
+    out = d_out.cpu().numpy()
+    if ctx is None:
+        c.close()
+    return out, st
+
+
+def noise_image(seed, h, w):
+    return np.random.default_rng(seed).integers(0, 256, (h, w), dtype=np.uint8)
+
+
+def blocky_image(seed, h, w):
+    """Smooth-ish random image: random values upsampled, plus noise (many weak/strong mixes)."""
+    rng = np.random.default_rng(seed)
+    small = rng.integers(0, 256, (max(1, h // 6 + 1), max(1, w // 6 + 1)))
+    big = np.kron(small, np.ones((6, 6)))[:h, :w]
+    return np.clip(big + rng.normal(0, 6, (h, w)), 0, 255).astype(np.uint8)
+
+
+# ------------------------------------------------------------------ integer path
+def test_small_workload_bit_exact():
+    img = synth.small()
+    out, st = run_int(img)
+    assert st["status"] == canny.CANNY_OK
+    assert np.array_equal(out, oracle.canny_u8(img))
+    cls, _ = run_int(img, stage="classify")
+    assert np.array_equal(cls, oracle.classify_u8(img))
+
+
+def test_medium_workload_bit_exact():
+    img = synth.medium()
+    out, st = run_int(img)
+    assert st["status"] == canny.CANNY_OK
+    want = oracle.canny_u8(img)
+    assert np.array_equal(out, want), int((out != want).sum())
+
+
+SIZES = [(1, 1), (1, 5), (5, 1), (2, 2), (3, 5), (5, 17), (17, 5), (7, 7), (31, 33), (32, 32),
+         (33, 31), (64, 64), (37, 100), (257, 513), (999, 1000), (2, 700), (700, 3)]
+
+
+@pytest.mark.parametrize("h,w", SIZES)
+@pytest.mark.parametrize("kind", ["synth", "noise", "blocky"])
+def test_sizes_bit_exact(h, w, kind):
+    seed = h * 1009 + w
+    if kind == "synth":
+        img = synth.image(seed, w, h, 6, 6, 10)
+    elif kind == "noise":
+        img = noise_image(seed, h, w)
+    else:
+        img = blocky_image(seed, h, w)
+    out, st = run_int(img)
+    assert st["status"] == canny.CANNY_OK
+    assert np.array_equal(out, oracle.canny_u8(img))
+    cls, _ = run_int(img, stage="classify")
+    assert np.array_equal(cls, oracle.classify_u8(img))
+
+
+@pytest.mark.parametrize("low,high", [(0, 0), (40, 40), (10, 200), (100, 1000), (0, 1442), (1, 2)])
+def test_thresholds_bit_exact(low, high):
+    img = blocky_image(5, 300, 420)
+    out, _ = run_int(img, low, high)
+    assert np.array_equal(out, oracle.canny_u8(img, low, high))
+
+
+def test_pitched_buffers_leave_padding_untouched():
+    h, w, pin, pout = 150, 203, 256, 240
+    img = synth.image(21, w, h, 5, 5, 8)
+    base_in = np.full((h, pin), 99, np.uint8)
+    base_in[:, :w] = img
+    d_in = dev(base_in)
+    d_out = torch.full((h, pout), 77, dtype=torch.uint8, device="cuda")
+    with canny.Canny(w, h) as c:
+        c.run_pitched(d_in[:, :w], d_out[:, :w])
+        torch.cuda.synchronize()
+    out = d_out.cpu().numpy()
+    assert (out[:, w:] == 77).all()
+    assert np.array_equal(out[:, :w], oracle.canny_u8(img))
+
+
+def test_context_reuse_smaller_images_and_determinism():
+    with canny.Canny(600, 400) as c:
+        for (h, w, seed) in [(400, 600, 1), (17, 33, 2), (400, 600, 3), (1, 1, 4), (399, 599, 5)]:
+            img = synth.image(seed, w, h, 8, 8, 8)
+            outs = [run_int(img, ctx=c)[0] for _ in range(3)]
+            assert all(np.array_equal(o, outs[0]) for o in outs)
+            assert np.array_equal(outs[0], oracle.canny_u8(img))
+
+
+def test_empty_image_is_a_no_op():
+    with canny.Canny(16, 16) as c:
+        img = canny.canny_image(0, 0, 0, 5, 0, 0)
+        canny.canny_run_pitched(c.ctx, img, 0)
+        canny.canny_run_batch(c.ctx, [], 0)
+
+
+def test_rejects_oversize_and_overlap():
+    with canny.Canny(64, 64) as c:
+        a = torch.zeros((70, 70), dtype=torch.uint8, device="cuda")
+        b = torch.zeros((70, 70), dtype=torch.uint8, device="cuda")
+        with pytest.raises(canny.CannyError) as e:
+            c.run_pitched(a, b)
+        assert e.value.status == canny.CANNY_EINVAL
+        with pytest.raises(canny.CannyError):
+            c.run_pitched(a[:10, :10], a[5:15, :10])      # overlapping output
+
+
+# ------------------------------------------------------------------ hysteresis alone
+def spiral_map(n, gap=1):
+    """1-pixel weak spiral (rings `gap` apart) with one strong pixel at its inner end."""
+    cls = np.zeros((n, n), np.uint8)
+    y0, x0, y1, x1 = 0, 0, n - 1, n - 1
+    path = []
+    step = gap + 1
+    while y0 <= y1 and x0 <= x1:
+        path += [(y0, x) for x in range(x0, x1 + 1)]
+        path += [(y, x1) for y in range(y0 + 1, y1 + 1)]
+        if y1 - y0 >= step:
+            path += [(y1, x) for x in range(x1 - 1, x0 - 1, -1)]
+        if x1 - x0 >= step:
+            path += [(y, x0) for y in range(y1 - 1, y0 + step - 1, -1)]
+        path += [(y0 + step, x) for x in range(x0, min(x0 + step, x1 + 1))]
+        y0, x0, y1, x1 = y0 + step, x0 + step, y1 - step, x1 - step
+    for (y, x) in path:
+        if 0 <= y < n and 0 <= x < n:
+            cls[y, x] = 1
+    y, x = path[-1]
+    cls[min(y, n - 1), min(x, n - 1)] = 2
+    return cls
+
+
+def run_hyst(cls, max_passes=0):
+    h, w = cls.shape
+    with canny.Canny(w, h, max_passes=max_passes) as c:
+        d_in = dev(cls)
+        d_out = torch.empty_like(d_in)
+        c.hysteresis(d_in, d_out)
+        torch.cuda.synchronize()
+        return d_out.cpu().numpy(), c.stats()
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_hysteresis_random_maps(seed):
+    rng = np.random.default_rng(seed)
+    h, w = (int(v) for v in rng.integers(1, 300, 2))
+    p = rng.dirichlet([3, 3, 0.3])
+    cls = rng.choice(3, size=(h, w), p=p).astype(np.uint8)
+    out, st = run_hyst(cls)
+    assert st["status"] == canny.CANNY_OK
+    assert np.array_equal(out, oracle.hysteresis(cls))
+
+
+def test_hysteresis_spiral_needs_many_passes():
+    cls = spiral_map(300)
+    out, st = run_hyst(cls)
+    assert st["status"] == canny.CANNY_OK
+    assert np.array_equal(out, oracle.hysteresis(cls))
+    assert (out == 255).sum() == (cls > 0).sum()          # the whole spiral is reached
+    assert st["hyst_passes"] > 20
+
+
+def test_hysteresis_pass_cap_reports_no_convergence():
+    cls = spiral_map(300)
+    out, st = run_hyst(cls, max_passes=1)
+    assert st["status"] == canny.CANNY_ENOCONVERGE
+    assert st["hyst_passes"] == 1
+
+
+def test_weak_chains_crossing_many_tiles():
+    # long straight and diagonal weak lines, strong only at one end
+    n = 700
+    cls = np.zeros((n, n), np.uint8)
+    cls[100, :] = 1
+    cls[100, 0] = 2
+    cls[:, 333] = 1
+    np.fill_diagonal(cls, 1)
+    cls[n - 1, n - 1] = 2
+    cls[::37, 600] = 1
+    out, _ = run_hyst(cls)
+    assert np.array_equal(out, oracle.hysteresis(cls))
+
+
+# ------------------------------------------------------------------ batch and host paths
+def test_batch_equals_oracle_and_single_runs():
+    sizes = [(64, 64), (1, 1), (0, 10), (33, 700), (257, 129), (512, 512), (5, 3), (100, 31)]
+    imgs = [synth.image(100 + i, w, h, 5, 5, 8) if w * h else np.zeros((h, w), np.uint8)
+            for i, (h, w) in enumerate(sizes)]
+    total = sum(w * h for h, w in sizes)
+    ins = [dev(im) for im in imgs]
+    outs = [torch.full(im.shape, 3, dtype=torch.uint8, device="cuda") for im in imgs]
+    with canny.Canny(total, 1) as c:
+        c.run_batch(list(zip(ins, outs)))
+        torch.cuda.synchronize()
+        st = c.stats()
+    assert st["status"] == canny.CANNY_OK and st["images"] == len(sizes)
+    for im, o in zip(imgs, outs):
+        if im.size:
+            assert np.array_equal(o.cpu().numpy(), oracle.canny_u8(im))
+
+
+def test_run_host_matches_device_path():
+    img = synth.image(8, 640, 480, 10, 10, 8)
+    out = np.zeros_like(img)
+    with canny.Canny(640, 480) as c:
+        canny.canny_run_host(c.ctx, img.ctypes.data, 640, out.ctypes.data, 640, 640, 480, 0)
+    assert np.array_equal(out, oracle.canny_u8(img))
+
+
+# ------------------------------------------------------------------ float path
+def float_reference(img, sigma=1.4, ksize=7, lo=0.1, hi=0.3):
+    S = oracle.gauss_f32(img, sigma, ksize)
+    gx, gy = oracle.sobel_f32(S)
+    M = oracle.magnitude_f32(gx, gy)
+    e, M2, cls = oracle.canny_f32(img, sigma, ksize, lo, hi, want_stages=True)
+    assert np.array_equal(M, M2)
+    return gx, gy, M, cls, e
+
+
+def ambiguous_mask(gx, gy, M, cls, lo, hi, tol=1e-3):
+    """Pixels where one of the oracle's float decisions is within tol (relative)."""
+    mmax = np.float32(M.max())
+    lo_t, hi_t = np.float32(lo) * mmax, np.float32(hi) * mmax
+
+    def near(a, b):
+        return np.abs(a - b) <= tol * np.maximum(np.abs(a), np.abs(b))
+
+    amb = near(M, lo_t) | near(M, hi_t)
+    ax, ay = np.abs(gx), np.abs(gy)
+    t = np.float32(0.41421356)
+    amb |= near(ay, ax * t) | near(ax, ay * t)
+    P = np.pad(M, 1)
+    h, w = M.shape
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            if dy or dx:
+                amb |= near(M, P[1 + dy:1 + dy + h, 1 + dx:1 + dx + w]) & (M > 0)
+    return amb
+
+
+def check_float_edges(got, want_e, gx, gy, M, cls, lo=0.1, hi=0.3):
+    diff = got != want_e
+    if not diff.any():
+        return 0
+    amb = ambiguous_mask(gx, gy, M, cls, lo, hi)
+    lab, _ = ndi.label((cls > 0) | amb, structure=np.ones((3, 3), int))
+    allowed = np.isin(lab, np.unique(lab[amb])) & (lab > 0) | amb
+    assert not (diff & ~allowed).any(), int((diff & ~allowed).sum())
+    return int(diff.sum())
+
+
+@pytest.mark.parametrize("which", ["small", "blocky", "medium"])
+def test_float_path(which):
+    img = {"small": synth.small, "medium": synth.medium,
+           "blocky": lambda: blocky_image(3, 333, 517)}[which]()
+    h, w = img.shape
+    gx, gy, M, cls, want = float_reference(img)
+    with canny.Canny(w, h, path=canny.CANNY_PATH_F32, low=0.1, high=0.3) as c:
+        d_in = dev(img)
+        d_mag = torch.empty((h, w), dtype=torch.float32, device="cuda")
+        d_max = torch.zeros(1, dtype=torch.float32, device="cuda")
+        c.magnitude(d_in, d_mag, d_max)
+        d_out = torch.empty_like(d_in)
+        c.run_pitched(d_in, d_out)
+        torch.cuda.synchronize()
+        st = c.stats()
+    Mg = d_mag.cpu().numpy()
+    assert np.all(np.abs(Mg - M) <= 1e-5 * np.maximum(np.abs(M), 1.0))
+    assert abs(float(d_max.item()) - float(M.max())) <= 1e-5 * float(M.max())
+    assert st["status"] == canny.CANNY_OK
+    check_float_edges(d_out.cpu().numpy(), want, gx, gy, M, cls)
+
+
+def test_float_other_sigma():
+    img = blocky_image(9, 200, 300)
+    gx, gy, M, cls, want = float_reference(img, 2.0, 11, 0.05, 0.2)
+    with canny.Canny(300, 200, path=canny.CANNY_PATH_F32, sigma=2.0, ksize=11, low=0.05, high=0.2) as c:
+        d_in = dev(img)
+        d_out = torch.empty_like(d_in)
+        c.run_pitched(d_in, d_out)
+        torch.cuda.synchronize()
+    check_float_edges(d_out.cpu().numpy(), want, gx, gy, M, cls, 0.05, 0.2)
+
+
+# ------------------------------------------------------------------ full-size workloads
+@pytest.mark.parametrize("which", ["uhd", "huge"])
+def test_full_size_workloads_bit_exact(which):
+    img = getattr(synth, which)()
+    out, st = run_int(img)
+    assert st["status"] == canny.CANNY_OK
+    want = oracle.canny_u8(img)
+    assert np.array_equal(out, want), int((out != want).sum())

@@ -1,0 +1,314 @@
+"""Throughput benchmark of the Canny pipeline on one GB300 (or N replicas).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = the whole pipeline (fused stencil, tile-local hysteresis, global
+hysteresis passes) over one synthetic 16384 x 16384 uint8 image (3200
+rectangles, 3200 disks, noise sigma 12; thresholds 40/100), inputs resident in
+HBM. Inputs (268 MB) and outputs (268 MB) are larger than the 129 MB L2, so no
+flush is needed between steps. Prints one JSON line.
+
+--impl reference times the CPU oracle (single thread) on a bounded sample of
+the same workload instead. Under torchrun (N > 1) each rank runs its own
+replica of the image: the units (images) are independent, so the job scales
+weakly with no collective on the data path; rank 0 prints the line with the
+max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+W = H = 16384
+N_OBJ = 3200
+NOISE = 12
+SEED = 3001
+LOW, HIGH = 40, 100
+METRIC = "Canny Mpixel/s & % of HBM roofline; batched vs plain loop; p50/p99 latency"
+UNIT = "Mpixel/s"
+WORKLOAD = "canny_int_16384x16384"
+# algorithmic bytes per pixel of the fused stencil: read the image byte, write the class byte
+K1_BYTES_PER_PX = 2
+# whole pipeline floor: stencil 2 B/px + tile-local hysteresis read + write 2 B/px
+PIPE_BYTES_PER_PX = 4
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def config(extra: dict | None = None) -> dict:
+    c = {"workload": WORKLOAD, "w": W, "h": H, "objects_per_kind": N_OBJ, "noise_sigma": NOISE,
+         "seed": SEED, "low": LOW, "high": HIGH, "path": "integer",
+         "l2": "inputs+outputs 512 MiB > 129 MB L2, no flush"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ------------------------------------------------------------------ distributed plumbing
+def dist_init(n_gpus: int):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("CANNY_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, world
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks during the timed region
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ CPU legs (oracle)
+def oracle_sample(img: np.ndarray, rows: int) -> tuple[float, str]:
+    """Time the oracle on the first `rows` rows of the image; returns (Mpixel/s, description)."""
+    import oracle
+    sample = np.ascontiguousarray(img[:rows])
+    t0 = time.perf_counter()
+    oracle.canny_u8(sample, LOW, HIGH)
+    dt = time.perf_counter() - t0
+    return sample.size / dt / 1e6, f"rows 0..{rows} of the {W}x{H} image ({sample.size / 1e6:.1f} Mpixel), 1 thread"
+
+
+def run_reference(args, rank: int, world: int) -> None:
+    if rank != 0:
+        return
+    from paper_1710_07745_gb300 import synth
+    rows = int(os.environ.get("CANNY_REF_ROWS", "2048"))
+    img = np.empty((rows, W), np.uint8)
+    full = synth.image(SEED, W, H, N_OBJ, N_OBJ, NOISE)
+    img[:] = full[:rows]
+    del full
+    for _ in range(args.warmup):
+        oracle_sample(img, rows)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_sample(img, rows)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = args.steps * img.size / tot / 1e6
+    sample = f"rows 0..{rows} of the {W}x{H} image ({img.size / 1e6:.1f} Mpixel) per step, 1 thread"
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * tot / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": config({"sample_rows": rows}),
+            "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank: int, world: int) -> None:
+    import torch
+
+    from paper_1710_07745_gb300 import canny, synth
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    peaks = measured_peaks()
+    img = synth.image(SEED, W, H, N_OBJ, N_OBJ, NOISE)
+    d_in = torch.from_numpy(img).cuda()
+    d_out = torch.empty_like(d_in)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    ctx = canny.Canny(W, H, low=LOW, high=HIGH)
+
+    for _ in range(max(3, args.warmup)):
+        ctx.run(d_in, d_out, stream)
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    if st["status"] != canny.CANNY_OK:
+        raise RuntimeError(f"pipeline status {st['status']}")
+    passes = int(st["hyst_passes"])
+
+    canny.canny_enable_timing(ctx.ctx, True)
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        canny.canny_run(ctx.ctx, d_in.data_ptr(), d_out.data_ptr(), sp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop() if clocks else None
+    tm = canny.canny_read_timing(ctx.ctx).as_dict()
+    canny.canny_enable_timing(ctx.ctx, False)
+    ms_max = max_over_ranks(ms, world)
+
+    px = W * H
+    value = world * args.steps * px / (ms_max / 1e3) / 1e6
+    k1_ms = tm["stencil_ms"] / max(1, tm["runs"])
+    k1_gbs = K1_BYTES_PER_PX * px / (k1_ms / 1e3) / 1e9
+    pipe_gbs = PIPE_BYTES_PER_PX * px / (ms / args.steps / 1e3) / 1e9
+    stages = {"runs": tm["runs"], "stencil_ms": round(k1_ms, 4),
+              "local_ms": round(tm["local_ms"] / max(1, tm["runs"]), 4),
+              "global_ms": round(tm["global_ms"] / max(1, tm["runs"]), 4),
+              "hyst_passes": passes, "pending_tiles": int(st["pending_tiles"])}
+    dominant = max(("stencil_ms", "local_ms", "global_ms"), key=lambda k: stages[k])
+
+    # end to end through the C ABI on pinned host buffers: H2D + pipeline + D2H every step
+    h_in = torch.from_numpy(img).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    for _ in range(2):
+        canny.canny_run_host(ctx.ctx, h_in.data_ptr(), W, h_out.data_ptr(), W, W, H, sp)
+    e2e_steps = max(1, min(args.steps, 5))
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        canny.canny_run_host(ctx.ctx, h_in.data_ptr(), W, h_out.data_ptr(), W, W, H, sp)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e_value = world * e2e_steps * px / e2e_s / 1e6
+    if not np.array_equal(h_out[:64].numpy(), d_out[:64].cpu().numpy()):
+        raise RuntimeError("host-buffer run differs from device run")
+
+    if rank != 0:
+        ctx.close()
+        return
+    cpu_v, cpu_sample = oracle_sample(img, int(os.environ.get("CANNY_CPU_ROWS", "4096")))
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic", "config": config(),
+        "roofline": {"kernel": "k1_classify_u8 (fused Gauss/Sobel/NMS/threshold stencil)",
+                     "bound": "hbm", "achieved": round(k1_gbs, 1), "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": round(k1_gbs / peaks["hbm_gbs"], 4),
+                     "traffic": None, "peak_source": peaks["source"],
+                     "bytes_per_launch": K1_BYTES_PER_PX * px},
+        "pipeline_roofline": {"achieved": round(pipe_gbs, 1), "unit": "GB/s",
+                              "bytes_per_px": PIPE_BYTES_PER_PX,
+                              "frac": round(pipe_gbs / peaks["hbm_gbs"], 4)},
+        "stages": stages, "dominant_stage": dominant,
+        "cpu_baseline": {"value": round(cpu_v, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": cpu_sample},
+        "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": px,
+                "d2h_bytes_per_step": px, "steps": e2e_steps},
+        "gpu_launches": int(args.steps * (3 + passes)),
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    rank, world = dist_init(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -163,6 +163,25 @@ canny_status canny_hysteresis(canny_ctx *ctx, const canny_image *img, void *stre
 canny_status canny_magnitude_f32(canny_ctx *ctx, const canny_image *img, float *d_mag,
                                  int d_mag_pitch, float *d_max, void *stream);
 
+/* Device time per stage, summed over the runs since the last canny_read_timing. */
+typedef struct {
+    int64_t runs;          /* runs timed */
+    double stencil_ms;     /* Steps 1-3 + thresholds (the fused stencil kernel) */
+    double local_ms;       /* hysteresis: per-tile fill */
+    double global_ms;      /* hysteresis: global passes */
+    double total_ms;       /* first stage start to last stage end, summed over runs */
+} canny_timing;
+
+/*
+ * Turn per-stage timing on (enable != 0) or off. While on, every canny_run /
+ * canny_run_pitched records CUDA events on its stream around each stage
+ * (at most 4096 runs between reads; later runs are not timed).
+ */
+canny_status canny_enable_timing(canny_ctx *ctx, int enable);
+
+/* Synchronise, sum the stage times of the runs timed since the last read into *out, reset. */
+canny_status canny_read_timing(canny_ctx *ctx, canny_timing *out);
+
 /* Copy the counters of the last run into *out. Synchronises the context's last stream. */
 canny_status canny_get_stats(canny_ctx *ctx, canny_stats *out);
 

@@ -44,6 +44,14 @@ class canny_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class canny_timing(ctypes.Structure):
+    _fields_ = [("runs", ctypes.c_int64), ("stencil_ms", ctypes.c_double), ("local_ms", ctypes.c_double),
+                ("global_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -64,6 +72,8 @@ SIGNATURES = {
     "canny_magnitude_f32": ([_P, ctypes.POINTER(canny_image), _P, ctypes.c_int, _P, _P],
                             ctypes.c_int),
     "canny_get_stats": ([_P, ctypes.POINTER(canny_stats)], ctypes.c_int),
+    "canny_enable_timing": ([_P, ctypes.c_int], ctypes.c_int),
+    "canny_read_timing": ([_P, ctypes.POINTER(canny_timing)], ctypes.c_int),
     "canny_strerror": ([ctypes.c_int], ctypes.c_char_p),
 }
 
@@ -154,6 +164,16 @@ def canny_get_stats(ctx: int) -> canny_stats:
     return st
 
 
+def canny_enable_timing(ctx: int, enable: bool) -> None:
+    _check(load().canny_enable_timing(ctx, 1 if enable else 0), "canny_enable_timing")
+
+
+def canny_read_timing(ctx: int) -> canny_timing:
+    t = canny_timing()
+    _check(load().canny_read_timing(ctx, ctypes.byref(t)), "canny_read_timing")
+    return t
+
+
 # ------------------------------------------------------------------ torch marshalling
 def _stream_ptr(stream) -> int:
     if stream is None:
@@ -167,10 +187,14 @@ def _stream_ptr(stream) -> int:
 def image_of(t_in, t_out, w: int | None = None, h: int | None = None) -> canny_image:
     """canny_image over two 2-D uint8 CUDA tensors (row stride = pitch)."""
     for t in (t_in, t_out):
-        if not t.is_cuda or t.dtype.itemsize != 1 or t.dim() != 2 or t.stride(1) != 1:
-            raise ValueError("expected 2-D uint8 CUDA tensors with unit column stride")
+        if not t.is_cuda or t.dtype.itemsize != 1 or t.dim() != 2:
+            raise ValueError("expected 2-D uint8 CUDA tensors")
+        if t.numel() and t.stride(1) != 1:
+            raise ValueError("expected unit column stride")
     hh = t_in.shape[0] if h is None else h
     ww = t_in.shape[1] if w is None else w
+    if ww == 0 or hh == 0:
+        return canny_image(0, 0, ww, hh, 0, 0)
     return canny_image(t_in.data_ptr(), t_out.data_ptr(), ww, hh, t_in.stride(0), t_out.stride(0))
 
 

@@ -35,6 +35,11 @@ struct canny_ctx {
 
     cudaStream_t last_stream = nullptr;
     canny_stats last = {};
+
+    // per-stage timing: 4 events per timed run
+    int timing = 0;
+    std::vector<cudaEvent_t> ev;
+    int ev_runs = 0;
 };
 
 namespace {
@@ -218,6 +223,8 @@ canny_status run_one(canny_ctx *c, const canny_image *im, cudaStream_t s, bool s
     if (st != CANNY_OK) return st;
     c->last.pixels = (int64_t)im->w * im->h;
     c->last.tiles = ntiles;
+    const int slot = (c->timing && c->ev_runs < (int)c->ev.size() / 4) ? c->ev_runs++ : -1;
+    if (slot >= 0) cudaEventRecord(c->ev[4 * slot + 0], s);
     if (stencil) {
         st = run_stencil(c, im, s);
     } else {
@@ -225,11 +232,15 @@ canny_status run_one(canny_ctx *c, const canny_image *im, cudaStream_t s, bool s
                                          cudaMemcpyDeviceToDevice, s));
     }
     if (st != CANNY_OK) return st;
+    if (slot >= 0) cudaEventRecord(c->ev[4 * slot + 1], s);
     st = from_cuda(hyst_reset(c->hs, ntiles, 1, max_passes_for(c, ntiles), s));
     if (st != CANNY_OK) return st;
     st = from_cuda(launch_hyst_local_single(c->hs, hyst_image(im, 0), s));
     if (st != CANNY_OK) return st;
-    return run_global(c, s);
+    if (slot >= 0) cudaEventRecord(c->ev[4 * slot + 2], s);
+    st = run_global(c, s);
+    if (slot >= 0) cudaEventRecord(c->ev[4 * slot + 3], s);
+    return st;
 }
 
 }  // namespace
@@ -307,6 +318,8 @@ void canny_destroy(canny_ctx *c)
     if (c->h_state) cudaFreeHost(c->h_state);
     if (c->h_imgs) cudaFreeHost(c->h_imgs);
     if (c->staging_free) cudaEventDestroy(c->staging_free);
+    for (auto &e : c->ev)
+        if (e) cudaEventDestroy(e);
     delete c;
 }
 
@@ -438,6 +451,41 @@ canny_status canny_magnitude_f32(canny_ctx *c, const canny_image *img, float *d_
         e = launch_k1f_magnitude(img->d_in, img->in_pitch, d_mag, d_mag_pitch, img->w, img->h, c->fp,
                                  false, d_max, s);
     return from_cuda(e);
+}
+
+canny_status canny_enable_timing(canny_ctx *c, int enable)
+{
+    if (!c) return CANNY_EINVAL;
+    if (enable && c->ev.empty()) {
+        c->ev.resize(4 * 4096, nullptr);
+        for (auto &e : c->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return CANNY_ECUDA; }
+    }
+    c->timing = enable ? 1 : 0;
+    c->ev_runs = 0;
+    return CANNY_OK;
+}
+
+canny_status canny_read_timing(canny_ctx *c, canny_timing *out)
+{
+    if (!c || !out) return CANNY_EINVAL;
+    *out = canny_timing{};
+    for (int r = 0; r < c->ev_runs; ++r) {
+        cudaEvent_t *e = &c->ev[4 * r];
+        if (cudaEventSynchronize(e[3]) != cudaSuccess) { c->ev_runs = 0; return CANNY_ECUDA; }
+        float a = 0, b = 0, g = 0, t = 0;
+        cudaEventElapsedTime(&a, e[0], e[1]);
+        cudaEventElapsedTime(&b, e[1], e[2]);
+        cudaEventElapsedTime(&g, e[2], e[3]);
+        cudaEventElapsedTime(&t, e[0], e[3]);
+        out->stencil_ms += a;
+        out->local_ms += b;
+        out->global_ms += g;
+        out->total_ms += t;
+        out->runs += 1;
+    }
+    c->ev_runs = 0;
+    return CANNY_OK;
 }
 
 canny_status canny_get_stats(canny_ctx *c, canny_stats *out)

@@ -68,7 +68,7 @@ __device__ __forceinline__ uint32_t nz_nibble(uint32_t w)
 // 4 bytes 0xFF/0x00 from the low 4 bits of t.
 __device__ __forceinline__ uint32_t nibble_bytes(uint32_t t)
 {
-    return ((t * 0x00204081u) & 0x01010101u) * 0xFFu;
+    return (((t & 0xFu) * 0x00204081u) & 0x01010101u) * 0xFFu;
 }
 
 // Row `lane` of tile (tx, ty): cand = class >= 1, strong = class >= 2.

@@ -185,6 +185,30 @@ canny_status canny_read_timing(canny_ctx *ctx, canny_timing *out);
 /* Copy the counters of the last run into *out. Synchronises the context's last stream. */
 canny_status canny_get_stats(canny_ctx *ctx, canny_stats *out);
 
+/*
+ * Integer pipeline without any device allocation. The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- code that
+ * runs under a device-memory budget held entirely by another allocator (a
+ * framework's caching allocator, a fixed arena), or a frame loop in which the
+ * implicit device synchronisation of cudaMalloc/cudaFree is not allowed.
+ *
+ * Same result as canny_run_pitched on an integer-path context with thresholds
+ * low/high (integers, 0 <= low <= high < 2^15). The caller passes the device
+ * input and output as for canny_run_pitched; no context is needed. The
+ * hysteresis scratch is one fixed device array in the library (about 2.8 MB,
+ * held on every GPU that loads the library until the process exits), so the
+ * image may have at most 16384 tiles of 32x32 pixels (16.8 Mpixel, e.g.
+ * 4096 x 4096); larger images return CANNY_EUNSUPPORTED before any work is
+ * queued. Every call shares that array: calls that overlap on the GPU (other
+ * streams, other threads) race and must be serialised by the caller. The first
+ * call on each device looks up the array's device address (set-up, once per
+ * device); make that first call before any stream capture. Returns after the
+ * work has finished: the hysteresis passes are driven by the host, which
+ * synchronises the stream after each pass.
+ */
+canny_status canny_run_noalloc(const uint8_t *d_in, int in_pitch, uint8_t *d_out, int out_pitch,
+                               int w, int h, int low, int high, void *stream);
+
 /* Static, human-readable message for a status. */
 const char *canny_strerror(canny_status s);
 

@@ -74,6 +74,8 @@ SIGNATURES = {
     "canny_get_stats": ([_P, ctypes.POINTER(canny_stats)], ctypes.c_int),
     "canny_enable_timing": ([_P, ctypes.c_int], ctypes.c_int),
     "canny_read_timing": ([_P, ctypes.POINTER(canny_timing)], ctypes.c_int),
+    "canny_run_noalloc": ([_P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                           ctypes.c_int, _P], ctypes.c_int),
     "canny_strerror": ([ctypes.c_int], ctypes.c_char_p),
 }
 
@@ -172,6 +174,13 @@ def canny_read_timing(ctx: int) -> canny_timing:
     t = canny_timing()
     _check(load().canny_read_timing(ctx, ctypes.byref(t)), "canny_read_timing")
     return t
+
+
+def canny_run_noalloc(d_in: int, in_pitch: int, d_out: int, out_pitch: int, w: int, h: int,
+                      low: int, high: int, stream: int = 0) -> None:
+    """Integer pipeline with no device allocation (fixed scratch, at most 16384 tiles)."""
+    _check(load().canny_run_noalloc(d_in, in_pitch, d_out, out_pitch, w, h, low, high, stream),
+           "canny_run_noalloc")
 
 
 # ------------------------------------------------------------------ torch marshalling

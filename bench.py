@@ -31,7 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 W = H = 16384
-N_OBJ = 3200
+N_OBJ = 3200  # objects per kind at 16384^2 (200 per 4096^2 of area)
 NOISE = 12
 SEED = 3001
 LOW, HIGH = 40, 100
@@ -197,6 +197,11 @@ def run_ours(args, rank: int, world: int) -> None:
 
     from paper_1710_07745_gb300 import canny, synth
 
+    global W, H, N_OBJ, WORKLOAD
+    if args.size:
+        W, H = (int(v) for v in args.size.lower().split("x"))
+        N_OBJ = synth.objects_for_area(W, H)
+        WORKLOAD = f"canny_int_{W}x{H}"
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     peaks = measured_peaks()
@@ -247,25 +252,33 @@ def run_ours(args, rank: int, world: int) -> None:
               "hyst_passes": passes, "pending_tiles": int(st["pending_tiles"])}
     dominant = max(("stencil_ms", "local_ms", "global_ms"), key=lambda k: stages[k])
 
-    # end to end through the C ABI on pinned host buffers: H2D + pipeline + D2H every step
-    h_in = torch.from_numpy(img).pin_memory()
-    h_out = torch.empty_like(h_in).pin_memory()
-    for _ in range(2):
-        canny.canny_run_host(ctx.ctx, h_in.data_ptr(), W, h_out.data_ptr(), W, W, H, sp)
-    e2e_steps = max(1, min(args.steps, 5))
-    barrier(world)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        canny.canny_run_host(ctx.ctx, h_in.data_ptr(), W, h_out.data_ptr(), W, W, H, sp)
-    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
-    e2e_value = world * e2e_steps * px / e2e_s / 1e6
-    if not np.array_equal(h_out[:64].numpy(), d_out[:64].cpu().numpy()):
-        raise RuntimeError("host-buffer run differs from device run")
+    e2e = None
+    if not args.no_e2e:
+        # end to end through the C ABI on pinned host buffers: H2D + pipeline + D2H every step
+        h_in = torch.from_numpy(img).pin_memory()
+        h_out = torch.empty_like(h_in).pin_memory()
+        for _ in range(2):
+            canny.canny_run_host(ctx.ctx, h_in.data_ptr(), W, h_out.data_ptr(), W, W, H, sp)
+        e2e_steps = max(1, min(args.steps, 5))
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            canny.canny_run_host(ctx.ctx, h_in.data_ptr(), W, h_out.data_ptr(), W, W, H, sp)
+        e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+        if not np.array_equal(h_out[:64].numpy(), d_out[:64].cpu().numpy()):
+            raise RuntimeError("host-buffer run differs from device run")
+        e2e = {"value": round(world * e2e_steps * px / e2e_s / 1e6, 1), "unit": UNIT,
+               "h2d_bytes_per_step": px, "d2h_bytes_per_step": px, "steps": e2e_steps}
 
     if rank != 0:
         ctx.close()
         return
-    cpu_v, cpu_sample = oracle_sample(img, int(os.environ.get("CANNY_CPU_ROWS", "4096")))
+    cpu = None
+    if not args.no_cpu:
+        rows = min(H, int(os.environ.get("CANNY_CPU_ROWS", "4096")))
+        cpu_v, cpu_sample = oracle_sample(img, rows)
+        cpu = {"value": round(cpu_v, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": cpu_sample}
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4),
@@ -280,10 +293,8 @@ def run_ours(args, rank: int, world: int) -> None:
                               "bytes_per_px": PIPE_BYTES_PER_PX,
                               "frac": round(pipe_gbs / peaks["hbm_gbs"], 4)},
         "stages": stages, "dominant_stage": dominant,
-        "cpu_baseline": {"value": round(cpu_v, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": cpu_sample},
-        "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": px,
-                "d2h_bytes_per_step": px, "steps": e2e_steps},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
         "gpu_launches": int(args.steps * (3 + passes)),
         "clocks": clk,
     }
@@ -297,6 +308,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--size", default=None, help="WxH instead of 16384x16384 (profiling runs)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

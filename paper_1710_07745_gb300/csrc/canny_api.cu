@@ -181,7 +181,7 @@ canny_status run_stencil(canny_ctx *c, const canny_image *im, cudaStream_t s)
 {
     if (c->p.path == CANNY_PATH_INT)
         return from_cuda(launch_k1_classify_u8(im->d_in, im->in_pitch, im->d_out, im->out_pitch,
-                                               im->w, im->h, c->it, s));
+                                               im->w, im->h, c->it, &c->hs.state->error, s));
     cudaError_t e = cudaMemsetAsync(c->d_max, 0, sizeof(float), s);
     if (e == cudaSuccess)
         e = launch_k1f_magnitude(im->d_in, im->in_pitch, c->mag, im->w, im->w, im->h, c->fp, true,
@@ -225,19 +225,30 @@ canny_status run_one(canny_ctx *c, const canny_image *im, cudaStream_t s, bool s
     c->last.tiles = ntiles;
     const int slot = (c->timing && c->ev_runs < (int)c->ev.size() / 4) ? c->ev_runs++ : -1;
     if (slot >= 0) cudaEventRecord(c->ev[4 * slot + 0], s);
-    if (stencil) {
-        st = run_stencil(c, im, s);
+    const HystImage himg = hyst_image(im, 0);
+    st = from_cuda(hyst_reset(c->hs, ntiles, 1, max_passes_for(c, ntiles), s, &himg));
+    if (st != CANNY_OK) return st;
+    if (stencil && c->p.path == CANNY_PATH_INT) {
+        // fused: Steps 1-3, thresholds and the tile-local fill in one kernel
+        st = from_cuda(launch_k1_edges_u8(im->d_in, im->in_pitch, im->w, im->h, c->it, c->hs, himg, s));
+        if (st != CANNY_OK) return st;
+        if (slot >= 0) {
+            cudaEventRecord(c->ev[4 * slot + 1], s);
+            cudaEventRecord(c->ev[4 * slot + 2], s);
+        }
     } else {
-        st = from_cuda(cudaMemcpy2DAsync(im->d_out, im->out_pitch, im->d_in, im->in_pitch, im->w, im->h,
-                                         cudaMemcpyDeviceToDevice, s));
+        if (stencil) {
+            st = run_stencil(c, im, s);
+        } else {
+            st = from_cuda(cudaMemcpy2DAsync(im->d_out, im->out_pitch, im->d_in, im->in_pitch, im->w, im->h,
+                                             cudaMemcpyDeviceToDevice, s));
+        }
+        if (st != CANNY_OK) return st;
+        if (slot >= 0) cudaEventRecord(c->ev[4 * slot + 1], s);
+        st = from_cuda(launch_hyst_local_single(c->hs, himg, s));
+        if (st != CANNY_OK) return st;
+        if (slot >= 0) cudaEventRecord(c->ev[4 * slot + 2], s);
     }
-    if (st != CANNY_OK) return st;
-    if (slot >= 0) cudaEventRecord(c->ev[4 * slot + 1], s);
-    st = from_cuda(hyst_reset(c->hs, ntiles, 1, max_passes_for(c, ntiles), s));
-    if (st != CANNY_OK) return st;
-    st = from_cuda(launch_hyst_local_single(c->hs, hyst_image(im, 0), s));
-    if (st != CANNY_OK) return st;
-    if (slot >= 0) cudaEventRecord(c->ev[4 * slot + 2], s);
     st = run_global(c, s);
     if (slot >= 0) cudaEventRecord(c->ev[4 * slot + 3], s);
     return st;
@@ -382,15 +393,24 @@ canny_status canny_run_batch(canny_ctx *c, int n, const canny_image *imgs, void 
     e = cudaMemcpyAsync(c->hs.imgs, c->h_imgs, sizeof(HystImage) * nimg, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaEventRecord(c->staging_free, s);
     if (e != cudaSuccess) return from_cuda(e);
-    for (int i = 0; i < n; ++i) {
-        if (imgs[i].w == 0 || imgs[i].h == 0) continue;
-        st = run_stencil(c, &imgs[i], s);
-        if (st != CANNY_OK) return st;
-    }
     st = from_cuda(hyst_reset(c->hs, ntiles, nimg, max_passes_for(c, ntiles), s));
     if (st != CANNY_OK) return st;
-    st = from_cuda(launch_hyst_local_batch(c->hs, ntiles, nimg, s));
-    if (st != CANNY_OK) return st;
+    if (c->p.path == CANNY_PATH_INT) {
+        for (uint32_t k = 0, i = 0; i < (uint32_t)n; ++i) {
+            if (imgs[i].w == 0 || imgs[i].h == 0) continue;
+            st = from_cuda(launch_k1_edges_u8(imgs[i].d_in, imgs[i].in_pitch, imgs[i].w, imgs[i].h, c->it, c->hs,
+                                              c->h_imgs[k++], s));
+            if (st != CANNY_OK) return st;
+        }
+    } else {
+        for (int i = 0; i < n; ++i) {
+            if (imgs[i].w == 0 || imgs[i].h == 0) continue;
+            st = run_stencil(c, &imgs[i], s);
+            if (st != CANNY_OK) return st;
+        }
+        st = from_cuda(launch_hyst_local_batch(c->hs, ntiles, nimg, s));
+        if (st != CANNY_OK) return st;
+    }
     return run_global(c, s);
 }
 
@@ -419,7 +439,7 @@ canny_status canny_run_host(canny_ctx *c, const uint8_t *h_in, int in_pitch, uin
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return from_cuda(e);
     const HystState *hst = (const HystState *)c->h_state;
-    return (hst->error & 1u) ? CANNY_ENOCONVERGE : CANNY_OK;
+    return (hst->error & 2u) ? CANNY_ECUDA : (hst->error & 1u) ? CANNY_ENOCONVERGE : CANNY_OK;
 }
 
 canny_status canny_hysteresis(canny_ctx *c, const canny_image *img, void *stream)
@@ -504,7 +524,7 @@ canny_status canny_get_stats(canny_ctx *c, canny_stats *out)
     out->hyst_passes = st->pass;
     out->hyst_tiles_visited = st->visited;
     out->pending_tiles = st->pending_tiles;
-    out->status = (st->error & 1u) ? CANNY_ENOCONVERGE : CANNY_OK;
+    out->status = (st->error & 2u) ? CANNY_ECUDA : (st->error & 1u) ? CANNY_ENOCONVERGE : CANNY_OK;
     return CANNY_OK;
 }
 

@@ -38,7 +38,7 @@ struct HystState {
     uint32_t done_ctas;       // CTAs finished in the current global pass
     uint32_t pass;            // global passes completed
     uint32_t max_passes;      // cap
-    uint32_t error;           // bit 0: cap reached with work left
+    uint32_t error;           // bit 0: cap reached with work left; bit 1: a pipeline wait ran out
     uint32_t visited;         // tile visits summed over passes
     uint32_t pending_tiles;   // tiles with unresolved weak pixels after the local fill
     uint32_t ntiles;          // tiles in this run
@@ -71,9 +71,21 @@ struct FloatParams {
     float lo_frac, hi_frac;
 };
 
-// ---------------------------------------------------------------- launchers (k1_stencil.cu)
+// ---------------------------------------------------------------- launchers (k1_fused.cu)
+// Integer Steps 1-3 + thresholds: class map (0/1/2) into cls. err: device word
+// that gets bit 1 if a shared-memory pipeline wait ran out.
 cudaError_t launch_k1_classify_u8(const uint8_t *in, int in_pitch, uint8_t *cls, int cls_pitch,
-                                  int w, int h, IntThresholds t, cudaStream_t s);
+                                  int w, int h, IntThresholds t, uint32_t *err, cudaStream_t s);
+// Integer Steps 1-4 up to the tile-local hysteresis: edges (0/255) into img.map,
+// tile masks / pending bitmaps / first worklist into hs (after hyst_reset).
+cudaError_t launch_k1_edges_u8(const uint8_t *in, int in_pitch, int w, int h, IntThresholds t,
+                               const HystScratch &hs, HystImage img, cudaStream_t s);
+
+// ---------------------------------------------------------------- TMA (tma.cu)
+bool tma_usable(const void *base, int pitch);
+bool encode_u8_map(void *tmap_out, const void *base, int w, int h, int pitch, int box_w, int box_h);
+
+// ---------------------------------------------------------------- launchers (k1_stencil_f32.cu)
 cudaError_t launch_k1f_magnitude(const uint8_t *in, int in_pitch, float *mag, int mag_pitch,
                                  int w, int h, const FloatParams &fp, bool nms, float *d_max,
                                  cudaStream_t s);
@@ -91,8 +103,10 @@ cudaError_t launch_hyst_local_batch(const HystScratch &hs, uint32_t ntiles, uint
 // (0 when not in a graph).
 cudaError_t launch_hyst_global_pass(const HystScratch &hs, int grid, bool in_graph,
                                     unsigned long long cond_handle, cudaStream_t s);
+// Clear the worklist stamps and the control block before a run; for a single
+// image, also store its descriptor as image 0 (the global passes read it).
 cudaError_t hyst_reset(const HystScratch &hs, uint32_t ntiles, uint32_t nimg,
-                       uint32_t max_passes, cudaStream_t s);
+                       uint32_t max_passes, cudaStream_t s, const HystImage *single = nullptr);
 int hyst_pass_grid();
 // Executable graph { while (cond) global pass } bound to this scratch.
 cudaError_t hyst_build_graph(const HystScratch &hs, cudaGraph_t *graph_out, cudaGraphExec_t *exec_out);

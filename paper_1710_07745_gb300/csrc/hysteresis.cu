@@ -16,124 +16,15 @@
 //                condition set by the last CTA of each pass.
 // Pending pixels live only in a compact bitmap, so the map never holds a value
 // other than 0/255 and no clean-up sweep is needed.
-#include "canny_internal.cuh"
+#include "hyst_tile.cuh"
 
 namespace canny {
 
 namespace {
 
-constexpr unsigned FULL = 0xffffffffu;
 constexpr int WARPS = 8;             // tiles per CTA in the local fill and the global pass
 constexpr int THREADS = WARPS * 32;
-
-// Bits of c that lie in a run (of consecutive set bits) containing a bit of s;
-// s must be a subset of c. Upward: adding s to c carries from the lowest seed of
-// each run past its top, clearing exactly the bits from that seed up; downward:
-// the same on the bit-reversed words.
-__device__ __forceinline__ uint32_t fill_runs(uint32_t s, uint32_t c)
-{
-    uint32_t up = (c & ~(c + s)) | s;
-    uint32_t rs = __brev(s), rc = __brev(c);
-    uint32_t dn = __brev((rc & ~(rc + rs)) | rs);
-    return up | dn;
-}
-
-// Grow e (subset of c) through 8-connected pixels of c inside the tile until
-// stable. Every round that changes something adds at least one pixel, so at
-// most 1024 + 1 rounds run.
-__device__ __forceinline__ uint32_t flood_tile(uint32_t e, uint32_t c, int lane)
-{
-    for (int it = 0; it < HT * HT + 2; ++it) {
-        uint32_t f = fill_runs(e, c);
-        uint32_t d = f | (f << 1) | (f >> 1);
-        uint32_t up = __shfl_up_sync(FULL, d, 1);
-        uint32_t dn = __shfl_down_sync(FULL, d, 1);
-        if (lane == 0) up = 0;
-        if (lane == HT - 1) dn = 0;
-        uint32_t ne = f | (c & (up | dn));
-        bool changed = __any_sync(FULL, ne != e);
-        e = ne;
-        if (!changed) break;
-    }
-    return e;
-}
-
-// 4-bit mask of the nonzero bytes of w (bit k = byte k).
-__device__ __forceinline__ uint32_t nz_nibble(uint32_t w)
-{
-    uint32_t m = (((w & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | w) & 0x80808080u;
-    return ((m >> 7) * 0x10204080u) >> 28;
-}
-
-// 4 bytes 0xFF/0x00 from the low 4 bits of t.
-__device__ __forceinline__ uint32_t nibble_bytes(uint32_t t)
-{
-    return (((t & 0xFu) * 0x00204081u) & 0x01010101u) * 0xFFu;
-}
-
-// Row `lane` of tile (tx, ty): cand = class >= 1, strong = class >= 2.
-__device__ __forceinline__ void load_row(const HystImage &im, int tx, int ty, int lane,
-                                         uint32_t &cand, uint32_t &strong)
-{
-    cand = strong = 0;
-    int y = ty * HT + lane, x0 = tx * HT;
-    if (y >= im.h) return;
-    const uint8_t *row = im.map + (int64_t)y * im.pitch + x0;
-    int n = min(HT, im.w - x0);
-    if (n == HT && (((uintptr_t)row) & 15) == 0) {
-        uint4 a = reinterpret_cast<const uint4 *>(row)[0];
-        uint4 b = reinterpret_cast<const uint4 *>(row)[1];
-        uint32_t wd[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            cand |= nz_nibble(wd[k]) << (4 * k);
-            strong |= nz_nibble(wd[k] & 0xFEFEFEFEu) << (4 * k);
-        }
-    } else {
-        for (int i = 0; i < n; ++i) {
-            uint8_t v = row[i];
-            if (v) cand |= 1u << i;
-            if (v >= 2) strong |= 1u << i;
-        }
-    }
-}
-
-// Write row `lane` of the tile as 255 where e is set, 0 elsewhere.
-__device__ __forceinline__ void store_row(const HystImage &im, int tx, int ty, int lane, uint32_t e)
-{
-    int y = ty * HT + lane, x0 = tx * HT;
-    if (y >= im.h) return;
-    uint8_t *row = im.map + (int64_t)y * im.pitch + x0;
-    int n = min(HT, im.w - x0);
-    if (n == HT && (((uintptr_t)row) & 15) == 0) {
-        uint4 a, b;
-        a.x = nibble_bytes(e); a.y = nibble_bytes(e >> 4); a.z = nibble_bytes(e >> 8); a.w = nibble_bytes(e >> 12);
-        b.x = nibble_bytes(e >> 16); b.y = nibble_bytes(e >> 20); b.z = nibble_bytes(e >> 24); b.w = nibble_bytes(e >> 28);
-        reinterpret_cast<uint4 *>(row)[0] = a;
-        reinterpret_cast<uint4 *>(row)[1] = b;
-    } else {
-        for (int i = 0; i < n; ++i) row[i] = ((e >> i) & 1) ? 255 : 0;
-    }
-}
-
-__device__ __forceinline__ int find_image(const HystImage *imgs, int nimg, uint32_t t)
-{
-    int lo = 0, hi = nimg - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (imgs[mid].tile_base <= t) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ void push(const HystScratch &hs, uint32_t list, uint32_t tile, uint32_t stamp)
-{
-    if (atomicMax(&hs.stamp[tile], stamp) < stamp) {
-        uint32_t idx = atomicAdd(&hs.state->list_count[list], 1u);
-        hs.lists[(size_t)list * hs.max_tiles + idx] = tile;
-    }
-}
+using namespace tile;
 
 // ---------------------------------------------------------------- local fill
 template <bool SINGLE>
@@ -152,25 +43,7 @@ hyst_local_kernel(HystScratch hs, HystImage single, uint32_t ntiles, uint32_t ni
     load_row(im, tx, ty, lane, cand, strong);
     const uint32_t e = flood_tile(strong, cand, lane);
     store_row(im, tx, ty, lane, e);
-    const uint32_t pend = cand & ~e;
-
-    TileMasks m;
-    m.edge_top = __shfl_sync(FULL, e, 0);
-    m.edge_bottom = __shfl_sync(FULL, e, HT - 1);
-    m.edge_left = __ballot_sync(FULL, e & 1u);
-    m.edge_right = __ballot_sync(FULL, e >> 31);
-    m.pend_top = __shfl_sync(FULL, pend, 0);
-    m.pend_bottom = __shfl_sync(FULL, pend, HT - 1);
-    m.pend_left = __ballot_sync(FULL, pend & 1u);
-    m.pend_right = __ballot_sync(FULL, pend >> 31);
-    const bool any_pend = __any_sync(FULL, pend != 0);
-    if (any_pend) hs.pend_bits[(size_t)t * HT + lane] = pend;
-    if (lane == 0) {
-        hs.masks[t] = m;
-        if (any_pend) atomicAdd(&hs.state->pending_tiles, 1u);
-        // pending pixels on the border may be reached from a neighbour: queue for pass 0
-        if (m.pend_top | m.pend_bottom | m.pend_left | m.pend_right) push(hs, 0, t, 1);
-    }
+    finish_tile(hs, t, e, cand, lane);
 }
 
 // ---------------------------------------------------------------- global pass
@@ -308,8 +181,10 @@ hyst_global_kernel(HystScratch hs, int in_graph, cudaGraphConditionalHandle cond
     }
 }
 
-__global__ void hyst_init_kernel(HystState *st, uint32_t ntiles, uint32_t nimg, uint32_t max_passes)
+__global__ void hyst_init_kernel(HystState *st, uint32_t ntiles, uint32_t nimg, uint32_t max_passes,
+                                 HystImage *imgs, HystImage single, int write_single)
 {
+    if (write_single) imgs[0] = single;
     HystState s = {};
     s.ntiles = ntiles;
     s.nimg = nimg;
@@ -334,11 +209,12 @@ int hyst_pass_grid()
 }
 
 cudaError_t hyst_reset(const HystScratch &hs, uint32_t ntiles, uint32_t nimg, uint32_t max_passes,
-                       cudaStream_t s)
+                       cudaStream_t s, const HystImage *single)
 {
     cudaError_t err = cudaMemsetAsync(hs.stamp, 0, sizeof(uint32_t) * (size_t)ntiles, s);
     if (err != cudaSuccess) return err;
-    hyst_init_kernel<<<1, 1, 0, s>>>(hs.state, ntiles, nimg, max_passes);
+    HystImage one = single ? *single : HystImage{};
+    hyst_init_kernel<<<1, 1, 0, s>>>(hs.state, ntiles, nimg, max_passes, hs.imgs, one, single ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,557 @@
+// k1_fused.cu -- the integer path of Steps 1-4 of the paper's Sec. 2.2.1 in one
+// kernel: Gaussian -> Sobel -> strength -> direction sector -> non-maximum
+// suppression -> double threshold -> tile-local hysteresis. The image is read
+// once and the edge map written once; the class map never leaves the SM.
+//
+// A CTA owns 960 columns x 64 rows (30 x 2 hysteresis tiles); each of its four
+// warps a 240-column strip of it.
+//
+// Phase 1, per warp, sliding down the 64 rows (plus a 4-row halo each side):
+//   - TMA loads the strip's input rows (272 bytes each: the strip and an
+//     8-byte halo per side, rounded out to 16-byte boundaries) in chunks of 6
+//     rows into a 4-stage shared-memory ring, one mbarrier per stage;
+//   - each lane takes 8 pixels: the binomial Gaussian runs on pairs of 16-bit
+//     lanes (vertical: a cascade of four pairwise sums; horizontal: packed
+//     words with the +128 rounding folded in), neighbour lanes trade halo
+//     values by shuffles; lanes 0 and 31 only serve halos;
+//   - the smoothed bytes become floats 2^23 + S and Sobel and the squared
+//     strength run in packed float2 arithmetic (__ffma2_rn etc.); every value
+//     is an integer below 2^24, so the result is exact;
+//   - only ~2% of pixels exceed the low threshold. A lane with such pixels
+//     stores its row of strengths and packed gradients in a 5-row ring and
+//     queues (row, lane) one row later; after every 3 rows the warp's lanes
+//     share the queued candidates (one entry each) and run the sector test and
+//     the suppression for them alone, setting bits in the CTA's weak/strong
+//     row bitmasks.
+// Phase 2, after a CTA barrier: either the class map is written from the
+// bitmasks (canny_classify), or each warp runs the tile flood fill of the
+// hysteresis on the bitmasks and writes 255/0 edge bytes plus the tile border
+// masks and pending bitmaps that the global passes need.
+#include <cuda.h>
+#include <string.h>
+
+#include "hyst_tile.cuh"
+
+namespace canny {
+
+namespace {
+
+using tile::FULL;
+
+constexpr int LPX = 8;                  // pixels per lane per row
+constexpr int WARPS = 4;
+constexpr int THREADS = WARPS * 32;
+constexpr int OUT_W = 30 * LPX;         // 240 output columns per warp
+constexpr int CTA_W = WARPS * OUT_W;    // 960 columns = 30 hysteresis tiles
+constexpr int BAND = 64;                // output rows = 2 hysteresis tiles
+constexpr int ITERS = BAND + 8;         // input rows Y0-4 .. Y0+BAND+3
+constexpr int UNROLL = 3;               // period of the 3-row windows
+constexpr int CH = 6;                   // input rows per TMA chunk
+constexpr int STAGES = 4;
+constexpr int NCH = ITERS / CH;         // 12 chunks per band
+constexpr int BOXA = 256, BOXB = 16;    // the two TMA boxes of a strip row
+constexpr uint32_t CHUNK_BYTES = (BOXA + BOXB) * CH;
+constexpr int RING = 5;                 // rows of candidate data kept per warp
+constexpr int TILES_X = CTA_W / HT, TILES_Y = BAND / HT;
+constexpr int MW = CTA_W / 32;          // bitmask words per CTA row
+static_assert(ITERS % UNROLL == 0 && ITERS % CH == 0, "");
+static_assert((CH * BOXA) % 128 == 0 && CH * BOXB <= 128, "TMA stage buffers must stay 128-byte aligned");
+
+constexpr uint32_t MAGIC = 0x4B000000u;             // float 2^23
+constexpr uint32_t BIAS = 0x00800080u;              // +128 in both 16-bit lanes
+constexpr uint32_t WAIT_LIMIT = 1u << 22;           // bounded mbarrier waits
+
+enum { MODE_CLASSMAP = 0, MODE_EDGES = 1 };
+
+struct alignas(128) WarpSmem {
+    uint8_t inA[STAGES][CH * BOXA];      // TMA destinations, 128-byte aligned
+    uint8_t inB[STAGES][128];            // CH * BOXB = 96 bytes used
+    float m2[RING][256];
+    uint32_t gxy[RING][256];             // (gx + 1024) | (gy + 1024) << 16
+    uint8_t cm[RING][32];                // per lane: which of its 8 pixels exceed the low threshold
+    uint32_t queue[UNROLL * 32];         // (row << 5) | lane
+    uint32_t qcount;
+    uint32_t pad;
+    unsigned long long full[STAGES];     // mbarriers of the input ring
+};
+
+struct alignas(128) Smem {
+    WarpSmem warp[WARPS];
+    uint32_t cand[BAND][MW];             // class >= 1 (weak or strong), bit = column
+    uint32_t strong[BAND][MW];           // class == 2
+};
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(saddr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(saddr(dst)), "l"(map), "r"(x), "r"(y), "r"(saddr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t perm(uint32_t a, uint32_t b, uint32_t sel) { return __byte_perm(a, b, sel); }
+
+// float 2^23 + (byte k of w)
+__device__ __forceinline__ float sbyte(uint32_t w, int k)
+{
+    return __uint_as_float(perm(w, MAGIC, 0x7540u | (uint32_t)k));
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.f, -1.f), a); }
+
+// 4 bytes of value 0/1 from the low 4 bits of t
+__device__ __forceinline__ uint32_t nib01(uint32_t t) { return ((t & 0xFu) * 0x00204081u) & 0x01010101u; }
+
+// Pixel k in [-1, 8] of a row held as pairs p[j] = (x_j, x_{j+4}), p[4] = (x_-1, x_8).
+__device__ __forceinline__ float &pix(float2 (&p)[5], int k)
+{
+    return k < 0 ? p[4].x : (k > 7 ? p[4].y : (k < 4 ? p[k].x : p[k - 4].y));
+}
+
+// ---------------------------------------------------------------- candidate suppression
+// Strength of pixel pp (0..255 in the warp strip) of ring row yy, or 0 if it is
+// not above the low threshold (such pixels can neither win nor suppress).
+__device__ __forceinline__ float ring_m2(const WarpSmem &ws, int pp, int yy)
+{
+    const int sl = ((yy % RING) + RING) % RING;
+    const uint32_t bit = (ws.cm[sl][pp >> 3] >> (pp & 7)) & 1u;
+    return bit ? ws.m2[sl][pp] : 0.f;
+}
+
+// Step 3 + thresholds for the candidate pixels of one queued (row, lane) entry.
+__device__ __forceinline__ void suppress_entry(const WarpSmem &ws, Smem &S, uint32_t entry, int wid, int Y0,
+                                               float hi2)
+{
+    const int y = (int)(entry >> 5), L = (int)(entry & 31u);
+    const int sl = y % RING;
+    uint32_t bits = ws.cm[sl][L];
+    while (bits) {
+        const int k = __ffs(bits) - 1;
+        bits &= bits - 1;
+        const int p = LPX * L + k;
+        const float m = ws.m2[sl][p];
+        const uint32_t g = ws.gxy[sl][p];
+        const int gx = (int)(g & 0xFFFFu) - 1024, gy = (int)(g >> 16) - 1024;
+        const int ax = abs(gx), ay = abs(gy);
+        float mn, mp;
+        if (ay * 32768 < ax * 13573) {                 // H: left / right
+            mn = ring_m2(ws, p - 1, y);
+            mp = ring_m2(ws, p + 1, y);
+        } else if (ax * 32768 < ay * 13573) {          // V: up / down
+            mn = ring_m2(ws, p, y - 1);
+            mp = ring_m2(ws, p, y + 1);
+        } else if (gx * gy > 0) {                      // D: up-left / down-right
+            mn = ring_m2(ws, p - 1, y - 1);
+            mp = ring_m2(ws, p + 1, y + 1);
+        } else {                                       // A: down-left / up-right
+            mn = ring_m2(ws, p - 1, y + 1);
+            mp = ring_m2(ws, p + 1, y - 1);
+        }
+        if (m > mn && m >= mp) {
+            const int col = wid * OUT_W + p - LPX, row = y - Y0;
+            atomicOr(&S.cand[row][col >> 5], 1u << (col & 31));
+            if (m > hi2) atomicOr(&S.strong[row][col >> 5], 1u << (col & 31));
+        }
+    }
+}
+
+// ---------------------------------------------------------------- phase 1
+template <bool TMA>
+__device__ __forceinline__ void stencil_band(const CUtensorMap *tmapA, const CUtensorMap *tmapB,
+                                             const uint8_t *__restrict__ in,
+                                             int in_pitch, int w, int h, IntThresholds t, Smem &S,
+                                             WarpSmem &ws, int wid, int lane, int X0, int Y0,
+                                             uint32_t *err)
+{
+    const int xl = X0 - LPX + LPX * lane;     // image column of the lane's first pixel
+    const bool border = xl <= 0 || xl + LPX >= w;
+    const bool out_lane = lane >= 1 && lane <= 30 && xl < w;
+    const int last = w - 1 - xl;               // index of the lane's last in-image pixel
+    const float lo2 = (float)min(t.lo2, 1 << 24), hi2 = (float)min(t.hi2, 1 << 24);
+    const bool direct_fast = !TMA && xl >= 0 && xl + LPX <= w &&
+                             ((((uintptr_t)in) | (uintptr_t)in_pitch | (uintptr_t)xl) & 7) == 0;
+
+    uint32_t rp[4] = {0, 0, 0, 0}, p1[4] = {0, 0, 0, 0}, p2[4] = {0, 0, 0, 0}, p3[4] = {0, 0, 0, 0};
+    float2 Sp[3][5];      // 2^23 + S by row slot (row mod 3), pairs (x_j, x_j+4), halo (x_-1, x_8)
+    float2 Dxp[3][4];     // S(x+1) - S(x-1) by row slot
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int j = 0; j < 5; ++j) Sp[a][j] = f2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) Dxp[a][j] = f2(0.f, 0.f);
+    }
+    uint32_t cm_prev = 0;
+    int r_prev = -1;
+    uint32_t last0 = 0, last1 = 0;            // words of input row h-1, for rows below the image
+    uint32_t pf0[UNROLL], pf1[UNROLL];        // direct-load prefetch
+
+    auto direct_load = [&](int y, uint32_t &w0, uint32_t &w1) {
+        const uint8_t *row = in + (int64_t)clampi(y, 0, h - 1) * in_pitch;
+        if (direct_fast) {
+            uint2 v = __ldg(reinterpret_cast<const uint2 *>(row + xl));
+            w0 = v.x;
+            w1 = v.y;
+        } else {
+            uint32_t b[LPX];
+#pragma unroll
+            for (int k = 0; k < LPX; ++k) b[k] = __ldg(row + clampi(xl + k, 0, w - 1));
+            w0 = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
+            w1 = b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24);
+        }
+    };
+    auto issue_chunk = [&](int c) {           // lane 0 only
+        const int slot = c % STAGES;
+        const int y = Y0 - 4 + c * CH;
+        mbar_expect_tx(&ws.full[slot], CHUNK_BYTES);
+        tma_load_2d(&ws.inA[slot][0], tmapA, X0 - 16, y, &ws.full[slot]);
+        tma_load_2d(&ws.inB[slot][0], tmapB, X0 + OUT_W, y, &ws.full[slot]);
+    };
+
+    if (TMA) {
+        if (lane == 0)
+            for (int c = 0; c < STAGES && c < NCH; ++c) issue_chunk(c);
+    } else {
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) direct_load(Y0 - 4 + u, pf0[u], pf1[u]);
+    }
+    bool failed = false;
+
+    for (int g = 0; g < ITERS; g += UNROLL) {
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            const int i = g + u;
+            const int yin = Y0 - 4 + i;          // input row of this iteration
+            const int s = yin - 2;               // smoothed row completed now
+            const int a = u % 3;                 // slot of row s
+            const int am1 = (u + 2) % 3, am2 = (u + 1) % 3;
+
+            // ---- the lane's 8 input bytes of row clamp(yin)
+            uint32_t w0, w1;
+            if (TMA) {
+                const int c = i / CH, off = i % CH, slot = c % STAGES;
+                if (off == 0 && !failed) {
+                    uint32_t n = 0;
+                    while (!mbar_try_wait(&ws.full[slot], (uint32_t)(c / STAGES) & 1u))
+                        if (++n > WAIT_LIMIT) { failed = true; break; }
+                    if (failed && lane == 0) atomicOr(err, 2u);
+                }
+                if (yin >= h) {
+                    w0 = last0;
+                    w1 = last1;
+                } else {
+                    const int rr = yin < 0 ? 4 : off;        // rows above the image repeat row 0
+                    const uint8_t *rowA = &ws.inA[slot][rr * BOXA];
+                    const uint8_t *rowB = &ws.inB[slot][rr * BOXB];
+                    if (!border) {
+                        const uint2 v = *reinterpret_cast<const uint2 *>(lane < 31 ? rowA + 8 + LPX * lane : rowB);
+                        w0 = v.x;
+                        w1 = v.y;
+                    } else {
+                        uint32_t b[LPX];
+#pragma unroll
+                        for (int k = 0; k < LPX; ++k) {
+                            const int o = clampi(xl + k, 0, w - 1) - (X0 - 16);   // 0 .. 271
+                            b[k] = o < BOXA ? rowA[o] : rowB[o - BOXA];
+                        }
+                        w0 = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
+                        w1 = b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24);
+                    }
+                    if (yin == h - 1) {
+                        last0 = w0;
+                        last1 = w1;
+                    }
+                }
+                if (off == CH - 1) {             // chunk consumed: refill its stage
+                    __syncwarp();
+                    if (lane == 0 && c + STAGES < NCH && !failed) {
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        issue_chunk(c + STAGES);
+                    }
+                }
+            } else {
+                w0 = pf0[u];
+                w1 = pf1[u];
+                if (i + UNROLL < ITERS) direct_load(yin + UNROLL, pf0[u], pf1[u]);
+            }
+
+            // ---- Step 1: vertical binomial cascade
+            uint32_t q[4];
+            q[0] = perm(w0, 0, 0x4240u);   // pixels (0, 2)
+            q[1] = perm(w0, 0, 0x4341u);   // pixels (1, 3)
+            q[2] = perm(w1, 0, 0x4240u);   // pixels (4, 6)
+            q[3] = perm(w1, 0, 0x4341u);   // pixels (5, 7)
+            uint32_t v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t n1 = rp[k] + q[k];
+                const uint32_t n2 = p1[k] + n1;
+                const uint32_t n3 = p2[k] + n2;
+                v[k] = p3[k] + n3;
+                rp[k] = q[k];
+                p1[k] = n1;
+                p2[k] = n2;
+                p3[k] = n3;
+            }
+            if (i < 4) continue;                 // cascade still filling (warp-uniform)
+
+            // ---- Step 1: horizontal binomial on the packed vertical sums
+            const uint32_t Lh = __shfl_up_sync(FULL, perm(v[2], v[3], 0x7632u), 1);   // (V-2, V-1)
+            const uint32_t Rh = __shfl_down_sync(FULL, perm(v[0], v[1], 0x5410u), 1); // (V8, V9)
+            const uint32_t A = perm(Lh, v[0], 0x5410u);   // (V-2, V0)
+            const uint32_t B = perm(Lh, v[1], 0x5432u);   // (V-1, V1)
+            const uint32_t C = perm(v[0], v[2], 0x5432u); // (V2, V4)
+            const uint32_t D = perm(v[1], v[3], 0x5432u); // (V3, V5)
+            const uint32_t F = perm(v[2], Rh, 0x5432u);   // (V6, V8)
+            const uint32_t G = perm(v[3], Rh, 0x7632u);   // (V7, V9)
+            const uint32_t he0 = A + C + BIAS + 4u * (B + v[1]) + 6u * v[0];   // (h0, h2)
+            const uint32_t ho0 = B + D + BIAS + 4u * (v[0] + C) + 6u * v[1];   // (h1, h3)
+            const uint32_t he1 = C + F + BIAS + 4u * (D + v[3]) + 6u * v[2];   // (h4, h6)
+            const uint32_t ho1 = D + G + BIAS + 4u * (v[2] + F) + 6u * v[3];   // (h5, h7)
+            Sp[a][0] = f2(sbyte(he0, 1), sbyte(he1, 1));   // (S0, S4)
+            Sp[a][1] = f2(sbyte(ho0, 1), sbyte(ho1, 1));   // (S1, S5)
+            Sp[a][2] = f2(sbyte(he0, 3), sbyte(he1, 3));   // (S2, S6)
+            Sp[a][3] = f2(sbyte(ho0, 3), sbyte(ho1, 3));   // (S3, S7)
+            Sp[a][4] = f2(__shfl_up_sync(FULL, Sp[a][3].y, 1), __shfl_down_sync(FULL, Sp[a][0].x, 1));
+            if (border) {
+                // replicate border on S: S(-1) = S(0), S(x >= w) = S(w - 1)
+                if (xl == 0) Sp[a][4].x = Sp[a][0].x;
+                if (last < LPX + 1) {
+                    float sl = Sp[a][4].x;
+#pragma unroll
+                    for (int k = -1; k <= LPX; ++k) if (k == last) sl = pix(Sp[a], k);
+#pragma unroll
+                    for (int k = -1; k <= LPX; ++k) if (k > last) pix(Sp[a], k) = sl;
+                }
+            }
+            if (s == 0) {                        // S(-1) = S(0)
+#pragma unroll
+                for (int j = 0; j < 5; ++j) Sp[am1][j] = Sp[a][j];
+            } else if (s >= h) {                 // S(h) = S(h - 1)
+#pragma unroll
+                for (int j = 0; j < 5; ++j) Sp[a][j] = Sp[am1][j];
+            }
+            // S(x+1) - S(x-1), pairwise
+            Dxp[a][0] = sub2(Sp[a][1], f2(Sp[a][4].x, Sp[a][3].x));
+            Dxp[a][1] = sub2(Sp[a][2], Sp[a][0]);
+            Dxp[a][2] = sub2(Sp[a][3], Sp[a][1]);
+            Dxp[a][3] = sub2(f2(Sp[a][0].y, Sp[a][4].y), Sp[a][2]);
+            if (s == 0) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) Dxp[am1][j] = Dxp[a][j];
+            }
+            if (i < 6) continue;
+
+            // ---- Step 2: Sobel and strength of row r = s-1 (slots am2, am1, a = rows r-1, r, r+1)
+            const int r = s - 1;
+            float2 E[5];
+#pragma unroll
+            for (int j = 0; j < 5; ++j) E[j] = sub2(Sp[a][j], Sp[am2][j]);
+            float2 gx[4], gy[4], m[4];
+            const float2 two = f2(2.f, 2.f);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                gx[j] = __fadd2_rn(__ffma2_rn(Dxp[am1][j], two, Dxp[am2][j]), Dxp[a][j]);
+                const float2 el = j > 0 ? E[j - 1] : f2(E[4].x, E[3].x);   // E(x-1)
+                const float2 er = j < 3 ? E[j + 1] : f2(E[0].y, E[4].y);   // E(x+1)
+                gy[j] = __fadd2_rn(__ffma2_rn(E[j], two, el), er);
+                m[j] = __ffma2_rn(gx[j], gx[j], __fmul2_rn(gy[j], gy[j]));
+            }
+            if (r < 0 || r >= h) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) m[j] = f2(0.f, 0.f);
+            } else if (border) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (xl + j < 0 || j > last) m[j].x = 0.f;
+                    if (xl + j + 4 < 0 || j + 4 > last) m[j].y = 0.f;
+                }
+            }
+            const float rowmax = fmaxf(fmaxf(fmaxf(m[0].x, m[0].y), fmaxf(m[1].x, m[1].y)),
+                                       fmaxf(fmaxf(m[2].x, m[2].y), fmaxf(m[3].x, m[3].y)));
+            uint32_t cm = 0;
+            const int rs = ((r % RING) + RING) % RING;
+            if (rowmax > lo2) {
+                // candidate lane: keep the row's strengths and gradients for the suppression
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    cm |= (m[j].x > lo2 ? 1u : 0u) << j;
+                    cm |= (m[j].y > lo2 ? 1u : 0u) << (j + 4);
+                }
+                float4 *dst = reinterpret_cast<float4 *>(&ws.m2[rs][LPX * lane]);
+                dst[0] = make_float4(m[0].x, m[1].x, m[2].x, m[3].x);
+                dst[1] = make_float4(m[0].y, m[1].y, m[2].y, m[3].y);
+                uint32_t gg[LPX];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    // 2^23 + 1024 + g holds g + 1024 in its low mantissa bits
+                    gg[j] = perm(__float_as_uint(gx[j].x + 8389632.0f), __float_as_uint(gy[j].x + 8389632.0f), 0x5410u);
+                    gg[j + 4] = perm(__float_as_uint(gx[j].y + 8389632.0f), __float_as_uint(gy[j].y + 8389632.0f), 0x5410u);
+                }
+                uint4 *gdst = reinterpret_cast<uint4 *>(&ws.gxy[rs][LPX * lane]);
+                gdst[0] = make_uint4(gg[0], gg[1], gg[2], gg[3]);
+                gdst[1] = make_uint4(gg[4], gg[5], gg[6], gg[7]);
+            }
+            ws.cm[rs][lane] = (uint8_t)cm;
+            // queue the previous row's candidates now that its lower neighbour row exists
+            if (cm_prev && out_lane && r_prev >= Y0 && r_prev < Y0 + BAND) {
+                const uint32_t idx = atomicAdd(&ws.qcount, 1u);
+                ws.queue[idx] = ((uint32_t)r_prev << 5) | (uint32_t)lane;
+            }
+            cm_prev = cm;
+            r_prev = r;
+        }
+        // ---- Step 3 + thresholds for the queued candidates (their rows +-1 are in the ring)
+        __syncwarp();
+        const uint32_t n = ws.qcount;
+        for (uint32_t j = lane; j < n; j += 32) suppress_entry(ws, S, ws.queue[j], wid, Y0, hi2);
+        __syncwarp();
+        if (lane == 0) ws.qcount = 0;
+        __syncwarp();
+    }
+    // the last Sobel row (Y0 + BAND) is below the band: nothing left to queue
+}
+
+// ---------------------------------------------------------------- kernel
+template <bool TMA, int MODE>
+__global__ void __launch_bounds__(THREADS, 2)
+k1_fused_kernel(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUtensorMap tmapB,
+                const uint8_t *__restrict__ in, int in_pitch,
+                int w, int h, IntThresholds t, uint8_t *__restrict__ out, int out_pitch, HystScratch hs,
+                HystImage img, uint32_t *err)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    WarpSmem &ws = S.warp[wid];
+    const int X0c = blockIdx.x * CTA_W, Y0 = blockIdx.y * BAND;
+    const int X0 = X0c + wid * OUT_W;
+
+    for (int k = threadIdx.x; k < BAND * MW; k += THREADS) {
+        (&S.cand[0][0])[k] = 0u;
+        (&S.strong[0][0])[k] = 0u;
+    }
+    for (int k = lane; k < RING * 32; k += 32) (&ws.cm[0][0])[k] = 0;
+    if (lane == 0) {
+        ws.qcount = 0;
+        if (TMA) {
+            for (int sidx = 0; sidx < STAGES; ++sidx) mbar_init(&ws.full[sidx], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+    }
+    __syncthreads();
+
+    if (X0 < w) stencil_band<TMA>(&tmapA, &tmapB, in, in_pitch, w, h, t, S, ws, wid, lane, X0, Y0, err);
+    __syncthreads();
+
+    if (MODE == MODE_CLASSMAP) {
+        // class byte = weak bit + strong bit
+        for (int k = threadIdx.x; k < BAND * MW; k += THREADS) {
+            const int row = k / MW, wj = k % MW;
+            const int y = Y0 + row, x = X0c + 32 * wj;
+            if (y >= h || x >= w) continue;
+            const uint32_t c = S.cand[row][wj], sgl = S.strong[row][wj];
+            uint32_t wd[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) wd[q] = nib01(c >> (4 * q)) + nib01(sgl >> (4 * q));
+            uint8_t *dst = out + (int64_t)y * out_pitch + x;
+            if (x + 32 <= w && ((((uintptr_t)dst)) & 15) == 0) {
+                reinterpret_cast<uint4 *>(dst)[0] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+                reinterpret_cast<uint4 *>(dst)[1] = make_uint4(wd[4], wd[5], wd[6], wd[7]);
+            } else {
+                for (int b = 0; b < 32 && x + b < w; ++b) dst[b] = (uint8_t)((wd[b >> 2] >> (8 * (b & 3))) & 0xFF);
+            }
+        }
+    } else {
+        // Step 4, tile-local: flood fill each of the CTA's 30 x 2 tiles from its bitmasks
+        for (int tl = wid; tl < TILES_X * TILES_Y; tl += WARPS) {
+            const int txl = tl % TILES_X, tyl = tl / TILES_X;
+            const int tx = blockIdx.x * TILES_X + txl, ty = blockIdx.y * TILES_Y + tyl;
+            if (tx >= img.ntx || ty >= img.nty) continue;         // warp-uniform
+            const uint32_t cand = S.cand[tyl * HT + lane][txl];
+            const uint32_t strong = S.strong[tyl * HT + lane][txl];
+            const uint32_t e = tile::flood_tile(strong, cand, lane);
+            tile::store_row(img, tx, ty, lane, e);
+            tile::finish_tile(hs, img.tile_base + (uint32_t)ty * (uint32_t)img.ntx + (uint32_t)tx, e, cand, lane);
+        }
+    }
+}
+
+template <bool TMA, int MODE>
+cudaError_t launch_mode(const CUtensorMap &tmapA, const CUtensorMap &tmapB, const uint8_t *in, int in_pitch, int w, int h, IntThresholds t,
+                        uint8_t *out, int out_pitch, const HystScratch &hs, const HystImage &img, uint32_t *err,
+                        cudaStream_t s)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k1_fused_kernel<TMA, MODE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid((w + CTA_W - 1) / CTA_W, (h + BAND - 1) / BAND);
+    k1_fused_kernel<TMA, MODE><<<grid, THREADS, sizeof(Smem), s>>>(tmapA, tmapB, in, in_pitch, w, h, t, out,
+                                                                    out_pitch, hs, img, err);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t launch_any(const uint8_t *in, int in_pitch, int w, int h, IntThresholds t, uint8_t *out,
+                       int out_pitch, const HystScratch &hs, const HystImage &img, uint32_t *err, cudaStream_t s)
+{
+    CUtensorMap tmapA, tmapB;
+    memset(&tmapA, 0, sizeof(tmapA));
+    memset(&tmapB, 0, sizeof(tmapB));
+    if (encode_u8_map(&tmapA, in, w, h, in_pitch, BOXA, CH) && encode_u8_map(&tmapB, in, w, h, in_pitch, BOXB, CH))
+        return launch_mode<true, MODE>(tmapA, tmapB, in, in_pitch, w, h, t, out, out_pitch, hs, img, err, s);
+    return launch_mode<false, MODE>(tmapA, tmapB, in, in_pitch, w, h, t, out, out_pitch, hs, img, err, s);
+}
+
+}  // namespace
+
+cudaError_t launch_k1_classify_u8(const uint8_t *in, int in_pitch, uint8_t *cls, int cls_pitch, int w, int h,
+                                  IntThresholds t, uint32_t *err, cudaStream_t s)
+{
+    if (w <= 0 || h <= 0) return cudaSuccess;
+    HystScratch none = {};
+    HystImage img = {};
+    return launch_any<MODE_CLASSMAP>(in, in_pitch, w, h, t, cls, cls_pitch, none, img, err, s);
+}
+
+cudaError_t launch_k1_edges_u8(const uint8_t *in, int in_pitch, int w, int h, IntThresholds t,
+                               const HystScratch &hs, HystImage img, cudaStream_t s)
+{
+    if (w <= 0 || h <= 0) return cudaSuccess;
+    return launch_any<MODE_EDGES>(in, in_pitch, w, h, t, img.map, img.pitch, hs, img, &hs.state->error, s);
+}
+
+}  // namespace canny

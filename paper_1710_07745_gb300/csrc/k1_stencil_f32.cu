@@ -1,8 +1,8 @@
-// k1_stencil.cu -- fused Steps 1-3 + double threshold (paper Sec. 2.2.1):
-// Gaussian -> Sobel -> strength -> direction sector -> non-maximum suppression
-// -> class map (0 none, 1 weak, 2 strong). One CTA per output tile; the tile and
-// its halo are staged in shared memory and nothing but the input and the class
-// map touches HBM.
+// k1_stencil_f32.cu -- float32 variant of the fused stencil (paper Sec. 2.2.1,
+// Steps 1-3): sigma-parametrised Gaussian -> Sobel -> L2 strength -> direction
+// sector -> non-maximum suppression, then the thresholds relative to the
+// image's largest strength (a second, elementwise kernel, since the maximum is
+// a grid-wide dependency). One CTA per output tile, staged in shared memory.
 #include "canny_internal.cuh"
 
 namespace canny {
@@ -10,113 +10,6 @@ namespace canny {
 namespace {
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
-
-// ============================================================== integer path
-constexpr int TX = 64, TY = 16;            // output tile
-constexpr int IN_X = TX + 8, IN_Y = TY + 8;  // input tile: halo 2 (Gauss) + 1 (Sobel) + 1 (NMS)
-constexpr int SX = TX + 4, SY = TY + 4;      // smoothed tile
-constexpr int MX = TX + 2, MY = TY + 2;      // strength tile
-constexpr int K1_THREADS = 256;
-
-// Q15 tan(22.5 deg) for the sector test: round((sqrt(2) - 1) * 2^15).
-constexpr int TAN_Q15 = 13573;
-
-__global__ void __launch_bounds__(K1_THREADS)
-k1_classify_u8_kernel(const uint8_t *__restrict__ in, int in_pitch, uint8_t *__restrict__ cls,
-                      int cls_pitch, int w, int h, IntThresholds t)
-{
-    __shared__ uint8_t I_s[IN_Y][IN_X];
-    __shared__ int H_s[IN_Y][SX];
-    __shared__ uint8_t S_s[SY][SX];
-    __shared__ int M_s[MY][MX];
-
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int tid = threadIdx.x;
-
-    // input with replicate border: I_s[r][c] = I(clamp(x0-4+c), clamp(y0-4+r))
-    for (int i = tid; i < IN_X * IN_Y; i += K1_THREADS) {
-        int r = i / IN_X, c = i % IN_X;
-        int X = clampi(x0 - 4 + c, 0, w - 1), Y = clampi(y0 - 4 + r, 0, h - 1);
-        I_s[r][c] = in[(int64_t)Y * in_pitch + X];
-    }
-    __syncthreads();
-
-    // Step 1, horizontal binomial pass at columns X = clamp(x0-2+c)
-    for (int i = tid; i < IN_Y * SX; i += K1_THREADS) {
-        int r = i / SX, c = i % SX;
-        int X = clampi(x0 - 2 + c, 0, w - 1);
-        int base = X - (x0 - 4);
-        int a0 = I_s[r][clampi(X - 2, 0, w - 1) - (x0 - 4)];
-        int a1 = I_s[r][clampi(X - 1, 0, w - 1) - (x0 - 4)];
-        int a2 = I_s[r][base];
-        int a3 = I_s[r][clampi(X + 1, 0, w - 1) - (x0 - 4)];
-        int a4 = I_s[r][clampi(X + 2, 0, w - 1) - (x0 - 4)];
-        H_s[r][c] = a0 + 4 * a1 + 6 * a2 + 4 * a3 + a4;
-    }
-    __syncthreads();
-
-    // Step 1, vertical pass and rounding: S_s[r][c] = S(clamp(x0-2+c), clamp(y0-2+r))
-    for (int i = tid; i < SY * SX; i += K1_THREADS) {
-        int r = i / SX, c = i % SX;
-        int Y = clampi(y0 - 2 + r, 0, h - 1);
-        int acc = 0;
-        const int wts[5] = {1, 4, 6, 4, 1};
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            int Yk = clampi(Y - 2 + k, 0, h - 1);
-            acc += wts[k] * H_s[Yk - (y0 - 4)][c];
-        }
-        S_s[r][c] = (uint8_t)((acc + 128) >> 8);
-    }
-    __syncthreads();
-
-    // Step 2, Sobel strength on the tile plus a 1-pixel ring (0 outside the image)
-    for (int i = tid; i < MY * MX; i += K1_THREADS) {
-        int r = i / MX, c = i % MX;
-        int X = x0 - 1 + c, Y = y0 - 1 + r;
-        int m2 = 0;
-        if (X >= 0 && X < w && Y >= 0 && Y < h) {
-            int sr = r + 1, sc = c + 1;   // S_s index of (X, Y)
-            int gx = (S_s[sr - 1][sc + 1] + 2 * S_s[sr][sc + 1] + S_s[sr + 1][sc + 1]) -
-                     (S_s[sr - 1][sc - 1] + 2 * S_s[sr][sc - 1] + S_s[sr + 1][sc - 1]);
-            int gy = (S_s[sr + 1][sc - 1] + 2 * S_s[sr + 1][sc] + S_s[sr + 1][sc + 1]) -
-                     (S_s[sr - 1][sc - 1] + 2 * S_s[sr - 1][sc] + S_s[sr - 1][sc + 1]);
-            m2 = gx * gx + gy * gy;
-        }
-        M_s[r][c] = m2;
-    }
-    __syncthreads();
-
-    // Step 3 + thresholds on the output tile
-    for (int i = tid; i < TY * TX; i += K1_THREADS) {
-        int r = i / TX, c = i % TX;
-        int X = x0 + c, Y = y0 + r;
-        if (X >= w || Y >= h) continue;
-        int sr = r + 2, sc = c + 2;
-        int gx = (S_s[sr - 1][sc + 1] + 2 * S_s[sr][sc + 1] + S_s[sr + 1][sc + 1]) -
-                 (S_s[sr - 1][sc - 1] + 2 * S_s[sr][sc - 1] + S_s[sr + 1][sc - 1]);
-        int gy = (S_s[sr + 1][sc - 1] + 2 * S_s[sr + 1][sc] + S_s[sr + 1][sc + 1]) -
-                 (S_s[sr - 1][sc - 1] + 2 * S_s[sr - 1][sc] + S_s[sr - 1][sc + 1]);
-        int ax = abs(gx), ay = abs(gy);
-        int mr = r + 1, mc = c + 1;
-        int m = M_s[mr][mc];
-        int mn, mp;
-        if (ay * 32768 < ax * TAN_Q15) {            // H: left / right
-            mn = M_s[mr][mc - 1]; mp = M_s[mr][mc + 1];
-        } else if (ax * 32768 < ay * TAN_Q15) {     // V: up / down
-            mn = M_s[mr - 1][mc]; mp = M_s[mr + 1][mc];
-        } else if ((gx > 0 && gy > 0) || (gx < 0 && gy < 0)) {  // D: up-left / down-right
-            mn = M_s[mr - 1][mc - 1]; mp = M_s[mr + 1][mc + 1];
-        } else {                                     // A: down-left / up-right
-            mn = M_s[mr + 1][mc - 1]; mp = M_s[mr - 1][mc + 1];
-        }
-        bool keep = (m > mn) && (m >= mp);
-        uint8_t v = 0;
-        if (keep && m > t.hi2) v = 2;
-        else if (keep && m > t.lo2) v = 1;
-        cls[(int64_t)Y * cls_pitch + X] = v;
-    }
-}
 
 // ============================================================== float32 variant
 // Same tiling; every product and sum is rounded separately (no contraction), in
@@ -260,15 +153,6 @@ __global__ void k1f_classify_kernel(const float *__restrict__ mag, int mag_pitch
 }
 
 }  // namespace
-
-cudaError_t launch_k1_classify_u8(const uint8_t *in, int in_pitch, uint8_t *cls, int cls_pitch,
-                                  int w, int h, IntThresholds t, cudaStream_t s)
-{
-    if (w <= 0 || h <= 0) return cudaSuccess;
-    dim3 grid((w + TX - 1) / TX, (h + TY - 1) / TY);
-    k1_classify_u8_kernel<<<grid, K1_THREADS, 0, s>>>(in, in_pitch, cls, cls_pitch, w, h, t);
-    return cudaGetLastError();
-}
 
 static size_t k1f_smem_bytes(int ksize)
 {

@@ -88,12 +88,6 @@ extern "C" canny_status canny_run_noalloc(const uint8_t *d_in, int in_pitch, uin
 
     cudaStream_t s = (cudaStream_t)stream;
     IntThresholds t = {low * low, high * high};
-    e = launch_k1_classify_u8(d_in, in_pitch, d_out, out_pitch, w, h, t, s);
-    if (e != cudaSuccess) return status_of(e);
-    // the control block and the queue stamps must start at zero on every call
-    const uint32_t cap = (uint32_t)(64 + (uint64_t)(4 * HT - 4) * ntiles);
-    e = hyst_reset(hs, (uint32_t)ntiles, 1, cap, s);
-    if (e != cudaSuccess) return status_of(e);
     HystImage im = {};
     im.map = d_out;
     im.w = w;
@@ -102,7 +96,11 @@ extern "C" canny_status canny_run_noalloc(const uint8_t *d_in, int in_pitch, uin
     im.ntx = (w + HT - 1) / HT;
     im.nty = (h + HT - 1) / HT;
     im.tile_base = 0;
-    e = launch_hyst_local_single(hs, im, s);
+    // the control block and the queue stamps must start at zero on every call
+    const uint32_t cap = (uint32_t)(64 + (uint64_t)(4 * HT - 4) * ntiles);
+    e = hyst_reset(hs, (uint32_t)ntiles, 1, cap, s, &im);
+    if (e != cudaSuccess) return status_of(e);
+    e = launch_k1_edges_u8(d_in, in_pitch, w, h, t, hs, im, s);
     if (e != cudaSuccess) return status_of(e);
     // global passes driven from the host: one pass, read the control block, repeat
     HystState st = {};
@@ -113,5 +111,5 @@ extern "C" canny_status canny_run_noalloc(const uint8_t *d_in, int in_pitch, uin
         if (e != cudaSuccess) return status_of(e);
         if (!st.keep_going) break;
     }
-    return (st.error & 1u) ? CANNY_ENOCONVERGE : CANNY_OK;
+    return (st.error & 2u) ? CANNY_ECUDA : (st.error & 1u) ? CANNY_ENOCONVERGE : CANNY_OK;
 }

@@ -38,8 +38,11 @@ LOW, HIGH = 40, 100
 METRIC = "Canny Mpixel/s & % of HBM roofline; batched vs plain loop; p50/p99 latency"
 UNIT = "Mpixel/s"
 WORKLOAD = "canny_int_16384x16384"
-# algorithmic bytes per pixel of the fused stencil: read the image byte, write the class byte
+# algorithmic bytes per pixel of the fused kernel: read the image byte, write the edge byte
 K1_BYTES_PER_PX = 2
+# ncu DRAM traffic of the fused kernel per 16384^2 launch, valid only for the kernel
+# source it was measured on (profiles/k1_fused_16384x8192.md: capture at half size, x2)
+K1_TRAFFIC = {"sha256_prefix": "671f2c5362dadbd3", "bytes": 469_000_000}
 # whole pipeline floor: stencil 2 B/px + tile-local hysteresis read + write 2 B/px
 PIPE_BYTES_PER_PX = 4
 
@@ -51,6 +54,17 @@ def measured_peaks() -> dict:
             d = json.load(f)
         return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
     return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def k1_traffic(w: int, h: int):
+    """Recorded ncu DRAM bytes per launch, if the kernel source is unchanged since."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_1710_07745_gb300", "csrc", "k1_fused.cu")
+    with open(src, "rb") as f:
+        digest = hashlib.sha256(f.read()).hexdigest()
+    if not digest.startswith(K1_TRAFFIC["sha256_prefix"]) or (w, h) != (16384, 16384):
+        return None
+    return K1_TRAFFIC["bytes"]
 
 
 def config(extra: dict | None = None) -> dict:
@@ -246,11 +260,12 @@ def run_ours(args, rank: int, world: int) -> None:
     k1_ms = tm["stencil_ms"] / max(1, tm["runs"])
     k1_gbs = K1_BYTES_PER_PX * px / (k1_ms / 1e3) / 1e9
     pipe_gbs = PIPE_BYTES_PER_PX * px / (ms / args.steps / 1e3) / 1e9
-    stages = {"runs": tm["runs"], "stencil_ms": round(k1_ms, 4),
+    stages = {"runs": tm["runs"], "reset_ms": round(tm["reset_ms"] / max(1, tm["runs"]), 4),
+              "stencil_ms": round(k1_ms, 4),
               "local_ms": round(tm["local_ms"] / max(1, tm["runs"]), 4),
               "global_ms": round(tm["global_ms"] / max(1, tm["runs"]), 4),
               "hyst_passes": passes, "pending_tiles": int(st["pending_tiles"])}
-    dominant = max(("stencil_ms", "local_ms", "global_ms"), key=lambda k: stages[k])
+    dominant = max(("reset_ms", "stencil_ms", "local_ms", "global_ms"), key=lambda k: stages[k])
 
     e2e = None
     if not args.no_e2e:
@@ -284,10 +299,10 @@ def run_ours(args, rank: int, world: int) -> None:
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic", "config": config(),
-        "roofline": {"kernel": "k1_classify_u8 (fused Gauss/Sobel/NMS/threshold stencil)",
+        "roofline": {"kernel": "k1_fused_kernel (Gauss/Sobel/NMS/threshold + tile-local hysteresis)",
                      "bound": "hbm", "achieved": round(k1_gbs, 1), "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": round(k1_gbs / peaks["hbm_gbs"], 4),
-                     "traffic": None, "peak_source": peaks["source"],
+                     "traffic": k1_traffic(W, H), "peak_source": peaks["source"],
                      "bytes_per_launch": K1_BYTES_PER_PX * px},
         "pipeline_roofline": {"achieved": round(pipe_gbs, 1), "unit": "GB/s",
                               "bytes_per_px": PIPE_BYTES_PER_PX,

@@ -166,8 +166,9 @@ canny_status canny_magnitude_f32(canny_ctx *ctx, const canny_image *img, float *
 /* Device time per stage, summed over the runs since the last canny_read_timing. */
 typedef struct {
     int64_t runs;          /* runs timed */
-    double stencil_ms;     /* Steps 1-3 + thresholds (the fused stencil kernel) */
-    double local_ms;       /* hysteresis: per-tile fill */
+    double reset_ms;       /* clearing the hysteresis worklist state */
+    double stencil_ms;     /* Steps 1-3 + thresholds (integer path: fused with the per-tile fill) */
+    double local_ms;       /* hysteresis: per-tile fill, when it runs as its own kernel */
     double global_ms;      /* hysteresis: global passes */
     double total_ms;       /* first stage start to last stage end, summed over runs */
 } canny_timing;

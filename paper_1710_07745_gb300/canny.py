@@ -45,8 +45,8 @@ class canny_stats(ctypes.Structure):
 
 
 class canny_timing(ctypes.Structure):
-    _fields_ = [("runs", ctypes.c_int64), ("stencil_ms", ctypes.c_double), ("local_ms", ctypes.c_double),
-                ("global_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
+    _fields_ = [("runs", ctypes.c_int64), ("reset_ms", ctypes.c_double), ("stencil_ms", ctypes.c_double),
+                ("local_ms", ctypes.c_double), ("global_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

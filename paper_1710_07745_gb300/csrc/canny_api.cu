@@ -36,13 +36,15 @@ struct canny_ctx {
     cudaStream_t last_stream = nullptr;
     canny_stats last = {};
 
-    // per-stage timing: 4 events per timed run
+    // per-stage timing: EV_PER_RUN events per timed run
     int timing = 0;
     std::vector<cudaEvent_t> ev;
     int ev_runs = 0;
 };
 
 namespace {
+
+constexpr int EV_PER_RUN = 5;   // before reset, after reset, after stencil, after local fill, after global
 
 canny_status from_cuda(cudaError_t e)
 {
@@ -223,18 +225,20 @@ canny_status run_one(canny_ctx *c, const canny_image *im, cudaStream_t s, bool s
     if (st != CANNY_OK) return st;
     c->last.pixels = (int64_t)im->w * im->h;
     c->last.tiles = ntiles;
-    const int slot = (c->timing && c->ev_runs < (int)c->ev.size() / 4) ? c->ev_runs++ : -1;
-    if (slot >= 0) cudaEventRecord(c->ev[4 * slot + 0], s);
+    const int slot = (c->timing && c->ev_runs < (int)c->ev.size() / EV_PER_RUN) ? c->ev_runs++ : -1;
+    cudaEvent_t *ev = slot >= 0 ? &c->ev[EV_PER_RUN * slot] : nullptr;
+    if (ev) cudaEventRecord(ev[0], s);
     const HystImage himg = hyst_image(im, 0);
     st = from_cuda(hyst_reset(c->hs, ntiles, 1, max_passes_for(c, ntiles), s, &himg));
     if (st != CANNY_OK) return st;
+    if (ev) cudaEventRecord(ev[1], s);
     if (stencil && c->p.path == CANNY_PATH_INT) {
         // fused: Steps 1-3, thresholds and the tile-local fill in one kernel
         st = from_cuda(launch_k1_edges_u8(im->d_in, im->in_pitch, im->w, im->h, c->it, c->hs, himg, s));
         if (st != CANNY_OK) return st;
-        if (slot >= 0) {
-            cudaEventRecord(c->ev[4 * slot + 1], s);
-            cudaEventRecord(c->ev[4 * slot + 2], s);
+        if (ev) {
+            cudaEventRecord(ev[2], s);
+            cudaEventRecord(ev[3], s);
         }
     } else {
         if (stencil) {
@@ -244,13 +248,13 @@ canny_status run_one(canny_ctx *c, const canny_image *im, cudaStream_t s, bool s
                                              cudaMemcpyDeviceToDevice, s));
         }
         if (st != CANNY_OK) return st;
-        if (slot >= 0) cudaEventRecord(c->ev[4 * slot + 1], s);
+        if (ev) cudaEventRecord(ev[2], s);
         st = from_cuda(launch_hyst_local_single(c->hs, himg, s));
         if (st != CANNY_OK) return st;
-        if (slot >= 0) cudaEventRecord(c->ev[4 * slot + 2], s);
+        if (ev) cudaEventRecord(ev[3], s);
     }
     st = run_global(c, s);
-    if (slot >= 0) cudaEventRecord(c->ev[4 * slot + 3], s);
+    if (ev) cudaEventRecord(ev[4], s);
     return st;
 }
 
@@ -477,7 +481,7 @@ canny_status canny_enable_timing(canny_ctx *c, int enable)
 {
     if (!c) return CANNY_EINVAL;
     if (enable && c->ev.empty()) {
-        c->ev.resize(4 * 4096, nullptr);
+        c->ev.resize(EV_PER_RUN * 4096, nullptr);
         for (auto &e : c->ev)
             if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return CANNY_ECUDA; }
     }
@@ -491,13 +495,15 @@ canny_status canny_read_timing(canny_ctx *c, canny_timing *out)
     if (!c || !out) return CANNY_EINVAL;
     *out = canny_timing{};
     for (int r = 0; r < c->ev_runs; ++r) {
-        cudaEvent_t *e = &c->ev[4 * r];
-        if (cudaEventSynchronize(e[3]) != cudaSuccess) { c->ev_runs = 0; return CANNY_ECUDA; }
-        float a = 0, b = 0, g = 0, t = 0;
-        cudaEventElapsedTime(&a, e[0], e[1]);
-        cudaEventElapsedTime(&b, e[1], e[2]);
-        cudaEventElapsedTime(&g, e[2], e[3]);
-        cudaEventElapsedTime(&t, e[0], e[3]);
+        cudaEvent_t *e = &c->ev[EV_PER_RUN * r];
+        if (cudaEventSynchronize(e[4]) != cudaSuccess) { c->ev_runs = 0; return CANNY_ECUDA; }
+        float z = 0, a = 0, b = 0, g = 0, t = 0;
+        cudaEventElapsedTime(&z, e[0], e[1]);
+        cudaEventElapsedTime(&a, e[1], e[2]);
+        cudaEventElapsedTime(&b, e[2], e[3]);
+        cudaEventElapsedTime(&g, e[3], e[4]);
+        cudaEventElapsedTime(&t, e[0], e[4]);
+        out->reset_ms += z;
         out->stencil_ms += a;
         out->local_ms += b;
         out->global_ms += g;

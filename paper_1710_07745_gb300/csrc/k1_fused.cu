@@ -3,30 +3,30 @@
 // suppression -> double threshold -> tile-local hysteresis. The image is read
 // once and the edge map written once; the class map never leaves the SM.
 //
-// A CTA owns 960 columns x 64 rows (30 x 2 hysteresis tiles); each of its four
-// warps a 240-column strip of it.
+// A CTA is one warp. It owns 224 columns x 64 rows (7 x 2 hysteresis tiles);
+// lane L handles the 8 pixels starting at column X0 - 8 + 8L, lanes 1..28 give
+// the output, lanes 0 and 29 serve halos, lanes 30 and 31 idle along.
 //
-// Phase 1, per warp, sliding down the 64 rows (plus a 4-row halo each side):
-//   - TMA loads the strip's input rows (272 bytes each: the strip and an
-//     8-byte halo per side, rounded out to 16-byte boundaries) in chunks of 6
-//     rows into a 4-stage shared-memory ring, one mbarrier per stage;
-//   - each lane takes 8 pixels: the binomial Gaussian runs on pairs of 16-bit
-//     lanes (vertical: a cascade of four pairwise sums; horizontal: packed
-//     words with the +128 rounding folded in), neighbour lanes trade halo
-//     values by shuffles; lanes 0 and 31 only serve halos;
+// Phase 1, sliding down the 64 rows (plus a 4-row halo each side):
+//   - TMA loads the strip's input rows (256 bytes from X0 - 16) in chunks of
+//     6 rows into a 4-stage shared-memory ring, one mbarrier per stage;
+//   - the binomial Gaussian runs on pairs of 16-bit lanes (vertical: a cascade
+//     of four pairwise sums; horizontal: packed words with the +128 rounding
+//     folded in); neighbour lanes trade halo values by shuffles;
 //   - the smoothed bytes become floats 2^23 + S and Sobel and the squared
 //     strength run in packed float2 arithmetic (__ffma2_rn etc.); every value
 //     is an integer below 2^24, so the result is exact;
-//   - only ~2% of pixels exceed the low threshold. A lane with such pixels
-//     stores its row of strengths and packed gradients in a 5-row ring and
-//     queues (row, lane) one row later; after every 3 rows the warp's lanes
-//     share the queued candidates (one entry each) and run the sector test and
-//     the suppression for them alone, setting bits in the CTA's weak/strong
-//     row bitmasks.
-// Phase 2, after a CTA barrier: either the class map is written from the
-// bitmasks (canny_classify), or each warp runs the tile flood fill of the
-// hysteresis on the bitmasks and writes 255/0 edge bytes plus the tile border
-// masks and pending bitmaps that the global passes need.
+//   - every row's strengths go to a 5-row ring in shared memory. Only ~2% of
+//     pixels exceed the low threshold: their lanes also store the packed
+//     gradients and queue one entry per such pixel, one row late; after every
+//     3 rows the lanes share the queued pixels (one each) and run the sector
+//     test and the suppression for them alone, setting bits in the strip's
+//     weak/strong row bitmasks. A non-candidate neighbour is at most the low
+//     threshold, below any candidate, so its stored strength decides nothing.
+// Phase 2: either the class map is written from the bitmasks (canny_classify),
+// or the warp runs the tile flood fill of the hysteresis on them and writes
+// 255/0 edge bytes plus the tile border masks and pending bitmaps that the
+// global passes need.
 #include <cuda.h>
 #include <string.h>
 
@@ -39,23 +39,23 @@ namespace {
 using tile::FULL;
 
 constexpr int LPX = 8;                  // pixels per lane per row
-constexpr int WARPS = 4;
-constexpr int THREADS = WARPS * 32;
-constexpr int OUT_W = 30 * LPX;         // 240 output columns per warp
-constexpr int CTA_W = WARPS * OUT_W;    // 960 columns = 30 hysteresis tiles
+constexpr int THREADS = 32;             // one warp per CTA
+constexpr int OUT_W = 28 * LPX;         // 224 output columns (lanes 1..28) = 7 hysteresis tiles
 constexpr int BAND = 64;                // output rows = 2 hysteresis tiles
 constexpr int ITERS = BAND + 8;         // input rows Y0-4 .. Y0+BAND+3
 constexpr int UNROLL = 3;               // period of the 3-row windows
-constexpr int CH = 6;                   // input rows per TMA chunk
-constexpr int STAGES = 4;
-constexpr int NCH = ITERS / CH;         // 12 chunks per band
-constexpr int BOXA = 256, BOXB = 16;    // the two TMA boxes of a strip row
-constexpr uint32_t CHUNK_BYTES = (BOXA + BOXB) * CH;
-constexpr int RING = 5;                 // rows of candidate data kept per warp
-constexpr int TILES_X = CTA_W / HT, TILES_Y = BAND / HT;
-constexpr int MW = CTA_W / 32;          // bitmask words per CTA row
+constexpr int CH = UNROLL;              // input rows per TMA chunk (one chunk per unrolled group)
+constexpr int STAGES = 4;               // chunks in flight: 12 rows ahead
+constexpr int NCH = ITERS / CH;         // 24 chunks per band
+constexpr int BOX = 256;                // TMA box width: columns X0-16 .. X0+239
+constexpr uint32_t CHUNK_BYTES = BOX * CH;
+constexpr int RING = 5;                 // rows of strengths kept
+constexpr int GRING = 4;                // rows of candidate gradients kept
+constexpr int QCAP = UNROLL * 28 * LPX; // candidate pixels of one 3-row group, at most
+constexpr int TILES_X = OUT_W / HT, TILES_Y = BAND / HT;
+constexpr int MW = OUT_W / 32;          // bitmask words per strip row
 static_assert(ITERS % UNROLL == 0 && ITERS % CH == 0, "");
-static_assert((CH * BOXA) % 128 == 0 && CH * BOXB <= 128, "TMA stage buffers must stay 128-byte aligned");
+static_assert((CH * BOX) % 128 == 0, "TMA stage buffers must stay 128-byte aligned");
 
 constexpr uint32_t MAGIC = 0x4B000000u;             // float 2^23
 constexpr uint32_t BIAS = 0x00800080u;              // +128 in both 16-bit lanes
@@ -63,22 +63,16 @@ constexpr uint32_t WAIT_LIMIT = 1u << 22;           // bounded mbarrier waits
 
 enum { MODE_CLASSMAP = 0, MODE_EDGES = 1 };
 
-struct alignas(128) WarpSmem {
-    uint8_t inA[STAGES][CH * BOXA];      // TMA destinations, 128-byte aligned
-    uint8_t inB[STAGES][128];            // CH * BOXB = 96 bytes used
-    float m2[RING][256];
-    uint32_t gxy[RING][256];             // (gx + 1024) | (gy + 1024) << 16
-    uint8_t cm[RING][32];                // per lane: which of its 8 pixels exceed the low threshold
-    uint32_t queue[UNROLL * 32];         // (row << 5) | lane
+struct alignas(128) Smem {
+    uint8_t in[STAGES][CH * BOX];        // TMA destinations, 128-byte aligned
+    float m2[RING][256];                 // strengths of the last rows, by row mod RING
+    uint32_t gxy[GRING][256];            // (gx + 1024) | (gy + 1024) << 16, candidate lanes only
+    uint16_t queue[QCAP];                // ((row - Y0) << 8) | pixel
+    uint32_t cand[BAND][MW];             // class >= 1 (weak or strong), bit = column
+    uint32_t strong[BAND][MW];           // class == 2
     uint32_t qcount;
     uint32_t pad;
     unsigned long long full[STAGES];     // mbarriers of the input ring
-};
-
-struct alignas(128) Smem {
-    WarpSmem warp[WARPS];
-    uint32_t cand[BAND][MW];             // class >= 1 (weak or strong), bit = column
-    uint32_t strong[BAND][MW];           // class == 2
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -138,67 +132,45 @@ __device__ __forceinline__ float &pix(float2 (&p)[5], int k)
 }
 
 // ---------------------------------------------------------------- candidate suppression
-// Strength of pixel pp (0..255 in the warp strip) of ring row yy, or 0 if it is
-// not above the low threshold (such pixels can neither win nor suppress).
-__device__ __forceinline__ float ring_m2(const WarpSmem &ws, int pp, int yy)
+// Step 3 + thresholds for one queued candidate pixel.
+__device__ __forceinline__ void suppress_pixel(Smem &S, uint32_t entry, int Y0, float hi2)
 {
-    const int sl = ((yy % RING) + RING) % RING;
-    const uint32_t bit = (ws.cm[sl][pp >> 3] >> (pp & 7)) & 1u;
-    return bit ? ws.m2[sl][pp] : 0.f;
-}
-
-// Step 3 + thresholds for the candidate pixels of one queued (row, lane) entry.
-__device__ __forceinline__ void suppress_entry(const WarpSmem &ws, Smem &S, uint32_t entry, int wid, int Y0,
-                                               float hi2)
-{
-    const int y = (int)(entry >> 5), L = (int)(entry & 31u);
-    const int sl = y % RING;
-    uint32_t bits = ws.cm[sl][L];
-    while (bits) {
-        const int k = __ffs(bits) - 1;
-        bits &= bits - 1;
-        const int p = LPX * L + k;
-        const float m = ws.m2[sl][p];
-        const uint32_t g = ws.gxy[sl][p];
-        const int gx = (int)(g & 0xFFFFu) - 1024, gy = (int)(g >> 16) - 1024;
-        const int ax = abs(gx), ay = abs(gy);
-        float mn, mp;
-        if (ay * 32768 < ax * 13573) {                 // H: left / right
-            mn = ring_m2(ws, p - 1, y);
-            mp = ring_m2(ws, p + 1, y);
-        } else if (ax * 32768 < ay * 13573) {          // V: up / down
-            mn = ring_m2(ws, p, y - 1);
-            mp = ring_m2(ws, p, y + 1);
-        } else if (gx * gy > 0) {                      // D: up-left / down-right
-            mn = ring_m2(ws, p - 1, y - 1);
-            mp = ring_m2(ws, p + 1, y + 1);
-        } else {                                       // A: down-left / up-right
-            mn = ring_m2(ws, p - 1, y + 1);
-            mp = ring_m2(ws, p + 1, y - 1);
-        }
-        if (m > mn && m >= mp) {
-            const int col = wid * OUT_W + p - LPX, row = y - Y0;
-            atomicOr(&S.cand[row][col >> 5], 1u << (col & 31));
-            if (m > hi2) atomicOr(&S.strong[row][col >> 5], 1u << (col & 31));
-        }
+    const int y = Y0 + (int)(entry >> 8), p = (int)(entry & 255u);
+    const int sl = y % RING, su = (y + RING - 1) % RING, sd = (y + 1) % RING;
+    const float m = S.m2[sl][p];
+    const uint32_t g = S.gxy[y % GRING][p];
+    // all eight neighbour strengths at once, then pick by sector
+    const float l = S.m2[sl][p - 1], r = S.m2[sl][p + 1];
+    const float ul = S.m2[su][p - 1], uc = S.m2[su][p], ur = S.m2[su][p + 1];
+    const float dl = S.m2[sd][p - 1], dc = S.m2[sd][p], dr = S.m2[sd][p + 1];
+    const int gx = (int)(g & 0xFFFFu) - 1024, gy = (int)(g >> 16) - 1024;
+    const int ax = abs(gx), ay = abs(gy);
+    const bool hz = ay * 32768 < ax * 13573;           // H: left / right
+    const bool vt = ax * 32768 < ay * 13573;           // V: up / down
+    const bool dg = gx * gy > 0;                       // D: up-left / down-right, else A
+    const float mn = hz ? l : vt ? uc : dg ? ul : dl;  // A: down-left / up-right
+    const float mp = hz ? r : vt ? dc : dg ? dr : ur;
+    if (m > mn && m >= mp) {
+        const int col = p - LPX, row = (int)(entry >> 8);
+        atomicOr(&S.cand[row][col >> 5], 1u << (col & 31));
+        if (m > hi2) atomicOr(&S.strong[row][col >> 5], 1u << (col & 31));
     }
 }
 
 // ---------------------------------------------------------------- phase 1
 template <bool TMA>
-__device__ __forceinline__ void stencil_band(const CUtensorMap *tmapA, const CUtensorMap *tmapB,
-                                             const uint8_t *__restrict__ in,
-                                             int in_pitch, int w, int h, IntThresholds t, Smem &S,
-                                             WarpSmem &ws, int wid, int lane, int X0, int Y0,
-                                             uint32_t *err)
+__device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint8_t *__restrict__ in,
+                                             int in_pitch, int w, int h, IntThresholds t, Smem &S, int lane,
+                                             int X0, int Y0, uint32_t *err)
 {
     const int xl = X0 - LPX + LPX * lane;     // image column of the lane's first pixel
     const bool border = xl <= 0 || xl + LPX >= w;
-    const bool out_lane = lane >= 1 && lane <= 30 && xl < w;
+    const bool out_lane = lane >= 1 && lane <= 28 && xl < w;
     const int last = w - 1 - xl;               // index of the lane's last in-image pixel
     const float lo2 = (float)min(t.lo2, 1 << 24), hi2 = (float)min(t.hi2, 1 << 24);
     const bool direct_fast = !TMA && xl >= 0 && xl + LPX <= w &&
                              ((((uintptr_t)in) | (uintptr_t)in_pitch | (uintptr_t)xl) & 7) == 0;
+    const int soff = min(LPX + LPX * lane, BOX - LPX);   // lane's bytes in a staged row
 
     uint32_t rp[4] = {0, 0, 0, 0}, p1[4] = {0, 0, 0, 0}, p2[4] = {0, 0, 0, 0}, p3[4] = {0, 0, 0, 0};
     float2 Sp[3][5];      // 2^23 + S by row slot (row mod 3), pairs (x_j, x_j+4), halo (x_-1, x_8)
@@ -231,10 +203,8 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmapA, const CUt
     };
     auto issue_chunk = [&](int c) {           // lane 0 only
         const int slot = c % STAGES;
-        const int y = Y0 - 4 + c * CH;
-        mbar_expect_tx(&ws.full[slot], CHUNK_BYTES);
-        tma_load_2d(&ws.inA[slot][0], tmapA, X0 - 16, y, &ws.full[slot]);
-        tma_load_2d(&ws.inB[slot][0], tmapB, X0 + OUT_W, y, &ws.full[slot]);
+        mbar_expect_tx(&S.full[slot], CHUNK_BYTES);
+        tma_load_2d(&S.in[slot][0], tmap, X0 - 16, Y0 - 4 + c * CH, &S.full[slot]);
     };
 
     if (TMA) {
@@ -245,6 +215,13 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmapA, const CUt
         for (int u = 0; u < UNROLL; ++u) direct_load(Y0 - 4 + u, pf0[u], pf1[u]);
     }
     bool failed = false;
+    auto wait_chunk = [&](int c) {
+        if (failed) return;
+        uint32_t n = 0;
+        while (!mbar_try_wait(&S.full[c % STAGES], (uint32_t)(c / STAGES) & 1u))
+            if (++n > WAIT_LIMIT) { failed = true; break; }
+        if (failed && lane == 0) atomicOr(err, 2u);
+    };
 
     for (int g = 0; g < ITERS; g += UNROLL) {
 #pragma unroll
@@ -258,31 +235,26 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmapA, const CUt
             // ---- the lane's 8 input bytes of row clamp(yin)
             uint32_t w0, w1;
             if (TMA) {
-                const int c = i / CH, off = i % CH, slot = c % STAGES;
-                if (off == 0 && !failed) {
-                    uint32_t n = 0;
-                    while (!mbar_try_wait(&ws.full[slot], (uint32_t)(c / STAGES) & 1u))
-                        if (++n > WAIT_LIMIT) { failed = true; break; }
-                    if (failed && lane == 0) atomicOr(err, 2u);
+                const int c = g / CH, off = u, slot = c % STAGES;
+                if (off == 0) {
+                    wait_chunk(c);
+                    if (yin < 0) wait_chunk(4 / CH);   // top band: row 0 is in that chunk
                 }
                 if (yin >= h) {
                     w0 = last0;
                     w1 = last1;
                 } else {
-                    const int rr = yin < 0 ? 4 : off;        // rows above the image repeat row 0
-                    const uint8_t *rowA = &ws.inA[slot][rr * BOXA];
-                    const uint8_t *rowB = &ws.inB[slot][rr * BOXB];
+                    // rows above the image repeat row 0, which sits in chunk 1 (yin = -4..-2) or 0
+                    const uint8_t *row = yin < 0 ? &S.in[(4 / CH) % STAGES][(4 % CH) * BOX] : &S.in[slot][off * BOX];
                     if (!border) {
-                        const uint2 v = *reinterpret_cast<const uint2 *>(lane < 31 ? rowA + 8 + LPX * lane : rowB);
+                        const uint2 v = *reinterpret_cast<const uint2 *>(row + soff);
                         w0 = v.x;
                         w1 = v.y;
                     } else {
                         uint32_t b[LPX];
 #pragma unroll
-                        for (int k = 0; k < LPX; ++k) {
-                            const int o = clampi(xl + k, 0, w - 1) - (X0 - 16);   // 0 .. 271
-                            b[k] = o < BOXA ? rowA[o] : rowB[o - BOXA];
-                        }
+                        for (int k = 0; k < LPX; ++k)
+                            b[k] = row[clampi(clampi(xl + k, 0, w - 1) - (X0 - 16), 0, BOX - 1)];
                         w0 = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
                         w1 = b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24);
                     }
@@ -396,20 +368,21 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmapA, const CUt
                     if (xl + j + 4 < 0 || j + 4 > last) m[j].y = 0.f;
                 }
             }
+            // every row's strengths go to the ring (neighbours of later candidates)
+            const int rs = ((r % RING) + RING) % RING, gs = ((r % GRING) + GRING) % GRING;
+            float4 *mdst = reinterpret_cast<float4 *>(&S.m2[rs][LPX * lane]);
+            mdst[0] = make_float4(m[0].x, m[1].x, m[2].x, m[3].x);
+            mdst[1] = make_float4(m[0].y, m[1].y, m[2].y, m[3].y);
             const float rowmax = fmaxf(fmaxf(fmaxf(m[0].x, m[0].y), fmaxf(m[1].x, m[1].y)),
                                        fmaxf(fmaxf(m[2].x, m[2].y), fmaxf(m[3].x, m[3].y)));
             uint32_t cm = 0;
-            const int rs = ((r % RING) + RING) % RING;
-            if (rowmax > lo2) {
-                // candidate lane: keep the row's strengths and gradients for the suppression
+            if (rowmax > lo2 && out_lane) {
+                // candidate lane: which pixels, and their gradients for the sector test
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     cm |= (m[j].x > lo2 ? 1u : 0u) << j;
                     cm |= (m[j].y > lo2 ? 1u : 0u) << (j + 4);
                 }
-                float4 *dst = reinterpret_cast<float4 *>(&ws.m2[rs][LPX * lane]);
-                dst[0] = make_float4(m[0].x, m[1].x, m[2].x, m[3].x);
-                dst[1] = make_float4(m[0].y, m[1].y, m[2].y, m[3].y);
                 uint32_t gg[LPX];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
@@ -417,67 +390,66 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmapA, const CUt
                     gg[j] = perm(__float_as_uint(gx[j].x + 8389632.0f), __float_as_uint(gy[j].x + 8389632.0f), 0x5410u);
                     gg[j + 4] = perm(__float_as_uint(gx[j].y + 8389632.0f), __float_as_uint(gy[j].y + 8389632.0f), 0x5410u);
                 }
-                uint4 *gdst = reinterpret_cast<uint4 *>(&ws.gxy[rs][LPX * lane]);
+                uint4 *gdst = reinterpret_cast<uint4 *>(&S.gxy[gs][LPX * lane]);
                 gdst[0] = make_uint4(gg[0], gg[1], gg[2], gg[3]);
                 gdst[1] = make_uint4(gg[4], gg[5], gg[6], gg[7]);
             }
-            ws.cm[rs][lane] = (uint8_t)cm;
             // queue the previous row's candidates now that its lower neighbour row exists
-            if (cm_prev && out_lane && r_prev >= Y0 && r_prev < Y0 + BAND) {
-                const uint32_t idx = atomicAdd(&ws.qcount, 1u);
-                ws.queue[idx] = ((uint32_t)r_prev << 5) | (uint32_t)lane;
+            if (cm_prev && r_prev >= Y0 && r_prev < Y0 + BAND) {
+                uint32_t idx = atomicAdd(&S.qcount, (uint32_t)__popc(cm_prev));
+                uint32_t bits = cm_prev;
+                while (bits) {
+                    const int k = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    S.queue[idx++] = (uint16_t)(((uint32_t)(r_prev - Y0) << 8) | (uint32_t)(LPX * lane + k));
+                }
             }
             cm_prev = cm;
             r_prev = r;
         }
-        // ---- Step 3 + thresholds for the queued candidates (their rows +-1 are in the ring)
+        // ---- Step 3 + thresholds for the queued pixels (their rows +-1 are in the ring)
         __syncwarp();
-        const uint32_t n = ws.qcount;
-        for (uint32_t j = lane; j < n; j += 32) suppress_entry(ws, S, ws.queue[j], wid, Y0, hi2);
+        const uint32_t n = S.qcount;
+        for (uint32_t j = lane; j < n; j += 32) suppress_pixel(S, S.queue[j], Y0, hi2);
         __syncwarp();
-        if (lane == 0) ws.qcount = 0;
+        if (lane == 0) S.qcount = 0;
         __syncwarp();
     }
-    // the last Sobel row (Y0 + BAND) is below the band: nothing left to queue
 }
 
 // ---------------------------------------------------------------- kernel
 template <bool TMA, int MODE>
-__global__ void __launch_bounds__(THREADS, 2)
-k1_fused_kernel(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUtensorMap tmapB,
-                const uint8_t *__restrict__ in, int in_pitch,
+__global__ void __launch_bounds__(THREADS, 12)
+k1_fused_kernel(const __grid_constant__ CUtensorMap tmap, const uint8_t *__restrict__ in, int in_pitch,
                 int w, int h, IntThresholds t, uint8_t *__restrict__ out, int out_pitch, HystScratch hs,
                 HystImage img, uint32_t *err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>(smem_raw);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    WarpSmem &ws = S.warp[wid];
-    const int X0c = blockIdx.x * CTA_W, Y0 = blockIdx.y * BAND;
-    const int X0 = X0c + wid * OUT_W;
+    const int lane = threadIdx.x;
+    const int X0 = blockIdx.x * OUT_W, Y0 = blockIdx.y * BAND;
 
-    for (int k = threadIdx.x; k < BAND * MW; k += THREADS) {
+    for (int k = lane; k < BAND * MW; k += THREADS) {
         (&S.cand[0][0])[k] = 0u;
         (&S.strong[0][0])[k] = 0u;
     }
-    for (int k = lane; k < RING * 32; k += 32) (&ws.cm[0][0])[k] = 0;
     if (lane == 0) {
-        ws.qcount = 0;
+        S.qcount = 0;
         if (TMA) {
-            for (int sidx = 0; sidx < STAGES; ++sidx) mbar_init(&ws.full[sidx], 1);
+            for (int sidx = 0; sidx < STAGES; ++sidx) mbar_init(&S.full[sidx], 1);
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
     }
-    __syncthreads();
+    __syncwarp();
 
-    if (X0 < w) stencil_band<TMA>(&tmapA, &tmapB, in, in_pitch, w, h, t, S, ws, wid, lane, X0, Y0, err);
-    __syncthreads();
+    stencil_band<TMA>(&tmap, in, in_pitch, w, h, t, S, lane, X0, Y0, err);
+    __syncwarp();
 
     if (MODE == MODE_CLASSMAP) {
         // class byte = weak bit + strong bit
-        for (int k = threadIdx.x; k < BAND * MW; k += THREADS) {
+        for (int k = lane; k < BAND * MW; k += THREADS) {
             const int row = k / MW, wj = k % MW;
-            const int y = Y0 + row, x = X0c + 32 * wj;
+            const int y = Y0 + row, x = X0 + 32 * wj;
             if (y >= h || x >= w) continue;
             const uint32_t c = S.cand[row][wj], sgl = S.strong[row][wj];
             uint32_t wd[8];
@@ -492,8 +464,8 @@ k1_fused_kernel(const __grid_constant__ CUtensorMap tmapA, const __grid_constant
             }
         }
     } else {
-        // Step 4, tile-local: flood fill each of the CTA's 30 x 2 tiles from its bitmasks
-        for (int tl = wid; tl < TILES_X * TILES_Y; tl += WARPS) {
+        // Step 4, tile-local: flood fill each of the strip's 7 x 2 tiles from its bitmasks
+        for (int tl = 0; tl < TILES_X * TILES_Y; ++tl) {
             const int txl = tl % TILES_X, tyl = tl / TILES_X;
             const int tx = blockIdx.x * TILES_X + txl, ty = blockIdx.y * TILES_Y + tyl;
             if (tx >= img.ntx || ty >= img.nty) continue;         // warp-uniform
@@ -507,7 +479,7 @@ k1_fused_kernel(const __grid_constant__ CUtensorMap tmapA, const __grid_constant
 }
 
 template <bool TMA, int MODE>
-cudaError_t launch_mode(const CUtensorMap &tmapA, const CUtensorMap &tmapB, const uint8_t *in, int in_pitch, int w, int h, IntThresholds t,
+cudaError_t launch_mode(const CUtensorMap &tmap, const uint8_t *in, int in_pitch, int w, int h, IntThresholds t,
                         uint8_t *out, int out_pitch, const HystScratch &hs, const HystImage &img, uint32_t *err,
                         cudaStream_t s)
 {
@@ -518,9 +490,9 @@ cudaError_t launch_mode(const CUtensorMap &tmapA, const CUtensorMap &tmapB, cons
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    dim3 grid((w + CTA_W - 1) / CTA_W, (h + BAND - 1) / BAND);
-    k1_fused_kernel<TMA, MODE><<<grid, THREADS, sizeof(Smem), s>>>(tmapA, tmapB, in, in_pitch, w, h, t, out,
-                                                                    out_pitch, hs, img, err);
+    dim3 grid((w + OUT_W - 1) / OUT_W, (h + BAND - 1) / BAND);
+    k1_fused_kernel<TMA, MODE><<<grid, THREADS, sizeof(Smem), s>>>(tmap, in, in_pitch, w, h, t, out, out_pitch,
+                                                                    hs, img, err);
     return cudaGetLastError();
 }
 
@@ -528,12 +500,11 @@ template <int MODE>
 cudaError_t launch_any(const uint8_t *in, int in_pitch, int w, int h, IntThresholds t, uint8_t *out,
                        int out_pitch, const HystScratch &hs, const HystImage &img, uint32_t *err, cudaStream_t s)
 {
-    CUtensorMap tmapA, tmapB;
-    memset(&tmapA, 0, sizeof(tmapA));
-    memset(&tmapB, 0, sizeof(tmapB));
-    if (encode_u8_map(&tmapA, in, w, h, in_pitch, BOXA, CH) && encode_u8_map(&tmapB, in, w, h, in_pitch, BOXB, CH))
-        return launch_mode<true, MODE>(tmapA, tmapB, in, in_pitch, w, h, t, out, out_pitch, hs, img, err, s);
-    return launch_mode<false, MODE>(tmapA, tmapB, in, in_pitch, w, h, t, out, out_pitch, hs, img, err, s);
+    CUtensorMap tmap;
+    memset(&tmap, 0, sizeof(tmap));
+    if (encode_u8_map(&tmap, in, w, h, in_pitch, BOX, CH))
+        return launch_mode<true, MODE>(tmap, in, in_pitch, w, h, t, out, out_pitch, hs, img, err, s);
+    return launch_mode<false, MODE>(tmap, in, in_pitch, w, h, t, out, out_pitch, hs, img, err, s);
 }
 
 }  // namespace

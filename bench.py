@@ -205,6 +205,73 @@ def run_reference(args, rank: int, world: int) -> None:
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ batched vs per-image loop
+BATCH_N, BATCH_LO, BATCH_HI, BATCH_SEED = 1024, 64, 2048, 4000
+
+
+def measure_batched(steps: int) -> dict:
+    """1024 images, sides log-uniform in [64, 2048]: one canny_run_batch call (a
+    persistent graph-captured launch over all images' units) against a loop of
+    canny_run_pitched calls on the same stream, inputs resident; outputs compared."""
+    import concurrent.futures as cf
+    import ctypes
+
+    import torch
+
+    from paper_1710_07745_gb300 import canny, synth
+
+    ws, hs = synth.batch_sizes(BATCH_N, BATCH_LO, BATCH_HI, BATCH_SEED)
+    with cf.ThreadPoolExecutor(max_workers=min(32, os.cpu_count() or 4)) as ex:
+        imgs = list(ex.map(lambda i: synth.batch_image(i, int(ws[i]), int(hs[i]), BATCH_SEED), range(BATCH_N)))
+    total = int(sum(int(w) * int(h) for w, h in zip(ws, hs)))
+    ins = [torch.from_numpy(im).cuda() for im in imgs]
+    outs_b = [torch.empty_like(x) for x in ins]
+    outs_l = [torch.empty_like(x) for x in ins]
+    lib = canny.load()
+    sp = torch.cuda.current_stream().cuda_stream
+    ctx = canny.Canny(total, 1, low=LOW, high=HIGH)
+    arr_b = (canny.canny_image * BATCH_N)(*[canny.image_of(a, b) for a, b in zip(ins, outs_b)])
+    arr_l = [canny.image_of(a, b) for a, b in zip(ins, outs_l)]
+    tune = canny.canny_autotune_batch(ctx.ctx, list(arr_b), sp,
+                                      os.path.join(os.path.expanduser("~"), ".cache", "canny_gb300_tune.jsonl")
+                                      if os.access(os.path.expanduser("~"), os.W_OK) else None).as_dict()
+    loop_ctx = canny.Canny(BATCH_HI, BATCH_HI, low=LOW, high=HIGH)
+    canny.canny_set_tuning(loop_ctx.ctx, tune["band"], tune["ctas_per_sm"])
+
+    def run_batch():
+        rc = lib.canny_run_batch(ctx.ctx, BATCH_N, arr_b, sp)
+        if rc:
+            raise canny.CannyError(rc, "canny_run_batch")
+
+    def run_loop():
+        for im in arr_l:
+            rc = lib.canny_run_pitched(loop_ctx.ctx, ctypes.byref(im), sp)
+            if rc:
+                raise canny.CannyError(rc, "canny_run_pitched")
+
+    res = {}
+    for name, fn in (("batch", run_batch), ("loop", run_loop)):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        res[name] = e0.elapsed_time(e1) / steps
+    same = all(torch.equal(a, b) for a, b in zip(outs_b, outs_l))
+    ctx.close()
+    loop_ctx.close()
+    return {"images": BATCH_N, "sides": [BATCH_LO, BATCH_HI], "pixels": total,
+            "batch_ms": round(res["batch"], 4), "loop_ms": round(res["loop"], 4),
+            "batch_mpx_s": round(total / res["batch"] / 1e3, 1), "loop_mpx_s": round(total / res["loop"] / 1e3, 1),
+            "speedup": round(res["loop"] / res["batch"], 2), "outputs_identical": bool(same),
+            "tuning": {"band": tune["band"], "ctas_per_sm": tune["ctas_per_sm"]}}
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, rank: int, world: int) -> None:
     import torch
@@ -285,6 +352,7 @@ def run_ours(args, rank: int, world: int) -> None:
         e2e = {"value": round(world * e2e_steps * px / e2e_s / 1e6, 1), "unit": UNIT,
                "h2d_bytes_per_step": px, "d2h_bytes_per_step": px, "steps": e2e_steps}
 
+    batched = None if args.no_batch else measure_batched(max(3, min(args.steps, 10)))
     if rank != 0:
         ctx.close()
         return
@@ -308,6 +376,7 @@ def run_ours(args, rank: int, world: int) -> None:
                               "bytes_per_px": PIPE_BYTES_PER_PX,
                               "frac": round(pipe_gbs / peaks["hbm_gbs"], 4)},
         "stages": stages, "dominant_stage": dominant,
+        "batched": batched,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(args.steps * (3 + passes)),
@@ -326,6 +395,7 @@ def main():
     ap.add_argument("--size", default=None, help="WxH instead of 16384x16384 (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-loop leg")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -183,6 +183,33 @@ canny_status canny_enable_timing(canny_ctx *ctx, int enable);
 /* Synchronise, sum the stage times of the runs timed since the last read into *out, reset. */
 canny_status canny_read_timing(canny_ctx *ctx, canny_timing *out);
 
+/*
+ * Launch configuration of the fused integer kernel: rows per unit of work
+ * (band: 64, 160 or 256; taller bands cut halo work, shorter ones balance small
+ * images better) and persistent CTAs per SM in batches.
+ */
+typedef struct {
+    int band;
+    int ctas_per_sm;
+    double ms;        /* canny_autotune_batch: measured time of one batch run */
+    int from_cache;   /* canny_autotune_batch: 1 if read from the cache file */
+    int reserved;
+} canny_tuning;
+
+/* Apply a configuration; CANNY_EINVAL for an unsupported band or CTA count. */
+canny_status canny_set_tuning(canny_ctx *ctx, const canny_tuning *t);
+canny_status canny_get_tuning(const canny_ctx *ctx, canny_tuning *out);
+
+/*
+ * Pick the configuration for batches like `imgs` (integer path): look up the
+ * size class (device, image count and mean area in octaves) in cache_path
+ * (JSON lines; NULL for none); if absent, time every candidate on this batch
+ * (each runs the batch three times; outputs are overwritten with the same
+ * edge maps), append the winner to cache_path, and apply it. Synchronous.
+ */
+canny_status canny_autotune_batch(canny_ctx *ctx, int n, const canny_image *imgs, void *stream,
+                                  const char *cache_path, canny_tuning *out);
+
 /* Copy the counters of the last run into *out. Synchronises the context's last stream. */
 canny_status canny_get_stats(canny_ctx *ctx, canny_stats *out);
 

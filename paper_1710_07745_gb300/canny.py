@@ -52,6 +52,14 @@ class canny_timing(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class canny_tuning(ctypes.Structure):
+    _fields_ = [("band", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("ms", ctypes.c_double),
+                ("from_cache", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -73,6 +81,10 @@ SIGNATURES = {
                             ctypes.c_int),
     "canny_get_stats": ([_P, ctypes.POINTER(canny_stats)], ctypes.c_int),
     "canny_enable_timing": ([_P, ctypes.c_int], ctypes.c_int),
+    "canny_set_tuning": ([_P, ctypes.POINTER(canny_tuning)], ctypes.c_int),
+    "canny_get_tuning": ([_P, ctypes.POINTER(canny_tuning)], ctypes.c_int),
+    "canny_autotune_batch": ([_P, ctypes.c_int, ctypes.POINTER(canny_image), _P, ctypes.c_char_p,
+                              ctypes.POINTER(canny_tuning)], ctypes.c_int),
     "canny_read_timing": ([_P, ctypes.POINTER(canny_timing)], ctypes.c_int),
     "canny_run_noalloc": ([_P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                            ctypes.c_int, _P], ctypes.c_int),
@@ -183,6 +195,27 @@ def canny_run_noalloc(d_in: int, in_pitch: int, d_out: int, out_pitch: int, w: i
            "canny_run_noalloc")
 
 
+def canny_set_tuning(ctx: int, band: int, ctas_per_sm: int) -> None:
+    t = canny_tuning(band, ctas_per_sm, 0.0, 0, 0)
+    _check(load().canny_set_tuning(ctx, ctypes.byref(t)), "canny_set_tuning")
+
+
+def canny_get_tuning(ctx: int) -> canny_tuning:
+    t = canny_tuning()
+    _check(load().canny_get_tuning(ctx, ctypes.byref(t)), "canny_get_tuning")
+    return t
+
+
+def canny_autotune_batch(ctx: int, imgs: Sequence[canny_image], stream: int = 0,
+                         cache_path: str | None = None) -> canny_tuning:
+    arr = (canny_image * len(imgs))(*imgs)
+    t = canny_tuning()
+    cp = cache_path.encode() if cache_path else None
+    _check(load().canny_autotune_batch(ctx, len(imgs), arr, stream, cp, ctypes.byref(t)),
+           "canny_autotune_batch")
+    return t
+
+
 # ------------------------------------------------------------------ torch marshalling
 def _stream_ptr(stream) -> int:
     if stream is None:
@@ -254,6 +287,13 @@ class Canny:
         img = canny_image(t_in.data_ptr(), 0, t_in.shape[1], t_in.shape[0], t_in.stride(0), 0)
         canny_magnitude_f32(self.ctx, img, t_mag.data_ptr(), t_mag.stride(0), t_max.data_ptr(),
                             _stream_ptr(stream))
+
+    def autotune_batch(self, pairs, stream=None, cache_path: str | None = None) -> dict:
+        return canny_autotune_batch(self.ctx, [image_of(a, b) for a, b in pairs], _stream_ptr(stream),
+                                    cache_path).as_dict()
+
+    def set_tuning(self, band: int, ctas_per_sm: int) -> None:
+        canny_set_tuning(self.ctx, band, ctas_per_sm)
 
     def stats(self) -> dict:
         return canny_get_stats(self.ctx).as_dict()

@@ -2,10 +2,13 @@
 // checks, context scratch, and the launch sequence of the pipeline
 //   stencil (Steps 1-3 + thresholds) -> local fill -> global passes (Step 4).
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
 #include <new>
+#include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "canny_internal.cuh"
@@ -40,6 +43,23 @@ struct canny_ctx {
     int timing = 0;
     std::vector<cudaEvent_t> ev;
     int ev_runs = 0;
+
+    // launch configuration of the fused kernel (canny_set_tuning / canny_autotune_batch)
+    int band = 64;                     // rows per unit of work
+    int ctas_per_sm = 12;              // persistent CTAs per SM in a batch
+
+    // integer-path batches: one graph per staging slot, descriptors uploaded from pinned memory
+    struct Slot {
+        unsigned char *h_blob = nullptr;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaEvent_t done = nullptr;
+        bool valid = false;            // graph matches the current scratch and configuration
+    } slots[2];
+    int next_slot = 0;
+    unsigned char *d_blob = nullptr;   // BatchHeader + BatchImage[cap] + CUtensorMap[cap]
+    uint32_t blob_cap = 0;
+    std::unordered_map<std::string, CUtensorMap> tmaps;   // encoded input maps, by (pointer, size, pitch)
 };
 
 namespace {
@@ -78,8 +98,20 @@ uint32_t tiles_of(int w, int h)
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+void drop_batch_graphs(canny_ctx *c)
+{
+    for (auto &sl : c->slots) {
+        if (sl.exec) cudaGraphExecDestroy(sl.exec);
+        if (sl.graph) cudaGraphDestroy(sl.graph);
+        sl.exec = nullptr;
+        sl.graph = nullptr;
+        sl.valid = false;
+    }
+}
+
 void free_hyst(canny_ctx *c)
 {
+    drop_batch_graphs(c);
     if (c->exec) cudaGraphExecDestroy(c->exec);
     if (c->graph) cudaGraphDestroy(c->graph);
     c->exec = nullptr;
@@ -183,7 +215,7 @@ canny_status run_stencil(canny_ctx *c, const canny_image *im, cudaStream_t s)
 {
     if (c->p.path == CANNY_PATH_INT)
         return from_cuda(launch_k1_classify_u8(im->d_in, im->in_pitch, im->d_out, im->out_pitch,
-                                               im->w, im->h, c->it, &c->hs.state->error, s));
+                                               im->w, im->h, c->it, &c->hs.state->error, s, c->band));
     cudaError_t e = cudaMemsetAsync(c->d_max, 0, sizeof(float), s);
     if (e == cudaSuccess)
         e = launch_k1f_magnitude(im->d_in, im->in_pitch, c->mag, im->w, im->w, im->h, c->fp, true,
@@ -234,7 +266,7 @@ canny_status run_one(canny_ctx *c, const canny_image *im, cudaStream_t s, bool s
     if (ev) cudaEventRecord(ev[1], s);
     if (stencil && c->p.path == CANNY_PATH_INT) {
         // fused: Steps 1-3, thresholds and the tile-local fill in one kernel
-        st = from_cuda(launch_k1_edges_u8(im->d_in, im->in_pitch, im->w, im->h, c->it, c->hs, himg, s));
+        st = from_cuda(launch_k1_edges_u8(im->d_in, im->in_pitch, im->w, im->h, c->it, c->hs, himg, s, c->band));
         if (st != CANNY_OK) return st;
         if (ev) {
             cudaEventRecord(ev[2], s);
@@ -256,6 +288,177 @@ canny_status run_one(canny_ctx *c, const canny_image *im, cudaStream_t s, bool s
     st = run_global(c, s);
     if (ev) cudaEventRecord(ev[4], s);
     return st;
+}
+
+// ---------------------------------------------------------------- integer-path batches
+// Blob layout, identical on host (pinned staging) and device: header, image
+// descriptors, input tensor maps; the host copy also carries the HystImage
+// array that is uploaded to the hysteresis scratch.
+struct BlobLayout {
+    size_t imgs, tmaps, himgs, dev_bytes, host_bytes;
+};
+
+BlobLayout blob_layout(uint32_t cap)
+{
+    BlobLayout L;
+    L.imgs = 128;
+    L.tmaps = align_up(L.imgs + sizeof(BatchImage) * cap, 128);
+    L.himgs = align_up(L.tmaps + sizeof(CUtensorMap) * cap, 128);
+    L.dev_bytes = L.himgs;
+    L.host_bytes = L.himgs + sizeof(HystImage) * cap;
+    return L;
+}
+
+canny_status ensure_blob(canny_ctx *c, uint32_t cap)
+{
+    if (c->d_blob && c->blob_cap >= cap) return CANNY_OK;
+    cudaDeviceSynchronize();
+    drop_batch_graphs(c);
+    if (cap < 64) cap = 64;
+    if (cap < c->blob_cap * 2) cap = c->blob_cap * 2;
+    if (c->d_blob) cudaFree(c->d_blob);
+    c->d_blob = nullptr;
+    for (auto &sl : c->slots) {
+        if (sl.h_blob) cudaFreeHost(sl.h_blob);
+        sl.h_blob = nullptr;
+    }
+    c->blob_cap = 0;
+    const BlobLayout L = blob_layout(cap);
+    if (cudaMalloc((void **)&c->d_blob, L.dev_bytes) != cudaSuccess) { cudaGetLastError(); return CANNY_ENOMEM; }
+    for (auto &sl : c->slots) {
+        if (cudaHostAlloc((void **)&sl.h_blob, L.host_bytes, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return CANNY_ENOMEM;
+        }
+        if (!sl.done && cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) return CANNY_ECUDA;
+    }
+    c->blob_cap = cap;
+    return CANNY_OK;
+}
+
+int sm_count()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    }
+    return n;
+}
+
+// The batch graph: upload descriptors -> clear stamps -> reset -> fused kernel
+// (persistent, pops units) -> while (work) global pass.
+canny_status build_batch_graph(canny_ctx *c, canny_ctx::Slot &sl)
+{
+    if (sl.exec) cudaGraphExecDestroy(sl.exec);
+    if (sl.graph) cudaGraphDestroy(sl.graph);
+    sl.exec = nullptr;
+    sl.graph = nullptr;
+    sl.valid = false;
+    const BlobLayout L = blob_layout(c->blob_cap);
+    BatchHeader *hdr = (BatchHeader *)c->d_blob;
+    const BatchImage *imgs = (const BatchImage *)(c->d_blob + L.imgs);
+    const CUtensorMap *tmaps = (const CUtensorMap *)(c->d_blob + L.tmaps);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return from_cuda(e);
+    cudaGraphNode_t up1, up2, clr, init, k1, loop;
+    e = cudaGraphAddMemcpyNode1D(&up1, g, nullptr, 0, c->d_blob, sl.h_blob, L.dev_bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaGraphAddMemcpyNode1D(&up2, g, nullptr, 0, c->hs.imgs, sl.h_blob + L.himgs,
+                                     sizeof(HystImage) * c->blob_cap, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        cudaMemsetParams mp = {};
+        mp.dst = c->hs.stamp;
+        mp.value = 0;
+        mp.elementSize = 4;
+        mp.width = c->hs.max_tiles;
+        mp.height = 1;
+        e = cudaGraphAddMemsetNode(&clr, g, nullptr, 0, &mp);
+    }
+    cudaGraphNode_t d_init[2] = {up1, clr};
+    if (e == cudaSuccess) e = hyst_add_init_from_header(g, d_init, 2, c->hs, hdr, &init);
+    cudaGraphNode_t d_k1[2] = {up2, init};
+    if (e == cudaSuccess)
+        e = k1_add_batch_node(g, d_k1, 2, c->band, imgs, tmaps, hdr, c->it, c->hs, sm_count() * c->ctas_per_sm, &k1);
+    if (e == cudaSuccess) e = hyst_add_loop(g, &k1, 1, c->hs, &loop);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&sl.exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        sl.exec = nullptr;
+        return CANNY_ECUDA;
+    }
+    sl.graph = g;
+    sl.valid = true;
+    return CANNY_OK;
+}
+
+// Tensor map of an input image, encoded once per (pointer, size, pitch).
+bool cached_map(canny_ctx *c, const canny_image *im, CUtensorMap *out)
+{
+    char key[96];
+    snprintf(key, sizeof(key), "%p:%d:%d:%d", (const void *)im->d_in, im->w, im->h, im->in_pitch);
+    auto it = c->tmaps.find(key);
+    if (it != c->tmaps.end()) {
+        *out = it->second;
+        return true;
+    }
+    if (!encode_k1_map(out, im->d_in, im->w, im->h, im->in_pitch)) return false;
+    if (c->tmaps.size() > 65536) c->tmaps.clear();
+    c->tmaps.emplace(key, *out);
+    return true;
+}
+
+canny_status run_batch_int(canny_ctx *c, int n, const canny_image *imgs, uint32_t nimg, uint32_t ntiles,
+                           cudaStream_t s)
+{
+    canny_status st = ensure_blob(c, nimg);
+    if (st != CANNY_OK) return st;
+    // the graph uploads blob_cap image descriptors into the hysteresis scratch
+    st = ensure_hyst(c, ntiles, c->blob_cap);
+    if (st != CANNY_OK) return st;
+    canny_ctx::Slot &sl = c->slots[c->next_slot];
+    c->next_slot ^= 1;
+    // the slot's staging buffer may still feed a batch launched two calls ago
+    if (cudaEventSynchronize(sl.done) != cudaSuccess) return CANNY_ECUDA;
+    if (!sl.valid) {
+        st = build_batch_graph(c, sl);
+        if (st != CANNY_OK) return st;
+    }
+    const BlobLayout L = blob_layout(c->blob_cap);
+    BatchHeader *hdr = (BatchHeader *)sl.h_blob;
+    BatchImage *bi = (BatchImage *)(sl.h_blob + L.imgs);
+    CUtensorMap *tm = (CUtensorMap *)(sl.h_blob + L.tmaps);
+    HystImage *hi = (HystImage *)(sl.h_blob + L.himgs);
+    uint32_t k = 0, tile_base = 0, unit_base = 0;
+    for (int i = 0; i < n; ++i) {
+        const canny_image *im = &imgs[i];
+        if (im->w == 0 || im->h == 0) continue;
+        hi[k] = hyst_image(im, tile_base);
+        BatchImage b = {};
+        b.img = hi[k];
+        b.in = im->d_in;
+        b.in_pitch = im->in_pitch;
+        b.unit_base = unit_base;
+        b.nsx = (im->w + k1_strip_width() - 1) / k1_strip_width();
+        b.tma = cached_map(c, im, &tm[k]) ? 1 : 0;
+        bi[k] = b;
+        tile_base += tiles_of(im->w, im->h);
+        unit_base += (uint32_t)k1_units(im->w, im->h, c->band);
+        ++k;
+    }
+    BatchHeader hh = {};
+    hh.nimg = nimg;
+    hh.total_units = unit_base;
+    hh.next_unit = 0;
+    hh.ntiles = ntiles;
+    hh.max_passes = max_passes_for(c, ntiles);
+    *hdr = hh;
+    cudaError_t e = cudaGraphLaunch(sl.exec, s);
+    if (e == cudaSuccess) e = cudaEventRecord(sl.done, s);
+    return from_cuda(e);
 }
 
 }  // namespace
@@ -335,6 +538,11 @@ void canny_destroy(canny_ctx *c)
     if (c->staging_free) cudaEventDestroy(c->staging_free);
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
+    for (auto &sl : c->slots) {
+        if (sl.h_blob) cudaFreeHost(sl.h_blob);
+        if (sl.done) cudaEventDestroy(sl.done);
+    }
+    if (c->d_blob) cudaFree(c->d_blob);
     delete c;
 }
 
@@ -371,6 +579,7 @@ canny_status canny_run_batch(canny_ctx *c, int n, const canny_image *imgs, void 
     c->last.tiles = ntiles;
     c->last_stream = s;
     if (nimg == 0) return CANNY_OK;
+    if (c->p.path == CANNY_PATH_INT) return run_batch_int(c, n, imgs, nimg, ntiles, s);
     canny_status st = ensure_hyst(c, ntiles, nimg);
     if (st != CANNY_OK) return st;
     if (c->h_imgs_cap < nimg) {
@@ -399,22 +608,13 @@ canny_status canny_run_batch(canny_ctx *c, int n, const canny_image *imgs, void 
     if (e != cudaSuccess) return from_cuda(e);
     st = from_cuda(hyst_reset(c->hs, ntiles, nimg, max_passes_for(c, ntiles), s));
     if (st != CANNY_OK) return st;
-    if (c->p.path == CANNY_PATH_INT) {
-        for (uint32_t k = 0, i = 0; i < (uint32_t)n; ++i) {
-            if (imgs[i].w == 0 || imgs[i].h == 0) continue;
-            st = from_cuda(launch_k1_edges_u8(imgs[i].d_in, imgs[i].in_pitch, imgs[i].w, imgs[i].h, c->it, c->hs,
-                                              c->h_imgs[k++], s));
-            if (st != CANNY_OK) return st;
-        }
-    } else {
-        for (int i = 0; i < n; ++i) {
-            if (imgs[i].w == 0 || imgs[i].h == 0) continue;
-            st = run_stencil(c, &imgs[i], s);
-            if (st != CANNY_OK) return st;
-        }
-        st = from_cuda(launch_hyst_local_batch(c->hs, ntiles, nimg, s));
+    for (int i = 0; i < n; ++i) {
+        if (imgs[i].w == 0 || imgs[i].h == 0) continue;
+        st = run_stencil(c, &imgs[i], s);
         if (st != CANNY_OK) return st;
     }
+    st = from_cuda(launch_hyst_local_batch(c->hs, ntiles, nimg, s));
+    if (st != CANNY_OK) return st;
     return run_global(c, s);
 }
 
@@ -511,6 +711,116 @@ canny_status canny_read_timing(canny_ctx *c, canny_timing *out)
         out->runs += 1;
     }
     c->ev_runs = 0;
+    return CANNY_OK;
+}
+
+canny_status canny_set_tuning(canny_ctx *c, const canny_tuning *t)
+{
+    if (!c || !t) return CANNY_EINVAL;
+    if (!k1_band_supported(t->band) || t->ctas_per_sm < 1 || t->ctas_per_sm > 32) return CANNY_EINVAL;
+    if (t->band != c->band || t->ctas_per_sm != c->ctas_per_sm) {
+        cudaDeviceSynchronize();
+        drop_batch_graphs(c);
+        c->band = t->band;
+        c->ctas_per_sm = t->ctas_per_sm;
+    }
+    return CANNY_OK;
+}
+
+canny_status canny_get_tuning(const canny_ctx *c, canny_tuning *out)
+{
+    if (!c || !out) return CANNY_EINVAL;
+    *out = canny_tuning{};
+    out->band = c->band;
+    out->ctas_per_sm = c->ctas_per_sm;
+    return CANNY_OK;
+}
+
+canny_status canny_autotune_batch(canny_ctx *c, int n, const canny_image *imgs, void *stream,
+                                  const char *cache_path, canny_tuning *out)
+{
+    if (!c || n < 0 || (n > 0 && !imgs)) return CANNY_EINVAL;
+    if (c->p.path != CANNY_PATH_INT) return CANNY_EUNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    // size class of the batch: image count and mean image area, in octaves
+    int64_t px = 0;
+    int nimg = 0;
+    for (int i = 0; i < n; ++i) {
+        if (imgs[i].w > 0 && imgs[i].h > 0) { px += (int64_t)imgs[i].w * imgs[i].h; ++nimg; }
+    }
+    if (nimg == 0) return CANNY_EINVAL;
+    int dev = 0;
+    cudaDeviceProp prop;
+    cudaGetDevice(&dev);
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return CANNY_ECUDA;
+    char key[256];
+    snprintf(key, sizeof(key), "%s|int|n%d|a%d", prop.name, (int)log2((double)nimg), (int)log2((double)px / nimg));
+    canny_tuning best = {};
+    if (cache_path && *cache_path) {
+        FILE *f = fopen(cache_path, "r");
+        if (f) {
+            char line[512];
+            while (fgets(line, sizeof(line), f)) {
+                char k[256];
+                int b = 0, q = 0;
+                double ms = 0;
+                if (sscanf(line, "{\"key\": \"%255[^\"]\", \"band\": %d, \"ctas_per_sm\": %d, \"ms\": %lf}", k, &b, &q,
+                           &ms) == 4 &&
+                    strcmp(k, key) == 0) {
+                    best.band = b;
+                    best.ctas_per_sm = q;
+                    best.ms = ms;
+                    best.from_cache = 1;
+                }
+            }
+            fclose(f);
+        }
+    }
+    if (!best.from_cache) {
+        // time every candidate on this batch: warm-up run, then two timed runs
+        const int bands[3] = {64, 160, 256};
+        const int ctas[2] = {8, 12};
+        cudaEvent_t e0, e1;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return CANNY_ECUDA;
+        best.ms = 1e30;
+        for (int bi = 0; bi < 3; ++bi) {
+            for (int ci = 0; ci < 2; ++ci) {
+                canny_tuning cand = {};
+                cand.band = bands[bi];
+                cand.ctas_per_sm = ctas[ci];
+                canny_status st = canny_set_tuning(c, &cand);
+                if (st == CANNY_OK) st = canny_run_batch(c, n, imgs, stream);
+                if (st == CANNY_OK && cudaEventRecord(e0, s) != cudaSuccess) st = CANNY_ECUDA;
+                for (int r = 0; r < 2 && st == CANNY_OK; ++r) st = canny_run_batch(c, n, imgs, stream);
+                if (st == CANNY_OK && cudaEventRecord(e1, s) != cudaSuccess) st = CANNY_ECUDA;
+                if (st == CANNY_OK && cudaEventSynchronize(e1) != cudaSuccess) st = CANNY_ECUDA;
+                if (st != CANNY_OK) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return st;
+                }
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms / 2 < best.ms) {
+                    best = cand;
+                    best.ms = ms / 2;
+                }
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (cache_path && *cache_path) {
+            FILE *f = fopen(cache_path, "a");
+            if (f) {
+                fprintf(f, "{\"key\": \"%s\", \"band\": %d, \"ctas_per_sm\": %d, \"ms\": %.6f}\n", key, best.band,
+                        best.ctas_per_sm, best.ms);
+                fclose(f);
+            }
+        }
+    }
+    canny_status st = canny_set_tuning(c, &best);
+    if (st != CANNY_OK) return st;
+    if (out) *out = best;
     return CANNY_OK;
 }
 

@@ -1,6 +1,7 @@
 // canny_internal.cuh -- types shared by the kernels and the C ABI of libcanny.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -71,15 +72,45 @@ struct FloatParams {
     float lo_frac, hi_frac;
 };
 
+// ---------------------------------------------------------------- batches
+// One image of a batch as the fused kernel sees it.
+struct BatchImage {
+    HystImage img;             // output map and tile geometry
+    const uint8_t *in;
+    int in_pitch;
+    uint32_t unit_base;        // index of the image's first (strip, band) unit
+    int nsx;                   // strips across
+    int tma;                   // 1 if tmaps[k] describes the input
+    int pad[2];
+};
+
+// Device header of a batch run, uploaded with the descriptors.
+struct BatchHeader {
+    uint32_t nimg, total_units, next_unit, ntiles, max_passes, pad[3];
+};
+
 // ---------------------------------------------------------------- launchers (k1_fused.cu)
+// Band heights the fused kernel is built for (rows per unit of work).
+bool k1_band_supported(int band);
+int k1_units(int w, int h, int band);
+int k1_strip_width();
+bool encode_k1_map(void *tmap_out, const uint8_t *in, int w, int h, int in_pitch);
 // Integer Steps 1-3 + thresholds: class map (0/1/2) into cls. err: device word
 // that gets bit 1 if a shared-memory pipeline wait ran out.
 cudaError_t launch_k1_classify_u8(const uint8_t *in, int in_pitch, uint8_t *cls, int cls_pitch,
-                                  int w, int h, IntThresholds t, uint32_t *err, cudaStream_t s);
+                                  int w, int h, IntThresholds t, uint32_t *err, cudaStream_t s, int band = 64);
 // Integer Steps 1-4 up to the tile-local hysteresis: edges (0/255) into img.map,
 // tile masks / pending bitmaps / first worklist into hs (after hyst_reset).
 cudaError_t launch_k1_edges_u8(const uint8_t *in, int in_pitch, int w, int h, IntThresholds t,
-                               const HystScratch &hs, HystImage img, cudaStream_t s);
+                               const HystScratch &hs, HystImage img, cudaStream_t s, int band = 64);
+// The same for every image of a batch: a persistent grid of `ctas` one-warp CTAs
+// pops (image, strip, band) units from hdr->next_unit.
+cudaError_t launch_k1_edges_batch(const BatchImage *imgs, const CUtensorMap *tmaps, BatchHeader *hdr,
+                                  IntThresholds t, const HystScratch &hs, int band, int ctas, cudaStream_t s);
+// The batch kernel as a node of graph g.
+cudaError_t k1_add_batch_node(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, int band,
+                              const BatchImage *imgs, const CUtensorMap *tmaps, BatchHeader *hdr, IntThresholds t,
+                              const HystScratch &hs, int ctas, cudaGraphNode_t *out);
 
 // ---------------------------------------------------------------- TMA (tma.cu)
 bool tma_usable(const void *base, int pitch);
@@ -110,5 +141,10 @@ cudaError_t hyst_reset(const HystScratch &hs, uint32_t ntiles, uint32_t nimg,
 int hyst_pass_grid();
 // Executable graph { while (cond) global pass } bound to this scratch.
 cudaError_t hyst_build_graph(const HystScratch &hs, cudaGraph_t *graph_out, cudaGraphExec_t *exec_out);
+// Graph pieces for the batch graph.
+cudaError_t hyst_add_loop(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, const HystScratch &hs,
+                          cudaGraphNode_t *out);
+cudaError_t hyst_add_init_from_header(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps,
+                                      const HystScratch &hs, const BatchHeader *hdr, cudaGraphNode_t *out);
 
 }  // namespace canny

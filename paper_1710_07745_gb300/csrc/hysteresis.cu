@@ -193,6 +193,16 @@ __global__ void hyst_init_kernel(HystState *st, uint32_t ntiles, uint32_t nimg, 
     *st = s;
 }
 
+__global__ void hyst_init_from_header_kernel(HystState *st, const BatchHeader *hdr)
+{
+    HystState s = {};
+    s.ntiles = hdr->ntiles;
+    s.nimg = hdr->nimg;
+    s.max_passes = hdr->max_passes;
+    s.keep_going = 1;
+    *st = s;
+}
+
 }  // namespace
 
 int hyst_pass_grid()
@@ -244,26 +254,21 @@ cudaError_t launch_hyst_global_pass(const HystScratch &hs, int grid, bool in_gra
     return cudaGetLastError();
 }
 
-// Build the executable graph { while (cond) hyst_global_kernel } for this scratch.
-cudaError_t hyst_build_graph(const HystScratch &hs, cudaGraph_t *graph_out, cudaGraphExec_t *exec_out)
+// Append { while (cond) hyst_global_kernel } to graph g after the given nodes.
+cudaError_t hyst_add_loop(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, const HystScratch &hs,
+                          cudaGraphNode_t *out)
 {
-    cudaGraph_t g = nullptr;
-    cudaGraphExec_t ex = nullptr;
-    cudaError_t err = cudaGraphCreate(&g, 0);
-    if (err != cudaSuccess) return err;
     cudaGraphConditionalHandle cond;
-    err = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
-    if (err != cudaSuccess) { cudaGraphDestroy(g); return err; }
+    cudaError_t err = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+    if (err != cudaSuccess) return err;
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = cond;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
-    cudaGraphNode_t cnode;
-    err = cudaGraphAddNode(&cnode, g, nullptr, nullptr, 0, &cp);
-    if (err != cudaSuccess) { cudaGraphDestroy(g); return err; }
+    err = cudaGraphAddNode(out, g, deps, nullptr, ndeps, &cp);
+    if (err != cudaSuccess) return err;
     cudaGraph_t body = cp.conditional.phGraph_out[0];
-
     HystScratch hs_copy = hs;
     int in_graph = 1;
     void *args[] = {&hs_copy, &in_graph, &cond};
@@ -274,10 +279,38 @@ cudaError_t hyst_build_graph(const HystScratch &hs, cudaGraph_t *graph_out, cuda
     kp.sharedMemBytes = 0;
     kp.kernelParams = args;
     cudaGraphNode_t knode;
-    err = cudaGraphAddKernelNode(&knode, body, nullptr, 0, &kp);
-    if (err != cudaSuccess) { cudaGraphDestroy(g); return err; }
-    err = cudaGraphInstantiate(&ex, g, 0);
-    if (err != cudaSuccess) { cudaGraphDestroy(g); return err; }
+    return cudaGraphAddKernelNode(&knode, body, nullptr, 0, &kp);
+}
+
+// Append the control-block reset that reads its sizes from a batch header.
+cudaError_t hyst_add_init_from_header(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps,
+                                      const HystScratch &hs, const BatchHeader *hdr, cudaGraphNode_t *out)
+{
+    HystState *st = hs.state;
+    const BatchHeader *h = hdr;
+    void *args[] = {&st, &h};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void *)hyst_init_from_header_kernel;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(1);
+    kp.kernelParams = args;
+    return cudaGraphAddKernelNode(out, g, deps, ndeps, &kp);
+}
+
+// Build the executable graph { while (cond) hyst_global_kernel } for this scratch.
+cudaError_t hyst_build_graph(const HystScratch &hs, cudaGraph_t *graph_out, cudaGraphExec_t *exec_out)
+{
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    cudaError_t err = cudaGraphCreate(&g, 0);
+    if (err != cudaSuccess) return err;
+    cudaGraphNode_t loop;
+    err = hyst_add_loop(g, nullptr, 0, hs, &loop);
+    if (err == cudaSuccess) err = cudaGraphInstantiate(&ex, g, 0);
+    if (err != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return err;
+    }
     *graph_out = g;
     *exec_out = ex;
     return cudaSuccess;

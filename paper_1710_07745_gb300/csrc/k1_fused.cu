@@ -3,13 +3,15 @@
 // suppression -> double threshold -> tile-local hysteresis. The image is read
 // once and the edge map written once; the class map never leaves the SM.
 //
-// A CTA is one warp. It owns 224 columns x 64 rows (7 x 2 hysteresis tiles);
-// lane L handles the 8 pixels starting at column X0 - 8 + 8L, lanes 1..28 give
-// the output, lanes 0 and 29 serve halos, lanes 30 and 31 idle along.
+// A CTA is one warp. Its unit of work is a strip of 224 columns x BAND rows
+// (BAND = 64, 160 or 256: 7 x BAND/32 hysteresis tiles); lane L handles the 8
+// pixels starting at column X0 - 8 + 8L, lanes 1..28 give the output, lanes 0
+// and 29 serve halos, lanes 30 and 31 idle along. One image: one CTA per unit.
+// A batch: a persistent grid pops units of all images from a device counter.
 //
-// Phase 1, sliding down the 64 rows (plus a 4-row halo each side):
+// Phase 1, sliding down the BAND rows (plus a 4-row halo each side):
 //   - TMA loads the strip's input rows (256 bytes from X0 - 16) in chunks of
-//     6 rows into a 4-stage shared-memory ring, one mbarrier per stage;
+//     3 rows into a 4-stage shared-memory ring, one mbarrier per stage;
 //   - the binomial Gaussian runs on pairs of 16-bit lanes (vertical: a cascade
 //     of four pairwise sums; horizontal: packed words with the +128 rounding
 //     folded in); neighbour lanes trade halo values by shuffles;
@@ -41,21 +43,28 @@ using tile::FULL;
 constexpr int LPX = 8;                  // pixels per lane per row
 constexpr int THREADS = 32;             // one warp per CTA
 constexpr int OUT_W = 28 * LPX;         // 224 output columns (lanes 1..28) = 7 hysteresis tiles
-constexpr int BAND = 64;                // output rows = 2 hysteresis tiles
-constexpr int ITERS = BAND + 8;         // input rows Y0-4 .. Y0+BAND+3
 constexpr int UNROLL = 3;               // period of the 3-row windows
 constexpr int CH = UNROLL;              // input rows per TMA chunk (one chunk per unrolled group)
 constexpr int STAGES = 4;               // chunks in flight: 12 rows ahead
-constexpr int NCH = ITERS / CH;         // 24 chunks per band
 constexpr int BOX = 256;                // TMA box width: columns X0-16 .. X0+239
 constexpr uint32_t CHUNK_BYTES = BOX * CH;
 constexpr int RING = 5;                 // rows of strengths kept
 constexpr int GRING = 4;                // rows of candidate gradients kept
 constexpr int QCAP = UNROLL * 28 * LPX; // candidate pixels of one 3-row group, at most
-constexpr int TILES_X = OUT_W / HT, TILES_Y = BAND / HT;
+constexpr int TILES_X = OUT_W / HT;
 constexpr int MW = OUT_W / 32;          // bitmask words per strip row
-static_assert(ITERS % UNROLL == 0 && ITERS % CH == 0, "");
 static_assert((CH * BOX) % 128 == 0, "TMA stage buffers must stay 128-byte aligned");
+
+// Rows per unit. Each unit consumes a whole number of full mbarrier phase
+// cycles (NCH a multiple of 2 * STAGES), so a persistent CTA can run unit after
+// unit on the same barriers.
+template <int BAND>
+struct Band {
+    static constexpr int ITERS = BAND + 8;          // input rows Y0-4 .. Y0+BAND+3
+    static constexpr int NCH = ITERS / CH;          // chunks per unit
+    static constexpr int TILES_Y = BAND / HT;
+    static_assert(BAND % HT == 0 && ITERS % UNROLL == 0 && NCH % (2 * STAGES) == 0, "bad band height");
+};
 
 constexpr uint32_t MAGIC = 0x4B000000u;             // float 2^23
 constexpr uint32_t BIAS = 0x00800080u;              // +128 in both 16-bit lanes
@@ -63,6 +72,7 @@ constexpr uint32_t WAIT_LIMIT = 1u << 22;           // bounded mbarrier waits
 
 enum { MODE_CLASSMAP = 0, MODE_EDGES = 1 };
 
+template <int BAND>
 struct alignas(128) Smem {
     uint8_t in[STAGES][CH * BOX];        // TMA destinations, 128-byte aligned
     float m2[RING][256];                 // strengths of the last rows, by row mod RING
@@ -133,7 +143,8 @@ __device__ __forceinline__ float &pix(float2 (&p)[5], int k)
 
 // ---------------------------------------------------------------- candidate suppression
 // Step 3 + thresholds for one queued candidate pixel.
-__device__ __forceinline__ void suppress_pixel(Smem &S, uint32_t entry, int Y0, float hi2)
+template <int BAND>
+__device__ __forceinline__ void suppress_pixel(Smem<BAND> &S, uint32_t entry, int Y0, float hi2)
 {
     const int y = Y0 + (int)(entry >> 8), p = (int)(entry & 255u);
     const int sl = y % RING, su = (y + RING - 1) % RING, sd = (y + 1) % RING;
@@ -158,11 +169,12 @@ __device__ __forceinline__ void suppress_pixel(Smem &S, uint32_t entry, int Y0, 
 }
 
 // ---------------------------------------------------------------- phase 1
-template <bool TMA>
+template <bool TMA, int BAND>
 __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint8_t *__restrict__ in,
-                                             int in_pitch, int w, int h, IntThresholds t, Smem &S, int lane,
+                                             int in_pitch, int w, int h, IntThresholds t, Smem<BAND> &S, int lane,
                                              int X0, int Y0, uint32_t *err)
 {
+    constexpr int ITERS = Band<BAND>::ITERS, NCH = Band<BAND>::NCH;
     const int xl = X0 - LPX + LPX * lane;     // image column of the lane's first pixel
     const bool border = xl <= 0 || xl + LPX >= w;
     const bool out_lane = lane >= 1 && lane <= 28 && xl < w;
@@ -417,57 +429,59 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint
     }
 }
 
-// ---------------------------------------------------------------- kernel
-template <bool TMA, int MODE>
-__global__ void __launch_bounds__(THREADS, 12)
-k1_fused_kernel(const __grid_constant__ CUtensorMap tmap, const uint8_t *__restrict__ in, int in_pitch,
-                int w, int h, IntThresholds t, uint8_t *__restrict__ out, int out_pitch, HystScratch hs,
-                HystImage img, uint32_t *err)
-{
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
-    const int lane = threadIdx.x;
-    const int X0 = blockIdx.x * OUT_W, Y0 = blockIdx.y * BAND;
+// ---------------------------------------------------------------- one unit
+// Everything one CTA does for one strip x band of one image.
+struct Unit {
+    const uint8_t *in;
+    int in_pitch, w, h;
+    int X0, Y0, sx, sy;        // strip origin, strip and band index
+    bool tma;
+};
 
+template <int BAND, int MODE>
+__device__ __forceinline__ void run_unit(const CUtensorMap *tmap, const Unit &U, IntThresholds t, uint8_t *out,
+                                         int out_pitch, const HystScratch &hs, const HystImage &img, uint32_t *err,
+                                         Smem<BAND> &S, int lane)
+{
+    constexpr int TILES_Y = Band<BAND>::TILES_Y;
     for (int k = lane; k < BAND * MW; k += THREADS) {
         (&S.cand[0][0])[k] = 0u;
         (&S.strong[0][0])[k] = 0u;
     }
-    if (lane == 0) {
-        S.qcount = 0;
-        if (TMA) {
-            for (int sidx = 0; sidx < STAGES; ++sidx) mbar_init(&S.full[sidx], 1);
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        }
-    }
+    if (lane == 0) S.qcount = 0;
     __syncwarp();
-
-    stencil_band<TMA>(&tmap, in, in_pitch, w, h, t, S, lane, X0, Y0, err);
+    if (U.tma) {
+        // the previous unit's reads of the stage buffers are done before TMA reuses them
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        stencil_band<true, BAND>(tmap, U.in, U.in_pitch, U.w, U.h, t, S, lane, U.X0, U.Y0, err);
+    } else {
+        stencil_band<false, BAND>(tmap, U.in, U.in_pitch, U.w, U.h, t, S, lane, U.X0, U.Y0, err);
+    }
     __syncwarp();
 
     if (MODE == MODE_CLASSMAP) {
         // class byte = weak bit + strong bit
         for (int k = lane; k < BAND * MW; k += THREADS) {
             const int row = k / MW, wj = k % MW;
-            const int y = Y0 + row, x = X0 + 32 * wj;
-            if (y >= h || x >= w) continue;
+            const int y = U.Y0 + row, x = U.X0 + 32 * wj;
+            if (y >= U.h || x >= U.w) continue;
             const uint32_t c = S.cand[row][wj], sgl = S.strong[row][wj];
             uint32_t wd[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) wd[q] = nib01(c >> (4 * q)) + nib01(sgl >> (4 * q));
             uint8_t *dst = out + (int64_t)y * out_pitch + x;
-            if (x + 32 <= w && ((((uintptr_t)dst)) & 15) == 0) {
+            if (x + 32 <= U.w && ((((uintptr_t)dst)) & 15) == 0) {
                 reinterpret_cast<uint4 *>(dst)[0] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
                 reinterpret_cast<uint4 *>(dst)[1] = make_uint4(wd[4], wd[5], wd[6], wd[7]);
             } else {
-                for (int b = 0; b < 32 && x + b < w; ++b) dst[b] = (uint8_t)((wd[b >> 2] >> (8 * (b & 3))) & 0xFF);
+                for (int b = 0; b < 32 && x + b < U.w; ++b) dst[b] = (uint8_t)((wd[b >> 2] >> (8 * (b & 3))) & 0xFF);
             }
         }
     } else {
-        // Step 4, tile-local: flood fill each of the strip's 7 x 2 tiles from its bitmasks
+        // Step 4, tile-local: flood fill each of the unit's 7 x BAND/32 tiles from its bitmasks
         for (int tl = 0; tl < TILES_X * TILES_Y; ++tl) {
             const int txl = tl % TILES_X, tyl = tl / TILES_X;
-            const int tx = blockIdx.x * TILES_X + txl, ty = blockIdx.y * TILES_Y + tyl;
+            const int tx = U.sx * TILES_X + txl, ty = U.sy * TILES_Y + tyl;
             if (tx >= img.ntx || ty >= img.nty) continue;         // warp-uniform
             const uint32_t cand = S.cand[tyl * HT + lane][txl];
             const uint32_t strong = S.strong[tyl * HT + lane][txl];
@@ -476,53 +490,202 @@ k1_fused_kernel(const __grid_constant__ CUtensorMap tmap, const uint8_t *__restr
             tile::finish_tile(hs, img.tile_base + (uint32_t)ty * (uint32_t)img.ntx + (uint32_t)tx, e, cand, lane);
         }
     }
+    __syncwarp();
 }
 
-template <bool TMA, int MODE>
-cudaError_t launch_mode(const CUtensorMap &tmap, const uint8_t *in, int in_pitch, int w, int h, IntThresholds t,
-                        uint8_t *out, int out_pitch, const HystScratch &hs, const HystImage &img, uint32_t *err,
-                        cudaStream_t s)
+template <int BAND>
+__device__ __forceinline__ void init_barriers(Smem<BAND> &S, int lane)
+{
+    if (lane == 0) {
+        for (int k = 0; k < STAGES; ++k) mbar_init(&S.full[k], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------- kernels
+// One image: one CTA per unit (blockIdx.x = strip, blockIdx.y = band).
+template <int BAND, int MODE>
+__global__ void __launch_bounds__(THREADS, 12)
+k1_fused_kernel(const __grid_constant__ CUtensorMap tmap, const uint8_t *__restrict__ in, int in_pitch,
+                int w, int h, int use_tma, IntThresholds t, uint8_t *__restrict__ out, int out_pitch,
+                HystScratch hs, HystImage img, uint32_t *err)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Smem<BAND> &S = *reinterpret_cast<Smem<BAND> *>(smem_raw);
+    const int lane = threadIdx.x;
+    init_barriers(S, lane);
+    Unit U;
+    U.in = in;
+    U.in_pitch = in_pitch;
+    U.w = w;
+    U.h = h;
+    U.sx = blockIdx.x;
+    U.sy = blockIdx.y;
+    U.X0 = U.sx * OUT_W;
+    U.Y0 = U.sy * BAND;
+    U.tma = use_tma != 0;
+    run_unit<BAND, MODE>(&tmap, U, t, out, out_pitch, hs, img, err, S, lane);
+}
+
+// A batch: a persistent grid pops (image, strip, band) units from a counter.
+template <int BAND>
+__global__ void __launch_bounds__(THREADS, 12)
+k1_fused_batch_kernel(const BatchImage *__restrict__ imgs, const CUtensorMap *__restrict__ tmaps,
+                      BatchHeader *hdr, IntThresholds t, HystScratch hs)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Smem<BAND> &S = *reinterpret_cast<Smem<BAND> *>(smem_raw);
+    const int lane = threadIdx.x;
+    init_barriers(S, lane);
+    const uint32_t total = hdr->total_units;
+    const int nimg = (int)hdr->nimg;
+    for (;;) {
+        uint32_t unit = 0;
+        if (lane == 0) unit = atomicAdd(&hdr->next_unit, 1u);
+        unit = __shfl_sync(FULL, unit, 0);
+        if (unit >= total) break;
+        int lo = 0, hi = nimg - 1;                     // last image whose units start at or before unit
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (imgs[mid].unit_base <= unit) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchImage &B = imgs[lo];
+        const uint32_t local = unit - B.unit_base;
+        Unit U;
+        U.in = B.in;
+        U.in_pitch = B.in_pitch;
+        U.w = B.img.w;
+        U.h = B.img.h;
+        U.sx = (int)(local % (uint32_t)B.nsx);
+        U.sy = (int)(local / (uint32_t)B.nsx);
+        U.X0 = U.sx * OUT_W;
+        U.Y0 = U.sy * BAND;
+        U.tma = B.tma != 0;
+        const HystImage img = B.img;
+        run_unit<BAND, MODE_EDGES>(&tmaps[lo], U, t, img.map, img.pitch, hs, img, &hs.state->error, S, lane);
+    }
+}
+
+template <int BAND, int MODE>
+cudaError_t launch_single(const CUtensorMap &tmap, bool tma, const uint8_t *in, int in_pitch, int w, int h,
+                          IntThresholds t, uint8_t *out, int out_pitch, const HystScratch &hs, const HystImage &img,
+                          uint32_t *err, cudaStream_t s)
 {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k1_fused_kernel<TMA, MODE>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+        cudaError_t e = cudaFuncSetAttribute(k1_fused_kernel<BAND, MODE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<BAND>));
         if (e != cudaSuccess) return e;
         attr = true;
     }
     dim3 grid((w + OUT_W - 1) / OUT_W, (h + BAND - 1) / BAND);
-    k1_fused_kernel<TMA, MODE><<<grid, THREADS, sizeof(Smem), s>>>(tmap, in, in_pitch, w, h, t, out, out_pitch,
-                                                                    hs, img, err);
+    k1_fused_kernel<BAND, MODE><<<grid, THREADS, sizeof(Smem<BAND>), s>>>(tmap, in, in_pitch, w, h, tma ? 1 : 0, t,
+                                                                          out, out_pitch, hs, img, err);
     return cudaGetLastError();
 }
 
 template <int MODE>
-cudaError_t launch_any(const uint8_t *in, int in_pitch, int w, int h, IntThresholds t, uint8_t *out,
+cudaError_t launch_any(int band, const uint8_t *in, int in_pitch, int w, int h, IntThresholds t, uint8_t *out,
                        int out_pitch, const HystScratch &hs, const HystImage &img, uint32_t *err, cudaStream_t s)
 {
     CUtensorMap tmap;
     memset(&tmap, 0, sizeof(tmap));
-    if (encode_u8_map(&tmap, in, w, h, in_pitch, BOX, CH))
-        return launch_mode<true, MODE>(tmap, in, in_pitch, w, h, t, out, out_pitch, hs, img, err, s);
-    return launch_mode<false, MODE>(tmap, in, in_pitch, w, h, t, out, out_pitch, hs, img, err, s);
+    const bool tma = encode_u8_map(&tmap, in, w, h, in_pitch, BOX, CH);
+    switch (band) {
+    case 160: return launch_single<160, MODE>(tmap, tma, in, in_pitch, w, h, t, out, out_pitch, hs, img, err, s);
+    case 256: return launch_single<256, MODE>(tmap, tma, in, in_pitch, w, h, t, out, out_pitch, hs, img, err, s);
+    default: return launch_single<64, MODE>(tmap, tma, in, in_pitch, w, h, t, out, out_pitch, hs, img, err, s);
+    }
+}
+
+template <int BAND>
+cudaError_t launch_batch_band(const BatchImage *imgs, const CUtensorMap *tmaps, BatchHeader *hdr, IntThresholds t,
+                              const HystScratch &hs, int ctas, cudaStream_t s)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k1_fused_batch_kernel<BAND>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<BAND>));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k1_fused_batch_kernel<BAND><<<ctas, THREADS, sizeof(Smem<BAND>), s>>>(imgs, tmaps, hdr, t, hs);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
+bool k1_band_supported(int band) { return band == 64 || band == 160 || band == 256; }
+
+int k1_units(int w, int h, int band)
+{
+    if (w <= 0 || h <= 0) return 0;
+    return ((w + OUT_W - 1) / OUT_W) * ((h + band - 1) / band);
+}
+
+int k1_strip_width() { return OUT_W; }
+
 cudaError_t launch_k1_classify_u8(const uint8_t *in, int in_pitch, uint8_t *cls, int cls_pitch, int w, int h,
-                                  IntThresholds t, uint32_t *err, cudaStream_t s)
+                                  IntThresholds t, uint32_t *err, cudaStream_t s, int band)
 {
     if (w <= 0 || h <= 0) return cudaSuccess;
     HystScratch none = {};
     HystImage img = {};
-    return launch_any<MODE_CLASSMAP>(in, in_pitch, w, h, t, cls, cls_pitch, none, img, err, s);
+    return launch_any<MODE_CLASSMAP>(band, in, in_pitch, w, h, t, cls, cls_pitch, none, img, err, s);
 }
 
 cudaError_t launch_k1_edges_u8(const uint8_t *in, int in_pitch, int w, int h, IntThresholds t,
-                               const HystScratch &hs, HystImage img, cudaStream_t s)
+                               const HystScratch &hs, HystImage img, cudaStream_t s, int band)
 {
     if (w <= 0 || h <= 0) return cudaSuccess;
-    return launch_any<MODE_EDGES>(in, in_pitch, w, h, t, img.map, img.pitch, hs, img, &hs.state->error, s);
+    return launch_any<MODE_EDGES>(band, in, in_pitch, w, h, t, img.map, img.pitch, hs, img, &hs.state->error, s);
+}
+
+cudaError_t launch_k1_edges_batch(const BatchImage *imgs, const CUtensorMap *tmaps, BatchHeader *hdr, IntThresholds t,
+                                  const HystScratch &hs, int band, int ctas, cudaStream_t s)
+{
+    switch (band) {
+    case 160: return launch_batch_band<160>(imgs, tmaps, hdr, t, hs, ctas, s);
+    case 256: return launch_batch_band<256>(imgs, tmaps, hdr, t, hs, ctas, s);
+    default: return launch_batch_band<64>(imgs, tmaps, hdr, t, hs, ctas, s);
+    }
+}
+
+template <int BAND>
+cudaError_t add_batch_node_band(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, const BatchImage *imgs,
+                                const CUtensorMap *tmaps, BatchHeader *hdr, IntThresholds t, const HystScratch &hs,
+                                int ctas, cudaGraphNode_t *out)
+{
+    cudaError_t e = cudaFuncSetAttribute(k1_fused_batch_kernel<BAND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(Smem<BAND>));
+    if (e != cudaSuccess) return e;
+    HystScratch hs_copy = hs;
+    void *args[] = {(void *)&imgs, (void *)&tmaps, (void *)&hdr, (void *)&t, (void *)&hs_copy};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void *)k1_fused_batch_kernel<BAND>;
+    kp.gridDim = dim3(ctas);
+    kp.blockDim = dim3(THREADS);
+    kp.sharedMemBytes = sizeof(Smem<BAND>);
+    kp.kernelParams = args;
+    return cudaGraphAddKernelNode(out, g, deps, ndeps, &kp);
+}
+
+cudaError_t k1_add_batch_node(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, int band,
+                              const BatchImage *imgs, const CUtensorMap *tmaps, BatchHeader *hdr, IntThresholds t,
+                              const HystScratch &hs, int ctas, cudaGraphNode_t *out)
+{
+    switch (band) {
+    case 160: return add_batch_node_band<160>(g, deps, ndeps, imgs, tmaps, hdr, t, hs, ctas, out);
+    case 256: return add_batch_node_band<256>(g, deps, ndeps, imgs, tmaps, hdr, t, hs, ctas, out);
+    default: return add_batch_node_band<64>(g, deps, ndeps, imgs, tmaps, hdr, t, hs, ctas, out);
+    }
+}
+
+bool encode_k1_map(void *tmap_out, const uint8_t *in, int w, int h, int in_pitch)
+{
+    return encode_u8_map(tmap_out, in, w, h, in_pitch, BOX, CH);
 }
 
 }  // namespace canny

@@ -326,3 +326,62 @@ def test_full_size_workloads_bit_exact(which):
     assert st["status"] == canny.CANNY_OK
     want = oracle.canny_u8(img)
     assert np.array_equal(out, want), int((out != want).sum())
+
+
+# ------------------------------------------------------------------ batched integer path
+def _batch_run(c, imgs):
+    ins = [dev(im) for im in imgs]
+    outs = [torch.full(im.shape, 3, dtype=torch.uint8, device="cuda") for im in imgs]
+    c.run_batch(list(zip(ins, outs)))
+    torch.cuda.synchronize()
+    return [o.cpu().numpy() for o in outs], c.stats()
+
+
+def test_batch_many_uneven_images_two_calls():
+    rng = np.random.default_rng(31)
+    sizes = [(int(h), int(w)) for h, w in rng.integers(1, 400, (150, 2))]
+    imgs = [synth.image(500 + i, w, h, 4, 4, 8) for i, (h, w) in enumerate(sizes)]
+    total = sum(w * h for h, w in sizes)
+    with canny.Canny(total, 1) as c:
+        for rep in range(2):           # two calls: alternate staging slots, reuse graphs
+            outs, st = _batch_run(c, imgs if rep == 0 else imgs[::-1])
+            assert st["status"] == canny.CANNY_OK
+            src = imgs if rep == 0 else imgs[::-1]
+            for im, o in zip(src, outs):
+                assert np.array_equal(o, oracle.canny_u8(im))
+
+
+@pytest.mark.parametrize("band,ctas", [(64, 8), (160, 12), (256, 4)])
+def test_every_tuning_gives_identical_edges(band, ctas):
+    imgs = [synth.image(900 + i, w, h, 8, 8, 10) for i, (h, w) in
+            enumerate([(300, 500), (1, 70), (257, 33), (700, 449)])]
+    total = sum(im.size for im in imgs)
+    with canny.Canny(max(total, 700 * 700), 1) as c:
+        c.set_tuning(band, ctas)
+        outs, st = _batch_run(c, imgs)
+        for im, o in zip(imgs, outs):
+            assert np.array_equal(o, oracle.canny_u8(im))
+    with canny.Canny(700, 700) as c:
+        c.set_tuning(band, ctas)
+        for im in imgs:
+            out, _ = run_int(im, ctx=c)
+            assert np.array_equal(out, oracle.canny_u8(im))
+
+
+def test_autotune_picks_a_supported_config_and_caches_it(tmp_path):
+    rng = np.random.default_rng(5)
+    sizes = [(int(h), int(w)) for h, w in rng.integers(64, 300, (40, 2))]
+    imgs = [synth.image(700 + i, w, h, 4, 4, 8) for i, (h, w) in enumerate(sizes)]
+    total = sum(w * h for h, w in sizes)
+    cache = str(tmp_path / "tune.jsonl")
+    ins = [dev(im) for im in imgs]
+    outs = [torch.empty_like(x) for x in ins]
+    with canny.Canny(total, 1) as c:
+        t1 = c.autotune_batch(list(zip(ins, outs)), cache_path=cache)
+        assert t1["band"] in (64, 160, 256) and t1["ctas_per_sm"] in (8, 12) and t1["from_cache"] == 0
+        t2 = c.autotune_batch(list(zip(ins, outs)), cache_path=cache)
+        assert t2["from_cache"] == 1 and (t2["band"], t2["ctas_per_sm"]) == (t1["band"], t1["ctas_per_sm"])
+        c.run_batch(list(zip(ins, outs)))
+        torch.cuda.synchronize()
+    for im, o in zip(imgs, outs):
+        assert np.array_equal(o.cpu().numpy(), oracle.canny_u8(im))

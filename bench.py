@@ -93,6 +93,12 @@ def barrier(world: int):
         dist.barrier()
 
 
+def job_value(world: int, steps: int, px_per_step: int, ms_max: float) -> float:
+    """Whole-job Mpixel/s: every rank runs its own image per step (weak scaling),
+    timed by the slowest rank."""
+    return world * steps * px_per_step / (ms_max / 1e3) / 1e6
+
+
 def max_over_ranks(v: float, world: int) -> float:
     if world == 1:
         return v
@@ -272,6 +278,65 @@ def measure_batched(steps: int) -> dict:
             "tuning": {"band": tune["band"], "ctas_per_sm": tune["ctas_per_sm"]}}
 
 
+# ------------------------------------------------------------------ serving
+SERVE_POOL, SERVE_LO, SERVE_HI, SERVE_SEED = 256, 128, 4096, 5000
+
+
+def measure_serving(n_requests: int, loads=(0.25, 0.5, 0.9), budget_gb: float = 16.0, streams: int = 3) -> dict:
+    """Continuous-batching server on Poisson arrivals, sides log-uniform in [128, 4096].
+
+    Request i carries image i mod 256 of a seeded pool (the sizes follow the stated
+    distribution; the pixels repeat). Capacity is measured first with every request
+    arriving at once; the offered loads are fractions of it. The serial baseline
+    (one canny_run_pitched at a time) runs the 0.25-load trace on its first 5000
+    requests."""
+    import concurrent.futures as cf
+
+    import torch
+
+    from paper_1710_07745_gb300 import canny, synth
+
+    ws, hs = synth.log_uniform_sizes(SERVE_SEED, SERVE_POOL, SERVE_LO, SERVE_HI)
+    with cf.ThreadPoolExecutor(max_workers=min(32, os.cpu_count() or 4)) as ex:
+        pool = list(ex.map(lambda i: synth.batch_image(i, int(ws[i]), int(hs[i]), SERVE_SEED), range(SERVE_POOL)))
+    pinned = [torch.from_numpy(im).pin_memory() for im in pool]
+    areas = np.array([im.size for im in pool], np.float64)
+    mean_area = float(areas.mean())
+
+    def trace(n, rate, seed):
+        t = synth.poisson_arrivals(seed, n, rate) if rate else np.zeros(n)
+        return [canny.canny_request(int(ws[i % SERVE_POOL]), int(hs[i % SERVE_POOL]),
+                                    pinned[i % SERVE_POOL].data_ptr(), int(ws[i % SERVE_POOL]), None, 0,
+                                    float(t[i] - t[0]) if rate else 0.0) for i in range(n)]
+
+    def cfg(serial):
+        return canny.canny_serve_config(budget_gb * 2 ** 30, streams, 4096, 256 << 20, serial, LOW, HIGH, 0, 0)
+
+    def summary(rep, offered=None):
+        d = rep.as_dict()
+        out = {"delivered_mpx_s": round(d["delivered_mpx_s"], 1), "p50_ms": round(d["p50_ms"], 3),
+               "p99_ms": round(d["p99_ms"], 3), "max_ms": round(d["max_ms"], 3),
+               "mean_batch_images": round(d["mean_batch_images"], 1), "peak_gb": round(d["peak_bytes"] / 2 ** 30, 2)}
+        if offered is not None:
+            out["offered_mpx_s"] = round(offered, 1)
+        return out
+
+    cap_rep = canny.canny_serve(cfg(0), trace(min(n_requests, 20000), 0.0, 1))
+    capacity = cap_rep.delivered_mpx_s                 # Mpixel/s
+    result = {"requests": n_requests, "sides": [SERVE_LO, SERVE_HI], "budget_gb": budget_gb, "streams": streams,
+              "pool_images": SERVE_POOL, "capacity_mpx_s": round(capacity, 1), "loads": []}
+    for k, load in enumerate(loads):
+        rate = load * capacity * 1e6 / mean_area        # requests per second
+        rep = canny.canny_serve(cfg(0), trace(n_requests, rate, 10 + k))
+        entry = summary(rep, load * capacity)
+        entry["load"] = load
+        result["loads"].append(entry)
+    rate = loads[0] * capacity * 1e6 / mean_area
+    ser = canny.canny_serve(cfg(1), trace(min(n_requests, 5000), rate, 10))
+    result["serial"] = dict(summary(ser, loads[0] * capacity), load=loads[0], requests=min(n_requests, 5000))
+    return result
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, rank: int, world: int) -> None:
     import torch
@@ -323,7 +388,7 @@ def run_ours(args, rank: int, world: int) -> None:
     ms_max = max_over_ranks(ms, world)
 
     px = W * H
-    value = world * args.steps * px / (ms_max / 1e3) / 1e6
+    value = job_value(world, args.steps, px, ms_max)
     k1_ms = tm["stencil_ms"] / max(1, tm["runs"])
     k1_gbs = K1_BYTES_PER_PX * px / (k1_ms / 1e3) / 1e9
     pipe_gbs = PIPE_BYTES_PER_PX * px / (ms / args.steps / 1e3) / 1e9
@@ -353,6 +418,7 @@ def run_ours(args, rank: int, world: int) -> None:
                "h2d_bytes_per_step": px, "d2h_bytes_per_step": px, "steps": e2e_steps}
 
     batched = None if args.no_batch else measure_batched(max(3, min(args.steps, 10)))
+    serving = None if args.no_serve else measure_serving(args.serve_requests)
     if rank != 0:
         ctx.close()
         return
@@ -377,6 +443,7 @@ def run_ours(args, rank: int, world: int) -> None:
                               "frac": round(pipe_gbs / peaks["hbm_gbs"], 4)},
         "stages": stages, "dominant_stage": dominant,
         "batched": batched,
+        "serving": serving,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(args.steps * (3 + passes)),
@@ -396,6 +463,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-loop leg")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serve-requests", type=int, default=100000)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -237,6 +237,49 @@ canny_status canny_get_stats(canny_ctx *ctx, canny_stats *out);
 canny_status canny_run_noalloc(const uint8_t *d_in, int in_pitch, uint8_t *d_out, int out_pitch,
                                int w, int h, int low, int high, void *stream);
 
+/* One request of a served trace. */
+typedef struct {
+    int w, h;               /* image size */
+    const uint8_t *h_in;    /* host, h rows of h_pitch bytes (page-locked memory copies fastest) */
+    int h_pitch;
+    uint8_t *h_out;         /* host buffer for the 0/255 edge map, or NULL to leave it on the device */
+    int out_pitch;
+    double arrival_s;       /* arrival time, seconds after the start of the run; non-decreasing */
+} canny_request;
+
+typedef struct {
+    double memory_budget_bytes;   /* device memory for the requests' inputs and outputs */
+    int streams;                  /* batches in flight at once (>= 1) */
+    int max_batch_images;         /* images per batch, at most */
+    int64_t max_batch_pixels;     /* pixels per batch, at most (>= the largest request) */
+    int serial;                   /* 1: one request at a time through canny_run_pitched (baseline) */
+    int low, high;                /* integer-path thresholds */
+    int band, ctas_per_sm;        /* fused-kernel configuration (0: defaults) */
+} canny_serve_config;
+
+typedef struct {
+    int64_t completed;
+    double wall_s;                /* first arrival to last completion */
+    double delivered_mpx_s;       /* pixels served / wall_s */
+    double p50_ms, p99_ms, max_ms;/* latency: completion (event observed) minus arrival */
+    int64_t batches;
+    double mean_batch_images;
+    int64_t peak_bytes;           /* most arena bytes in use at once */
+} canny_serve_report;
+
+/*
+ * Serve a request trace in real time with continuous batching (integer path).
+ * Requests arriving while earlier ones run are admitted in arrival order as
+ * soon as the memory budget has room for their input and output buffers;
+ * every idle stream takes all admitted, not-yet-running requests as one
+ * canny_run_batch, so batches of later arrivals overlap earlier ones on the
+ * GPU. Each result equals the request's canny_run_pitched result. Writes the
+ * per-request latencies (ms) to latency_ms if not NULL. Synchronous: returns
+ * when every request has completed. The budget is allocated once per call.
+ */
+canny_status canny_serve(const canny_serve_config *cfg, int n, const canny_request *reqs, double *latency_ms,
+                         canny_serve_report *out);
+
 /* Static, human-readable message for a status. */
 const char *canny_strerror(canny_status s);
 

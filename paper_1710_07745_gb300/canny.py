@@ -60,6 +60,27 @@ class canny_tuning(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class canny_request(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_int), ("h", ctypes.c_int), ("h_in", ctypes.c_void_p), ("h_pitch", ctypes.c_int),
+                ("h_out", ctypes.c_void_p), ("out_pitch", ctypes.c_int), ("arrival_s", ctypes.c_double)]
+
+
+class canny_serve_config(ctypes.Structure):
+    _fields_ = [("memory_budget_bytes", ctypes.c_double), ("streams", ctypes.c_int),
+                ("max_batch_images", ctypes.c_int), ("max_batch_pixels", ctypes.c_int64),
+                ("serial", ctypes.c_int), ("low", ctypes.c_int), ("high", ctypes.c_int),
+                ("band", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
+
+
+class canny_serve_report(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("wall_s", ctypes.c_double), ("delivered_mpx_s", ctypes.c_double),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("batches", ctypes.c_int64), ("mean_batch_images", ctypes.c_double), ("peak_bytes", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -85,6 +106,8 @@ SIGNATURES = {
     "canny_get_tuning": ([_P, ctypes.POINTER(canny_tuning)], ctypes.c_int),
     "canny_autotune_batch": ([_P, ctypes.c_int, ctypes.POINTER(canny_image), _P, ctypes.c_char_p,
                               ctypes.POINTER(canny_tuning)], ctypes.c_int),
+    "canny_serve": ([ctypes.POINTER(canny_serve_config), ctypes.c_int, ctypes.POINTER(canny_request), _P,
+                     ctypes.POINTER(canny_serve_report)], ctypes.c_int),
     "canny_read_timing": ([_P, ctypes.POINTER(canny_timing)], ctypes.c_int),
     "canny_run_noalloc": ([_P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                            ctypes.c_int, _P], ctypes.c_int),
@@ -214,6 +237,15 @@ def canny_autotune_batch(ctx: int, imgs: Sequence[canny_image], stream: int = 0,
     _check(load().canny_autotune_batch(ctx, len(imgs), arr, stream, cp, ctypes.byref(t)),
            "canny_autotune_batch")
     return t
+
+
+def canny_serve(cfg: canny_serve_config, reqs, latency_ms=None) -> canny_serve_report:
+    """Serve a request trace (sequence of canny_request); latency_ms: optional float64 array."""
+    arr = (canny_request * len(reqs))(*reqs)
+    rep = canny_serve_report()
+    lat = latency_ms.ctypes.data if latency_ms is not None else None
+    _check(load().canny_serve(ctypes.byref(cfg), len(reqs), arr, lat, ctypes.byref(rep)), "canny_serve")
+    return rep
 
 
 # ------------------------------------------------------------------ torch marshalling

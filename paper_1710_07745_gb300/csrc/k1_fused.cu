@@ -564,6 +564,12 @@ k1_fused_batch_kernel(const BatchImage *__restrict__ imgs, const CUtensorMap *__
         U.Y0 = U.sy * BAND;
         U.tma = B.tma != 0;
         const HystImage img = B.img;
+        if (U.tma && lane == 0) {
+            // the descriptor was rewritten in global memory since the TMA unit may
+            // last have cached one at this address: order that write before its use
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&tmaps[lo]) : "memory");
+        }
+        __syncwarp();
         run_unit<BAND, MODE_EDGES>(&tmaps[lo], U, t, img.map, img.pitch, hs, img, &hs.state->error, S, lane);
     }
 }

@@ -1,0 +1,284 @@
+// serve.cu -- canny_serve: a continuous-batching request loop over the batch API.
+//
+// Requests (host images with arrival times) are admitted in arrival order as
+// device memory frees up: each admitted request gets its input and output
+// buffers from a device arena of a fixed byte budget, its input is copied in,
+// and every stream that is idle takes all admitted, not-yet-running requests as
+// one canny_run_batch. Several streams keep batches in flight at once, so new
+// arrivals start while earlier ones are still on the GPU. A request completes
+// when its batch's event fires; its latency is completion minus arrival, and
+// its memory returns to the arena. The serial mode runs the same trace one
+// request at a time through canny_run_pitched, as the baseline.
+#include <algorithm>
+#include <chrono>
+#include <deque>
+#include <map>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "canny_internal.cuh"
+
+namespace canny {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+// First-fit allocator over one device allocation; 256-byte granules.
+class Arena {
+public:
+    bool init(size_t bytes)
+    {
+        bytes_ = bytes / 256 * 256;
+        if (cudaMalloc((void **)&base_, bytes_) != cudaSuccess) {
+            cudaGetLastError();
+            base_ = nullptr;
+            return false;
+        }
+        free_[0] = bytes_;
+        return true;
+    }
+    ~Arena()
+    {
+        if (base_) cudaFree(base_);
+    }
+    uint8_t *alloc(size_t n)
+    {
+        n = (n + 255) / 256 * 256;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= n) {
+                const size_t off = it->first, len = it->second;
+                free_.erase(it);
+                if (len > n) free_[off + n] = len - n;
+                used_ += n;
+                peak_ = std::max(peak_, used_);
+                return base_ + off;
+            }
+        }
+        return nullptr;
+    }
+    void release(uint8_t *p, size_t n)
+    {
+        n = (n + 255) / 256 * 256;
+        size_t off = (size_t)(p - base_);
+        used_ -= n;
+        auto next = free_.lower_bound(off);
+        if (next != free_.end() && off + n == next->first) {
+            n += next->second;
+            free_.erase(next);
+        }
+        auto prev = free_.lower_bound(off);
+        if (prev != free_.begin()) {
+            --prev;
+            if (prev->first + prev->second == off) {
+                prev->second += n;
+                return;
+            }
+        }
+        free_[off] = n;
+    }
+    size_t peak() const { return peak_; }
+
+private:
+    uint8_t *base_ = nullptr;
+    size_t bytes_ = 0, used_ = 0, peak_ = 0;
+    std::map<size_t, size_t> free_;
+};
+
+struct Admitted {
+    int req;
+    uint8_t *in, *out;
+    int pitch;
+    size_t bytes;     // per buffer
+};
+
+struct Lane {
+    cudaStream_t stream = nullptr;
+    canny_ctx *ctx = nullptr;
+    cudaEvent_t done = nullptr;
+    std::vector<Admitted> running;
+};
+
+double pct(std::vector<double> v, double q)
+{
+    if (v.empty()) return 0.0;
+    std::sort(v.begin(), v.end());
+    const double pos = q * (double)(v.size() - 1);
+    const size_t lo = (size_t)pos;
+    const size_t hi = std::min(lo + 1, v.size() - 1);
+    return v[lo] + (v[hi] - v[lo]) * (pos - (double)lo);
+}
+
+}  // namespace
+}  // namespace canny
+
+using namespace canny;
+
+extern "C" canny_status canny_serve(const canny_serve_config *cfg, int n, const canny_request *reqs,
+                                    double *latency_ms, canny_serve_report *out)
+{
+    if (!cfg || n < 0 || (n > 0 && !reqs) || !out) return CANNY_EINVAL;
+    if (cfg->streams < 1 || cfg->max_batch_images < 1 || cfg->max_batch_pixels < 1 || cfg->memory_budget_bytes <= 0)
+        return CANNY_EINVAL;
+    int64_t max_px = 0;
+    int max_w = 1, max_h = 1;
+    for (int i = 0; i < n; ++i) {
+        const canny_request &r = reqs[i];
+        if (r.w <= 0 || r.h <= 0 || !r.h_in || r.h_pitch < r.w || (r.h_out && r.out_pitch < r.w)) return CANNY_EINVAL;
+        if (i > 0 && r.arrival_s < reqs[i - 1].arrival_s) return CANNY_EINVAL;   // arrival order
+        max_px = std::max<int64_t>(max_px, (int64_t)r.w * r.h);
+        max_w = std::max(max_w, r.w);
+        max_h = std::max(max_h, r.h);
+    }
+    if (max_px > cfg->max_batch_pixels) return CANNY_EINVAL;
+    *out = canny_serve_report{};
+    if (n == 0) return CANNY_OK;
+
+    canny_params p;
+    canny_params_default(&p);
+    p.low = (float)cfg->low;
+    p.high = (float)cfg->high;
+    Arena arena;
+    if (!arena.init((size_t)cfg->memory_budget_bytes)) return CANNY_ENOMEM;
+
+    const int nlanes = cfg->serial ? 1 : cfg->streams;
+    std::vector<Lane> lanes(nlanes);
+    canny_status st = CANNY_OK;
+    for (auto &L : lanes) {
+        if (cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess) {
+            st = CANNY_ECUDA;
+            break;
+        }
+        // serial: one image at a time; batched: a pixel budget per batch
+        const int64_t cap = cfg->serial ? max_px : cfg->max_batch_pixels;
+        st = cfg->serial ? canny_create(max_w, max_h, &p, &L.ctx)
+                         : canny_create((int)std::min<int64_t>(cap, 1 << 30), 1, &p, &L.ctx);
+        if (st != CANNY_OK) break;
+        if (cfg->band) {
+            canny_tuning t = {cfg->band, cfg->ctas_per_sm ? cfg->ctas_per_sm : 12, 0.0, 0, 0};
+            st = canny_set_tuning(L.ctx, &t);
+            if (st != CANNY_OK) break;
+        }
+    }
+
+    std::vector<double> lat((size_t)n, 0.0);
+    std::deque<int> waiting;                 // arrived, not yet admitted
+    std::vector<Admitted> admitted;          // admitted, not yet running
+    int next = 0, done = 0;
+    int64_t batches = 0, batched_images = 0;
+    const auto t0 = Clock::now();
+    auto now_s = [&]() { return std::chrono::duration<double>(Clock::now() - t0).count(); };
+    double last_done = 0.0;
+
+    while (st == CANNY_OK && done < n) {
+        const double now = now_s();
+        while (next < n && reqs[next].arrival_s <= now) waiting.push_back(next++);
+        // completions
+        for (auto &L : lanes) {
+            if (L.running.empty()) continue;
+            const cudaError_t q = cudaEventQuery(L.done);
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess) { st = CANNY_ECUDA; break; }
+            const double t = now_s();
+            for (const Admitted &a : L.running) {
+                lat[a.req] = (t - reqs[a.req].arrival_s) * 1e3;
+                arena.release(a.in, a.bytes);
+                arena.release(a.out, a.bytes);
+            }
+            done += (int)L.running.size();
+            last_done = t;
+            L.running.clear();
+        }
+        if (st != CANNY_OK) break;
+        // admission in arrival order, as far as the memory budget allows
+        while (!waiting.empty()) {
+            const canny_request &r = reqs[waiting.front()];
+            const int pitch = (r.w + 15) / 16 * 16;
+            const size_t bytes = (size_t)pitch * (size_t)r.h;
+            uint8_t *in = arena.alloc(bytes);
+            if (!in) break;
+            uint8_t *o = arena.alloc(bytes);
+            if (!o) { arena.release(in, bytes); break; }
+            admitted.push_back({waiting.front(), in, o, pitch, bytes});
+            waiting.pop_front();
+        }
+        // every idle stream takes the admitted requests as one batch
+        bool launched = false;
+        for (auto &L : lanes) {
+            if (!L.running.empty() || admitted.empty()) continue;
+            std::vector<canny_image> imgs;
+            int64_t px = 0;
+            size_t k = 0;
+            for (; k < admitted.size(); ++k) {
+                const canny_request &r = reqs[admitted[k].req];
+                const int64_t a = (int64_t)r.w * r.h;
+                if ((int)k >= cfg->max_batch_images || px + a > cfg->max_batch_pixels || (cfg->serial && k >= 1)) break;
+                px += a;
+            }
+            L.running.assign(admitted.begin(), admitted.begin() + (long)k);
+            admitted.erase(admitted.begin(), admitted.begin() + (long)k);
+            for (const Admitted &a : L.running) {
+                const canny_request &r = reqs[a.req];
+                if (cudaMemcpy2DAsync(a.in, a.pitch, r.h_in, r.h_pitch, r.w, r.h, cudaMemcpyHostToDevice, L.stream) !=
+                    cudaSuccess) { st = CANNY_ECUDA; break; }
+                imgs.push_back(canny_image{a.in, a.out, r.w, r.h, a.pitch, a.pitch});
+            }
+            if (st != CANNY_OK) break;
+            st = cfg->serial ? canny_run_pitched(L.ctx, &imgs[0], L.stream)
+                             : canny_run_batch(L.ctx, (int)imgs.size(), imgs.data(), L.stream);
+            if (st != CANNY_OK) break;
+            for (const Admitted &a : L.running) {
+                const canny_request &r = reqs[a.req];
+                if (r.h_out && cudaMemcpy2DAsync(r.h_out, r.out_pitch, a.out, a.pitch, r.w, r.h,
+                                                 cudaMemcpyDeviceToHost, L.stream) != cudaSuccess) {
+                    st = CANNY_ECUDA;
+                    break;
+                }
+            }
+            if (st == CANNY_OK && cudaEventRecord(L.done, L.stream) != cudaSuccess) st = CANNY_ECUDA;
+            ++batches;
+            batched_images += (int64_t)L.running.size();
+            launched = true;
+        }
+        if (st != CANNY_OK) break;
+        if (!launched) {
+            // nothing to start: wait for the next arrival or a completion
+            bool busy = false;
+            for (auto &L : lanes) busy |= !L.running.empty();
+            if (!busy && admitted.empty() && waiting.empty() && next < n) {
+                const double dt = reqs[next].arrival_s - now_s();
+                if (dt > 2e-4) std::this_thread::sleep_for(std::chrono::duration<double>(dt - 1e-4));
+            } else {
+                std::this_thread::yield();
+            }
+        }
+    }
+
+    for (auto &L : lanes) {
+        if (L.stream) cudaStreamSynchronize(L.stream);
+        for (const Admitted &a : L.running) {
+            arena.release(a.in, a.bytes);
+            arena.release(a.out, a.bytes);
+        }
+        if (L.ctx) canny_destroy(L.ctx);
+        if (L.done) cudaEventDestroy(L.done);
+        if (L.stream) cudaStreamDestroy(L.stream);
+    }
+    if (st != CANNY_OK) return st;
+
+    int64_t px = 0;
+    for (int i = 0; i < n; ++i) px += (int64_t)reqs[i].w * reqs[i].h;
+    const double span = last_done - reqs[0].arrival_s;
+    out->completed = done;
+    out->wall_s = span;
+    out->delivered_mpx_s = span > 0 ? (double)px / span / 1e6 : 0.0;
+    out->p50_ms = pct(lat, 0.50);
+    out->p99_ms = pct(lat, 0.99);
+    out->max_ms = *std::max_element(lat.begin(), lat.end());
+    out->batches = batches;
+    out->mean_batch_images = batches ? (double)batched_images / (double)batches : 0.0;
+    out->peak_bytes = (int64_t)arena.peak();
+    if (latency_ms) std::copy(lat.begin(), lat.end(), latency_ms);
+    return CANNY_OK;
+}

@@ -385,3 +385,58 @@ def test_autotune_picks_a_supported_config_and_caches_it(tmp_path):
         torch.cuda.synchronize()
     for im, o in zip(imgs, outs):
         assert np.array_equal(o.cpu().numpy(), oracle.canny_u8(im))
+
+
+# ------------------------------------------------------------------ serving
+def _trace(n, seed, spread_s):
+    rng = np.random.default_rng(seed)
+    sizes = [(int(h), int(w)) for h, w in rng.integers(16, 320, (n, 2))]
+    imgs = [synth.image(1200 + i, w, h, 4, 4, 8) for i, (h, w) in enumerate(sizes)]
+    arrivals = np.sort(rng.random(n) * spread_s)
+    return imgs, arrivals
+
+
+def _serve(imgs, arrivals, serial=0, budget=64 << 20, streams=2, max_batch_images=64):
+    outs = [np.full(im.shape, 9, np.uint8) for im in imgs]
+    reqs = [canny.canny_request(im.shape[1], im.shape[0], im.ctypes.data, im.strides[0],
+                                o.ctypes.data, o.strides[0], float(t))
+            for im, o, t in zip(imgs, outs, arrivals)]
+    cfg = canny.canny_serve_config(float(budget), streams, max_batch_images, 1 << 24, serial, 40, 100, 0, 0)
+    lat = np.zeros(len(imgs))
+    rep = canny.canny_serve(cfg, reqs, lat).as_dict()
+    return outs, rep, lat
+
+
+def test_serving_results_equal_alone_and_in_the_mix():
+    imgs, arrivals = _trace(60, 11, 0.05)
+    outs, rep, lat = _serve(imgs, arrivals)
+    assert rep["completed"] == len(imgs) and (lat > 0).all()
+    outs_serial, rep_s, _ = _serve(imgs, arrivals, serial=1)
+    for im, o, o1 in zip(imgs, outs, outs_serial):
+        want = oracle.canny_u8(im)
+        assert np.array_equal(o, want)        # in the mix
+        assert np.array_equal(o1, want)       # alone
+    assert rep["batches"] < len(imgs) and rep["mean_batch_images"] > 1.0
+
+
+def test_serving_under_a_tight_memory_budget():
+    imgs, arrivals = _trace(30, 12, 0.0)     # everything arrives at once
+    biggest = max((((im.shape[1] + 15) // 16) * 16) * im.shape[0] for im in imgs)
+    budget = 2 * (biggest + 256) * 3         # room for about three requests
+    outs, rep, _ = _serve(imgs, arrivals, budget=budget)
+    assert rep["completed"] == len(imgs) and rep["peak_bytes"] <= budget
+    for im, o in zip(imgs, outs):
+        assert np.array_equal(o, oracle.canny_u8(im))
+
+
+def test_batch_tma_inputs_rewritten_between_calls():
+    """Pitches that are multiples of 16 take the TMA path; the descriptors of a
+    later batch reuse the device addresses of the earlier one's."""
+    with canny.Canny(4 * 512 * 512, 1) as c:
+        for rep in range(4):
+            imgs = [synth.image(3000 + 10 * rep + i, w, h, 5, 5, 8)
+                    for i, (h, w) in enumerate([(232, 32), (300, 480), (64, 16), (511, 496)])]
+            outs, st = _batch_run(c, imgs)
+            assert st["status"] == canny.CANNY_OK
+            for im, o in zip(imgs, outs):
+                assert np.array_equal(o, oracle.canny_u8(im))

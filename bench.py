@@ -42,9 +42,14 @@ WORKLOAD = "canny_int_16384x16384"
 K1_BYTES_PER_PX = 2
 # ncu DRAM traffic of the fused kernel per 16384^2 launch, valid only for the kernel
 # source it was measured on (profiles/k1_fused_16384x8192.md: capture at half size, x2)
-K1_TRAFFIC = {"sha256_prefix": "671f2c5362dadbd3", "bytes": 469_000_000}
+K1_TRAFFIC = {"sha256_prefix": "701b3075bb099baf", "bytes": 468_588_032}
 # whole pipeline floor: stencil 2 B/px + tile-local hysteresis read + write 2 B/px
 PIPE_BYTES_PER_PX = 4
+# ncu smsp__inst_executed.sum of the fused kernel per pixel (same capture and source
+# as K1_TRAFFIC: 268,961,924 warp instructions on 16384 x 8192 pixels)
+K1_INST = {"sha256_prefix": "701b3075bb099baf", "warp_inst_per_px": 268_961_924 / (16384 * 8192)}
+# warp instructions an SM can issue per clock (4 schedulers, one each)
+ISSUE_PER_SM_CLK = 4
 
 
 def measured_peaks() -> dict:
@@ -56,15 +61,40 @@ def measured_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-def k1_traffic(w: int, h: int):
-    """Recorded ncu DRAM bytes per launch, if the kernel source is unchanged since."""
+def k1_digest() -> str:
     import hashlib
     src = os.path.join(ROOT, "paper_1710_07745_gb300", "csrc", "k1_fused.cu")
     with open(src, "rb") as f:
-        digest = hashlib.sha256(f.read()).hexdigest()
-    if not digest.startswith(K1_TRAFFIC["sha256_prefix"]) or (w, h) != (16384, 16384):
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def k1_traffic(w: int, h: int):
+    """Recorded ncu DRAM bytes per launch, if the kernel source is unchanged since."""
+    if not k1_digest().startswith(K1_TRAFFIC["sha256_prefix"]) or (w, h) != (16384, 16384):
         return None
     return K1_TRAFFIC["bytes"]
+
+
+def alu_roofline(px: int, k1_ms: float, hbm_gbs: float, clk: dict | None) -> dict | None:
+    """Issue-rate roofline of the fused kernel: its recorded warp instructions per
+    launch over the CUDA-event launch time, against SMs x 4 issue slots x the SM clock.
+    None once the kernel source differs from the one the count was taken on."""
+    import torch
+    if not k1_digest().startswith(K1_INST["sha256_prefix"]):
+        return None
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+    peak = sms * ISSUE_PER_SM_CLK * mhz * 1e6 / 1e9            # G warp instructions / s
+    inst = K1_INST["warp_inst_per_px"] * px
+    achieved = inst / (k1_ms / 1e3) / 1e9
+    alu_px_s = peak * 1e9 / K1_INST["warp_inst_per_px"]      # pixel rate if issue-bound
+    hbm_px_s = hbm_gbs * 1e9 / K1_BYTES_PER_PX               # pixel rate if HBM-bound
+    px_s = px / (k1_ms / 1e3)
+    return {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak, 1), "unit": "Ginst/s",
+            "frac": round(achieved / peak, 4), "warp_inst_per_px": round(K1_INST["warp_inst_per_px"], 4),
+            "peak_basis": f"{sms} SMs x {ISSUE_PER_SM_CLK} warp instructions/clock x {mhz:.0f} MHz",
+            "bound_mpx_s": {"alu": round(alu_px_s / 1e6, 1), "hbm": round(hbm_px_s / 1e6, 1)},
+            "frac_of_min_bound": round(px_s / min(alu_px_s, hbm_px_s), 4)}
 
 
 def config(extra: dict | None = None) -> dict:
@@ -180,6 +210,23 @@ def oracle_sample(img: np.ndarray, rows: int) -> tuple[float, str]:
     return sample.size / dt / 1e6, f"rows 0..{rows} of the {W}x{H} image ({sample.size / 1e6:.1f} Mpixel), 1 thread"
 
 
+def oracle_images_parallel(imgs: list) -> dict:
+    """The oracle once per image, one image per thread on every host core (the
+    images are independent; the ctypes call releases the GIL)."""
+    import concurrent.futures as cf
+
+    import oracle
+    cores = os.cpu_count() or 1
+    oracle.lib()
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(lambda im: oracle.canny_u8(im, LOW, HIGH), imgs))
+    dt = time.perf_counter() - t0
+    px = sum(im.size for im in imgs)
+    return {"value": round(px / dt / 1e6, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"all {len(imgs)} images ({px / 1e6:.1f} Mpixel), one image per thread"}
+
+
 def run_reference(args, rank: int, world: int) -> None:
     if rank != 0:
         return
@@ -215,7 +262,7 @@ def run_reference(args, rank: int, world: int) -> None:
 BATCH_N, BATCH_LO, BATCH_HI, BATCH_SEED = 1024, 64, 2048, 4000
 
 
-def measure_batched(steps: int) -> dict:
+def measure_batched(steps: int, cpu: bool = False) -> dict:
     """1024 images, sides log-uniform in [64, 2048]: one canny_run_batch call (a
     persistent graph-captured launch over all images' units) against a loop of
     canny_run_pitched calls on the same stream, inputs resident; outputs compared."""
@@ -271,25 +318,114 @@ def measure_batched(steps: int) -> dict:
     same = all(torch.equal(a, b) for a, b in zip(outs_b, outs_l))
     ctx.close()
     loop_ctx.close()
+    cpu_line = oracle_images_parallel(imgs) if cpu else None
     return {"images": BATCH_N, "sides": [BATCH_LO, BATCH_HI], "pixels": total,
             "batch_ms": round(res["batch"], 4), "loop_ms": round(res["loop"], 4),
             "batch_mpx_s": round(total / res["batch"] / 1e3, 1), "loop_mpx_s": round(total / res["loop"] / 1e3, 1),
             "speedup": round(res["loop"] / res["batch"], 2), "outputs_identical": bool(same),
-            "tuning": {"band": tune["band"], "ctas_per_sm": tune["ctas_per_sm"]}}
+            "tuning": {"band": tune["band"], "ctas_per_sm": tune["ctas_per_sm"]},
+            "cpu_baseline": cpu_line}
+
+
+# ------------------------------------------------------------------ the other image sizes
+def measure_configs() -> list:
+    """Per-image pipeline times on the smaller synthetic workloads: each run timed
+    alone with CUDA events (median), stage averages from the library's own events.
+    These images fit in the 129 MB L2 except 7680 x 4320 (66 MB in + out: mostly)."""
+    import torch
+
+    from paper_1710_07745_gb300 import canny, synth
+
+    cases = [("canny_int_512x512", synth.small, canny.CANNY_PATH_INT, 100),
+             ("canny_int_4096x4096", synth.medium, canny.CANNY_PATH_INT, 50),
+             ("canny_f32_4096x4096", synth.medium, canny.CANNY_PATH_F32, 50),
+             ("canny_int_7680x4320", synth.uhd, canny.CANNY_PATH_INT, 50)]
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    out = []
+    for name, gen, path, n in cases:
+        img = gen()
+        h, w = img.shape
+        d_in = torch.from_numpy(img).cuda()
+        d_out = torch.empty_like(d_in)
+        if path == canny.CANNY_PATH_INT:
+            ctx = canny.Canny(w, h, low=LOW, high=HIGH)
+        else:
+            ctx = canny.Canny(w, h, path=path, low=0.1, high=0.3, sigma=1.4, ksize=7)
+        for _ in range(10):
+            canny.canny_run(ctx.ctx, d_in.data_ptr(), d_out.data_ptr(), sp)
+        torch.cuda.synchronize()
+        canny.canny_enable_timing(ctx.ctx, True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for e0, e1 in ev:
+            e0.record(stream)
+            canny.canny_run(ctx.ctx, d_in.data_ptr(), d_out.data_ptr(), sp)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        tm = canny.canny_read_timing(ctx.ctx).as_dict()
+        canny.canny_enable_timing(ctx.ctx, False)
+        st = ctx.stats()
+        ms = statistics.median(e0.elapsed_time(e1) for e0, e1 in ev)
+        runs = max(1, tm["runs"])
+        out.append({"workload": name, "w": w, "h": h, "runs": n, "median_ms": round(ms, 4),
+                    "mpx_s": round(w * h / ms / 1e3, 1),
+                    "stencil_ms": round(tm["stencil_ms"] / runs, 4),
+                    "local_ms": round(tm["local_ms"] / runs, 4),
+                    "global_ms": round(tm["global_ms"] / runs, 4),
+                    "hyst_passes": int(st["hyst_passes"])})
+        ctx.close()
+        del d_in, d_out
+    return out
+
+
+def measure_float_on(d_in, d_out, name: str, n: int) -> dict:
+    """The float32 variant (sigma 1.4, 7 taps, thresholds 0.1 / 0.3 of the largest
+    strength) on an image already on the device: n runs timed with CUDA events."""
+    import torch
+
+    from paper_1710_07745_gb300 import canny
+
+    h, w = d_in.shape
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    ctx = canny.Canny(w, h, path=canny.CANNY_PATH_F32, low=0.1, high=0.3, sigma=1.4, ksize=7)
+    for _ in range(3):
+        canny.canny_run(ctx.ctx, d_in.data_ptr(), d_out.data_ptr(), sp)
+    torch.cuda.synchronize()
+    canny.canny_enable_timing(ctx.ctx, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n):
+        canny.canny_run(ctx.ctx, d_in.data_ptr(), d_out.data_ptr(), sp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    tm = canny.canny_read_timing(ctx.ctx).as_dict()
+    canny.canny_enable_timing(ctx.ctx, False)
+    st = ctx.stats()
+    ctx.close()
+    runs = max(1, tm["runs"])
+    return {"workload": name, "w": w, "h": h, "runs": n, "mean_ms": round(ms, 4),
+            "mpx_s": round(w * h / ms / 1e3, 1), "stencil_ms": round(tm["stencil_ms"] / runs, 4),
+            "global_ms": round(tm["global_ms"] / runs, 4), "hyst_passes": int(st["hyst_passes"])}
 
 
 # ------------------------------------------------------------------ serving
 SERVE_POOL, SERVE_LO, SERVE_HI, SERVE_SEED = 256, 128, 4096, 5000
 
 
-def measure_serving(n_requests: int, loads=(0.25, 0.5, 0.9), budget_gb: float = 16.0, streams: int = 3) -> dict:
+def measure_serving(n_requests: int, loads=(0.1, 0.25, 0.5, 0.9, 1.5), budget_gb: float = 16.0, streams: int = 3,
+                    max_trace_s: float = 8.0) -> dict:
     """Continuous-batching server on Poisson arrivals, sides log-uniform in [128, 4096].
 
     Request i carries image i mod 256 of a seeded pool (the sizes follow the stated
     distribution; the pixels repeat). Capacity is measured first with every request
-    arriving at once; the offered loads are fractions of it. The serial baseline
-    (one canny_run_pitched at a time) runs the 0.25-load trace on its first 5000
-    requests."""
+    arriving at once; the offered loads are fractions of it (above 1: overload, the
+    queue grows). Each load's trace has n_requests requests, or fewer when that
+    would span more than max_trace_s seconds of arrivals (at least 5000). The
+    serial baseline (one canny_run_pitched at a time) runs the second load's trace
+    on its first 5000 requests."""
     import concurrent.futures as cf
 
     import torch
@@ -327,13 +463,16 @@ def measure_serving(n_requests: int, loads=(0.25, 0.5, 0.9), budget_gb: float = 
               "pool_images": SERVE_POOL, "capacity_mpx_s": round(capacity, 1), "loads": []}
     for k, load in enumerate(loads):
         rate = load * capacity * 1e6 / mean_area        # requests per second
-        rep = canny.canny_serve(cfg(0), trace(n_requests, rate, 10 + k))
+        n = min(n_requests, max(5000, int(max_trace_s * rate)))
+        rep = canny.canny_serve(cfg(0), trace(n, rate, 10 + k))
         entry = summary(rep, load * capacity)
         entry["load"] = load
+        entry["requests"] = n
         result["loads"].append(entry)
-    rate = loads[0] * capacity * 1e6 / mean_area
-    ser = canny.canny_serve(cfg(1), trace(min(n_requests, 5000), rate, 10))
-    result["serial"] = dict(summary(ser, loads[0] * capacity), load=loads[0], requests=min(n_requests, 5000))
+    ls = loads[min(1, len(loads) - 1)]
+    rate = ls * capacity * 1e6 / mean_area
+    ser = canny.canny_serve(cfg(1), trace(min(n_requests, 5000), rate, 10 + min(1, len(loads) - 1)))
+    result["serial"] = dict(summary(ser, ls * capacity), load=ls, requests=min(n_requests, 5000))
     return result
 
 
@@ -347,7 +486,8 @@ def run_ours(args, rank: int, world: int) -> None:
     if args.size:
         W, H = (int(v) for v in args.size.lower().split("x"))
         N_OBJ = synth.objects_for_area(W, H)
-        WORKLOAD = f"canny_int_{W}x{H}"
+    if args.size or args.path != "int":
+        WORKLOAD = f"canny_{args.path}_{W}x{H}"
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     peaks = measured_peaks()
@@ -356,7 +496,10 @@ def run_ours(args, rank: int, world: int) -> None:
     d_out = torch.empty_like(d_in)
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
-    ctx = canny.Canny(W, H, low=LOW, high=HIGH)
+    if args.path == "int":
+        ctx = canny.Canny(W, H, low=LOW, high=HIGH)
+    else:   # float32 variant (profiling runs): sigma 1.4, 7 taps, thresholds 0.1 / 0.3 of the largest strength
+        ctx = canny.Canny(W, H, path=canny.CANNY_PATH_F32, low=0.1, high=0.3, sigma=1.4, ksize=7)
 
     for _ in range(max(3, args.warmup)):
         ctx.run(d_in, d_out, stream)
@@ -401,23 +544,41 @@ def run_ours(args, rank: int, world: int) -> None:
 
     e2e = None
     if not args.no_e2e:
-        # end to end through the C ABI on pinned host buffers: H2D + pipeline + D2H every step
-        h_in = torch.from_numpy(img).pin_memory()
-        h_out = torch.empty_like(h_in).pin_memory()
-        for _ in range(2):
-            canny.canny_run_host(ctx.ctx, h_in.data_ptr(), W, h_out.data_ptr(), W, W, H, sp)
-        e2e_steps = max(1, min(args.steps, 5))
+        # end to end through the C ABI on pinned host buffers: every step uploads its
+        # frame, runs the pipeline and downloads the edge map; canny_run_frames overlaps
+        # consecutive steps (upload i+1 / pipeline i / download i-1)
+        h_in = [torch.from_numpy(img).pin_memory() for _ in range(2)]
+        h_out = [torch.empty_like(h_in[0]).pin_memory() for _ in range(2)]
+        e2e_steps = max(4, min(args.steps, 10))
+        ins = [h_in[i % 2].data_ptr() for i in range(e2e_steps)]
+        outs = [h_out[i % 2].data_ptr() for i in range(e2e_steps)]
+        canny.canny_run_frames(ctx.ctx, ins[:2], W, outs[:2], W, W, H, sp)      # builds the frame graphs
         barrier(world)
         t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            canny.canny_run_host(ctx.ctx, h_in.data_ptr(), W, h_out.data_ptr(), W, W, H, sp)
+        canny.canny_run_frames(ctx.ctx, ins, W, outs, W, W, H, sp)
         e2e_s = max_over_ranks(time.perf_counter() - t0, world)
-        if not np.array_equal(h_out[:64].numpy(), d_out[:64].cpu().numpy()):
+        ref = d_out[:64].cpu().numpy()
+        if not all(np.array_equal(o[:64].numpy(), ref) for o in h_out):
             raise RuntimeError("host-buffer run differs from device run")
+        # one call per image (canny_run_host: upload, pipeline, download, no overlap)
+        for _ in range(2):
+            canny.canny_run_host(ctx.ctx, ins[0], W, outs[0], W, W, H, sp)
+        single_steps = max(1, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for i in range(single_steps):
+            canny.canny_run_host(ctx.ctx, ins[i % 2], W, outs[i % 2], W, W, H, sp)
+        single_s = max_over_ranks(time.perf_counter() - t0, world)
         e2e = {"value": round(world * e2e_steps * px / e2e_s / 1e6, 1), "unit": UNIT,
-               "h2d_bytes_per_step": px, "d2h_bytes_per_step": px, "steps": e2e_steps}
+               "h2d_bytes_per_step": px, "d2h_bytes_per_step": px, "steps": e2e_steps,
+               "api": "canny_run_frames (pinned host buffers)",
+               "single_call": {"value": round(world * single_steps * px / single_s / 1e6, 1),
+                               "api": "canny_run_host", "steps": single_steps}}
 
-    batched = None if args.no_batch else measure_batched(max(3, min(args.steps, 10)))
+    configs = None if args.no_configs else measure_configs()
+    if configs is not None:
+        configs.append(measure_float_on(d_in, d_out, f"canny_f32_{W}x{H}", 10))
+    batched = None if args.no_batch else measure_batched(max(3, min(args.steps, 10)),
+                                                          cpu=rank == 0 and not args.no_cpu)
     serving = None if args.no_serve else measure_serving(args.serve_requests)
     if rank != 0:
         ctx.close()
@@ -432,16 +593,18 @@ def run_ours(args, rank: int, world: int) -> None:
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-        "data": "synthetic", "config": config(),
+        "data": "synthetic", "config": config({"path": "integer" if args.path == "int" else "float32"}),
         "roofline": {"kernel": "k1_fused_kernel (Gauss/Sobel/NMS/threshold + tile-local hysteresis)",
                      "bound": "hbm", "achieved": round(k1_gbs, 1), "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": round(k1_gbs / peaks["hbm_gbs"], 4),
                      "traffic": k1_traffic(W, H), "peak_source": peaks["source"],
                      "bytes_per_launch": K1_BYTES_PER_PX * px},
+        "alu_roofline": alu_roofline(px, k1_ms, peaks["hbm_gbs"], clk),
         "pipeline_roofline": {"achieved": round(pipe_gbs, 1), "unit": "GB/s",
                               "bytes_per_px": PIPE_BYTES_PER_PX,
                               "frac": round(pipe_gbs / peaks["hbm_gbs"], 4)},
         "stages": stages, "dominant_stage": dominant,
+        "configs": configs,
         "batched": batched,
         "serving": serving,
         "cpu_baseline": cpu,
@@ -464,6 +627,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-loop leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-configs", action="store_true", help="skip the smaller-image leg")
+    ap.add_argument("--path", choices=["int", "f32"], default="int",
+                    help="f32: time the float32 variant instead (profiling runs)")
     ap.add_argument("--serve-requests", type=int, default=100000)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -144,6 +144,24 @@ canny_status canny_run_host(canny_ctx *ctx, const uint8_t *h_in, int in_pitch, u
                             int out_pitch, int w, int h, void *stream);
 
 /*
+ * A sequence of n frames of one size w x h on host buffers (video): frame i is
+ * read from h_in[i] (h rows of in_pitch bytes) and its edge map written to
+ * h_out[i] (h rows of out_pitch bytes). The paper points to real-time video
+ * processing on multicore processors (Sec. 2.1, ref. [14]) and to high
+ * resolution image and video work (Sec. 4); here consecutive frames overlap:
+ * the upload of frame i+1, the pipeline on frame i and the download of frame
+ * i-1 run at the same time on three streams, and each frame's pipeline is one
+ * replay of a CUDA graph built once per frame size (two device slots).
+ * Each output equals canny_run_host on that frame. Pinned host buffers are
+ * needed for the copies to overlap. Returns after the last edge map is in
+ * h_out; CANNY_ENOCONVERGE if any frame reached the hysteresis pass cap.
+ * Device buffers, streams and graphs are owned by the context. The work on
+ * `stream` (the pipelines) starts after what is already queued on it.
+ */
+canny_status canny_run_frames(canny_ctx *ctx, int n, const uint8_t *const *h_in, int in_pitch,
+                              uint8_t *const *h_out, int out_pitch, int w, int h, void *stream);
+
+/*
  * Steps 1-3 and the double threshold only: the class map before hysteresis,
  * 0 (none), 1 (weak) or 2 (strong) per pixel, into img->d_out.
  */

@@ -96,6 +96,8 @@ SIGNATURES = {
     "canny_run_batch": ([_P, ctypes.c_int, ctypes.POINTER(canny_image), _P], ctypes.c_int),
     "canny_run_host": ([_P, _P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P],
                        ctypes.c_int),
+    "canny_run_frames": ([_P, ctypes.c_int, ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P), ctypes.c_int,
+                          ctypes.c_int, ctypes.c_int, _P], ctypes.c_int),
     "canny_classify": ([_P, ctypes.POINTER(canny_image), _P], ctypes.c_int),
     "canny_hysteresis": ([_P, ctypes.POINTER(canny_image), _P], ctypes.c_int),
     "canny_magnitude_f32": ([_P, ctypes.POINTER(canny_image), _P, ctypes.c_int, _P, _P],
@@ -179,6 +181,18 @@ def canny_run_batch(ctx: int, imgs: Sequence[canny_image], stream: int = 0) -> N
 def canny_run_host(ctx: int, h_in: int, in_pitch: int, h_out: int, out_pitch: int, w: int, h: int,
                    stream: int = 0) -> None:
     _check(load().canny_run_host(ctx, h_in, in_pitch, h_out, out_pitch, w, h, stream), "canny_run_host")
+
+
+def canny_run_frames(ctx: int, h_in: Sequence[int], in_pitch: int, h_out: Sequence[int], out_pitch: int,
+                     w: int, h: int, stream: int = 0) -> None:
+    """n frames on host buffers (addresses h_in[i] / h_out[i]), uploads, pipelines and
+    downloads of consecutive frames overlapped."""
+    n = len(h_in)
+    if len(h_out) != n:
+        raise ValueError("h_in and h_out differ in length")
+    arr_in = (_P * max(n, 1))(*h_in)
+    arr_out = (_P * max(n, 1))(*h_out)
+    _check(load().canny_run_frames(ctx, n, arr_in, in_pitch, arr_out, out_pitch, w, h, stream), "canny_run_frames")
 
 
 def canny_classify(ctx: int, img: canny_image, stream: int = 0) -> None:

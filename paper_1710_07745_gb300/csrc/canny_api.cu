@@ -60,6 +60,19 @@ struct canny_ctx {
     unsigned char *d_blob = nullptr;   // BatchHeader + BatchImage[cap] + CUtensorMap[cap]
     uint32_t blob_cap = 0;
     std::unordered_map<std::string, CUtensorMap> tmaps;   // encoded input maps, by (pointer, size, pitch)
+
+    // frame sequences (canny_run_frames): two device slots, each with a graph of one
+    // frame's whole pipeline; uploads and downloads run on streams of their own
+    struct FrameSlot {
+        uint8_t *d_in = nullptr, *d_out = nullptr;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaEvent_t up = nullptr, comp = nullptr, down = nullptr;
+    } fslots[2];
+    int frame_w = 0, frame_h = 0, frame_pitch = 0;   // size the slot buffers hold; graphs valid if exec set
+    cudaStream_t s_up = nullptr, s_down = nullptr, s_cap = nullptr;
+    cudaEvent_t frame_start = nullptr;
+    uint32_t *d_frame_err = nullptr;                  // OR of the frames' hysteresis error bits
 };
 
 namespace {
@@ -98,8 +111,31 @@ uint32_t tiles_of(int w, int h)
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Frame graphs hold the scratch pointers and the band height: dropped with the batch graphs.
+void drop_frame_graphs(canny_ctx *c)
+{
+    for (auto &f : c->fslots) {
+        if (f.exec) cudaGraphExecDestroy(f.exec);
+        if (f.graph) cudaGraphDestroy(f.graph);
+        f.exec = nullptr;
+        f.graph = nullptr;
+    }
+}
+
+void free_frames(canny_ctx *c)
+{
+    drop_frame_graphs(c);
+    for (auto &f : c->fslots) {
+        if (f.d_in) cudaFree(f.d_in);
+        if (f.d_out) cudaFree(f.d_out);
+        f.d_in = f.d_out = nullptr;
+    }
+    c->frame_w = c->frame_h = c->frame_pitch = 0;
+}
+
 void drop_batch_graphs(canny_ctx *c)
 {
+    drop_frame_graphs(c);
     for (auto &sl : c->slots) {
         if (sl.exec) cudaGraphExecDestroy(sl.exec);
         if (sl.graph) cudaGraphDestroy(sl.graph);
@@ -216,6 +252,13 @@ canny_status run_stencil(canny_ctx *c, const canny_image *im, cudaStream_t s)
     if (c->p.path == CANNY_PATH_INT)
         return from_cuda(launch_k1_classify_u8(im->d_in, im->in_pitch, im->d_out, im->out_pitch,
                                                im->w, im->h, c->it, &c->hs.state->error, s, c->band));
+    if (!c->mag) {
+        // the stored strength image is only needed for a class map of the float path
+        if (cudaMalloc((void **)&c->mag, sizeof(float) * (size_t)c->max_w * c->max_h) != cudaSuccess) {
+            cudaGetLastError();
+            return CANNY_ENOMEM;
+        }
+    }
     cudaError_t e = cudaMemsetAsync(c->d_max, 0, sizeof(float), s);
     if (e == cudaSuccess)
         e = launch_k1f_magnitude(im->d_in, im->in_pitch, c->mag, im->w, im->w, im->h, c->fp, true,
@@ -237,6 +280,16 @@ HystImage hyst_image(const canny_image *im, uint32_t base)
     h.nty = (im->h + HT - 1) / HT;
     h.tile_base = base;
     return h;
+}
+
+// Float path, Steps 1-4 up to the tile-local hysteresis: pass 1 finds the largest
+// squared strength, pass 2 recomputes the stencil and writes edges and tile state.
+canny_status run_float_fused(canny_ctx *c, const canny_image *im, const HystImage &himg, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(c->d_max, 0, sizeof(float), s);
+    if (e == cudaSuccess) e = launch_k1f_max(im->d_in, im->in_pitch, im->w, im->h, c->fp, c->d_max, s);
+    if (e == cudaSuccess) e = launch_k1f_edges(im->d_in, im->in_pitch, im->w, im->h, c->fp, c->d_max, c->hs, himg, s);
+    return from_cuda(e);
 }
 
 uint32_t max_passes_for(const canny_ctx *c, uint32_t ntiles)
@@ -272,13 +325,17 @@ canny_status run_one(canny_ctx *c, const canny_image *im, cudaStream_t s, bool s
             cudaEventRecord(ev[2], s);
             cudaEventRecord(ev[3], s);
         }
-    } else {
-        if (stencil) {
-            st = run_stencil(c, im, s);
-        } else {
-            st = from_cuda(cudaMemcpy2DAsync(im->d_out, im->out_pitch, im->d_in, im->in_pitch, im->w, im->h,
-                                             cudaMemcpyDeviceToDevice, s));
+    } else if (stencil) {
+        // float path: two stencil passes, the second fused with the tile-local fill
+        st = run_float_fused(c, im, himg, s);
+        if (st != CANNY_OK) return st;
+        if (ev) {
+            cudaEventRecord(ev[2], s);
+            cudaEventRecord(ev[3], s);
         }
+    } else {
+        st = from_cuda(cudaMemcpy2DAsync(im->d_out, im->out_pitch, im->d_in, im->in_pitch, im->w, im->h,
+                                         cudaMemcpyDeviceToDevice, s));
         if (st != CANNY_OK) return st;
         if (ev) cudaEventRecord(ev[2], s);
         st = from_cuda(launch_hyst_local_single(c->hs, himg, s));
@@ -516,8 +573,7 @@ canny_status canny_create(int max_w, int max_h, const canny_params *p, canny_ctx
     st = ensure_hyst(c, tiles_of(max_w, max_h), 1);
     if (st != CANNY_OK) { canny_destroy(c); return st; }
     if (p->path == CANNY_PATH_F32) {
-        e = cudaMalloc((void **)&c->mag, sizeof(float) * (size_t)max_w * max_h);
-        if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_max, sizeof(float));
+        e = cudaMalloc((void **)&c->d_max, sizeof(float));
         if (e != cudaSuccess) { cudaGetLastError(); canny_destroy(c); return CANNY_ENOMEM; }
     }
     *out = c;
@@ -543,6 +599,17 @@ void canny_destroy(canny_ctx *c)
         if (sl.done) cudaEventDestroy(sl.done);
     }
     if (c->d_blob) cudaFree(c->d_blob);
+    free_frames(c);
+    for (auto &f : c->fslots) {
+        if (f.up) cudaEventDestroy(f.up);
+        if (f.comp) cudaEventDestroy(f.comp);
+        if (f.down) cudaEventDestroy(f.down);
+    }
+    if (c->frame_start) cudaEventDestroy(c->frame_start);
+    if (c->s_up) cudaStreamDestroy(c->s_up);
+    if (c->s_down) cudaStreamDestroy(c->s_down);
+    if (c->s_cap) cudaStreamDestroy(c->s_cap);
+    if (c->d_frame_err) cudaFree(c->d_frame_err);
     delete c;
 }
 
@@ -608,13 +675,14 @@ canny_status canny_run_batch(canny_ctx *c, int n, const canny_image *imgs, void 
     if (e != cudaSuccess) return from_cuda(e);
     st = from_cuda(hyst_reset(c->hs, ntiles, nimg, max_passes_for(c, ntiles), s));
     if (st != CANNY_OK) return st;
+    base = 0;
     for (int i = 0; i < n; ++i) {
-        if (imgs[i].w == 0 || imgs[i].h == 0) continue;
-        st = run_stencil(c, &imgs[i], s);
+        const uint32_t t = tiles_of(imgs[i].w, imgs[i].h);
+        if (!t) continue;
+        st = run_float_fused(c, &imgs[i], hyst_image(&imgs[i], base), s);
         if (st != CANNY_OK) return st;
+        base += t;
     }
-    st = from_cuda(launch_hyst_local_batch(c->hs, ntiles, nimg, s));
-    if (st != CANNY_OK) return st;
     return run_global(c, s);
 }
 
@@ -753,7 +821,7 @@ canny_status canny_autotune_batch(canny_ctx *c, int n, const canny_image *imgs, 
     cudaDeviceProp prop;
     cudaGetDevice(&dev);
     if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return CANNY_ECUDA;
-    char key[256];
+    char key[320];   // device name (at most 256) + the size classes
     snprintf(key, sizeof(key), "%s|int|n%d|a%d", prop.name, (int)log2((double)nimg), (int)log2((double)px / nimg));
     canny_tuning best = {};
     if (cache_path && *cache_path) {
@@ -822,6 +890,154 @@ canny_status canny_autotune_batch(canny_ctx *c, int n, const canny_image *imgs, 
     if (st != CANNY_OK) return st;
     if (out) *out = best;
     return CANNY_OK;
+}
+
+// ---------------------------------------------------------------- frame sequences
+namespace {
+
+// Streams, events and the error word, created once.
+canny_status ensure_frame_streams(canny_ctx *c)
+{
+    if (c->s_up) return CANNY_OK;
+    cudaError_t e = cudaStreamCreateWithFlags(&c->s_up, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->s_down, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->s_cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->frame_start, cudaEventDisableTiming);
+    for (auto &f : c->fslots) {
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f.up, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f.comp, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f.down, cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_frame_err, sizeof(uint32_t));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return from_cuda(e);
+    }
+    return CANNY_OK;
+}
+
+// One frame's pipeline on slot f as a graph: { reset -> stencil (+ tile fill) }
+// captured as a child graph, then the global-pass while-loop, then the error OR.
+canny_status build_frame_graph(canny_ctx *c, canny_ctx::FrameSlot &f)
+{
+    const canny_image im = {f.d_in, f.d_out, c->frame_w, c->frame_h, c->frame_pitch, c->frame_pitch};
+    const uint32_t ntiles = tiles_of(im.w, im.h);
+    const HystImage himg = hyst_image(&im, 0);
+    cudaGraph_t body = nullptr, g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->s_cap, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return from_cuda(e);
+    canny_status st = from_cuda(hyst_reset(c->hs, ntiles, 1, max_passes_for(c, ntiles), c->s_cap, &himg));
+    if (st == CANNY_OK) {
+        if (c->p.path == CANNY_PATH_INT)
+            st = from_cuda(launch_k1_edges_u8(im.d_in, im.in_pitch, im.w, im.h, c->it, c->hs, himg, c->s_cap, c->band));
+        else
+            st = run_float_fused(c, &im, himg, c->s_cap);
+    }
+    e = cudaStreamEndCapture(c->s_cap, &body);
+    if (st == CANNY_OK && e != cudaSuccess) st = from_cuda(e);
+    if (st != CANNY_OK) {
+        cudaGetLastError();
+        if (body) cudaGraphDestroy(body);
+        return st;
+    }
+    cudaGraphNode_t child, loop, eor;
+    e = cudaGraphCreate(&g, 0);
+    if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&child, g, nullptr, 0, body);
+    if (e == cudaSuccess) e = hyst_add_loop(g, &child, 1, c->hs, &loop);
+    if (e == cudaSuccess) e = hyst_add_error_or(g, &loop, 1, c->hs, c->d_frame_err, &eor);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&f.exec, g, 0);
+    cudaGraphDestroy(body);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        f.exec = nullptr;
+        return from_cuda(e);
+    }
+    f.graph = g;
+    return CANNY_OK;
+}
+
+canny_status ensure_frames(canny_ctx *c, int w, int h)
+{
+    canny_status st = ensure_frame_streams(c);
+    if (st != CANNY_OK) return st;
+    const int pitch = (w + 15) / 16 * 16;                 // 16-byte rows: the TMA path
+    const size_t need = (size_t)pitch * (size_t)h;
+    if ((size_t)c->frame_pitch * (size_t)c->frame_h < need || !c->fslots[0].d_in) {
+        free_frames(c);
+        for (auto &f : c->fslots) {
+            if (cudaMalloc((void **)&f.d_in, need) != cudaSuccess || cudaMalloc((void **)&f.d_out, need) != cudaSuccess) {
+                cudaGetLastError();
+                free_frames(c);
+                return CANNY_ENOMEM;
+            }
+        }
+    } else if (c->frame_w != w || c->frame_h != h) {
+        drop_frame_graphs(c);
+    }
+    c->frame_w = w;
+    c->frame_h = h;
+    c->frame_pitch = pitch;
+    for (auto &f : c->fslots) {
+        if (f.exec) continue;
+        st = build_frame_graph(c, f);
+        if (st != CANNY_OK) return st;
+    }
+    return CANNY_OK;
+}
+
+}  // namespace
+
+canny_status canny_run_frames(canny_ctx *c, int n, const uint8_t *const *h_in, int in_pitch,
+                              uint8_t *const *h_out, int out_pitch, int w, int h, void *stream)
+{
+    if (!c || n < 0 || w < 0 || h < 0 || w > c->max_w || h > c->max_h) return CANNY_EINVAL;
+    if (n > 0 && (!h_in || !h_out)) return CANNY_EINVAL;
+    if (n == 0 || w == 0 || h == 0) return CANNY_OK;
+    if (in_pitch < w || out_pitch < w) return CANNY_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!h_in[i] || !h_out[i]) return CANNY_EINVAL;
+    const uint32_t ntiles = tiles_of(w, h);
+    canny_status st = ensure_hyst(c, ntiles, 1);
+    if (st != CANNY_OK) return st;
+    st = ensure_frames(c, w, h);
+    if (st != CANNY_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int pitch = c->frame_pitch;
+    cudaError_t e = cudaMemsetAsync(c->d_frame_err, 0, sizeof(uint32_t), s);
+    // the copy streams start after everything already queued on s
+    if (e == cudaSuccess) e = cudaEventRecord(c->frame_start, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_up, c->frame_start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_down, c->frame_start, 0);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        canny_ctx::FrameSlot &f = c->fslots[i & 1];
+        // upload frame i once the pipeline of frame i-2 has read this slot's input
+        if (i >= 2) e = cudaStreamWaitEvent(c->s_up, f.comp, 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(f.d_in, pitch, h_in[i], in_pitch, w, h, cudaMemcpyHostToDevice, c->s_up);
+        if (e == cudaSuccess) e = cudaEventRecord(f.up, c->s_up);
+        // pipeline of frame i once it is uploaded and frame i-2's edges are downloaded
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, f.up, 0);
+        if (e == cudaSuccess && i >= 2) e = cudaStreamWaitEvent(s, f.down, 0);
+        if (e == cudaSuccess) e = cudaGraphLaunch(f.exec, s);
+        if (e == cudaSuccess) e = cudaEventRecord(f.comp, s);
+        // download frame i's edges
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_down, f.comp, 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(h_out[i], out_pitch, f.d_out, pitch, w, h, cudaMemcpyDeviceToHost, c->s_down);
+        if (e == cudaSuccess) e = cudaEventRecord(f.down, c->s_down);
+    }
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->fslots[(n - 1) & 1].down, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_state, c->d_frame_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return from_cuda(e);
+    c->last = canny_stats{};
+    c->last.images = n;
+    c->last.pixels = (int64_t)n * w * h;
+    c->last.tiles = ntiles;
+    c->last_stream = s;
+    const uint32_t err = c->h_state[0];
+    return (err & 2u) ? CANNY_ECUDA : (err & 1u) ? CANNY_ENOCONVERGE : CANNY_OK;
 }
 
 canny_status canny_get_stats(canny_ctx *c, canny_stats *out)

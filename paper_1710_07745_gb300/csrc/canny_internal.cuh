@@ -124,6 +124,16 @@ cudaError_t launch_k1f_classify(const float *mag_nms, int mag_pitch, uint8_t *cl
                                 int w, int h, const float *d_max, float lo_frac, float hi_frac,
                                 cudaStream_t s);
 
+// ---------------------------------------------------------------- launchers (k1_fused_f32.cu)
+// Float path pass 1: the image's largest squared strength, atomicMax'ed into
+// *d_smax (as float bits; the caller zeroes it first).
+cudaError_t launch_k1f_max(const uint8_t *in, int in_pitch, int w, int h, const FloatParams &fp, float *d_smax,
+                           cudaStream_t s);
+// Float path pass 2: Steps 1-4 up to the tile-local hysteresis with thresholds
+// relative to sqrt(*d_smax): edges into img.map, tile state into hs (after hyst_reset).
+cudaError_t launch_k1f_edges(const uint8_t *in, int in_pitch, int w, int h, const FloatParams &fp,
+                             const float *d_smax, const HystScratch &hs, HystImage img, cudaStream_t s);
+
 // ---------------------------------------------------------------- launchers (hysteresis.cu)
 // Local fill over all tiles of one image whose class map is already in img.map.
 cudaError_t launch_hyst_local_single(const HystScratch &hs, HystImage img, cudaStream_t s);
@@ -144,6 +154,10 @@ cudaError_t hyst_build_graph(const HystScratch &hs, cudaGraph_t *graph_out, cuda
 // Graph pieces for the batch graph.
 cudaError_t hyst_add_loop(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, const HystScratch &hs,
                           cudaGraphNode_t *out);
+// Append { *acc |= state->error } after the given nodes (errors of one run of a
+// sequence survive the next run's reset).
+cudaError_t hyst_add_error_or(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, const HystScratch &hs,
+                              uint32_t *acc, cudaGraphNode_t *out);
 cudaError_t hyst_add_init_from_header(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps,
                                       const HystScratch &hs, const BatchHeader *hdr, cudaGraphNode_t *out);
 

@@ -203,6 +203,13 @@ __global__ void hyst_init_from_header_kernel(HystState *st, const BatchHeader *h
     *st = s;
 }
 
+// OR a run's error bits into an accumulator that outlives the next reset.
+__global__ void hyst_error_or_kernel(const HystState *st, uint32_t *acc)
+{
+    const uint32_t e = st->error;
+    if (e) atomicOr(acc, e);
+}
+
 }  // namespace
 
 int hyst_pass_grid()
@@ -280,6 +287,20 @@ cudaError_t hyst_add_loop(cudaGraph_t g, const cudaGraphNode_t *deps, size_t nde
     kp.kernelParams = args;
     cudaGraphNode_t knode;
     return cudaGraphAddKernelNode(&knode, body, nullptr, 0, &kp);
+}
+
+// Append { *acc |= state->error } to graph g after the given nodes.
+cudaError_t hyst_add_error_or(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, const HystScratch &hs,
+                              uint32_t *acc, cudaGraphNode_t *out)
+{
+    const HystState *st = hs.state;
+    void *args[] = {(void *)&st, (void *)&acc};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void *)hyst_error_or_kernel;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(1);
+    kp.kernelParams = args;
+    return cudaGraphAddKernelNode(out, g, deps, ndeps, &kp);
 }
 
 // Append the control-block reset that reads its sizes from a batch header.

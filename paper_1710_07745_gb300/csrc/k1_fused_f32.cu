@@ -1,0 +1,310 @@
+// k1_fused_f32.cu -- the float32 variant of Steps 1-4 (paper Sec. 2.2.1) without a
+// stored strength image. The thresholds are fractions of the image's largest
+// strength, a grid-wide dependency, so the stencil runs twice over the input:
+//
+//   pass 1 (k1f_max_kernel): Gaussian -> Sobel -> squared strength s = gx^2 + gy^2
+//     for every pixel, reduced to the image maximum smax (one atomicMax per CTA);
+//   pass 2 (k1f_edges_kernel): the same stencil again, then on the few pixels
+//     that can pass the low threshold: strength M = sqrt(s), direction sector,
+//     suppression, double threshold; then the tile flood fill of the hysteresis
+//     on 32 x 32 tiles and the 0/255 edge bytes, tile border masks and pending
+//     bitmaps for the global passes.
+//
+// Each pass reads the input byte once; pass 2 writes the edge byte once. The
+// largest strength is Mmax = sqrt(smax) exactly: a correctly rounded square
+// root is monotonic, so the largest root is the root of the largest s.
+//
+// Arithmetic follows the float32 definition operation by operation (no
+// contraction except where a product by 2 is exact): horizontal pass then
+// vertical pass, taps accumulated from the first, replicate border; Sobel
+// columns summed top to bottom; s = (gx*gx) + (gy*gy); M = sqrt_rn(s).
+//
+// A CTA of 256 threads covers a block of 64 rows x 128 columns (2 x 4 tiles)
+// and stages it in shared memory: input (as float, with a halo of R + 2 rows
+// and R + 2 (rounded up to 4) columns, R = ksize / 2), the horizontal pass,
+// the smoothed image S, the squared strengths (with a 1-pixel ring for the
+// suppression). Buffers alias once they are dead, so a 7-tap kernel needs
+// 80 KB and two CTAs fit on an SM.
+#include "hyst_tile.cuh"
+
+namespace canny {
+
+namespace {
+
+constexpr int FB_W = 128, FB_H = 64;            // output block
+constexpr int FB_THREADS = 256;
+constexpr int FB_WARPS = FB_THREADS / 32;
+constexpr int FB_TX = FB_W / HT, FB_TY = FB_H / HT;
+static_assert(FB_TX * FB_TY == FB_WARPS, "one warp per tile in the flood stage");
+
+struct Geometry {
+    int R, padx, pady;         // Gaussian radius; input halo (columns rounded up to 4)
+    int IY, IX;                // staged input rows / columns
+    int SX, SY;                // smoothed image: columns x0-2 .. x0+FB_W+1, rows y0-2 .. y0+FB_H+1
+    int MX, MY;                // squared strength with its ring: x0-1 .. x0+FB_W, y0-1 .. y0+FB_H
+    int region0, region1;      // floats: input then S; horizontal pass then s
+};
+
+__host__ __device__ inline Geometry geometry(int ksize)
+{
+    Geometry g;
+    g.R = ksize / 2;
+    g.pady = g.R + 2;
+    g.padx = (g.R + 2 + 3) / 4 * 4;
+    g.IY = FB_H + 2 * g.pady;
+    g.IX = FB_W + 2 * g.padx;
+    g.SX = FB_W + 4;
+    g.SY = FB_H + 4;
+    g.MX = FB_W + 2;
+    g.MY = FB_H + 2;
+    const int a = g.IY * g.IX, b = g.SY * g.SX, c = g.IY * g.SX, d = g.MY * g.MX;
+    g.region0 = a > b ? a : b;
+    g.region1 = c > d ? c : d;
+    return g;
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+
+// One Gaussian tap sum: taps[0]*src[0] + taps[1]*src[stride] + ..., each product
+// and each sum rounded. KS = 0: run-time ksize (taps read by index).
+template <int KS>
+__device__ __forceinline__ float tap_sum(const FloatParams &fp, const float *src, int stride)
+{
+    if (KS > 0) {
+        float acc = fmul(fp.taps[0], src[0]);
+#pragma unroll
+        for (int k = 1; k < KS; ++k) acc = fadd(acc, fmul(fp.taps[k], src[k * stride]));
+        return acc;
+    }
+    float acc = fmul(fp.taps[0], src[0]);
+    for (int k = 1; k < fp.ksize; ++k) acc = fadd(acc, fmul(fp.taps[k], src[k * stride]));
+    return acc;
+}
+
+// Sobel at the S entry (r, c) of a row-major S block with row stride sx, in the
+// definition's order; a + 2*b is formed as fma(2, b, a), which is the same
+// single rounding since 2*b is exact.
+__device__ __forceinline__ void sobel_at(const float *S, int sx, int r, int c, float &gx, float &gy)
+{
+    const float *u = S + (r - 1) * sx + c, *m = S + r * sx + c, *d = S + (r + 1) * sx + c;
+    float right = __fmaf_rn(2.f, m[1], u[1]);
+    right = fadd(right, d[1]);
+    float left = __fmaf_rn(2.f, m[-1], u[-1]);
+    left = fadd(left, d[-1]);
+    float down = __fmaf_rn(2.f, d[0], d[-1]);
+    down = fadd(down, d[1]);
+    float up = __fmaf_rn(2.f, u[0], u[-1]);
+    up = fadd(up, u[1]);
+    gx = fadd(right, -left);
+    gy = fadd(down, -up);
+}
+
+__device__ __forceinline__ float strength2(float gx, float gy) { return fadd(fmul(gx, gx), fmul(gy, gy)); }
+
+// Steps 1-2 for one block up to the smoothed image S (left in region 0).
+template <int KS>
+__device__ __forceinline__ void smooth_block(const uint8_t *__restrict__ in, int in_pitch, int w, int h,
+                                             const FloatParams &fp, const Geometry &g, int x0, int y0,
+                                             float *r0, float *r1)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ox = x0 - g.padx, oy = y0 - g.pady;
+    float *I_s = r0, *H_s = r1;
+    // stage the input, replicate border by clamping
+    for (int r = warp; r < g.IY; r += FB_WARPS) {
+        const uint8_t *row = in + (int64_t)clampi(oy + r, 0, h - 1) * in_pitch;
+        for (int c = lane; c < g.IX; c += 32) I_s[r * g.IX + c] = (float)__ldg(row + clampi(ox + c, 0, w - 1));
+    }
+    __syncthreads();
+    // horizontal pass at columns clamp(x0 - 2 + c), for every staged row
+    for (int r = warp; r < g.IY; r += FB_WARPS) {
+        for (int c = lane; c < g.SX; c += 32) {
+            const int X = clampi(x0 - 2 + c, 0, w - 1);
+            H_s[r * g.SX + c] = tap_sum<KS>(fp, I_s + r * g.IX + (X - g.R - ox), 1);
+        }
+    }
+    __syncthreads();
+    // vertical pass at rows clamp(y0 - 2 + r): S(clamp(x), clamp(y)) into region 0
+    float *S_s = r0;
+    for (int r = warp; r < g.SY; r += FB_WARPS) {
+        const int Y = clampi(y0 - 2 + r, 0, h - 1);
+        const float *src = H_s + (Y - g.R - oy) * g.SX;
+        for (int c = lane; c < g.SX; c += 32) S_s[r * g.SX + c] = tap_sum<KS>(fp, src + c, g.SX);
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- pass 1
+template <int KS>
+__global__ void __launch_bounds__(FB_THREADS, 2)
+k1f_max_kernel(const uint8_t *__restrict__ in, int in_pitch, int w, int h, FloatParams fp, float *d_smax)
+{
+    extern __shared__ __align__(16) float fsm[];
+    const Geometry g = geometry(KS > 0 ? KS : fp.ksize);
+    float *r0 = fsm, *r1 = fsm + g.region0;
+    const int x0 = blockIdx.x * FB_W, y0 = blockIdx.y * FB_H;
+    smooth_block<KS>(in, in_pitch, w, h, fp, g, x0, y0, r0, r1);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float best = 0.f;
+    for (int r = warp; r < FB_H; r += FB_WARPS) {
+        if (y0 + r >= h) break;
+        for (int c = lane; c < FB_W; c += 32) {
+            if (x0 + c >= w) break;
+            float gx, gy;
+            sobel_at(r0, g.SX, r + 2, c + 2, gx, gy);
+            best = fmaxf(best, strength2(gx, gy));
+        }
+    }
+    __shared__ float red[FB_WARPS];
+    for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(tile::FULL, best, o));
+    if (lane == 0) red[warp] = best;
+    __syncthreads();
+    if (tid == 0) {
+        float m = 0.f;
+        for (int k = 0; k < FB_WARPS; ++k) m = fmaxf(m, red[k]);
+        // non-negative floats order like their bit patterns
+        atomicMax(reinterpret_cast<unsigned int *>(d_smax), __float_as_uint(m));
+    }
+}
+
+// ---------------------------------------------------------------- pass 2
+template <int KS>
+__global__ void __launch_bounds__(FB_THREADS, 2)
+k1f_edges_kernel(const uint8_t *__restrict__ in, int in_pitch, int w, int h, FloatParams fp,
+                 const float *__restrict__ d_smax, HystScratch hs, HystImage img)
+{
+    extern __shared__ __align__(16) float fsm[];
+    __shared__ uint32_t cand_s[FB_H][FB_TX], strong_s[FB_H][FB_TX];
+    const Geometry g = geometry(KS > 0 ? KS : fp.ksize);
+    float *r0 = fsm, *r1 = fsm + g.region0;
+    const int x0 = blockIdx.x * FB_W, y0 = blockIdx.y * FB_H;
+    smooth_block<KS>(in, in_pitch, w, h, fp, g, x0, y0, r0, r1);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    // squared strength on the block and its ring (0 outside the image) into region 1
+    const float *S_s = r0;
+    float *s_s = r1;
+    for (int r = warp; r < g.MY; r += FB_WARPS) {
+        const int Y = y0 - 1 + r;
+        for (int c = lane; c < g.MX; c += 32) {
+            const int X = x0 - 1 + c;
+            float s = 0.f;
+            if (X >= 0 && X < w && Y >= 0 && Y < h) {
+                float gx, gy;
+                sobel_at(S_s, g.SX, r + 1, c + 1, gx, gy);
+                s = strength2(gx, gy);
+            }
+            s_s[r * g.MX + c] = s;
+        }
+    }
+    __syncthreads();
+
+    // thresholds: fractions of Mmax = sqrt(smax), float products as in the definition
+    const float mmax = __fsqrt_rn(*d_smax);
+    const float lo_t = fmul(fp.lo_frac, mmax), hi_t = fmul(fp.hi_frac, mmax);
+    const float t_min = fminf(lo_t, hi_t);
+    // necessary condition for sqrt_rn(s) > t_min: s > t_min^2 (1 - 2^-23); 1e-4 of slack
+    const float s_pre = fmul(fmul(t_min, t_min), 0.9999f);
+
+    // Step 3 + thresholds: one (row, tile column) per warp iteration, lane = column
+    for (int item = warp; item < FB_H * FB_TX; item += FB_WARPS) {
+        const int r = item / FB_TX, tc = item % FB_TX;
+        const int mc = 1 + HT * tc + lane, mr = r + 1;      // index in s_s
+        const float s = s_s[mr * g.MX + mc];
+        bool weak = false, strong = false;
+        if (s > s_pre) {
+            const float m = __fsqrt_rn(s);
+            float gx, gy;
+            sobel_at(S_s, g.SX, r + 2, mc + 1, gx, gy);
+            const float t = 0.41421356f, ax = fabsf(gx), ay = fabsf(gy);
+            int dn, dp;                                         // offsets of n- and n+ in s_s
+            if (ay < fmul(ax, t)) { dn = -1; dp = 1; }                                  // H
+            else if (ax < fmul(ay, t)) { dn = -g.MX; dp = g.MX; }                       // V
+            else if ((gx > 0.f && gy > 0.f) || (gx < 0.f && gy < 0.f)) { dn = -g.MX - 1; dp = g.MX + 1; }  // D
+            else { dn = g.MX - 1; dp = -g.MX + 1; }             // A: down-left / up-right
+            const float mn = __fsqrt_rn(s_s[mr * g.MX + mc + dn]);
+            const float mp = __fsqrt_rn(s_s[mr * g.MX + mc + dp]);
+            const bool keep = (m > mn) && (m >= mp);
+            strong = keep && m > hi_t;
+            weak = keep && (m > lo_t || strong);
+        }
+        const uint32_t wm = __ballot_sync(tile::FULL, weak), sm = __ballot_sync(tile::FULL, strong);
+        if (lane == 0) {
+            cand_s[r][tc] = wm;
+            strong_s[r][tc] = sm;
+        }
+    }
+    __syncthreads();
+
+    // Step 4, tile-local: warp k floods tile k of the block
+    const int txl = warp % FB_TX, tyl = warp / FB_TX;
+    const int tx = blockIdx.x * FB_TX + txl, ty = blockIdx.y * FB_TY + tyl;
+    if (tx < img.ntx && ty < img.nty) {
+        const uint32_t cand = cand_s[tyl * HT + lane][txl];
+        const uint32_t strong = strong_s[tyl * HT + lane][txl];
+        const uint32_t e = tile::flood_tile(strong, cand, lane);
+        tile::store_row(img, tx, ty, lane, e);
+        tile::finish_tile(hs, img.tile_base + (uint32_t)ty * (uint32_t)img.ntx + (uint32_t)tx, e, cand, lane);
+    }
+}
+
+size_t fused_smem_bytes(int ksize)
+{
+    const Geometry g = geometry(ksize);
+    return sizeof(float) * ((size_t)g.region0 + (size_t)g.region1);
+}
+
+template <int KS>
+cudaError_t launch_pair(const uint8_t *in, int in_pitch, int w, int h, const FloatParams &fp, float *d_smax,
+                        const HystScratch *hs, const HystImage *img, cudaStream_t s)
+{
+    static bool attr = false;
+    if (!attr) {
+        const int bytes = (int)fused_smem_bytes(KS > 0 ? KS : MAX_KSIZE);
+        cudaError_t e = cudaFuncSetAttribute(k1f_max_kernel<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k1f_edges_kernel<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const dim3 grid((w + FB_W - 1) / FB_W, (h + FB_H - 1) / FB_H);
+    const size_t smem = fused_smem_bytes(fp.ksize);
+    if (!hs) {
+        k1f_max_kernel<KS><<<grid, FB_THREADS, smem, s>>>(in, in_pitch, w, h, fp, d_smax);
+    } else {
+        k1f_edges_kernel<KS><<<grid, FB_THREADS, smem, s>>>(in, in_pitch, w, h, fp, d_smax, *hs, *img);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t dispatch(const uint8_t *in, int in_pitch, int w, int h, const FloatParams &fp, float *d_smax,
+                     const HystScratch *hs, const HystImage *img, cudaStream_t s)
+{
+    if (w <= 0 || h <= 0) return cudaSuccess;
+    switch (fp.ksize) {
+    case 3: return launch_pair<3>(in, in_pitch, w, h, fp, d_smax, hs, img, s);
+    case 5: return launch_pair<5>(in, in_pitch, w, h, fp, d_smax, hs, img, s);
+    case 7: return launch_pair<7>(in, in_pitch, w, h, fp, d_smax, hs, img, s);
+    case 9: return launch_pair<9>(in, in_pitch, w, h, fp, d_smax, hs, img, s);
+    case 11: return launch_pair<11>(in, in_pitch, w, h, fp, d_smax, hs, img, s);
+    default: return launch_pair<0>(in, in_pitch, w, h, fp, d_smax, hs, img, s);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_k1f_max(const uint8_t *in, int in_pitch, int w, int h, const FloatParams &fp, float *d_smax,
+                           cudaStream_t s)
+{
+    return dispatch(in, in_pitch, w, h, fp, d_smax, nullptr, nullptr, s);
+}
+
+cudaError_t launch_k1f_edges(const uint8_t *in, int in_pitch, int w, int h, const FloatParams &fp,
+                             const float *d_smax, const HystScratch &hs, HystImage img, cudaStream_t s)
+{
+    return dispatch(in, in_pitch, w, h, fp, const_cast<float *>(d_smax), &hs, &img, s);
+}
+
+}  // namespace canny

@@ -5,6 +5,8 @@ strength within 1e-5 relative, edge maps equal except where the oracle's own
 decision is within 1e-3 of a threshold or neighbour (and what is connected to
 such a pixel).
 """
+import ctypes
+
 import numpy as np
 import pytest
 import scipy.ndimage as ndi
@@ -243,6 +245,76 @@ def test_run_host_matches_device_path():
     assert np.array_equal(out, oracle.canny_u8(img))
 
 
+def pinned(a):
+    t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    return t
+
+
+def frames_run(ctx, frames, w, h, pin=True):
+    outs = [np.full((h, w), 7, np.uint8) for _ in frames]
+    if pin:
+        ins_t = [pinned(f) for f in frames]
+        outs_t = [pinned(o) for o in outs]
+        canny.canny_run_frames(ctx.ctx, [t.data_ptr() for t in ins_t], w, [t.data_ptr() for t in outs_t], w, w, h)
+        return [t.numpy().copy() for t in outs_t]
+    canny.canny_run_frames(ctx.ctx, [f.ctypes.data for f in frames], w, [o.ctypes.data for o in outs], w, w, h)
+    return outs
+
+
+def test_frames_equal_single_runs_and_oracle():
+    frames = [synth.image(600 + i, 300, 200, 8, 8, 8) for i in range(7)]
+    with canny.Canny(320, 240) as c:
+        got = frames_run(c, frames, 300, 200)
+        assert c.stats()["images"] == 7
+        # pageable host buffers: same results, copies do not overlap
+        got_pageable = frames_run(c, frames, 300, 200, pin=False)
+        for f, g, gp in zip(frames, got, got_pageable):
+            want = oracle.canny_u8(f)
+            assert np.array_equal(g, want)
+            assert np.array_equal(gp, want)
+            single = np.zeros_like(f)
+            canny.canny_run_host(c.ctx, f.ctypes.data, 300, single.ctypes.data, 300, 300, 200, 0)
+            assert np.array_equal(single, want)
+
+
+def test_frames_new_size_and_new_tuning_rebuild_the_graphs():
+    with canny.Canny(512, 512) as c:
+        for (w, h) in [(512, 512), (97, 131), (512, 300)]:
+            frames = [blocky_image(w * 3 + h + i, h, w) for i in range(3)]
+            got = frames_run(c, frames, w, h)
+            for f, g in zip(frames, got):
+                assert np.array_equal(g, oracle.canny_u8(f))
+        c.set_tuning(160, 12)
+        frames = [blocky_image(77 + i, 300, 300) for i in range(4)]
+        got = frames_run(c, frames, 300, 300)
+        for f, g in zip(frames, got):
+            assert np.array_equal(g, oracle.canny_u8(f))
+
+
+def test_frames_single_frame_and_float_path():
+    img = blocky_image(5, 150, 222)
+    with canny.Canny(222, 150) as c:
+        assert np.array_equal(frames_run(c, [img], 222, 150)[0], oracle.canny_u8(img))
+    frames = [blocky_image(40 + i, 150, 222) for i in range(3)]
+    with canny.Canny(222, 150, path=canny.CANNY_PATH_F32, low=0.1, high=0.3) as c:
+        got = frames_run(c, frames, 222, 150)
+    for f, g in zip(frames, got):
+        assert np.array_equal(g, oracle.canny_f32(f, 1.4, 7, 0.1, 0.3))
+
+
+def test_frames_argument_errors():
+    lib = canny.load()
+    with canny.Canny(64, 64) as c:
+        P = ctypes.c_void_p
+        one = (P * 1)(None)
+        buf = np.zeros((64, 64), np.uint8)
+        good = (P * 1)(buf.ctypes.data)
+        assert lib.canny_run_frames(c.ctx, 1, one, 64, good, 64, 64, 64, None) == canny.CANNY_EINVAL
+        assert lib.canny_run_frames(c.ctx, 1, good, 64, good, 64, 65, 64, None) == canny.CANNY_EINVAL
+        assert lib.canny_run_frames(c.ctx, 1, good, 32, good, 64, 64, 64, None) == canny.CANNY_EINVAL
+        assert lib.canny_run_frames(c.ctx, 0, None, 64, None, 64, 64, 64, None) == canny.CANNY_OK
+
+
 # ------------------------------------------------------------------ float path
 def float_reference(img, sigma=1.4, ksize=7, lo=0.1, hi=0.3):
     S = oracle.gauss_f32(img, sigma, ksize)
@@ -316,6 +388,68 @@ def test_float_other_sigma():
         c.run_pitched(d_in, d_out)
         torch.cuda.synchronize()
     check_float_edges(d_out.cpu().numpy(), want, gx, gy, M, cls, 0.05, 0.2)
+
+
+def run_float(img, sigma=1.4, ksize=7, lo=0.1, hi=0.3):
+    h, w = img.shape
+    with canny.Canny(max(w, 1), max(h, 1), path=canny.CANNY_PATH_F32, sigma=sigma, ksize=ksize,
+                     low=lo, high=hi) as c:
+        d_in = dev(img)
+        d_out = torch.full((h, w), 7, dtype=torch.uint8, device="cuda")
+        c.run_pitched(d_in, d_out)
+        torch.cuda.synchronize()
+        st = c.stats()
+    return d_out.cpu().numpy(), st
+
+
+# Two stencil passes, the second fused with the tile fill, in the definition's
+# operation order: the edge maps are expected to equal the fp32 oracle's exactly
+# (the tolerance check is the bar; equality is what the operation order gives).
+@pytest.mark.parametrize("ksize,sigma", [(3, 0.8), (5, 1.0), (7, 1.4), (9, 2.0), (11, 2.0), (13, 2.5), (31, 6.0)])
+@pytest.mark.parametrize("h,w", [(200, 300), (67, 131), (129, 257)])
+def test_float_fused_every_kernel_size(ksize, sigma, h, w):
+    img = blocky_image(ksize * 7 + h, h, w)
+    gx, gy, M, cls, want = float_reference(img, sigma, ksize, 0.08, 0.25)
+    got, st = run_float(img, sigma, ksize, 0.08, 0.25)
+    assert st["status"] == canny.CANNY_OK
+    check_float_edges(got, want, gx, gy, M, cls, 0.08, 0.25)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("h,w", [(1, 1), (1, 7), (5, 1), (3, 3), (31, 33), (64, 128), (65, 129)])
+def test_float_fused_tiny_and_block_edges(h, w):
+    img = noise_image(h * 1000 + w, h, w)
+    gx, gy, M, cls, want = float_reference(img)
+    got, st = run_float(img)
+    assert st["status"] == canny.CANNY_OK
+    check_float_edges(got, want, gx, gy, M, cls)
+    assert np.array_equal(got, want)
+
+
+def test_float_fused_flat_image_has_no_edges():
+    img = np.full((100, 150), 77, np.uint8)
+    got, st = run_float(img)
+    assert st["status"] == canny.CANNY_OK
+    assert not got.any()
+
+
+def test_float_batch_equals_single_runs_and_oracle():
+    sizes = [(96, 130), (33, 47), (200, 64), (1, 9), (150, 150)]
+    imgs = [blocky_image(50 + i, h, w) for i, (h, w) in enumerate(sizes)]
+    total = sum(h * w for h, w in sizes)
+    ins = [dev(im) for im in imgs]
+    outs = [torch.full_like(x, 7) for x in ins]
+    with canny.Canny(total, 1, path=canny.CANNY_PATH_F32, low=0.1, high=0.3) as c:
+        c.run_batch(list(zip(ins, outs)))
+        torch.cuda.synchronize()
+        assert c.stats()["status"] == canny.CANNY_OK
+    for im, o in zip(imgs, outs):
+        gx, gy, M, cls, want = float_reference(im)
+        got = o.cpu().numpy()
+        check_float_edges(got, want, gx, gy, M, cls)
+        assert np.array_equal(got, want)
+        single, _ = run_float(im)
+        assert np.array_equal(got, single)
 
 
 # ------------------------------------------------------------------ full-size workloads

@@ -47,44 +47,84 @@ hyst_local_kernel(HystScratch hs, HystImage single, uint32_t ntiles, uint32_t ni
 }
 
 // ---------------------------------------------------------------- global pass
-__device__ __forceinline__ void global_item(const HystScratch &hs, uint32_t t, uint32_t k, int lane,
-                                            int nimg)
+// Neighbour directions of a tile, as bits of the "affected" mask.
+enum { NB_U, NB_UL, NB_UR, NB_D, NB_DL, NB_DR, NB_L, NB_R };
+
+// Tiles one worklist entry may chase into within a pass before the rest is
+// queued for the next pass, and the depth of the per-warp chase stack.
+constexpr int CHASE_BUDGET = 512;
+constexpr int CHASE_STACK = 32;
+
+// Border masks as other warps last wrote them: loads that bypass L1, since
+// tiles are revisited within one pass and L1 is not coherent across SMs.
+__device__ __forceinline__ TileMasks masks_cg(const TileMasks *m)
 {
-    const TileMasks mu = hs.masks[t];
-    if ((mu.pend_top | mu.pend_bottom | mu.pend_left | mu.pend_right) == 0) return;
+    const uint4 *p = reinterpret_cast<const uint4 *>(m);
+    const uint4 a = __ldcg(p), b = __ldcg(p + 1);
+    TileMasks r;
+    r.edge_top = a.x; r.edge_bottom = a.y; r.edge_left = a.z; r.edge_right = a.w;
+    r.pend_top = b.x; r.pend_bottom = b.y; r.pend_left = b.z; r.pend_right = b.w;
+    return r;
+}
+
+__device__ __forceinline__ uint32_t edge_bottom_cg(const TileMasks *m) { return __ldcg(&m->edge_bottom); }
+__device__ __forceinline__ uint32_t edge_top_cg(const TileMasks *m) { return __ldcg(&m->edge_top); }
+__device__ __forceinline__ uint32_t edge_left_cg(const TileMasks *m) { return __ldcg(&m->edge_left); }
+__device__ __forceinline__ uint32_t edge_right_cg(const TileMasks *m) { return __ldcg(&m->edge_right); }
+
+// Neighbour of tile t in direction d (NB_*) for an image ntx tiles wide:
+// t + dy * ntx + dx, with dx + 1 and dy + 1 packed two bits per direction.
+__device__ __forceinline__ uint32_t neighbour(uint32_t t, int d, uint32_t ntx)
+{
+    const int dx = (int)((0x8861u >> (2 * d)) & 3u) - 1;    // 0, -1, 1, 0, -1, 1, -1, 1
+    const int dy = (int)((0x5A80u >> (2 * d)) & 3u) - 1;    // -1, -1, -1, 1, 1, 1, 0, 0
+    return (uint32_t)((int64_t)t + (int64_t)dy * ntx + dx);
+}
+
+// Tile t takes the edges on its neighbours' borders as seeds for its pending
+// border pixels and grows them through its pending pixels. Returns (in every
+// lane) the mask of neighbours (NB_* bits) whose facing border has pending
+// pixels next to an edge this call added; *ntx_out = the image's tiles across.
+__device__ __forceinline__ uint32_t global_item(const HystScratch &hs, uint32_t t, int lane, int nimg,
+                                                uint32_t *ntx_out)
+{
+    const TileMasks mu = masks_cg(&hs.masks[t]);
+    if ((mu.pend_top | mu.pend_bottom | mu.pend_left | mu.pend_right) == 0) return 0;
     const HystImage im = hs.imgs[find_image(hs.imgs, nimg, t)];
     const uint32_t local = t - im.tile_base;
     const int tx = (int)(local % (uint32_t)im.ntx), ty = (int)(local / (uint32_t)im.ntx);
     const bool hasL = tx > 0, hasR = tx < im.ntx - 1, hasU = ty > 0, hasD = ty < im.nty - 1;
     const uint32_t ntx = (uint32_t)im.ntx;
+    *ntx_out = ntx;
+    const TileMasks *M = hs.masks;
 
     // seeds: pending border pixels next to an edge pixel of a neighbouring tile
     uint32_t s_top = 0, s_bot = 0, s_left = 0, s_right = 0;
     if (hasU && mu.pend_top) {
-        uint32_t a = hs.masks[t - ntx].edge_bottom;
+        uint32_t a = edge_bottom_cg(&M[t - ntx]);
         uint32_t ring = a | (a << 1) | (a >> 1);
-        if (hasL && (hs.masks[t - ntx - 1].edge_bottom >> 31)) ring |= 1u;
-        if (hasR && (hs.masks[t - ntx + 1].edge_bottom & 1u)) ring |= 1u << 31;
+        if (hasL && (edge_bottom_cg(&M[t - ntx - 1]) >> 31)) ring |= 1u;
+        if (hasR && (edge_bottom_cg(&M[t - ntx + 1]) & 1u)) ring |= 1u << 31;
         s_top = ring & mu.pend_top;
     }
     if (hasD && mu.pend_bottom) {
-        uint32_t a = hs.masks[t + ntx].edge_top;
+        uint32_t a = edge_top_cg(&M[t + ntx]);
         uint32_t ring = a | (a << 1) | (a >> 1);
-        if (hasL && (hs.masks[t + ntx - 1].edge_top >> 31)) ring |= 1u;
-        if (hasR && (hs.masks[t + ntx + 1].edge_top & 1u)) ring |= 1u << 31;
+        if (hasL && (edge_top_cg(&M[t + ntx - 1]) >> 31)) ring |= 1u;
+        if (hasR && (edge_top_cg(&M[t + ntx + 1]) & 1u)) ring |= 1u << 31;
         s_bot = ring & mu.pend_bottom;
     }
     if (hasL && mu.pend_left) {
-        uint32_t a = hs.masks[t - 1].edge_right;
+        uint32_t a = edge_right_cg(&M[t - 1]);
         s_left = (a | (a << 1) | (a >> 1)) & mu.pend_left;
     }
     if (hasR && mu.pend_right) {
-        uint32_t a = hs.masks[t + 1].edge_left;
+        uint32_t a = edge_left_cg(&M[t + 1]);
         s_right = (a | (a << 1) | (a >> 1)) & mu.pend_right;
     }
-    if ((s_top | s_bot | s_left | s_right) == 0) return;
+    if ((s_top | s_bot | s_left | s_right) == 0) return 0;
 
-    uint32_t p = hs.pend_bits[(size_t)t * HT + lane];
+    uint32_t p = __ldcg(&hs.pend_bits[(size_t)t * HT + lane]);
     uint32_t e0 = ((s_left >> lane) & 1u) | (((s_right >> lane) & 1u) << 31);
     if (lane == 0) e0 |= s_top;
     if (lane == HT - 1) e0 |= s_bot;
@@ -109,6 +149,7 @@ __device__ __forceinline__ void global_item(const HystScratch &hs, uint32_t t, u
     const uint32_t e_left = __ballot_sync(FULL, e & 1u), e_right = __ballot_sync(FULL, e >> 31);
     const uint32_t p_top = __shfl_sync(FULL, p, 0), p_bot = __shfl_sync(FULL, p, HT - 1);
     const uint32_t p_left = __ballot_sync(FULL, p & 1u), p_right = __ballot_sync(FULL, p >> 31);
+    uint32_t aff = 0;
     if (lane == 0) {
         TileMasks *mt = &hs.masks[t];
         if (e_top) atomicOr(&mt->edge_top, e_top);
@@ -120,53 +161,90 @@ __device__ __forceinline__ void global_item(const HystScratch &hs, uint32_t t, u
         atomicAnd(&mt->pend_left, p_left);
         atomicAnd(&mt->pend_right, p_right);
         __threadfence();
-        // queue neighbours whose facing border has pending pixels next to a new edge
-        const uint32_t nl = (k + 1) & 1u, st = k + 2;
+        // neighbours whose facing border has pending pixels next to a new edge
         if (hasU && e_top) {
             uint32_t d = e_top | (e_top << 1) | (e_top >> 1);
-            if (hs.masks[t - ntx].pend_bottom & d) push(hs, nl, t - ntx, st);
-            if (hasL && (e_top & 1u) && (hs.masks[t - ntx - 1].pend_bottom >> 31)) push(hs, nl, t - ntx - 1, st);
-            if (hasR && (e_top >> 31) && (hs.masks[t - ntx + 1].pend_bottom & 1u)) push(hs, nl, t - ntx + 1, st);
+            if (__ldcg(&M[t - ntx].pend_bottom) & d) aff |= 1u << NB_U;
+            if (hasL && (e_top & 1u) && (__ldcg(&M[t - ntx - 1].pend_bottom) >> 31)) aff |= 1u << NB_UL;
+            if (hasR && (e_top >> 31) && (__ldcg(&M[t - ntx + 1].pend_bottom) & 1u)) aff |= 1u << NB_UR;
         }
         if (hasD && e_bot) {
             uint32_t d = e_bot | (e_bot << 1) | (e_bot >> 1);
-            if (hs.masks[t + ntx].pend_top & d) push(hs, nl, t + ntx, st);
-            if (hasL && (e_bot & 1u) && (hs.masks[t + ntx - 1].pend_top >> 31)) push(hs, nl, t + ntx - 1, st);
-            if (hasR && (e_bot >> 31) && (hs.masks[t + ntx + 1].pend_top & 1u)) push(hs, nl, t + ntx + 1, st);
+            if (__ldcg(&M[t + ntx].pend_top) & d) aff |= 1u << NB_D;
+            if (hasL && (e_bot & 1u) && (__ldcg(&M[t + ntx - 1].pend_top) >> 31)) aff |= 1u << NB_DL;
+            if (hasR && (e_bot >> 31) && (__ldcg(&M[t + ntx + 1].pend_top) & 1u)) aff |= 1u << NB_DR;
         }
         if (hasL && e_left) {
             uint32_t d = e_left | (e_left << 1) | (e_left >> 1);
-            if (hs.masks[t - 1].pend_right & d) push(hs, nl, t - 1, st);
+            if (__ldcg(&M[t - 1].pend_right) & d) aff |= 1u << NB_L;
         }
         if (hasR && e_right) {
             uint32_t d = e_right | (e_right << 1) | (e_right >> 1);
-            if (hs.masks[t + 1].pend_left & d) push(hs, nl, t + 1, st);
+            if (__ldcg(&M[t + 1].pend_left) & d) aff |= 1u << NB_R;
         }
     }
+    return __shfl_sync(FULL, aff, 0);   // lane 0's mask updates and fence precede every lane's later loads
 }
 
+// One pass over the current worklist. A warp that adds edges next to a
+// neighbour's pending pixels follows them into that neighbour at once (depth
+// first, up to CHASE_BUDGET tiles per worklist entry), so a chain of weak pixels
+// across many tiles costs one pass, not one pass per tile; what the budget or
+// the stack cannot take is queued for the next pass. A tile may be visited by
+// two warps at a time: both only add edges, and each re-reads the masks, so the
+// result is the same.
 __global__ void __launch_bounds__(THREADS)
 hyst_global_kernel(HystScratch hs, int in_graph, cudaGraphConditionalHandle cond)
 {
+    __shared__ uint32_t stack[WARPS][CHASE_STACK];
+    __shared__ uint32_t visits;
     HystState *st = hs.state;
     const uint32_t k = *(volatile uint32_t *)&st->pass;
     const uint32_t cur = k & 1u, nxt = cur ^ 1u;
     const uint32_t count = *(volatile uint32_t *)&st->list_count[cur];
     const int nimg = (int)st->nimg;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const uint32_t warp = (blockIdx.x * THREADS + threadIdx.x) >> 5;
     const uint32_t nwarps = gridDim.x * WARPS;
     const uint32_t *list = hs.lists + (size_t)cur * hs.max_tiles;
-    for (uint32_t i = warp; i < count; i += nwarps) global_item(hs, list[i], k, lane, nimg);
+    if (threadIdx.x == 0) visits = 0;
+    __syncthreads();
+    uint32_t my_visits = 0;
+    for (uint32_t i = warp; i < count; i += nwarps) {
+        uint32_t t = list[i];
+        int sp = 0, budget = CHASE_BUDGET;
+        for (;;) {
+            uint32_t ntx = 0;
+            uint32_t aff = global_item(hs, t, lane, nimg, &ntx);
+            ++my_visits;
+            while (aff) {
+                const int d = __ffs(aff) - 1;
+                aff &= aff - 1;
+                const uint32_t n = neighbour(t, d, ntx);
+                if (sp < CHASE_STACK && budget > 0) {
+                    if (lane == 0) stack[wl][sp] = n;
+                    ++sp;
+                    --budget;
+                } else if (lane == 0) {
+                    push(hs, nxt, n, k + 2);
+                }
+            }
+            __syncwarp();
+            if (sp == 0) break;
+            t = stack[wl][--sp];
+            __syncwarp();
+        }
+    }
+    if (lane == 0) atomicAdd(&visits, my_visits);
 
     __syncthreads();
     if (threadIdx.x == 0) {
+        atomicAdd(&st->visited, visits);
         __threadfence();
         if (atomicAdd(&st->done_ctas, 1u) == gridDim.x - 1) {
             __threadfence();
             const uint32_t next = atomicAdd(&st->list_count[nxt], 0u);
             st->list_count[cur] = 0;
-            st->visited += count;
             st->pass = k + 1;
             st->done_ctas = 0;
             bool more = next > 0;

@@ -288,8 +288,9 @@ def measure_batched(steps: int, cpu: bool = False) -> dict:
     tune = canny.canny_autotune_batch(ctx.ctx, list(arr_b), sp,
                                       os.path.join(os.path.expanduser("~"), ".cache", "canny_gb300_tune.jsonl")
                                       if os.access(os.path.expanduser("~"), os.W_OK) else None).as_dict()
+    # the loop keeps the single-image default (64-row bands), its faster setting for
+    # images this small; the batch's tuned band would shrink its grids
     loop_ctx = canny.Canny(BATCH_HI, BATCH_HI, low=LOW, high=HIGH)
-    canny.canny_set_tuning(loop_ctx.ctx, tune["band"], tune["ctas_per_sm"])
 
     def run_batch():
         rc = lib.canny_run_batch(ctx.ctx, BATCH_N, arr_b, sp)

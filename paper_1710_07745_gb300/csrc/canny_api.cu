@@ -847,12 +847,12 @@ canny_status canny_autotune_batch(canny_ctx *c, int n, const canny_image *imgs, 
     if (!best.from_cache) {
         // time every candidate on this batch: warm-up run, then two timed runs
         const int bands[3] = {64, 160, 256};
-        const int ctas[2] = {8, 12};
+        const int ctas[3] = {8, 12, 16};
         cudaEvent_t e0, e1;
         if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return CANNY_ECUDA;
         best.ms = 1e30;
         for (int bi = 0; bi < 3; ++bi) {
-            for (int ci = 0; ci < 2; ++ci) {
+            for (int ci = 0; ci < 3; ++ci) {
                 canny_tuning cand = {};
                 cand.band = bands[bi];
                 cand.ctas_per_sm = ctas[ci];

@@ -9,9 +9,12 @@
 //                pixels are still unresolved ("pending") and which border pixels
 //                are edges or pending;
 //   global pass  a tile on the worklist takes the edges on its neighbours'
-//                borders as seeds for its pending border pixels, grows them, and
-//                queues any neighbour whose facing border gained edges while it
-//                still has pending pixels there. Passes repeat until the
+//                borders as seeds for its pending border pixels and grows them
+//                (the lanes of a warp first check 32 entries for seeds at once;
+//                the warp grows the few that have some). A neighbour whose
+//                facing border gained edges next to its pending pixels is
+//                followed at once by the same warp, or queued for the next pass
+//                when the warp's budget runs out. Passes repeat until the
 //                worklist is empty; a CUDA-graph while-node drives the loop, its
 //                condition set by the last CTA of each pass.
 // Pending pixels live only in a compact bitmap, so the map never holds a value
@@ -81,24 +84,28 @@ __device__ __forceinline__ uint32_t neighbour(uint32_t t, int d, uint32_t ntx)
     return (uint32_t)((int64_t)t + (int64_t)dy * ntx + dx);
 }
 
-// Tile t takes the edges on its neighbours' borders as seeds for its pending
-// border pixels and grows them through its pending pixels. Returns (in every
-// lane) the mask of neighbours (NB_* bits) whose facing border has pending
-// pixels next to an edge this call added; *ntx_out = the image's tiles across.
-__device__ __forceinline__ uint32_t global_item(const HystScratch &hs, uint32_t t, int lane, int nimg,
-                                                uint32_t *ntx_out)
+// Where tile t sits, and which of its pending border pixels touch an edge pixel
+// of a neighbouring tile (the seeds of its growth). Lane-independent: a warp
+// calls it for one tile, or each lane for its own.
+struct TileSeeds {
+    HystImage im;
+    int tx, ty;
+    uint32_t top, bot, left, right;
+};
+
+__device__ __forceinline__ bool find_seeds(const HystScratch &hs, uint32_t t, int nimg, TileSeeds &sd)
 {
     const TileMasks mu = masks_cg(&hs.masks[t]);
-    if ((mu.pend_top | mu.pend_bottom | mu.pend_left | mu.pend_right) == 0) return 0;
-    const HystImage im = hs.imgs[find_image(hs.imgs, nimg, t)];
+    if ((mu.pend_top | mu.pend_bottom | mu.pend_left | mu.pend_right) == 0) return false;
+    sd.im = hs.imgs[find_image(hs.imgs, nimg, t)];
+    const HystImage &im = sd.im;
     const uint32_t local = t - im.tile_base;
     const int tx = (int)(local % (uint32_t)im.ntx), ty = (int)(local / (uint32_t)im.ntx);
+    sd.tx = tx;
+    sd.ty = ty;
     const bool hasL = tx > 0, hasR = tx < im.ntx - 1, hasU = ty > 0, hasD = ty < im.nty - 1;
     const uint32_t ntx = (uint32_t)im.ntx;
-    *ntx_out = ntx;
     const TileMasks *M = hs.masks;
-
-    // seeds: pending border pixels next to an edge pixel of a neighbouring tile
     uint32_t s_top = 0, s_bot = 0, s_left = 0, s_right = 0;
     if (hasU && mu.pend_top) {
         uint32_t a = edge_bottom_cg(&M[t - ntx]);
@@ -122,8 +129,24 @@ __device__ __forceinline__ uint32_t global_item(const HystScratch &hs, uint32_t 
         uint32_t a = edge_left_cg(&M[t + 1]);
         s_right = (a | (a << 1) | (a >> 1)) & mu.pend_right;
     }
-    if ((s_top | s_bot | s_left | s_right) == 0) return 0;
+    sd.top = s_top;
+    sd.bot = s_bot;
+    sd.left = s_left;
+    sd.right = s_right;
+    return (s_top | s_bot | s_left | s_right) != 0;
+}
 
+// Tile t grows its seeds through its pending pixels (whole warp, lane = row).
+// Returns (in every lane) the mask of neighbours (NB_* bits) whose facing
+// border has pending pixels next to an edge this call added.
+__device__ __forceinline__ uint32_t grow_tile(const HystScratch &hs, uint32_t t, const TileSeeds &sd, int lane)
+{
+    const HystImage &im = sd.im;
+    const int tx = sd.tx, ty = sd.ty;
+    const bool hasL = tx > 0, hasR = tx < im.ntx - 1, hasU = ty > 0, hasD = ty < im.nty - 1;
+    const uint32_t ntx = (uint32_t)im.ntx;
+    const TileMasks *M = hs.masks;
+    const uint32_t s_top = sd.top, s_bot = sd.bot, s_left = sd.left, s_right = sd.right;
     uint32_t p = __ldcg(&hs.pend_bits[(size_t)t * HT + lane]);
     uint32_t e0 = ((s_left >> lane) & 1u) | (((s_right >> lane) & 1u) << 31);
     if (lane == 0) e0 |= s_top;
@@ -210,29 +233,49 @@ hyst_global_kernel(HystScratch hs, int in_graph, cudaGraphConditionalHandle cond
     if (threadIdx.x == 0) visits = 0;
     __syncthreads();
     uint32_t my_visits = 0;
-    for (uint32_t i = warp; i < count; i += nwarps) {
-        uint32_t t = list[i];
-        int sp = 0, budget = CHASE_BUDGET;
-        for (;;) {
-            uint32_t ntx = 0;
-            uint32_t aff = global_item(hs, t, lane, nimg, &ntx);
-            ++my_visits;
-            while (aff) {
-                const int d = __ffs(aff) - 1;
-                aff &= aff - 1;
-                const uint32_t n = neighbour(t, d, ntx);
-                if (sp < CHASE_STACK && budget > 0) {
-                    if (lane == 0) stack[wl][sp] = n;
-                    ++sp;
-                    --budget;
-                } else if (lane == 0) {
-                    push(hs, nxt, n, k + 2);
+    // each lane checks one worklist entry for seeds; the warp then grows the
+    // tiles that have some, one after the other, and follows their chains
+    for (uint32_t base = warp * 32u; base < count; base += nwarps * 32u) {
+        const uint32_t i = base + (uint32_t)lane;
+        uint32_t mine = 0;
+        bool has = false;
+        if (i < count) {
+            TileSeeds sd;
+            mine = list[i];
+            has = find_seeds(hs, mine, nimg, sd);
+        }
+        my_visits += (lane == 0) ? min(32u, count - base) : 0u;   // entries examined
+        uint32_t todo = __ballot_sync(FULL, has);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            uint32_t t = __shfl_sync(FULL, mine, src);
+            int sp = 0, budget = CHASE_BUDGET;
+            for (;;) {
+                TileSeeds sd;
+                uint32_t aff = 0, ntx = 0;
+                if (find_seeds(hs, t, nimg, sd)) {
+                    aff = grow_tile(hs, t, sd, lane);
+                    ntx = (uint32_t)sd.im.ntx;
                 }
+                ++my_visits;
+                while (aff) {
+                    const int d = __ffs(aff) - 1;
+                    aff &= aff - 1;
+                    const uint32_t n = neighbour(t, d, ntx);
+                    if (sp < CHASE_STACK && budget > 0) {
+                        if (lane == 0) stack[wl][sp] = n;
+                        ++sp;
+                        --budget;
+                    } else if (lane == 0) {
+                        push(hs, nxt, n, k + 2);
+                    }
+                }
+                __syncwarp();
+                if (sp == 0) break;
+                t = stack[wl][--sp];
+                __syncwarp();
             }
-            __syncwarp();
-            if (sp == 0) break;
-            t = stack[wl][--sp];
-            __syncwarp();
         }
     }
     if (lane == 0) atomicAdd(&visits, my_visits);

@@ -11,20 +11,24 @@
 //
 // Phase 1, sliding down the BAND rows (plus a 4-row halo each side):
 //   - TMA loads the strip's input rows (256 bytes from X0 - 16) in chunks of
-//     3 rows into a 4-stage shared-memory ring, one mbarrier per stage;
+//     3 rows into a 2-stage shared-memory ring, one mbarrier per stage;
 //   - the binomial Gaussian runs on pairs of 16-bit lanes (vertical: a cascade
 //     of four pairwise sums; horizontal: packed words with the +128 rounding
 //     folded in); neighbour lanes trade halo values by shuffles;
-//   - the smoothed bytes become floats 2^23 + S and Sobel and the squared
+//   - the smoothed bytes become floats S (2^23 + S from a byte permute, minus
+//     2^23) and Sobel (column sums and row differences) and the squared
 //     strength run in packed float2 arithmetic (__ffma2_rn etc.); every value
 //     is an integer below 2^24, so the result is exact;
 //   - every row's strengths go to a 5-row ring in shared memory. Only ~2% of
-//     pixels exceed the low threshold: their lanes also store the packed
-//     gradients and queue one entry per such pixel, one row late; after every
-//     3 rows the lanes share the queued pixels (one each) and run the sector
-//     test and the suppression for them alone, setting bits in the strip's
-//     weak/strong row bitmasks. A non-candidate neighbour is at most the low
-//     threshold, below any candidate, so its stored strength decides nothing.
+//     pixels exceed the low threshold: their lanes keep the row's gradients in
+//     registers and, one row later, queue one entry per such pixel holding its
+//     column, row and gradients; after every 3 rows the lanes share the queued
+//     pixels (one each) and run the sector test and the suppression for them
+//     alone, setting bits in the strip's weak/strong row bitmasks. A
+//     non-candidate neighbour is at most the low threshold, below any
+//     candidate, so its stored strength decides nothing.
+// Shared memory stays under 13 KB per CTA and registers at 128 per thread, so
+// 16 one-warp CTAs fit on an SM.
 // Phase 2: either the class map is written from the bitmasks (canny_classify),
 // or the warp runs the tile flood fill of the hysteresis on them and writes
 // 255/0 edge bytes plus the tile border masks and pending bitmaps that the
@@ -45,11 +49,10 @@ constexpr int THREADS = 32;             // one warp per CTA
 constexpr int OUT_W = 28 * LPX;         // 224 output columns (lanes 1..28) = 7 hysteresis tiles
 constexpr int UNROLL = 3;               // period of the 3-row windows
 constexpr int CH = UNROLL;              // input rows per TMA chunk (one chunk per unrolled group)
-constexpr int STAGES = 4;               // chunks in flight: 12 rows ahead
+constexpr int STAGES = 2;               // chunks in flight: 6 rows ahead
 constexpr int BOX = 256;                // TMA box width: columns X0-16 .. X0+239
 constexpr uint32_t CHUNK_BYTES = BOX * CH;
 constexpr int RING = 5;                 // rows of strengths kept
-constexpr int GRING = 4;                // rows of candidate gradients kept
 constexpr int QCAP = UNROLL * 28 * LPX; // candidate pixels of one 3-row group, at most
 constexpr int TILES_X = OUT_W / HT;
 constexpr int MW = OUT_W / 32;          // bitmask words per strip row
@@ -76,8 +79,7 @@ template <int BAND>
 struct alignas(128) Smem {
     uint8_t in[STAGES][CH * BOX];        // TMA destinations, 128-byte aligned
     float m2[RING][256];                 // strengths of the last rows, by row mod RING
-    uint32_t gxy[GRING][256];            // (gx + 1024) | (gy + 1024) << 16, candidate lanes only
-    uint16_t queue[QCAP];                // ((row - Y0) << 8) | pixel
+    uint32_t queue[QCAP];                // pixel | row in group << 8 | (gx + 1024) << 10 | (gy + 1024) << 21
     uint32_t cand[BAND][MW];             // class >= 1 (weak or strong), bit = column
     uint32_t strong[BAND][MW];           // class == 2
     uint32_t qcount;
@@ -143,18 +145,18 @@ __device__ __forceinline__ float &pix(float2 (&p)[5], int k)
 
 // ---------------------------------------------------------------- candidate suppression
 // Step 3 + thresholds for one queued candidate pixel.
+// ybase: image row of the group's first queued row.
 template <int BAND>
-__device__ __forceinline__ void suppress_pixel(Smem<BAND> &S, uint32_t entry, int Y0, float hi2)
+__device__ __forceinline__ void suppress_pixel(Smem<BAND> &S, uint32_t entry, int ybase, int Y0, float hi2)
 {
-    const int y = Y0 + (int)(entry >> 8), p = (int)(entry & 255u);
+    const int y = ybase + (int)((entry >> 8) & 3u), p = (int)(entry & 255u);
     const int sl = y % RING, su = (y + RING - 1) % RING, sd = (y + 1) % RING;
     const float m = S.m2[sl][p];
-    const uint32_t g = S.gxy[y % GRING][p];
     // all eight neighbour strengths at once, then pick by sector
     const float l = S.m2[sl][p - 1], r = S.m2[sl][p + 1];
     const float ul = S.m2[su][p - 1], uc = S.m2[su][p], ur = S.m2[su][p + 1];
     const float dl = S.m2[sd][p - 1], dc = S.m2[sd][p], dr = S.m2[sd][p + 1];
-    const int gx = (int)(g & 0xFFFFu) - 1024, gy = (int)(g >> 16) - 1024;
+    const int gx = (int)((entry >> 10) & 2047u) - 1024, gy = (int)(entry >> 21) - 1024;
     const int ax = abs(gx), ay = abs(gy);
     const bool hz = ay * 32768 < ax * 13573;           // H: left / right
     const bool vt = ax * 32768 < ay * 13573;           // V: up / down
@@ -162,7 +164,7 @@ __device__ __forceinline__ void suppress_pixel(Smem<BAND> &S, uint32_t entry, in
     const float mn = hz ? l : vt ? uc : dg ? ul : dl;  // A: down-left / up-right
     const float mp = hz ? r : vt ? dc : dg ? dr : ur;
     if (m > mn && m >= mp) {
-        const int col = p - LPX, row = (int)(entry >> 8);
+        const int col = p - LPX, row = y - Y0;
         atomicOr(&S.cand[row][col >> 5], 1u << (col & 31));
         if (m > hi2) atomicOr(&S.strong[row][col >> 5], 1u << (col & 31));
     }
@@ -185,17 +187,16 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint
     const int soff = min(LPX + LPX * lane, BOX - LPX);   // lane's bytes in a staged row
 
     uint32_t rp[4] = {0, 0, 0, 0}, p1[4] = {0, 0, 0, 0}, p2[4] = {0, 0, 0, 0}, p3[4] = {0, 0, 0, 0};
-    float2 Sp[3][5];      // 2^23 + S by row slot (row mod 3), pairs (x_j, x_j+4), halo (x_-1, x_8)
-    float2 Dxp[3][4];     // S(x+1) - S(x-1) by row slot
+    float2 Sp[3][5];      // S by row slot (row mod 3), pairs (x_j, x_j+4), halo (x_-1, x_8)
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
 #pragma unroll
         for (int j = 0; j < 5; ++j) Sp[a][j] = f2(0.f, 0.f);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) Dxp[a][j] = f2(0.f, 0.f);
     }
-    uint32_t cm_prev = 0;
-    int r_prev = -1;
+    uint32_t cm_prev = 0;                     // candidate pixels of the previous row
+    uint32_t gprev[LPX];                      // their gradients, (gx + 1024) | (gy + 1024) << 11
+#pragma unroll
+    for (int k = 0; k < LPX; ++k) gprev[k] = 0;
     uint32_t last0 = 0, last1 = 0;            // words of input row h-1, for rows below the image
     uint32_t pf0[UNROLL], pf1[UNROLL];        // direct-load prefetch
 
@@ -321,10 +322,12 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint
             const uint32_t ho0 = B + D + BIAS + 4u * (v[0] + C) + 6u * v[1];   // (h1, h3)
             const uint32_t he1 = C + F + BIAS + 4u * (D + v[3]) + 6u * v[2];   // (h4, h6)
             const uint32_t ho1 = D + G + BIAS + 4u * (v[2] + F) + 6u * v[3];   // (h5, h7)
-            Sp[a][0] = f2(sbyte(he0, 1), sbyte(he1, 1));   // (S0, S4)
-            Sp[a][1] = f2(sbyte(ho0, 1), sbyte(ho1, 1));   // (S1, S5)
-            Sp[a][2] = f2(sbyte(he0, 3), sbyte(he1, 3));   // (S2, S6)
-            Sp[a][3] = f2(sbyte(ho0, 3), sbyte(ho1, 3));   // (S3, S7)
+            // S as floats: 2^23 + byte from a byte permute, minus 2^23 (exact)
+            const float2 unbias = f2(-8388608.f, -8388608.f);
+            Sp[a][0] = __fadd2_rn(f2(sbyte(he0, 1), sbyte(he1, 1)), unbias);   // (S0, S4)
+            Sp[a][1] = __fadd2_rn(f2(sbyte(ho0, 1), sbyte(ho1, 1)), unbias);   // (S1, S5)
+            Sp[a][2] = __fadd2_rn(f2(sbyte(he0, 3), sbyte(he1, 3)), unbias);   // (S2, S6)
+            Sp[a][3] = __fadd2_rn(f2(sbyte(ho0, 3), sbyte(ho1, 3)), unbias);   // (S3, S7)
             Sp[a][4] = f2(__shfl_up_sync(FULL, Sp[a][3].y, 1), __shfl_down_sync(FULL, Sp[a][0].x, 1));
             if (border) {
                 // replicate border on S: S(-1) = S(0), S(x >= w) = S(w - 1)
@@ -344,27 +347,23 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint
 #pragma unroll
                 for (int j = 0; j < 5; ++j) Sp[a][j] = Sp[am1][j];
             }
-            // S(x+1) - S(x-1), pairwise
-            Dxp[a][0] = sub2(Sp[a][1], f2(Sp[a][4].x, Sp[a][3].x));
-            Dxp[a][1] = sub2(Sp[a][2], Sp[a][0]);
-            Dxp[a][2] = sub2(Sp[a][3], Sp[a][1]);
-            Dxp[a][3] = sub2(f2(Sp[a][0].y, Sp[a][4].y), Sp[a][2]);
-            if (s == 0) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) Dxp[am1][j] = Dxp[a][j];
-            }
             if (i < 6) continue;
 
             // ---- Step 2: Sobel and strength of row r = s-1 (slots am2, am1, a = rows r-1, r, r+1)
             const int r = s - 1;
-            float2 E[5];
-#pragma unroll
-            for (int j = 0; j < 5; ++j) E[j] = sub2(Sp[a][j], Sp[am2][j]);
-            float2 gx[4], gy[4], m[4];
+            float2 E[5], CS[5];
             const float2 two = f2(2.f, 2.f);
 #pragma unroll
+            for (int j = 0; j < 5; ++j) {
+                E[j] = sub2(Sp[a][j], Sp[am2][j]);                                     // S(r+1) - S(r-1)
+                CS[j] = __fadd2_rn(__ffma2_rn(Sp[am1][j], two, Sp[am2][j]), Sp[a][j]);  // column sums (<= 1020)
+            }
+            float2 gx[4], gy[4], m[4];
+#pragma unroll
             for (int j = 0; j < 4; ++j) {
-                gx[j] = __fadd2_rn(__ffma2_rn(Dxp[am1][j], two, Dxp[am2][j]), Dxp[a][j]);
+                const float2 cl = j > 0 ? CS[j - 1] : f2(CS[4].x, CS[3].x);   // column sum at x-1
+                const float2 cr = j < 3 ? CS[j + 1] : f2(CS[0].y, CS[4].y);   // column sum at x+1
+                gx[j] = sub2(cr, cl);
                 const float2 el = j > 0 ? E[j - 1] : f2(E[4].x, E[3].x);   // E(x-1)
                 const float2 er = j < 3 ? E[j + 1] : f2(E[0].y, E[4].y);   // E(x+1)
                 gy[j] = __fadd2_rn(__ffma2_rn(E[j], two, el), er);
@@ -381,12 +380,21 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint
                 }
             }
             // every row's strengths go to the ring (neighbours of later candidates)
-            const int rs = ((r % RING) + RING) % RING, gs = ((r % GRING) + GRING) % GRING;
+            const int rs = ((r % RING) + RING) % RING;
             float4 *mdst = reinterpret_cast<float4 *>(&S.m2[rs][LPX * lane]);
             mdst[0] = make_float4(m[0].x, m[1].x, m[2].x, m[3].x);
             mdst[1] = make_float4(m[0].y, m[1].y, m[2].y, m[3].y);
             const float rowmax = fmaxf(fmaxf(fmaxf(m[0].x, m[0].y), fmaxf(m[1].x, m[1].y)),
                                        fmaxf(fmaxf(m[2].x, m[2].y), fmaxf(m[3].x, m[3].y)));
+            // queue the previous row's candidates now that its lower neighbour row exists
+            // (row offset u within this group's queued rows Y0 - 8 + g .. Y0 - 6 + g)
+            if (cm_prev && r - 1 >= Y0 && r - 1 < Y0 + BAND) {
+                uint32_t idx = atomicAdd(&S.qcount, (uint32_t)__popc(cm_prev));
+#pragma unroll
+                for (int k = 0; k < LPX; ++k)      // static indices keep gprev in registers
+                    if ((cm_prev >> k) & 1u)
+                        S.queue[idx++] = (uint32_t)(LPX * lane + k) | ((uint32_t)u << 8) | (gprev[k] << 10);
+            }
             uint32_t cm = 0;
             if (rowmax > lo2 && out_lane) {
                 // candidate lane: which pixels, and their gradients for the sector test
@@ -395,34 +403,22 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint
                     cm |= (m[j].x > lo2 ? 1u : 0u) << j;
                     cm |= (m[j].y > lo2 ? 1u : 0u) << (j + 4);
                 }
-                uint32_t gg[LPX];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    // 2^23 + 1024 + g holds g + 1024 in its low mantissa bits
-                    gg[j] = perm(__float_as_uint(gx[j].x + 8389632.0f), __float_as_uint(gy[j].x + 8389632.0f), 0x5410u);
-                    gg[j + 4] = perm(__float_as_uint(gx[j].y + 8389632.0f), __float_as_uint(gy[j].y + 8389632.0f), 0x5410u);
-                }
-                uint4 *gdst = reinterpret_cast<uint4 *>(&S.gxy[gs][LPX * lane]);
-                gdst[0] = make_uint4(gg[0], gg[1], gg[2], gg[3]);
-                gdst[1] = make_uint4(gg[4], gg[5], gg[6], gg[7]);
-            }
-            // queue the previous row's candidates now that its lower neighbour row exists
-            if (cm_prev && r_prev >= Y0 && r_prev < Y0 + BAND) {
-                uint32_t idx = atomicAdd(&S.qcount, (uint32_t)__popc(cm_prev));
-                uint32_t bits = cm_prev;
-                while (bits) {
-                    const int k = __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    S.queue[idx++] = (uint16_t)(((uint32_t)(r_prev - Y0) << 8) | (uint32_t)(LPX * lane + k));
+                    // 2^23 + 1024 + g holds g + 1024 (11 bits) in its low mantissa bits;
+                    // shifted left by 11, the exponent bits leave the word
+                    const uint32_t ax = __float_as_uint(gx[j].x + 8389632.0f), ay = __float_as_uint(gy[j].x + 8389632.0f);
+                    const uint32_t bx = __float_as_uint(gx[j].y + 8389632.0f), by = __float_as_uint(gy[j].y + 8389632.0f);
+                    gprev[j] = (ax & 2047u) | (ay << 11);
+                    gprev[j + 4] = (bx & 2047u) | (by << 11);
                 }
             }
             cm_prev = cm;
-            r_prev = r;
         }
         // ---- Step 3 + thresholds for the queued pixels (their rows +-1 are in the ring)
         __syncwarp();
         const uint32_t n = S.qcount;
-        for (uint32_t j = lane; j < n; j += 32) suppress_pixel(S, S.queue[j], Y0, hi2);
+        for (uint32_t j = lane; j < n; j += 32) suppress_pixel(S, S.queue[j], Y0 - 8 + g, Y0, hi2);
         __syncwarp();
         if (lane == 0) S.qcount = 0;
         __syncwarp();
@@ -506,7 +502,7 @@ __device__ __forceinline__ void init_barriers(Smem<BAND> &S, int lane)
 // ---------------------------------------------------------------- kernels
 // One image: one CTA per unit (blockIdx.x = strip, blockIdx.y = band).
 template <int BAND, int MODE>
-__global__ void __launch_bounds__(THREADS, 12)
+__global__ void __launch_bounds__(THREADS, BAND == 64 ? 16 : 12)
 k1_fused_kernel(const __grid_constant__ CUtensorMap tmap, const uint8_t *__restrict__ in, int in_pitch,
                 int w, int h, int use_tma, IntThresholds t, uint8_t *__restrict__ out, int out_pitch,
                 HystScratch hs, HystImage img, uint32_t *err)
@@ -530,7 +526,7 @@ k1_fused_kernel(const __grid_constant__ CUtensorMap tmap, const uint8_t *__restr
 
 // A batch: a persistent grid pops (image, strip, band) units from a counter.
 template <int BAND>
-__global__ void __launch_bounds__(THREADS, 12)
+__global__ void __launch_bounds__(THREADS, BAND == 64 ? 16 : 12)
 k1_fused_batch_kernel(const BatchImage *__restrict__ imgs, const CUtensorMap *__restrict__ tmaps,
                       BatchHeader *hdr, IntThresholds t, HystScratch hs)
 {

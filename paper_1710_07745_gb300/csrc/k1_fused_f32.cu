@@ -21,10 +21,15 @@
 //
 // A CTA of 256 threads covers a block of 64 rows x 128 columns (2 x 4 tiles)
 // and stages it in shared memory: input (as float, with a halo of R + 2 rows
-// and R + 2 (rounded up to 4) columns, R = ksize / 2), the horizontal pass,
-// the smoothed image S, the squared strengths (with a 1-pixel ring for the
-// suppression). Buffers alias once they are dead, so a 7-tap kernel needs
-// 80 KB and two CTAs fit on an SM.
+// and R + 2 columns rounded up to 16, R = ksize / 2; 16-byte vector loads
+// where the block lies inside the image), the horizontal pass, the smoothed
+// image S, the squared strengths (with a 1-pixel ring for the suppression).
+// Buffers alias once they are dead, so a 7-tap kernel needs 86 KB and two CTAs
+// fit on an SM. Work is done on pixel pairs that share their shared-memory
+// loads (the horizontal pass pairs two rows, the vertical pass and Sobel pair
+// two columns); the arithmetic itself is scalar and correctly rounded per
+// operation (__fmul_rn / __fadd_rn, and __fmaf_rn only where the product by 2
+// is exact).
 #include "hyst_tile.cuh"
 
 namespace canny {
@@ -41,7 +46,8 @@ struct Geometry {
     int R, padx, pady;         // Gaussian radius; input halo (columns rounded up to 4)
     int IY, IX;                // staged input rows / columns
     int SX, SY;                // smoothed image: columns x0-2 .. x0+FB_W+1, rows y0-2 .. y0+FB_H+1
-    int MX, MY;                // squared strength with its ring: x0-1 .. x0+FB_W, y0-1 .. y0+FB_H
+    int MX, MY;                // squared strength with its ring, rows y0-1 .. y0+FB_H; column j is
+                               // x0-2+j like S (the ring uses j = 1 .. FB_W+2), MX the row stride
     int region0, region1;      // floats: input then S; horizontal pass then s
 };
 
@@ -50,12 +56,12 @@ __host__ __device__ inline Geometry geometry(int ksize)
     Geometry g;
     g.R = ksize / 2;
     g.pady = g.R + 2;
-    g.padx = (g.R + 2 + 3) / 4 * 4;
+    g.padx = (g.R + 2 + 15) / 16 * 16;      // 16-byte aligned input rows
     g.IY = FB_H + 2 * g.pady;
     g.IX = FB_W + 2 * g.padx;
     g.SX = FB_W + 4;
     g.SY = FB_H + 4;
-    g.MX = FB_W + 2;
+    g.MX = FB_W + 4;
     g.MY = FB_H + 2;
     const int a = g.IY * g.IX, b = g.SY * g.SX, c = g.IY * g.SX, d = g.MY * g.MX;
     g.region0 = a > b ? a : b;
@@ -67,19 +73,31 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v,
 __device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
 
-// One Gaussian tap sum: taps[0]*src[0] + taps[1]*src[stride] + ..., each product
-// and each sum rounded. KS = 0: run-time ksize (taps read by index).
-template <int KS>
-__device__ __forceinline__ float tap_sum(const FloatParams &fp, const float *src, int stride)
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// One Gaussian tap sum on a pair of independent sums:
+// taps[0]*v(0) + taps[1]*v(1) + ..., each product and each sum rounded. The
+// pair shares its loads; the arithmetic is scalar __fmul_rn / __fadd_rn per
+// lane, which are never merged into a fused multiply-add (a paired multiply
+// followed by a paired add was observed to round once, like an FMA).
+// KS = 0: run-time ksize (taps read by index).
+template <int KS, typename Load>
+__device__ __forceinline__ float2 tap_sum2(const FloatParams &fp, Load v)
 {
+    float2 x = v(0);
+    float2 acc = f2(fmul(fp.taps[0], x.x), fmul(fp.taps[0], x.y));
     if (KS > 0) {
-        float acc = fmul(fp.taps[0], src[0]);
 #pragma unroll
-        for (int k = 1; k < KS; ++k) acc = fadd(acc, fmul(fp.taps[k], src[k * stride]));
+        for (int k = 1; k < KS; ++k) {
+            x = v(k);
+            acc = f2(fadd(acc.x, fmul(fp.taps[k], x.x)), fadd(acc.y, fmul(fp.taps[k], x.y)));
+        }
         return acc;
     }
-    float acc = fmul(fp.taps[0], src[0]);
-    for (int k = 1; k < fp.ksize; ++k) acc = fadd(acc, fmul(fp.taps[k], src[k * stride]));
+    for (int k = 1; k < fp.ksize; ++k) {
+        x = v(k);
+        acc = f2(fadd(acc.x, fmul(fp.taps[k], x.x)), fadd(acc.y, fmul(fp.taps[k], x.y)));
+    }
     return acc;
 }
 
@@ -103,6 +121,32 @@ __device__ __forceinline__ void sobel_at(const float *S, int sx, int r, int c, f
 
 __device__ __forceinline__ float strength2(float gx, float gy) { return fadd(fmul(gx, gx), fmul(gy, gy)); }
 
+// Squared strengths of the pixel pair at S entries (r, c), (r, c + 1), c even:
+// the operations of sobel_at + strength2 on each pixel, sharing the loads.
+__device__ __forceinline__ float2 strength2_pair(const float *S, int sx, int r, int c)
+{
+    const float *u = S + (r - 1) * sx + c - 2, *m = S + r * sx + c - 2, *d = S + (r + 1) * sx + c - 2;
+    // columns c-2 .. c+3 of rows r-1, r, r+1 as aligned pairs
+    const float2 u0 = *reinterpret_cast<const float2 *>(u), u1 = *reinterpret_cast<const float2 *>(u + 2),
+                 u2 = *reinterpret_cast<const float2 *>(u + 4);
+    const float2 m0 = *reinterpret_cast<const float2 *>(m), m1 = *reinterpret_cast<const float2 *>(m + 2),
+                 m2 = *reinterpret_cast<const float2 *>(m + 4);
+    const float2 d0 = *reinterpret_cast<const float2 *>(d), d1 = *reinterpret_cast<const float2 *>(d + 2),
+                 d2 = *reinterpret_cast<const float2 *>(d + 4);
+    const float U[5] = {u0.y, u1.x, u1.y, u2.x, 0.f}, M[5] = {m0.y, m1.x, m1.y, m2.x, 0.f},
+                D[5] = {d0.y, d1.x, d1.y, d2.x, 0.f};    // columns c-1 .. c+2
+    float out[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {                      // pixel at column c + i: index 1 + i
+        const float right = fadd(__fmaf_rn(2.f, M[2 + i], U[2 + i]), D[2 + i]);
+        const float left = fadd(__fmaf_rn(2.f, M[i], U[i]), D[i]);
+        const float down = fadd(__fmaf_rn(2.f, D[1 + i], D[i]), D[2 + i]);
+        const float up = fadd(__fmaf_rn(2.f, U[1 + i], U[i]), U[2 + i]);
+        out[i] = strength2(fadd(right, -left), fadd(down, -up));
+    }
+    return f2(out[0], out[1]);
+}
+
 // Steps 1-2 for one block up to the smoothed image S (left in region 0).
 template <int KS>
 __device__ __forceinline__ void smooth_block(const uint8_t *__restrict__ in, int in_pitch, int w, int h,
@@ -112,26 +156,73 @@ __device__ __forceinline__ void smooth_block(const uint8_t *__restrict__ in, int
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ox = x0 - g.padx, oy = y0 - g.pady;
     float *I_s = r0, *H_s = r1;
-    // stage the input, replicate border by clamping
-    for (int r = warp; r < g.IY; r += FB_WARPS) {
-        const uint8_t *row = in + (int64_t)clampi(oy + r, 0, h - 1) * in_pitch;
-        for (int c = lane; c < g.IX; c += 32) I_s[r * g.IX + c] = (float)__ldg(row + clampi(ox + c, 0, w - 1));
-    }
-    __syncthreads();
-    // horizontal pass at columns clamp(x0 - 2 + c), for every staged row
-    for (int r = warp; r < g.IY; r += FB_WARPS) {
-        for (int c = lane; c < g.SX; c += 32) {
-            const int X = clampi(x0 - 2 + c, 0, w - 1);
-            H_s[r * g.SX + c] = tap_sum<KS>(fp, I_s + r * g.IX + (X - g.R - ox), 1);
+    // stage the input, replicate border by clamping (rows always; columns only
+    // in blocks that reach past the image's left or right edge)
+    const bool vec = ox >= 0 && ox + g.IX <= w && ((((uintptr_t)in) | (uintptr_t)in_pitch) & 15) == 0;
+    if (vec) {
+        const int per_row = g.IX / 16;
+        for (int i = tid; i < g.IY * per_row; i += FB_THREADS) {
+            const int r = i / per_row, j = i - r * per_row;
+            const uint8_t *src = in + (int64_t)clampi(oy + r, 0, h - 1) * in_pitch + ox + 16 * j;
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(src));
+            const uint32_t wd[4] = {v.x, v.y, v.z, v.w};
+            float4 *dst = reinterpret_cast<float4 *>(I_s + r * g.IX + 16 * j);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                // float 2^23 + byte, minus 2^23: the byte's value, exactly
+                const float2 lo = __fadd2_rn(f2(__uint_as_float(__byte_perm(wd[q], 0x4B000000u, 0x7640u)),
+                                                __uint_as_float(__byte_perm(wd[q], 0x4B000000u, 0x7641u))),
+                                             f2(-8388608.f, -8388608.f));
+                const float2 hi = __fadd2_rn(f2(__uint_as_float(__byte_perm(wd[q], 0x4B000000u, 0x7642u)),
+                                                __uint_as_float(__byte_perm(wd[q], 0x4B000000u, 0x7643u))),
+                                             f2(-8388608.f, -8388608.f));
+                dst[q] = make_float4(lo.x, lo.y, hi.x, hi.y);
+            }
+        }
+    } else {
+        for (int r = warp; r < g.IY; r += FB_WARPS) {
+            const uint8_t *row = in + (int64_t)clampi(oy + r, 0, h - 1) * in_pitch;
+            for (int c = lane; c < g.IX; c += 32) I_s[r * g.IX + c] = (float)__ldg(row + clampi(ox + c, 0, w - 1));
         }
     }
     __syncthreads();
-    // vertical pass at rows clamp(y0 - 2 + r): S(clamp(x), clamp(y)) into region 0
+    // horizontal pass at columns clamp(x0 - 2 + c), rows paired (2p, 2p + 1)
+    {
+        const int pairs = g.IY / 2;
+        auto hpass = [&](int p, int c) {
+            const int X = clampi(x0 - 2 + c, 0, w - 1);
+            const float *a = I_s + (2 * p) * g.IX + (X - g.R - ox);
+            const float *b = a + g.IX;
+            const float2 acc = tap_sum2<KS>(fp, [&](int k) { return f2(a[k], b[k]); });
+            H_s[(2 * p) * g.SX + c] = acc.x;
+            H_s[(2 * p + 1) * g.SX + c] = acc.y;
+        };
+        for (int p = warp; p < pairs; p += FB_WARPS)
+            for (int c = lane; c < FB_W; c += 32) hpass(p, c);
+        for (int i = tid; i < pairs * (g.SX - FB_W); i += FB_THREADS) {     // the last SX - 128 columns
+            const int p = i / (g.SX - FB_W);
+            hpass(p, FB_W + (i - p * (g.SX - FB_W)));
+        }
+    }
+    __syncthreads();
+    // vertical pass at rows clamp(y0 - 2 + r), columns paired (2q, 2q + 1):
+    // S(clamp(x), clamp(y)) into region 0
     float *S_s = r0;
-    for (int r = warp; r < g.SY; r += FB_WARPS) {
-        const int Y = clampi(y0 - 2 + r, 0, h - 1);
-        const float *src = H_s + (Y - g.R - oy) * g.SX;
-        for (int c = lane; c < g.SX; c += 32) S_s[r * g.SX + c] = tap_sum<KS>(fp, src + c, g.SX);
+    {
+        const int qn = g.SX / 2;
+        auto vpass = [&](int r, int q) {
+            const int Y = clampi(y0 - 2 + r, 0, h - 1);
+            const float *src = H_s + (Y - g.R - oy) * g.SX + 2 * q;
+            const float2 acc =
+                tap_sum2<KS>(fp, [&](int k) { return *reinterpret_cast<const float2 *>(src + k * g.SX); });
+            *reinterpret_cast<float2 *>(S_s + r * g.SX + 2 * q) = acc;
+        };
+        for (int r = warp; r < g.SY; r += FB_WARPS)
+            for (int q = lane; q < 64; q += 32) vpass(r, q);
+        for (int i = tid; i < g.SY * (qn - 64); i += FB_THREADS) {          // the last pairs of each row
+            const int r = i / (qn - 64);
+            vpass(r, 64 + (i - r * (qn - 64)));
+        }
     }
     __syncthreads();
 }
@@ -150,11 +241,12 @@ k1f_max_kernel(const uint8_t *__restrict__ in, int in_pitch, int w, int h, Float
     float best = 0.f;
     for (int r = warp; r < FB_H; r += FB_WARPS) {
         if (y0 + r >= h) break;
-        for (int c = lane; c < FB_W; c += 32) {
+        for (int q = lane; q < FB_W / 2; q += 32) {
+            const int c = 2 * q;                          // pixels x0 + c, x0 + c + 1
             if (x0 + c >= w) break;
-            float gx, gy;
-            sobel_at(r0, g.SX, r + 2, c + 2, gx, gy);
-            best = fmaxf(best, strength2(gx, gy));
+            const float2 s2 = strength2_pair(r0, g.SX, r + 2, c + 2);
+            best = fmaxf(best, s2.x);
+            if (x0 + c + 1 < w) best = fmaxf(best, s2.y);
         }
     }
     __shared__ float red[FB_WARPS];
@@ -186,18 +278,31 @@ k1f_edges_kernel(const uint8_t *__restrict__ in, int in_pitch, int w, int h, Flo
     // squared strength on the block and its ring (0 outside the image) into region 1
     const float *S_s = r0;
     float *s_s = r1;
+    // pairs of columns j = 2 .. FB_W + 1 (S row r + 1 is image row y0 - 1 + r)
     for (int r = warp; r < g.MY; r += FB_WARPS) {
         const int Y = y0 - 1 + r;
-        for (int c = lane; c < g.MX; c += 32) {
-            const int X = x0 - 1 + c;
-            float s = 0.f;
-            if (X >= 0 && X < w && Y >= 0 && Y < h) {
-                float gx, gy;
-                sobel_at(S_s, g.SX, r + 1, c + 1, gx, gy);
-                s = strength2(gx, gy);
+        const bool row_in = Y >= 0 && Y < h;
+        for (int q = lane; q < FB_W / 2; q += 32) {
+            const int j = 2 + 2 * q, X = x0 - 2 + j;
+            float2 s2 = f2(0.f, 0.f);
+            if (row_in && X < w) {
+                s2 = strength2_pair(S_s, g.SX, r + 1, j);
+                if (X + 1 >= w) s2.y = 0.f;
             }
-            s_s[r * g.MX + c] = s;
+            *reinterpret_cast<float2 *>(s_s + r * g.MX + j) = s2;
         }
+    }
+    // the ring's outer columns j = 1 and j = FB_W + 2
+    for (int i = tid; i < 2 * g.MY; i += FB_THREADS) {
+        const int r = i >> 1, j = (i & 1) ? FB_W + 2 : 1;
+        const int X = x0 - 2 + j, Y = y0 - 1 + r;
+        float s = 0.f;
+        if (X >= 0 && X < w && Y >= 0 && Y < h) {
+            float gx, gy;
+            sobel_at(S_s, g.SX, r + 1, j, gx, gy);
+            s = strength2(gx, gy);
+        }
+        s_s[r * g.MX + j] = s;
     }
     __syncthreads();
 
@@ -211,13 +316,13 @@ k1f_edges_kernel(const uint8_t *__restrict__ in, int in_pitch, int w, int h, Flo
     // Step 3 + thresholds: one (row, tile column) per warp iteration, lane = column
     for (int item = warp; item < FB_H * FB_TX; item += FB_WARPS) {
         const int r = item / FB_TX, tc = item % FB_TX;
-        const int mc = 1 + HT * tc + lane, mr = r + 1;      // index in s_s
+        const int mc = 2 + HT * tc + lane, mr = r + 1;      // index in s_s (and S column)
         const float s = s_s[mr * g.MX + mc];
         bool weak = false, strong = false;
         if (s > s_pre) {
             const float m = __fsqrt_rn(s);
             float gx, gy;
-            sobel_at(S_s, g.SX, r + 2, mc + 1, gx, gy);
+            sobel_at(S_s, g.SX, r + 2, mc, gx, gy);
             const float t = 0.41421356f, ax = fabsf(gx), ay = fabsf(gy);
             int dn, dp;                                         // offsets of n- and n+ in s_s
             if (ay < fmul(ax, t)) { dn = -1; dp = 1; }                                  // H

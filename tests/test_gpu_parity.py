@@ -450,6 +450,16 @@ def test_float_fused_tiny_and_block_edges(h, w):
     assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("seed", range(24))
+def test_float_fused_exact_on_many_images(seed):
+    # suppression ties between neighbours are decided by the last bit of the
+    # strengths, so any rounding that differs from the definition shows up here
+    img = blocky_image(1000 + seed, 96 + seed, 130 + 3 * seed)
+    got, st = run_float(img)
+    assert st["status"] == canny.CANNY_OK
+    assert np.array_equal(got, oracle.canny_f32(img, 1.4, 7, 0.1, 0.3))
+
+
 def test_float_fused_flat_image_has_no_edges():
     img = np.full((100, 150), 77, np.uint8)
     got, st = run_float(img)

@@ -474,6 +474,10 @@ def measure_serving(n_requests: int, loads=(0.1, 0.25, 0.5, 0.9, 1.5), budget_gb
     rate = ls * capacity * 1e6 / mean_area
     ser = canny.canny_serve(cfg(1), trace(min(n_requests, 5000), rate, 10 + min(1, len(loads) - 1)))
     result["serial"] = dict(summary(ser, ls * capacity), load=ls, requests=min(n_requests, 5000))
+    # capacity of the serial loop (one canny_run_pitched per request, all arriving at once)
+    ser_cap = canny.canny_serve(cfg(1), trace(min(n_requests, 5000), 0.0, 1)).delivered_mpx_s
+    result["serial_capacity_mpx_s"] = round(ser_cap, 1)
+    result["capacity_vs_serial"] = round(capacity / ser_cap, 2) if ser_cap > 0 else None
     return result
 
 

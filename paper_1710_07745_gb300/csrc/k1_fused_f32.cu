@@ -86,17 +86,17 @@ __device__ __forceinline__ float2 tap_sum2(const FloatParams &fp, Load v)
 {
     float2 x = v(0);
     float2 acc = f2(fmul(fp.taps[0], x.x), fmul(fp.taps[0], x.y));
-    if (KS > 0) {
+    if constexpr (KS > 0) {
 #pragma unroll
         for (int k = 1; k < KS; ++k) {
             x = v(k);
             acc = f2(fadd(acc.x, fmul(fp.taps[k], x.x)), fadd(acc.y, fmul(fp.taps[k], x.y)));
         }
-        return acc;
-    }
-    for (int k = 1; k < fp.ksize; ++k) {
-        x = v(k);
-        acc = f2(fadd(acc.x, fmul(fp.taps[k], x.x)), fadd(acc.y, fmul(fp.taps[k], x.y)));
+    } else {
+        for (int k = 1; k < fp.ksize; ++k) {
+            x = v(k);
+            acc = f2(fadd(acc.x, fmul(fp.taps[k], x.x)), fadd(acc.y, fmul(fp.taps[k], x.y)));
+        }
     }
     return acc;
 }

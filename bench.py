@@ -328,6 +328,43 @@ def measure_batched(steps: int, cpu: bool = False) -> dict:
             "cpu_baseline": cpu_line}
 
 
+# ------------------------------------------------------------------ host link
+def host_link_bound(h_in, h_out, d_a, d_b, px: int) -> dict:
+    """The host link's own rate, for the end-to-end roofline: plain copies of one
+    step's bytes between the pinned buffers and device memory, each direction
+    alone and both at once on two streams (CUDA events)."""
+    import torch
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def timed(fn, reps=5):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps
+
+    def h2d():
+        with torch.cuda.stream(s1):
+            d_a.copy_(h_in, non_blocking=True)
+
+    def d2h():
+        with torch.cuda.stream(s2):
+            h_out.copy_(d_b, non_blocking=True)
+
+    def both():
+        h2d()
+        d2h()
+
+    t_h2d, t_d2h, t_both = timed(h2d), timed(d2h), timed(both)
+    nbytes = h_in.numel()
+    return {"h2d_gbs": round(nbytes / t_h2d / 1e9, 1), "d2h_gbs": round(nbytes / t_d2h / 1e9, 1),
+            "both_gbs": round(2 * nbytes / t_both / 1e9, 1),
+            "bound_mpx_s": round(px / t_both / 1e6, 1)}
+
+
 # ------------------------------------------------------------------ the other image sizes
 def measure_configs() -> list:
     """Per-image pipeline times on the smaller synthetic workloads: each run timed
@@ -577,7 +614,8 @@ def run_ours(args, rank: int, world: int) -> None:
                "h2d_bytes_per_step": px, "d2h_bytes_per_step": px, "steps": e2e_steps,
                "api": "canny_run_frames (pinned host buffers)",
                "single_call": {"value": round(world * single_steps * px / single_s / 1e6, 1),
-                               "api": "canny_run_host", "steps": single_steps}}
+                               "api": "canny_run_host", "steps": single_steps},
+               "link_bound": host_link_bound(h_in[0], h_out[0], d_in, d_out, px)}
 
     configs = None if args.no_configs else measure_configs()
     if configs is not None:

@@ -258,9 +258,11 @@ canny_status canny_run_noalloc(const uint8_t *d_in, int in_pitch, uint8_t *d_out
 /* One request of a served trace. */
 typedef struct {
     int w, h;               /* image size */
-    const uint8_t *h_in;    /* host, h rows of h_pitch bytes (page-locked memory copies fastest) */
+    const uint8_t *h_in;    /* host, h rows of h_pitch bytes; page-locked, 16-byte aligned buffers with
+                               h_pitch == w are read by one kernel per batch, others by copy-engine copies */
     int h_pitch;
-    uint8_t *h_out;         /* host buffer for the 0/255 edge map, or NULL to leave it on the device */
+    uint8_t *h_out;         /* host buffer for the 0/255 edge map (same rule as h_in), or NULL to leave
+                               it on the device */
     int out_pitch;
     double arrival_s;       /* arrival time, seconds after the start of the run; non-decreasing */
 } canny_request;
@@ -268,7 +270,7 @@ typedef struct {
 typedef struct {
     double memory_budget_bytes;   /* device memory for the requests' inputs and outputs */
     int streams;                  /* batches in flight at once (>= 1) */
-    int max_batch_images;         /* images per batch, at most */
+    int max_batch_images;         /* images per batch, at most (1 .. 65535) */
     int64_t max_batch_pixels;     /* pixels per batch, at most (>= the largest request) */
     int serial;                   /* 1: one request at a time through canny_run_pitched (baseline) */
     int low, high;                /* integer-path thresholds */

@@ -1014,7 +1014,9 @@ canny_status canny_run_frames(canny_ctx *c, int n, const uint8_t *const *h_in, i
         // upload frame i once the pipeline of frame i-2 has read this slot's input
         if (i >= 2) e = cudaStreamWaitEvent(c->s_up, f.comp, 0);
         if (e == cudaSuccess)
-            e = cudaMemcpy2DAsync(f.d_in, pitch, h_in[i], in_pitch, w, h, cudaMemcpyHostToDevice, c->s_up);
+            e = (in_pitch == w && pitch == w)   // contiguous: one linear copy
+                    ? cudaMemcpyAsync(f.d_in, h_in[i], (size_t)w * h, cudaMemcpyHostToDevice, c->s_up)
+                    : cudaMemcpy2DAsync(f.d_in, pitch, h_in[i], in_pitch, w, h, cudaMemcpyHostToDevice, c->s_up);
         if (e == cudaSuccess) e = cudaEventRecord(f.up, c->s_up);
         // pipeline of frame i once it is uploaded and frame i-2's edges are downloaded
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, f.up, 0);
@@ -1024,7 +1026,9 @@ canny_status canny_run_frames(canny_ctx *c, int n, const uint8_t *const *h_in, i
         // download frame i's edges
         if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_down, f.comp, 0);
         if (e == cudaSuccess)
-            e = cudaMemcpy2DAsync(h_out[i], out_pitch, f.d_out, pitch, w, h, cudaMemcpyDeviceToHost, c->s_down);
+            e = (out_pitch == w && pitch == w)
+                    ? cudaMemcpyAsync(h_out[i], f.d_out, (size_t)w * h, cudaMemcpyDeviceToHost, c->s_down)
+                    : cudaMemcpy2DAsync(h_out[i], out_pitch, f.d_out, pitch, w, h, cudaMemcpyDeviceToHost, c->s_down);
         if (e == cudaSuccess) e = cudaEventRecord(f.down, c->s_down);
     }
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->fslots[(n - 1) & 1].down, 0);

@@ -112,6 +112,23 @@ cudaError_t k1_add_batch_node(cudaGraph_t g, const cudaGraphNode_t *deps, size_t
                               const BatchImage *imgs, const CUtensorMap *tmaps, BatchHeader *hdr, IntThresholds t,
                               const HystScratch &hs, int ctas, cudaGraphNode_t *out);
 
+// ---------------------------------------------------------------- host images (hostio.cu)
+// One image between a tight, 16-byte aligned, device-accessible host buffer and
+// a pitched device buffer.
+struct HostCopy {
+    uint8_t *host;       // gather: source; scatter: destination (h rows of w bytes, no padding)
+    uint8_t *dev;        // gather: destination; scatter: source (h rows of dev_pitch bytes)
+    int w, h, dev_pitch, pad;
+};
+// True if host (pitch bytes per row, w wide) can take the kernel path: pinned and
+// mapped at the same address, 16-byte aligned, rows without padding.
+bool host_copy_ok(const void *host, int pitch, int w);
+uint64_t host_copy_words(int w, int h);
+// Copies d_copies[0 .. n) (a device array, n <= 65535) in one launch; total_words =
+// the sum of host_copy_words over the copies.
+cudaError_t launch_gather(const HostCopy *d_copies, int n, uint64_t total_words, cudaStream_t s);
+cudaError_t launch_scatter(const HostCopy *d_copies, int n, uint64_t total_words, cudaStream_t s);
+
 // ---------------------------------------------------------------- TMA (tma.cu)
 bool tma_usable(const void *base, int pitch);
 bool encode_u8_map(void *tmap_out, const void *base, int w, int h, int pitch, int box_w, int box_h);

@@ -2,9 +2,11 @@
 //
 // Requests (host images with arrival times) are admitted in arrival order as
 // device memory frees up: each admitted request gets its input and output
-// buffers from a device arena of a fixed byte budget, its input is copied in,
-// and every stream that is idle takes all admitted, not-yet-running requests as
-// one canny_run_batch. Several streams keep batches in flight at once, so new
+// buffers from a device arena of a fixed byte budget, and every stream that is
+// idle takes all admitted, not-yet-running requests as one batch: one gather
+// launch uploads their pinned host images (a copy-engine copy serves any other
+// host buffer), one canny_run_batch runs them, one scatter launch writes the
+// edge maps back. Several streams keep batches in flight at once, so new
 // arrivals start while earlier ones are still on the GPU. A request completes
 // when its batch's event fires; its latency is completion minus arrival, and
 // its memory returns to the arena. The serial mode runs the same trace one
@@ -97,7 +99,38 @@ struct Lane {
     canny_ctx *ctx = nullptr;
     cudaEvent_t done = nullptr;
     std::vector<Admitted> running;
+    // copy descriptors of the running batch: pinned staging and their device copies
+    HostCopy *h_copies = nullptr, *d_copies = nullptr;   // [2 * cap]: inputs, then outputs
 };
+
+// Uploads (or downloads) the batch's images: one gather (scatter) launch for the
+// pinned, tight, aligned host buffers, a copy-engine copy for any other.
+cudaError_t move_images(Lane &L, const canny_request *reqs, int cap, bool upload)
+{
+    HostCopy *hc = L.h_copies + (upload ? 0 : cap);
+    HostCopy *dc = L.d_copies + (upload ? 0 : cap);
+    int n = 0;
+    uint64_t words = 0;
+    for (const Admitted &a : L.running) {
+        const canny_request &r = reqs[a.req];
+        uint8_t *host = upload ? const_cast<uint8_t *>(r.h_in) : r.h_out;
+        const int hp = upload ? r.h_pitch : r.out_pitch;
+        if (!host) continue;
+        if (host_copy_ok(host, hp, r.w)) {
+            hc[n++] = HostCopy{host, upload ? a.in : a.out, r.w, r.h, a.pitch, 0};
+            words += host_copy_words(r.w, r.h);
+            continue;
+        }
+        const cudaError_t e =
+            upload ? cudaMemcpy2DAsync(a.in, a.pitch, host, hp, r.w, r.h, cudaMemcpyHostToDevice, L.stream)
+                   : cudaMemcpy2DAsync(host, hp, a.out, a.pitch, r.w, r.h, cudaMemcpyDeviceToHost, L.stream);
+        if (e != cudaSuccess) return e;
+    }
+    if (n == 0) return cudaSuccess;
+    cudaError_t e = cudaMemcpyAsync(dc, hc, sizeof(HostCopy) * n, cudaMemcpyHostToDevice, L.stream);
+    if (e != cudaSuccess) return e;
+    return upload ? launch_gather(dc, n, words, L.stream) : launch_scatter(dc, n, words, L.stream);
+}
 
 double pct(std::vector<double> v, double q)
 {
@@ -118,7 +151,8 @@ extern "C" canny_status canny_serve(const canny_serve_config *cfg, int n, const 
                                     double *latency_ms, canny_serve_report *out)
 {
     if (!cfg || n < 0 || (n > 0 && !reqs) || !out) return CANNY_EINVAL;
-    if (cfg->streams < 1 || cfg->max_batch_images < 1 || cfg->max_batch_pixels < 1 || cfg->memory_budget_bytes <= 0)
+    if (cfg->streams < 1 || cfg->max_batch_images < 1 || cfg->max_batch_images > 65535 || cfg->max_batch_pixels < 1 ||
+        cfg->memory_budget_bytes <= 0)
         return CANNY_EINVAL;
     int64_t max_px = 0;
     int max_w = 1, max_h = 1;
@@ -155,6 +189,13 @@ extern "C" canny_status canny_serve(const canny_serve_config *cfg, int n, const 
         st = cfg->serial ? canny_create(max_w, max_h, &p, &L.ctx)
                          : canny_create((int)std::min<int64_t>(cap, 1 << 30), 1, &p, &L.ctx);
         if (st != CANNY_OK) break;
+        const size_t cbytes = sizeof(HostCopy) * 2 * (size_t)cfg->max_batch_images;
+        if (cudaHostAlloc((void **)&L.h_copies, cbytes, cudaHostAllocDefault) != cudaSuccess ||
+            cudaMalloc((void **)&L.d_copies, cbytes) != cudaSuccess) {
+            cudaGetLastError();
+            st = CANNY_ENOMEM;
+            break;
+        }
         if (cfg->band) {
             canny_tuning t = {cfg->band, cfg->ctas_per_sm ? cfg->ctas_per_sm : 12, 0.0, 0, 0};
             st = canny_set_tuning(L.ctx, &t);
@@ -220,22 +261,13 @@ extern "C" canny_status canny_serve(const canny_serve_config *cfg, int n, const 
             admitted.erase(admitted.begin(), admitted.begin() + (long)k);
             for (const Admitted &a : L.running) {
                 const canny_request &r = reqs[a.req];
-                if (cudaMemcpy2DAsync(a.in, a.pitch, r.h_in, r.h_pitch, r.w, r.h, cudaMemcpyHostToDevice, L.stream) !=
-                    cudaSuccess) { st = CANNY_ECUDA; break; }
                 imgs.push_back(canny_image{a.in, a.out, r.w, r.h, a.pitch, a.pitch});
             }
-            if (st != CANNY_OK) break;
+            if (move_images(L, reqs, cfg->max_batch_images, true) != cudaSuccess) { st = CANNY_ECUDA; break; }
             st = cfg->serial ? canny_run_pitched(L.ctx, &imgs[0], L.stream)
                              : canny_run_batch(L.ctx, (int)imgs.size(), imgs.data(), L.stream);
             if (st != CANNY_OK) break;
-            for (const Admitted &a : L.running) {
-                const canny_request &r = reqs[a.req];
-                if (r.h_out && cudaMemcpy2DAsync(r.h_out, r.out_pitch, a.out, a.pitch, r.w, r.h,
-                                                 cudaMemcpyDeviceToHost, L.stream) != cudaSuccess) {
-                    st = CANNY_ECUDA;
-                    break;
-                }
-            }
+            if (move_images(L, reqs, cfg->max_batch_images, false) != cudaSuccess) st = CANNY_ECUDA;
             if (st == CANNY_OK && cudaEventRecord(L.done, L.stream) != cudaSuccess) st = CANNY_ECUDA;
             ++batches;
             batched_images += (int64_t)L.running.size();
@@ -262,6 +294,8 @@ extern "C" canny_status canny_serve(const canny_serve_config *cfg, int n, const 
             arena.release(a.out, a.bytes);
         }
         if (L.ctx) canny_destroy(L.ctx);
+        if (L.h_copies) cudaFreeHost(L.h_copies);
+        if (L.d_copies) cudaFree(L.d_copies);
         if (L.done) cudaEventDestroy(L.done);
         if (L.stream) cudaStreamDestroy(L.stream);
     }

@@ -587,6 +587,50 @@ def test_serving_results_equal_alone_and_in_the_mix():
     assert rep["batches"] < len(imgs) and rep["mean_batch_images"] > 1.0
 
 
+def test_serving_pinned_and_pageable_host_buffers():
+    # pinned, tight and aligned buffers go through one gather / scatter kernel per
+    # batch; pageable, unaligned or padded ones through copy-engine copies
+    imgs, arrivals = _trace(40, 13, 0.02)
+    reqs, keep, outs = [], [], []
+    for i, (im, t) in enumerate(zip(imgs, arrivals)):
+        h, w = im.shape
+        kind = i % 4
+        if kind == 0:                                  # pinned, tight: kernel path both ways
+            src = torch.from_numpy(im.copy()).pin_memory()
+            dst = torch.full((h, w), 9, dtype=torch.uint8).pin_memory()
+            keep += [src, dst]
+            reqs.append(canny.canny_request(w, h, src.data_ptr(), w, dst.data_ptr(), w, float(t)))
+            outs.append(lambda d=dst: d.numpy())
+        elif kind == 1:                                # pageable
+            dst = np.full((h, w), 9, np.uint8)
+            keep += [im, dst]
+            reqs.append(canny.canny_request(w, h, im.ctypes.data, w, dst.ctypes.data, w, float(t)))
+            outs.append(lambda d=dst: d)
+        elif kind == 2:                                # pinned but one byte off 16-byte alignment
+            buf = torch.zeros(h * w + 1, dtype=torch.uint8).pin_memory()
+            buf[1:] = torch.from_numpy(im.reshape(-1))
+            dbuf = torch.full((h * w + 1,), 9, dtype=torch.uint8).pin_memory()
+            keep += [buf, dbuf]
+            reqs.append(canny.canny_request(w, h, buf.data_ptr() + 1, w, dbuf.data_ptr() + 1, w, float(t)))
+            outs.append(lambda d=dbuf, h=h, w=w: d[1:].numpy().reshape(h, w))
+        else:                                          # pinned, padded rows
+            src = torch.zeros((h, w + 7), dtype=torch.uint8).pin_memory()
+            src[:, :w] = torch.from_numpy(im)
+            dst = torch.full((h, w + 5), 9, dtype=torch.uint8).pin_memory()
+            keep += [src, dst]
+            reqs.append(canny.canny_request(w, h, src.data_ptr(), w + 7, dst.data_ptr(), w + 5, float(t)))
+            outs.append(lambda d=dst, w=w: d.numpy()[:, :w])
+    cfg = canny.canny_serve_config(float(64 << 20), 2, 64, 1 << 24, 0, 40, 100, 0, 0)
+    rep = canny.canny_serve(cfg, reqs).as_dict()
+    assert rep["completed"] == len(imgs)
+    for i, (im, get) in enumerate(zip(imgs, outs)):
+        assert np.array_equal(get(), oracle.canny_u8(im)), i
+    # padding bytes of the padded output rows are untouched
+    for i in range(3, len(imgs), 4):
+        d = keep[2 * i + 1].numpy()
+        assert (d[:, imgs[i].shape[1]:] == 9).all()
+
+
 def test_serving_under_a_tight_memory_budget():
     imgs, arrivals = _trace(30, 12, 0.0)     # everything arrives at once
     biggest = max((((im.shape[1] + 15) // 16) * 16) * im.shape[0] for im in imgs)

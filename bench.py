@@ -410,7 +410,8 @@ def measure_configs() -> list:
                     "stencil_ms": round(tm["stencil_ms"] / runs, 4),
                     "local_ms": round(tm["local_ms"] / runs, 4),
                     "global_ms": round(tm["global_ms"] / runs, 4),
-                    "hyst_passes": int(st["hyst_passes"])})
+                    "hyst_passes": int(st["hyst_passes"]), "pending_tiles": int(st["pending_tiles"]),
+                    "tiles_visited": int(st["hyst_tiles_visited"])})
         ctx.close()
         del d_in, d_out
     return out
@@ -446,7 +447,8 @@ def measure_float_on(d_in, d_out, name: str, n: int) -> dict:
     runs = max(1, tm["runs"])
     return {"workload": name, "w": w, "h": h, "runs": n, "mean_ms": round(ms, 4),
             "mpx_s": round(w * h / ms / 1e3, 1), "stencil_ms": round(tm["stencil_ms"] / runs, 4),
-            "global_ms": round(tm["global_ms"] / runs, 4), "hyst_passes": int(st["hyst_passes"])}
+            "global_ms": round(tm["global_ms"] / runs, 4), "hyst_passes": int(st["hyst_passes"]),
+            "pending_tiles": int(st["pending_tiles"]), "tiles_visited": int(st["hyst_tiles_visited"])}
 
 
 # ------------------------------------------------------------------ serving
@@ -581,7 +583,8 @@ def run_ours(args, rank: int, world: int) -> None:
               "stencil_ms": round(k1_ms, 4),
               "local_ms": round(tm["local_ms"] / max(1, tm["runs"]), 4),
               "global_ms": round(tm["global_ms"] / max(1, tm["runs"]), 4),
-              "hyst_passes": passes, "pending_tiles": int(st["pending_tiles"])}
+              "hyst_passes": passes, "pending_tiles": int(st["pending_tiles"]),
+              "tiles_visited": int(st["hyst_tiles_visited"])}
     dominant = max(("reset_ms", "stencil_ms", "local_ms", "global_ms"), key=lambda k: stages[k])
 
     e2e = None

@@ -420,22 +420,13 @@ canny_status build_batch_graph(canny_ctx *c, canny_ctx::Slot &sl)
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaGraphCreate(&g, 0);
     if (e != cudaSuccess) return from_cuda(e);
-    cudaGraphNode_t up1, up2, clr, init, k1, loop;
+    cudaGraphNode_t up1, up2, init, k1, loop;
     e = cudaGraphAddMemcpyNode1D(&up1, g, nullptr, 0, c->d_blob, sl.h_blob, L.dev_bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaGraphAddMemcpyNode1D(&up2, g, nullptr, 0, c->hs.imgs, sl.h_blob + L.himgs,
                                      sizeof(HystImage) * c->blob_cap, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) {
-        cudaMemsetParams mp = {};
-        mp.dst = c->hs.stamp;
-        mp.value = 0;
-        mp.elementSize = 4;
-        mp.width = c->hs.max_tiles;
-        mp.height = 1;
-        e = cudaGraphAddMemsetNode(&clr, g, nullptr, 0, &mp);
-    }
-    cudaGraphNode_t d_init[2] = {up1, clr};
-    if (e == cudaSuccess) e = hyst_add_init_from_header(g, d_init, 2, c->hs, hdr, &init);
+    // (the worklist stamps need no clearing: the fused kernel writes every tile's stamp)
+    if (e == cudaSuccess) e = hyst_add_init_from_header(g, &up1, 1, c->hs, hdr, &init);
     cudaGraphNode_t d_k1[2] = {up2, init};
     if (e == cudaSuccess)
         e = k1_add_batch_node(g, d_k1, 2, c->band, imgs, tmaps, hdr, c->it, c->hs, sm_count() * c->ctas_per_sm, &k1);

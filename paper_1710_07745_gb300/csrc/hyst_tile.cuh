@@ -140,7 +140,11 @@ __device__ __forceinline__ void finish_tile(const HystScratch &hs, uint32_t t, u
         hs.masks[t] = m;
         if (any_pend) atomicAdd(&hs.state->pending_tiles, 1u);
         // pending pixels on the border may be reached from a neighbour: queue for pass 0
-        if (m.pend_top | m.pend_bottom | m.pend_left | m.pend_right) push(hs, 0, t, 1);
+        // every tile of a run writes its own stamp here, so no clearing pass is needed:
+        // 1 = queued for pass 0, 0 = not queued
+        const bool queue = (m.pend_top | m.pend_bottom | m.pend_left | m.pend_right) != 0;
+        hs.stamp[t] = queue ? 1u : 0u;
+        if (queue) hs.lists[atomicAdd(&hs.state->list_count[0], 1u)] = t;
     }
 }
 

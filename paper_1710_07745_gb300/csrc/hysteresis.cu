@@ -349,8 +349,7 @@ int hyst_pass_grid()
 cudaError_t hyst_reset(const HystScratch &hs, uint32_t ntiles, uint32_t nimg, uint32_t max_passes,
                        cudaStream_t s, const HystImage *single)
 {
-    cudaError_t err = cudaMemsetAsync(hs.stamp, 0, sizeof(uint32_t) * (size_t)ntiles, s);
-    if (err != cudaSuccess) return err;
+    // the worklist stamps need no clearing: the local fill writes every tile's stamp
     HystImage one = single ? *single : HystImage{};
     hyst_init_kernel<<<1, 1, 0, s>>>(hs.state, ntiles, nimg, max_passes, hs.imgs, one, single ? 1 : 0);
     return cudaGetLastError();

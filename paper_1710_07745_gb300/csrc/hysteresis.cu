@@ -95,9 +95,7 @@ struct TileSeeds {
 
 __device__ __forceinline__ bool find_seeds(const HystScratch &hs, uint32_t t, int nimg, TileSeeds &sd)
 {
-    const TileMasks mu = masks_cg(&hs.masks[t]);
-    if ((mu.pend_top | mu.pend_bottom | mu.pend_left | mu.pend_right) == 0) return false;
-    sd.im = hs.imgs[find_image(hs.imgs, nimg, t)];
+    sd.im = hs.imgs[find_image(hs.imgs, nimg, t)];      // read-only during the pass: cached
     const HystImage &im = sd.im;
     const uint32_t local = t - im.tile_base;
     const int tx = (int)(local % (uint32_t)im.ntx), ty = (int)(local / (uint32_t)im.ntx);
@@ -106,40 +104,31 @@ __device__ __forceinline__ bool find_seeds(const HystScratch &hs, uint32_t t, in
     const bool hasL = tx > 0, hasR = tx < im.ntx - 1, hasU = ty > 0, hasD = ty < im.nty - 1;
     const uint32_t ntx = (uint32_t)im.ntx;
     const TileMasks *M = hs.masks;
-    uint32_t s_top = 0, s_bot = 0, s_left = 0, s_right = 0;
-    if (hasU && mu.pend_top) {
-        uint32_t a = edge_bottom_cg(&M[t - ntx]);
-        uint32_t ring = a | (a << 1) | (a >> 1);
-        if (hasL && (edge_bottom_cg(&M[t - ntx - 1]) >> 31)) ring |= 1u;
-        if (hasR && (edge_bottom_cg(&M[t - ntx + 1]) & 1u)) ring |= 1u << 31;
-        s_top = ring & mu.pend_top;
-    }
-    if (hasD && mu.pend_bottom) {
-        uint32_t a = edge_top_cg(&M[t + ntx]);
-        uint32_t ring = a | (a << 1) | (a >> 1);
-        if (hasL && (edge_top_cg(&M[t + ntx - 1]) >> 31)) ring |= 1u;
-        if (hasR && (edge_top_cg(&M[t + ntx + 1]) & 1u)) ring |= 1u << 31;
-        s_bot = ring & mu.pend_bottom;
-    }
-    if (hasL && mu.pend_left) {
-        uint32_t a = edge_right_cg(&M[t - 1]);
-        s_left = (a | (a << 1) | (a >> 1)) & mu.pend_left;
-    }
-    if (hasR && mu.pend_right) {
-        uint32_t a = edge_left_cg(&M[t + 1]);
-        s_right = (a | (a << 1) | (a >> 1)) & mu.pend_right;
-    }
-    sd.top = s_top;
-    sd.bot = s_bot;
-    sd.left = s_left;
-    sd.right = s_right;
-    return (s_top | s_bot | s_left | s_right) != 0;
+    // every word this test may need, loaded at once (one round trip to L2)
+    const TileMasks mu = masks_cg(&M[t]);
+    const uint32_t eu = hasU ? edge_bottom_cg(&M[t - ntx]) : 0u;
+    const uint32_t eul = hasU && hasL ? edge_bottom_cg(&M[t - ntx - 1]) : 0u;
+    const uint32_t eur = hasU && hasR ? edge_bottom_cg(&M[t - ntx + 1]) : 0u;
+    const uint32_t ed = hasD ? edge_top_cg(&M[t + ntx]) : 0u;
+    const uint32_t edl = hasD && hasL ? edge_top_cg(&M[t + ntx - 1]) : 0u;
+    const uint32_t edr = hasD && hasR ? edge_top_cg(&M[t + ntx + 1]) : 0u;
+    const uint32_t el = hasL ? edge_right_cg(&M[t - 1]) : 0u;
+    const uint32_t er = hasR ? edge_left_cg(&M[t + 1]) : 0u;
+    // pending border pixels next to an edge pixel of a neighbouring tile
+    const uint32_t ring_top = eu | (eu << 1) | (eu >> 1) | (eul >> 31) | ((eur & 1u) << 31);
+    const uint32_t ring_bot = ed | (ed << 1) | (ed >> 1) | (edl >> 31) | ((edr & 1u) << 31);
+    sd.top = ring_top & mu.pend_top;
+    sd.bot = ring_bot & mu.pend_bottom;
+    sd.left = (el | (el << 1) | (el >> 1)) & mu.pend_left;
+    sd.right = (er | (er << 1) | (er >> 1)) & mu.pend_right;
+    return (sd.top | sd.bot | sd.left | sd.right) != 0;
 }
 
 // Tile t grows its seeds through its pending pixels (whole warp, lane = row).
 // Returns (in every lane) the mask of neighbours (NB_* bits) whose facing
 // border has pending pixels next to an edge this call added.
-__device__ __forceinline__ uint32_t grow_tile(const HystScratch &hs, uint32_t t, const TileSeeds &sd, int lane)
+__device__ __forceinline__ uint32_t grow_tile(const HystScratch &hs, uint32_t t, const TileSeeds &sd, int lane,
+                                              uint32_t p)
 {
     const HystImage &im = sd.im;
     const int tx = sd.tx, ty = sd.ty;
@@ -147,7 +136,6 @@ __device__ __forceinline__ uint32_t grow_tile(const HystScratch &hs, uint32_t t,
     const uint32_t ntx = (uint32_t)im.ntx;
     const TileMasks *M = hs.masks;
     const uint32_t s_top = sd.top, s_bot = sd.bot, s_left = sd.left, s_right = sd.right;
-    uint32_t p = __ldcg(&hs.pend_bits[(size_t)t * HT + lane]);
     uint32_t e0 = ((s_left >> lane) & 1u) | (((s_right >> lane) & 1u) << 31);
     if (lane == 0) e0 |= s_top;
     if (lane == HT - 1) e0 |= s_bot;
@@ -183,7 +171,13 @@ __device__ __forceinline__ uint32_t grow_tile(const HystScratch &hs, uint32_t t,
         atomicAnd(&mt->pend_bottom, p_bot);
         atomicAnd(&mt->pend_left, p_left);
         atomicAnd(&mt->pend_right, p_right);
-        __threadfence();
+        // Only a block-scope fence (this warp reads these masks again when it
+        // follows into a neighbour): a warp of another CTA working on a neighbour
+        // at the same time may miss these edges, but this warp checks that
+        // neighbour's pending border next and follows into it (a stale pending
+        // mask only has more bits), so no seed is lost; the end of the pass
+        // orders everything for the next one.
+        __threadfence_block();
         // neighbours whose facing border has pending pixels next to a new edge
         if (hasU && e_top) {
             uint32_t d = e_top | (e_top << 1) | (e_top >> 1);
@@ -206,7 +200,7 @@ __device__ __forceinline__ uint32_t grow_tile(const HystScratch &hs, uint32_t t,
             if (__ldcg(&M[t + 1].pend_left) & d) aff |= 1u << NB_R;
         }
     }
-    return __shfl_sync(FULL, aff, 0);   // lane 0's mask updates and fence precede every lane's later loads
+    return __shfl_sync(FULL, aff, 0);
 }
 
 // One pass over the current worklist. A warp that adds edges next to a
@@ -254,8 +248,9 @@ hyst_global_kernel(HystScratch hs, int in_graph, cudaGraphConditionalHandle cond
             for (;;) {
                 TileSeeds sd;
                 uint32_t aff = 0, ntx = 0;
+                const uint32_t p_row = __ldcg(&hs.pend_bits[(size_t)t * HT + lane]);   // issued with the masks
                 if (find_seeds(hs, t, nimg, sd)) {
-                    aff = grow_tile(hs, t, sd, lane);
+                    aff = grow_tile(hs, t, sd, lane, p_row);
                     ntx = (uint32_t)sd.im.ntx;
                 }
                 ++my_visits;

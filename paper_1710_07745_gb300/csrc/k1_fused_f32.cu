@@ -147,18 +147,53 @@ __device__ __forceinline__ float2 strength2_pair(const float *S, int sx, int r, 
     return f2(out[0], out[1]);
 }
 
-// Steps 1-2 for one block up to the smoothed image S (left in region 0).
+// float(byte k of w), exactly: 2^23 + byte from a byte permute, minus 2^23.
+__device__ __forceinline__ float byte_f(uint32_t w, int k)
+{
+    return __fadd_rn(__uint_as_float(__byte_perm(w, 0x4B000000u, 0x7640u | (uint32_t)k)), -8388608.f);
+}
+
+// Horizontal pass of one row for NOUT consecutive outputs H[c0 .. c0+NOUT) at
+// image columns x0 - 2 + c0 + q, straight from global memory: the 48 bytes from
+// the 16-byte aligned column x0 + c0 - 16 hold every input these outputs read
+// (for a radius up to 14). No clamping: the caller checks the block is inside.
+template <int KS, int NOUT>
+__device__ __forceinline__ void hrow_regs(const uint8_t *row, int x0, int c0, const FloatParams &fp, float *dst)
+{
+    constexpr int R = KS / 2;
+    const uint4 *src = reinterpret_cast<const uint4 *>(row + x0 + c0 - 16);
+    const uint4 a = __ldg(src), b = __ldg(src + 1), c = __ldg(src + 2);
+    const uint32_t wd[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+    // window index of image column x0 - 2 + c0 + q - R + k is 14 + q - R + k
+    constexpr int LO = 14 - R, N = NOUT + 2 * R;
+    float v[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = byte_f(wd[(LO + i) >> 2], (LO + i) & 3);
+    float out[NOUT];
+#pragma unroll
+    for (int q = 0; q < NOUT; ++q) {
+        float acc = fmul(fp.taps[0], v[q]);
+#pragma unroll
+        for (int k = 1; k < KS; ++k) acc = fadd(acc, fmul(fp.taps[k], v[q + k]));
+        out[q] = acc;
+    }
+#pragma unroll
+    for (int q = 0; q < NOUT; q += 4)
+        *reinterpret_cast<float4 *>(dst + q) = make_float4(out[q], out[q + 1], out[q + 2], out[q + 3]);
+}
+
+// Step 1's horizontal pass through a staged copy of the input (blocks at the
+// image's left or right edge, or inputs without 16-byte alignment): the input
+// block is staged as floats with clamped columns, then H is computed at the
+// clamped columns, rows paired.
 template <int KS>
-__device__ __forceinline__ void smooth_block(const uint8_t *__restrict__ in, int in_pitch, int w, int h,
+__device__ __forceinline__ void staged_hpass(const uint8_t *__restrict__ in, int in_pitch, int w, int h,
                                              const FloatParams &fp, const Geometry &g, int x0, int y0,
-                                             float *r0, float *r1)
+                                             float *I_s, float *H_s, bool aligned)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ox = x0 - g.padx, oy = y0 - g.pady;
-    float *I_s = r0, *H_s = r1;
-    // stage the input, replicate border by clamping (rows always; columns only
-    // in blocks that reach past the image's left or right edge)
-    const bool vec = ox >= 0 && ox + g.IX <= w && ((((uintptr_t)in) | (uintptr_t)in_pitch) & 15) == 0;
+    const bool vec = ox >= 0 && ox + g.IX <= w && aligned;
     if (vec) {
         const int per_row = g.IX / 16;
         for (int i = tid; i < g.IY * per_row; i += FB_THREADS) {
@@ -204,12 +239,42 @@ __device__ __forceinline__ void smooth_block(const uint8_t *__restrict__ in, int
             hpass(p, FB_W + (i - p * (g.SX - FB_W)));
         }
     }
+}
+
+// Steps 1-2 for one block up to the smoothed image S (left in region 0).
+template <int KS>
+__device__ __forceinline__ void smooth_block(const uint8_t *__restrict__ in, int in_pitch, int w, int h,
+                                             const FloatParams &fp, const Geometry &g, int x0, int y0,
+                                             float *r0, float *r1)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int oy = y0 - g.pady;
+    float *I_s = r0, *H_s = r1;
+    // horizontal pass; the border is replicated by clamping (rows always,
+    // columns only in blocks that reach past the image's left or right edge)
+    const bool aligned = ((((uintptr_t)in) | (uintptr_t)in_pitch) & 15) == 0;
+    if (KS > 0 && KS <= 29 && aligned && x0 >= 16 && x0 + FB_W + 32 <= w) {
+        // inside the image: horizontal pass from registers, lane = row (a row
+        // stride of SX = 132 floats keeps the 16-byte stores conflict-free)
+        constexpr int NSEG = FB_W / 16;                     // 8 segments of 16 outputs, then 4 more
+        const int rblocks = (g.IY + 31) / 32;
+        for (int item = warp; item < (NSEG + 1) * rblocks; item += FB_WARPS) {
+            const int seg = item % (NSEG + 1), r = 32 * (item / (NSEG + 1)) + lane;
+            if (r >= g.IY) continue;
+            const uint8_t *row = in + (int64_t)clampi(oy + r, 0, h - 1) * in_pitch;
+            if (seg < NSEG) hrow_regs<(KS > 0 ? KS : 3), 16>(row, x0, 16 * seg, fp, H_s + r * g.SX + 16 * seg);
+            else hrow_regs<(KS > 0 ? KS : 3), 4>(row, x0, FB_W, fp, H_s + r * g.SX + FB_W);
+        }
+        __syncthreads();
+    } else {
+        staged_hpass<KS>(in, in_pitch, w, h, fp, g, x0, y0, I_s, H_s, aligned);
+    }
     __syncthreads();
     // vertical pass at rows clamp(y0 - 2 + r), columns paired (2q, 2q + 1):
     // S(clamp(x), clamp(y)) into region 0
     float *S_s = r0;
     {
-        const int qn = g.SX / 2;
+        const int qn = g.SX / 2;                            // 66 column pairs
         auto vpass = [&](int r, int q) {
             const int Y = clampi(y0 - 2 + r, 0, h - 1);
             const float *src = H_s + (Y - g.R - oy) * g.SX + 2 * q;
@@ -217,11 +282,33 @@ __device__ __forceinline__ void smooth_block(const uint8_t *__restrict__ in, int
                 tap_sum2<KS>(fp, [&](int k) { return *reinterpret_cast<const float2 *>(src + k * g.SX); });
             *reinterpret_cast<float2 *>(S_s + r * g.SX + 2 * q) = acc;
         };
-        for (int r = warp; r < g.SY; r += FB_WARPS)
-            for (int q = lane; q < 64; q += 32) vpass(r, q);
-        for (int i = tid; i < g.SY * (qn - 64); i += FB_THREADS) {          // the last pairs of each row
-            const int r = i / (qn - 64);
-            vpass(r, 64 + (i - r * (qn - 64)));
+        // four output rows per item: where their source rows are consecutive (no
+        // clamping) the KS + 3 rows are loaded once and shared
+        constexpr int RB = 4;
+        const int groups = g.SY / RB;
+        for (int item = tid; item < groups * qn; item += FB_THREADS) {
+            const int rg = item / qn, q = item - rg * qn, rb = RB * rg;
+            const int Ya = clampi(y0 - 2 + rb, 0, h - 1), Yb = clampi(y0 - 2 + rb + RB - 1, 0, h - 1);
+            if constexpr (KS > 0) {
+                if (Yb - Ya == RB - 1) {
+                    const float *src = H_s + (Ya - g.R - oy) * g.SX + 2 * q;
+                    float2 win[KS + RB - 1];
+#pragma unroll
+                    for (int i = 0; i < KS + RB - 1; ++i) win[i] = *reinterpret_cast<const float2 *>(src + i * g.SX);
+#pragma unroll
+                    for (int o = 0; o < RB; ++o) {
+                        float2 acc = f2(fmul(fp.taps[0], win[o].x), fmul(fp.taps[0], win[o].y));
+#pragma unroll
+                        for (int k = 1; k < KS; ++k)
+                            acc = f2(fadd(acc.x, fmul(fp.taps[k], win[o + k].x)),
+                                     fadd(acc.y, fmul(fp.taps[k], win[o + k].y)));
+                        *reinterpret_cast<float2 *>(S_s + (rb + o) * g.SX + 2 * q) = acc;
+                    }
+                    continue;
+                }
+            }
+#pragma unroll 1
+            for (int o = 0; o < RB; ++o) vpass(rb + o, q);
         }
     }
     __syncthreads();

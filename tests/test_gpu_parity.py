@@ -430,7 +430,7 @@ def run_float(img, sigma=1.4, ksize=7, lo=0.1, hi=0.3):
 # operation order: the edge maps are expected to equal the fp32 oracle's exactly
 # (the tolerance check is the bar; equality is what the operation order gives).
 @pytest.mark.parametrize("ksize,sigma", [(3, 0.8), (5, 1.0), (7, 1.4), (9, 2.0), (11, 2.0), (13, 2.5), (31, 6.0)])
-@pytest.mark.parametrize("h,w", [(200, 300), (67, 131), (129, 257)])
+@pytest.mark.parametrize("h,w", [(200, 300), (67, 131), (129, 257), (100, 512), (67, 400)])
 def test_float_fused_every_kernel_size(ksize, sigma, h, w):
     img = blocky_image(ksize * 7 + h, h, w)
     gx, gy, M, cls, want = float_reference(img, sigma, ksize, 0.08, 0.25)
@@ -454,7 +454,10 @@ def test_float_fused_tiny_and_block_edges(h, w):
 def test_float_fused_exact_on_many_images(seed):
     # suppression ties between neighbours are decided by the last bit of the
     # strengths, so any rounding that differs from the definition shows up here
-    img = blocky_image(1000 + seed, 96 + seed, 130 + 3 * seed)
+    # odd widths take the staged path; widths that are multiples of 16 and at least
+    # 288 also take the register path for the blocks inside the image
+    w = 130 + 3 * seed if seed % 2 else 288 + 16 * seed
+    img = blocky_image(1000 + seed, 96 + seed, w)
     got, st = run_float(img)
     assert st["status"] == canny.CANNY_OK
     assert np.array_equal(got, oracle.canny_f32(img, 1.4, 7, 0.1, 0.3))

@@ -384,8 +384,6 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint
             float4 *mdst = reinterpret_cast<float4 *>(&S.m2[rs][LPX * lane]);
             mdst[0] = make_float4(m[0].x, m[1].x, m[2].x, m[3].x);
             mdst[1] = make_float4(m[0].y, m[1].y, m[2].y, m[3].y);
-            const float rowmax = fmaxf(fmaxf(fmaxf(m[0].x, m[0].y), fmaxf(m[1].x, m[1].y)),
-                                       fmaxf(fmaxf(m[2].x, m[2].y), fmaxf(m[3].x, m[3].y)));
             // queue the previous row's candidates now that its lower neighbour row exists
             // (row offset u within this group's queued rows Y0 - 8 + g .. Y0 - 6 + g)
             if (cm_prev && r - 1 >= Y0 && r - 1 < Y0 + BAND) {
@@ -395,25 +393,24 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint
                     if ((cm_prev >> k) & 1u)
                         S.queue[idx++] = (uint32_t)(LPX * lane + k) | ((uint32_t)u << 8) | (gprev[k] << 10);
             }
+            // which pixels are candidates, and their gradients for the sector test (computed
+            // for every lane without a branch: nearly every row has a candidate somewhere)
             uint32_t cm = 0;
-            if (rowmax > lo2 && out_lane) {
-                // candidate lane: which pixels, and their gradients for the sector test
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    cm |= (m[j].x > lo2 ? 1u : 0u) << j;
-                    cm |= (m[j].y > lo2 ? 1u : 0u) << (j + 4);
-                }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    // 2^23 + 1024 + g holds g + 1024 (11 bits) in its low mantissa bits;
-                    // shifted left by 11, the exponent bits leave the word
-                    const uint32_t ax = __float_as_uint(gx[j].x + 8389632.0f), ay = __float_as_uint(gy[j].x + 8389632.0f);
-                    const uint32_t bx = __float_as_uint(gx[j].y + 8389632.0f), by = __float_as_uint(gy[j].y + 8389632.0f);
-                    gprev[j] = (ax & 2047u) | (ay << 11);
-                    gprev[j + 4] = (bx & 2047u) | (by << 11);
-                }
+            for (int j = 0; j < 4; ++j) {
+                cm |= (m[j].x > lo2 ? 1u : 0u) << j;
+                cm |= (m[j].y > lo2 ? 1u : 0u) << (j + 4);
             }
-            cm_prev = cm;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                // 2^23 + 1024 + g holds g + 1024 (11 bits) in its low mantissa bits;
+                // shifted left by 11, the exponent bits leave the word
+                const uint32_t ax = __float_as_uint(gx[j].x + 8389632.0f), ay = __float_as_uint(gy[j].x + 8389632.0f);
+                const uint32_t bx = __float_as_uint(gx[j].y + 8389632.0f), by = __float_as_uint(gy[j].y + 8389632.0f);
+                gprev[j] = (ax & 2047u) | (ay << 11);
+                gprev[j + 4] = (bx & 2047u) | (by << 11);
+            }
+            cm_prev = out_lane ? cm : 0u;
         }
         // ---- Step 3 + thresholds for the queued pixels (their rows +-1 are in the ring)
         __syncwarp();

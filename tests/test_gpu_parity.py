@@ -579,7 +579,10 @@ def _serve(imgs, arrivals, serial=0, budget=64 << 20, streams=2, max_batch_image
 
 
 def test_serving_results_equal_alone_and_in_the_mix():
-    imgs, arrivals = _trace(60, 11, 0.05)
+    # half the requests arrive together (they must share batches), the rest spread
+    # over 20 ms, arriving while earlier batches run
+    imgs, arrivals = _trace(60, 11, 0.02)
+    arrivals[:30] = 0.0
     outs, rep, lat = _serve(imgs, arrivals)
     assert rep["completed"] == len(imgs) and (lat > 0).all()
     outs_serial, rep_s, _ = _serve(imgs, arrivals, serial=1)

@@ -42,12 +42,12 @@ WORKLOAD = "canny_int_16384x16384"
 K1_BYTES_PER_PX = 2
 # ncu DRAM traffic of the fused kernel per 16384^2 launch, valid only for the kernel
 # source it was measured on (profiles/k1_fused_16384x8192.md: capture at half size, x2)
-K1_TRAFFIC = {"sha256_prefix": "e03876185b9c2f5c", "bytes": 467_478_528}
+K1_TRAFFIC = {"sha256_prefix": "86fce3b153800ed2", "bytes": 467_558_400}
 # whole pipeline floor: stencil 2 B/px + tile-local hysteresis read + write 2 B/px
 PIPE_BYTES_PER_PX = 4
 # ncu smsp__inst_executed.sum of the fused kernel per pixel (same capture and source
-# as K1_TRAFFIC: 285,353,421 warp instructions on 16384 x 8192 pixels)
-K1_INST = {"sha256_prefix": "e03876185b9c2f5c", "warp_inst_per_px": 285_353_421 / (16384 * 8192)}
+# as K1_TRAFFIC: 284,931,895 warp instructions on 16384 x 8192 pixels)
+K1_INST = {"sha256_prefix": "86fce3b153800ed2", "warp_inst_per_px": 284_931_895 / (16384 * 8192)}
 # warp instructions an SM can issue per clock (4 schedulers, one each)
 ISSUE_PER_SM_CLK = 4
 
@@ -655,7 +655,8 @@ def run_ours(args, rank: int, world: int) -> None:
         "serving": serving,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": int(args.steps * (3 + passes)),
+        # per step: the control-block reset, the fused kernel, one kernel per global pass
+        "gpu_launches": int(args.steps * (2 + passes)),
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)

@@ -431,7 +431,12 @@ struct Unit {
     bool tma;
 };
 
-template <int BAND, int MODE>
+// PATH: 0 = per unit (U.tma), 1 = TMA only, 2 = direct loads only. A kernel that
+// holds one path only is compiled for that path alone (no register pressure
+// from the other).
+enum { PATH_EITHER = 0, PATH_TMA = 1, PATH_DIRECT = 2 };
+
+template <int BAND, int MODE, int PATH>
 __device__ __forceinline__ void run_unit(const CUtensorMap *tmap, const Unit &U, IntThresholds t, uint8_t *out,
                                          int out_pitch, const HystScratch &hs, const HystImage &img, uint32_t *err,
                                          Smem<BAND> &S, int lane)
@@ -443,12 +448,14 @@ __device__ __forceinline__ void run_unit(const CUtensorMap *tmap, const Unit &U,
     }
     if (lane == 0) S.qcount = 0;
     __syncwarp();
-    if (U.tma) {
+    if (PATH == PATH_TMA || (PATH == PATH_EITHER && U.tma)) {
         // the previous unit's reads of the stage buffers are done before TMA reuses them
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        stencil_band<true, BAND>(tmap, U.in, U.in_pitch, U.w, U.h, t, S, lane, U.X0, U.Y0, err);
+        if constexpr (PATH != PATH_DIRECT)
+            stencil_band<true, BAND>(tmap, U.in, U.in_pitch, U.w, U.h, t, S, lane, U.X0, U.Y0, err);
     } else {
-        stencil_band<false, BAND>(tmap, U.in, U.in_pitch, U.w, U.h, t, S, lane, U.X0, U.Y0, err);
+        if constexpr (PATH != PATH_TMA)
+            stencil_band<false, BAND>(tmap, U.in, U.in_pitch, U.w, U.h, t, S, lane, U.X0, U.Y0, err);
     }
     __syncwarp();
 
@@ -498,10 +505,10 @@ __device__ __forceinline__ void init_barriers(Smem<BAND> &S, int lane)
 
 // ---------------------------------------------------------------- kernels
 // One image: one CTA per unit (blockIdx.x = strip, blockIdx.y = band).
-template <int BAND, int MODE>
+template <int BAND, int MODE, int PATH>
 __global__ void __launch_bounds__(THREADS, BAND == 64 ? 16 : 12)
 k1_fused_kernel(const __grid_constant__ CUtensorMap tmap, const uint8_t *__restrict__ in, int in_pitch,
-                int w, int h, int use_tma, IntThresholds t, uint8_t *__restrict__ out, int out_pitch,
+                int w, int h, IntThresholds t, uint8_t *__restrict__ out, int out_pitch,
                 HystScratch hs, HystImage img, uint32_t *err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -517,8 +524,8 @@ k1_fused_kernel(const __grid_constant__ CUtensorMap tmap, const uint8_t *__restr
     U.sy = blockIdx.y;
     U.X0 = U.sx * OUT_W;
     U.Y0 = U.sy * BAND;
-    U.tma = use_tma != 0;
-    run_unit<BAND, MODE>(&tmap, U, t, out, out_pitch, hs, img, err, S, lane);
+    U.tma = PATH == PATH_TMA;
+    run_unit<BAND, MODE, PATH>(&tmap, U, t, out, out_pitch, hs, img, err, S, lane);
 }
 
 // A batch: a persistent grid pops (image, strip, band) units from a counter.
@@ -563,7 +570,8 @@ k1_fused_batch_kernel(const BatchImage *__restrict__ imgs, const CUtensorMap *__
             asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&tmaps[lo]) : "memory");
         }
         __syncwarp();
-        run_unit<BAND, MODE_EDGES>(&tmaps[lo], U, t, img.map, img.pitch, hs, img, &hs.state->error, S, lane);
+        run_unit<BAND, MODE_EDGES, PATH_EITHER>(&tmaps[lo], U, t, img.map, img.pitch, hs, img, &hs.state->error, S,
+                                                lane);
     }
 }
 
@@ -574,14 +582,21 @@ cudaError_t launch_single(const CUtensorMap &tmap, bool tma, const uint8_t *in, 
 {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k1_fused_kernel<BAND, MODE>,
+        cudaError_t e = cudaFuncSetAttribute(k1_fused_kernel<BAND, MODE, PATH_TMA>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<BAND>));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k1_fused_kernel<BAND, MODE, PATH_DIRECT>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<BAND>));
         if (e != cudaSuccess) return e;
         attr = true;
     }
     dim3 grid((w + OUT_W - 1) / OUT_W, (h + BAND - 1) / BAND);
-    k1_fused_kernel<BAND, MODE><<<grid, THREADS, sizeof(Smem<BAND>), s>>>(tmap, in, in_pitch, w, h, tma ? 1 : 0, t,
-                                                                          out, out_pitch, hs, img, err);
+    if (tma)
+        k1_fused_kernel<BAND, MODE, PATH_TMA><<<grid, THREADS, sizeof(Smem<BAND>), s>>>(
+            tmap, in, in_pitch, w, h, t, out, out_pitch, hs, img, err);
+    else
+        k1_fused_kernel<BAND, MODE, PATH_DIRECT><<<grid, THREADS, sizeof(Smem<BAND>), s>>>(
+            tmap, in, in_pitch, w, h, t, out, out_pitch, hs, img, err);
     return cudaGetLastError();
 }
 

@@ -121,7 +121,14 @@ void canny_destroy(canny_ctx *ctx);
  */
 canny_status canny_run(canny_ctx *ctx, const uint8_t *d_in, uint8_t *d_out, void *stream);
 
-/* Edge map of one image of any size up to the context's, with its own pitches. */
+/*
+ * Edge map of one image of any size up to the context's, with its own pitches.
+ * An input whose base address or pitch is not a multiple of 16 bytes is first
+ * copied on the device into a 16-byte pitched staging buffer of the context
+ * (allocated on first need, which synchronises the device once, and kept until
+ * canny_destroy); if that allocation fails the image is read directly instead.
+ * Same for canny_run (pitch max_w) and canny_run_host.
+ */
 canny_status canny_run_pitched(canny_ctx *ctx, const canny_image *img, void *stream);
 
 /*

@@ -128,6 +128,13 @@ uint64_t host_copy_words(int w, int h);
 // the sum of host_copy_words over the copies.
 cudaError_t launch_gather(const HostCopy *d_copies, int n, uint64_t total_words, cudaStream_t s);
 cudaError_t launch_scatter(const HostCopy *d_copies, int n, uint64_t total_words, cudaStream_t s);
+// A device image (any pitch and alignment) copied into 16-byte pitched rows.
+struct Repitch {
+    const uint8_t *src;
+    uint8_t *dst;        // 16-byte aligned, dst_pitch a multiple of 16
+    int w, h, src_pitch, dst_pitch;
+};
+cudaError_t launch_repitch(const Repitch &c, cudaStream_t s);
 
 // ---------------------------------------------------------------- TMA (tma.cu)
 bool tma_usable(const void *base, int pitch);

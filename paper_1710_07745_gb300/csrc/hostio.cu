@@ -1,5 +1,6 @@
-// hostio.cu -- moving many images between tight host buffers and pitched device
-// buffers in one launch. The copy engines move a pitched (2D) copy row by row,
+// hostio.cu -- moving images into (and out of) 16-byte pitched device buffers:
+// tight host buffers, many in one launch, and device inputs whose base or pitch
+// the TMA path cannot use. The copy engines move a pitched (2D) copy row by row,
 // which for request-sized images (rows of about a kilobyte) runs at a fraction
 // of the host link's rate; these kernels instead read (or write) the tight host
 // image as one contiguous range of 16-byte words over the link, and place the
@@ -81,8 +82,7 @@ scatter_kernel(const HostCopy *__restrict__ copies)
     }
 }
 
-// CTAs per copy: about eight resident CTAs per SM over the whole launch.
-dim3 io_grid(int n, uint64_t total_words)
+int sm_total()
 {
     static int sms = 0;
     if (!sms) {
@@ -90,6 +90,13 @@ dim3 io_grid(int n, uint64_t total_words)
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
     }
+    return sms;
+}
+
+// CTAs per copy: about eight resident CTAs per SM over the whole launch.
+dim3 io_grid(int n, uint64_t total_words)
+{
+    const int sms = sm_total();
     const uint64_t per_copy = total_words / (uint64_t)n;                  // average words per copy
     uint64_t x = (uint64_t)sms * 8 / (uint64_t)n;
     const uint64_t useful = (per_copy + IO_THREADS - 1) / IO_THREADS;       // CTAs one copy can keep busy
@@ -98,7 +105,47 @@ dim3 io_grid(int n, uint64_t total_words)
     return dim3((unsigned)x, (unsigned)n);
 }
 
+// One 16-byte chunk of a destination row (chunk i of copy c): byte loads from
+// the source (served by L1), one 16-byte store.
+__device__ __forceinline__ void repitch_chunk(const Repitch &c, uint64_t i)
+{
+    const int chunks = (c.w + 15) / 16;
+    const int y = (int)(i / (uint64_t)chunks), x = 16 * (int)(i - (uint64_t)y * chunks);
+    const uint8_t *src = c.src + (int64_t)y * c.src_pitch + x;
+    const int n = min(16, c.w - x);
+    uint32_t wd[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+        if (k < n) wd[k >> 2] |= (uint32_t)__ldg(src + k) << (8 * (k & 3));
+    uint8_t *dst = c.dst + (int64_t)y * c.dst_pitch + x;
+    if (n == 16) {
+        *reinterpret_cast<uint4 *>(dst) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if (k < n) dst[k] = (uint8_t)(wd[k >> 2] >> (8 * (k & 3)));
+    }
+}
+
+__global__ void __launch_bounds__(IO_THREADS)
+repitch_kernel(Repitch c)
+{
+    const uint64_t total = (uint64_t)((c.w + 15) / 16) * (uint64_t)c.h;
+    for (uint64_t i = blockIdx.x * (uint64_t)IO_THREADS + threadIdx.x; i < total; i += (uint64_t)gridDim.x * IO_THREADS)
+        repitch_chunk(c, i);
+}
+
 }  // namespace
+
+cudaError_t launch_repitch(const Repitch &c, cudaStream_t s)
+{
+    if (c.w <= 0 || c.h <= 0) return cudaSuccess;
+    if ((((uintptr_t)c.dst) | (uintptr_t)c.dst_pitch) & 15) return cudaErrorInvalidValue;
+    const uint64_t work = (uint64_t)((c.w + 15) / 16) * (uint64_t)c.h;
+    const uint64_t need = (work + IO_THREADS - 1) / IO_THREADS, cap = (uint64_t)sm_total() * 8;
+    repitch_kernel<<<(unsigned)(need < cap ? need : cap), IO_THREADS, 0, s>>>(c);
+    return cudaGetLastError();
+}
 
 bool host_copy_ok(const void *host, int pitch, int w)
 {

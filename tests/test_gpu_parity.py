@@ -117,6 +117,33 @@ def test_pitched_buffers_leave_padding_untouched():
     assert np.array_equal(out[:, :w], oracle.canny_u8(img))
 
 
+def test_unaligned_input_base_and_pitch_are_staged():
+    # inputs the TMA path cannot read (odd base address, odd pitch) are copied into
+    # pitched staging first; results equal the oracle's, single and batched
+    img = synth.image(77, 301, 203, 6, 6, 8)
+    big = np.zeros((203, 320), np.uint8)
+    big[:, 3:304] = img
+    d_big = dev(big)
+    d_view = d_big[:, 3:304]                       # base offset by 3 bytes, pitch 320
+    out = torch.full((203, 301), 7, dtype=torch.uint8, device="cuda")
+    with canny.Canny(301, 203) as c:
+        c.run_pitched(d_view, out)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), oracle.canny_u8(img))
+    with canny.Canny(301, 203, path=canny.CANNY_PATH_F32, low=0.1, high=0.3) as c:
+        c.run_pitched(d_view, out)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), oracle.canny_f32(img, 1.4, 7, 0.1, 0.3))
+    outs = [torch.full((203, 301), 7, dtype=torch.uint8, device="cuda") for _ in range(3)]
+    ins = [d_view, dev(img), d_big[:, 1:302]]
+    wants = [oracle.canny_u8(img), oracle.canny_u8(img), oracle.canny_u8(big[:, 1:302])]
+    with canny.Canny(3 * 301 * 203, 1) as c:
+        c.run_batch(list(zip(ins, outs)))
+        torch.cuda.synchronize()
+    for o, want in zip(outs, wants):
+        assert np.array_equal(o.cpu().numpy(), want)
+
+
 def test_context_reuse_smaller_images_and_determinism():
     with canny.Canny(600, 400) as c:
         for (h, w, seed) in [(400, 600, 1), (17, 33, 2), (400, 600, 3), (1, 1, 4), (399, 599, 5)]:

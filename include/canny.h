@@ -211,14 +211,16 @@ canny_status canny_read_timing(canny_ctx *ctx, canny_timing *out);
 /*
  * Launch configuration of the fused integer kernel: rows per unit of work
  * (band: 64, 160 or 256; taller bands cut halo work, shorter ones balance small
- * images better) and persistent CTAs per SM in batches.
+ * images better) and persistent CTAs per SM in batches. direct_loads = 1 reads
+ * inputs whose base or pitch is not a multiple of 16 bytes directly instead of
+ * repitching them into staging first (slower; no staging memory); 0 or 1.
  */
 typedef struct {
     int band;
     int ctas_per_sm;
     double ms;        /* canny_autotune_batch: measured time of one batch run */
     int from_cache;   /* canny_autotune_batch: 1 if read from the cache file */
-    int reserved;
+    int direct_loads;
 } canny_tuning;
 
 /* Apply a configuration; CANNY_EINVAL for an unsupported band or CTA count. */

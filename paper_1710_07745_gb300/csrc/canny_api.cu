@@ -47,21 +47,24 @@ struct canny_ctx {
     // launch configuration of the fused kernel (canny_set_tuning / canny_autotune_batch)
     int band = 64;                     // rows per unit of work
     int ctas_per_sm = 12;              // persistent CTAs per SM in a batch
+    int direct_loads = 0;              // 1: inputs the TMA path cannot read are not repitched
 
-    // integer-path batches: one graph per staging slot, descriptors uploaded from pinned memory
+    // integer-path batches: per staging slot one graph per fused-kernel variant
+    // ([0] TMA or direct loads per image, [1] TMA only), descriptors uploaded
+    // from pinned memory
     struct Slot {
         unsigned char *h_blob = nullptr;
-        cudaGraph_t graph = nullptr;
-        cudaGraphExec_t exec = nullptr;
+        cudaGraph_t graph[2] = {nullptr, nullptr};
+        cudaGraphExec_t exec[2] = {nullptr, nullptr};
         cudaEvent_t done = nullptr;
-        bool valid = false;            // graph matches the current scratch and configuration
+        bool valid[2] = {false, false};   // graph matches the current scratch and configuration
     } slots[2];
     int next_slot = 0;
-    unsigned char *d_blob = nullptr;   // BatchHeader + BatchImage[cap] + CUtensorMap[cap]
+    unsigned char *d_blob = nullptr;   // BatchHeader + BatchImage[cap] + CUtensorMap[cap] + Repitch[cap]
 
-    // 16-byte pitched copy of a single-image input the TMA path cannot read
-    uint8_t *d_stage = nullptr;
-    size_t stage_cap = 0;
+    // 16-byte pitched copies of inputs the TMA path cannot read (single image / batch)
+    uint8_t *d_stage = nullptr, *d_bstage = nullptr;
+    size_t stage_cap = 0, bstage_cap = 0;
     uint32_t blob_cap = 0;
     std::unordered_map<std::string, CUtensorMap> tmaps;   // encoded input maps, by (pointer, size, pitch)
 
@@ -140,13 +143,14 @@ void free_frames(canny_ctx *c)
 void drop_batch_graphs(canny_ctx *c)
 {
     drop_frame_graphs(c);
-    for (auto &sl : c->slots) {
-        if (sl.exec) cudaGraphExecDestroy(sl.exec);
-        if (sl.graph) cudaGraphDestroy(sl.graph);
-        sl.exec = nullptr;
-        sl.graph = nullptr;
-        sl.valid = false;
-    }
+    for (auto &sl : c->slots)
+        for (int v = 0; v < 2; ++v) {
+            if (sl.exec[v]) cudaGraphExecDestroy(sl.exec[v]);
+            if (sl.graph[v]) cudaGraphDestroy(sl.graph[v]);
+            sl.exec[v] = nullptr;
+            sl.graph[v] = nullptr;
+            sl.valid[v] = false;
+        }
 }
 
 void free_hyst(canny_ctx *c)
@@ -310,7 +314,7 @@ bool ensure_stage(uint8_t **buf, size_t *cap, size_t need)
 // the copy costs 2 bytes per pixel of HBM traffic. *im is updated to the copy.
 canny_status stage_input(canny_ctx *c, canny_image *im, cudaStream_t s)
 {
-    if (tma_usable(im->d_in, im->in_pitch)) return CANNY_OK;
+    if (c->direct_loads || tma_usable(im->d_in, im->in_pitch)) return CANNY_OK;
     const int pitch = (int)align_up((size_t)im->w, 16);
     if (!ensure_stage(&c->d_stage, &c->stage_cap, (size_t)pitch * im->h)) return CANNY_OK;   // direct loads
     const Repitch r = {im->d_in, c->d_stage, im->w, im->h, im->in_pitch, pitch};
@@ -397,7 +401,7 @@ canny_status run_one(canny_ctx *c, const canny_image *im, cudaStream_t s, bool s
 // descriptors, input tensor maps; the host copy also carries the HystImage
 // array that is uploaded to the hysteresis scratch.
 struct BlobLayout {
-    size_t imgs, tmaps, himgs, dev_bytes, host_bytes;
+    size_t imgs, tmaps, stage, himgs, dev_bytes, host_bytes;
 };
 
 BlobLayout blob_layout(uint32_t cap)
@@ -405,7 +409,8 @@ BlobLayout blob_layout(uint32_t cap)
     BlobLayout L;
     L.imgs = 128;
     L.tmaps = align_up(L.imgs + sizeof(BatchImage) * cap, 128);
-    L.himgs = align_up(L.tmaps + sizeof(CUtensorMap) * cap, 128);
+    L.stage = align_up(L.tmaps + sizeof(CUtensorMap) * cap, 128);
+    L.himgs = align_up(L.stage + sizeof(Repitch) * cap, 128);
     L.dev_bytes = L.himgs;
     L.host_bytes = L.himgs + sizeof(HystImage) * cap;
     return L;
@@ -449,15 +454,16 @@ int sm_count()
     return n;
 }
 
-// The batch graph: upload descriptors -> clear stamps -> reset -> fused kernel
-// (persistent, pops units) -> while (work) global pass.
-canny_status build_batch_graph(canny_ctx *c, canny_ctx::Slot &sl)
+// The batch graph: upload descriptors -> reset, repitch inputs the TMA path
+// cannot read -> fused kernel (persistent, pops units) -> while (work) global pass.
+// Variant 1 holds the TMA-only fused kernel (every input TMA-readable).
+canny_status build_batch_graph(canny_ctx *c, canny_ctx::Slot &sl, int v)
 {
-    if (sl.exec) cudaGraphExecDestroy(sl.exec);
-    if (sl.graph) cudaGraphDestroy(sl.graph);
-    sl.exec = nullptr;
-    sl.graph = nullptr;
-    sl.valid = false;
+    if (sl.exec[v]) cudaGraphExecDestroy(sl.exec[v]);
+    if (sl.graph[v]) cudaGraphDestroy(sl.graph[v]);
+    sl.exec[v] = nullptr;
+    sl.graph[v] = nullptr;
+    sl.valid[v] = false;
     const BlobLayout L = blob_layout(c->blob_cap);
     BatchHeader *hdr = (BatchHeader *)c->d_blob;
     const BatchImage *imgs = (const BatchImage *)(c->d_blob + L.imgs);
@@ -472,19 +478,23 @@ canny_status build_batch_graph(canny_ctx *c, canny_ctx::Slot &sl)
                                      sizeof(HystImage) * c->blob_cap, cudaMemcpyHostToDevice);
     // (the worklist stamps need no clearing: the fused kernel writes every tile's stamp)
     if (e == cudaSuccess) e = hyst_add_init_from_header(g, &up1, 1, c->hs, hdr, &init);
-    cudaGraphNode_t d_k1[2] = {up2, init};
+    cudaGraphNode_t stage;
     if (e == cudaSuccess)
-        e = k1_add_batch_node(g, d_k1, 2, c->band, imgs, tmaps, hdr, c->it, c->hs, sm_count() * c->ctas_per_sm, &k1);
+        e = add_repitch_list_node(g, &up1, 1, (const Repitch *)(c->d_blob + L.stage), hdr, &stage);
+    cudaGraphNode_t d_k1[3] = {up2, init, stage};
+    if (e == cudaSuccess)
+        e = k1_add_batch_node(g, d_k1, 3, c->band, v == 1, imgs, tmaps, hdr, c->it, c->hs,
+                              sm_count() * c->ctas_per_sm, &k1);
     if (e == cudaSuccess) e = hyst_add_loop(g, &k1, 1, c->hs, &loop);
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&sl.exec, g, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&sl.exec[v], g, 0);
     if (e != cudaSuccess) {
         cudaGetLastError();
         cudaGraphDestroy(g);
-        sl.exec = nullptr;
+        sl.exec[v] = nullptr;
         return CANNY_ECUDA;
     }
-    sl.graph = g;
-    sl.valid = true;
+    sl.graph[v] = g;
+    sl.valid[v] = true;
     return CANNY_OK;
 }
 
@@ -516,21 +526,37 @@ canny_status run_batch_int(canny_ctx *c, int n, const canny_image *imgs, uint32_
     c->next_slot ^= 1;
     // the slot's staging buffer may still feed a batch launched two calls ago
     if (cudaEventSynchronize(sl.done) != cudaSuccess) return CANNY_ECUDA;
-    if (!sl.valid) {
-        st = build_batch_graph(c, sl);
-        if (st != CANNY_OK) return st;
-    }
     const BlobLayout L = blob_layout(c->blob_cap);
     BatchHeader *hdr = (BatchHeader *)sl.h_blob;
     BatchImage *bi = (BatchImage *)(sl.h_blob + L.imgs);
     CUtensorMap *tm = (CUtensorMap *)(sl.h_blob + L.tmaps);
+    Repitch *rp = (Repitch *)(sl.h_blob + L.stage);
     HystImage *hi = (HystImage *)(sl.h_blob + L.himgs);
-    // (inputs the TMA path cannot read take the direct-load variant here: for
-    // batch-sized images copying them into pitched staging first measured no faster)
-    uint32_t k = 0, tile_base = 0, unit_base = 0;
+    // inputs the TMA path cannot read are repitched into the batch staging
+    // buffer by the graph's first kernel (direct loads run at about a third of
+    // the TMA path's speed); if that buffer cannot be had they are read directly
+    size_t stage_need = 0;
+    for (int i = 0; i < n; ++i)
+        if (imgs[i].w > 0 && imgs[i].h > 0 && !tma_usable(imgs[i].d_in, imgs[i].in_pitch))
+            stage_need += align_up(align_up((size_t)imgs[i].w, 16) * (size_t)imgs[i].h, 256);
+    const bool staged =
+        !c->direct_loads && (stage_need == 0 || ensure_stage(&c->d_bstage, &c->bstage_cap, stage_need));
+    uint32_t k = 0, tile_base = 0, unit_base = 0, nstage = 0, stage_tasks = 0;
+    size_t stage_off = 0;
+    bool all_tma = true;
     for (int i = 0; i < n; ++i) {
-        const canny_image *im = &imgs[i];
+        canny_image im_use = imgs[i];
+        const canny_image *im = &im_use;
         if (im->w == 0 || im->h == 0) continue;
+        if (staged && !tma_usable(im->d_in, im->in_pitch)) {
+            const int pitch = (int)align_up((size_t)im->w, 16);
+            uint8_t *dst = c->d_bstage + stage_off;
+            rp[nstage++] = Repitch{im->d_in, dst, im->w, im->h, im->in_pitch, pitch, stage_tasks};
+            stage_tasks += repitch_tasks(im->w, im->h);
+            stage_off += align_up((size_t)pitch * (size_t)im->h, 256);
+            im_use.d_in = dst;
+            im_use.in_pitch = pitch;
+        }
         hi[k] = hyst_image(im, tile_base);
         BatchImage b = {};
         b.img = hi[k];
@@ -539,6 +565,7 @@ canny_status run_batch_int(canny_ctx *c, int n, const canny_image *imgs, uint32_
         b.unit_base = unit_base;
         b.nsx = (im->w + k1_strip_width() - 1) / k1_strip_width();
         b.tma = cached_map(c, im, &tm[k]) ? 1 : 0;
+        all_tma = all_tma && b.tma;
         bi[k] = b;
         tile_base += tiles_of(im->w, im->h);
         unit_base += (uint32_t)k1_units(im->w, im->h, c->band);
@@ -550,8 +577,15 @@ canny_status run_batch_int(canny_ctx *c, int n, const canny_image *imgs, uint32_
     hh.next_unit = 0;
     hh.ntiles = ntiles;
     hh.max_passes = max_passes_for(c, ntiles);
+    hh.nstage = nstage;
+    hh.stage_tasks = stage_tasks;
     *hdr = hh;
-    cudaError_t e = cudaGraphLaunch(sl.exec, s);
+    const int v = all_tma ? 1 : 0;
+    if (!sl.valid[v]) {
+        st = build_batch_graph(c, sl, v);
+        if (st != CANNY_OK) return st;
+    }
+    cudaError_t e = cudaGraphLaunch(sl.exec[v], s);
     if (e == cudaSuccess) e = cudaEventRecord(sl.done, s);
     return from_cuda(e);
 }
@@ -638,6 +672,7 @@ void canny_destroy(canny_ctx *c)
     }
     if (c->d_blob) cudaFree(c->d_blob);
     if (c->d_stage) cudaFree(c->d_stage);
+    if (c->d_bstage) cudaFree(c->d_bstage);
     free_frames(c);
     for (auto &f : c->fslots) {
         if (f.up) cudaEventDestroy(f.up);
@@ -825,6 +860,8 @@ canny_status canny_set_tuning(canny_ctx *c, const canny_tuning *t)
 {
     if (!c || !t) return CANNY_EINVAL;
     if (!k1_band_supported(t->band) || t->ctas_per_sm < 1 || t->ctas_per_sm > 32) return CANNY_EINVAL;
+    if (t->direct_loads != 0 && t->direct_loads != 1) return CANNY_EINVAL;
+    c->direct_loads = t->direct_loads;
     if (t->band != c->band || t->ctas_per_sm != c->ctas_per_sm) {
         cudaDeviceSynchronize();
         drop_batch_graphs(c);
@@ -840,6 +877,7 @@ canny_status canny_get_tuning(const canny_ctx *c, canny_tuning *out)
     *out = canny_tuning{};
     out->band = c->band;
     out->ctas_per_sm = c->ctas_per_sm;
+    out->direct_loads = c->direct_loads;
     return CANNY_OK;
 }
 
@@ -863,6 +901,7 @@ canny_status canny_autotune_batch(canny_ctx *c, int n, const canny_image *imgs, 
     char key[320];   // device name (at most 256) + the size classes
     snprintf(key, sizeof(key), "%s|int|n%d|a%d", prop.name, (int)log2((double)nimg), (int)log2((double)px / nimg));
     canny_tuning best = {};
+    best.direct_loads = c->direct_loads;
     if (cache_path && *cache_path) {
         FILE *f = fopen(cache_path, "r");
         if (f) {
@@ -895,6 +934,7 @@ canny_status canny_autotune_batch(canny_ctx *c, int n, const canny_image *imgs, 
                 canny_tuning cand = {};
                 cand.band = bands[bi];
                 cand.ctas_per_sm = ctas[ci];
+                cand.direct_loads = c->direct_loads;
                 canny_status st = canny_set_tuning(c, &cand);
                 if (st == CANNY_OK) st = canny_run_batch(c, n, imgs, stream);
                 if (st == CANNY_OK && cudaEventRecord(e0, s) != cudaSuccess) st = CANNY_ECUDA;

@@ -86,7 +86,9 @@ struct BatchImage {
 
 // Device header of a batch run, uploaded with the descriptors.
 struct BatchHeader {
-    uint32_t nimg, total_units, next_unit, ntiles, max_passes, pad[3];
+    uint32_t nimg, total_units, next_unit, ntiles, max_passes;
+    uint32_t nstage, stage_tasks;   // inputs repitched into staging first (Repitch list), their tasks
+    uint32_t pad;
 };
 
 // ---------------------------------------------------------------- launchers (k1_fused.cu)
@@ -103,12 +105,10 @@ cudaError_t launch_k1_classify_u8(const uint8_t *in, int in_pitch, uint8_t *cls,
 // tile masks / pending bitmaps / first worklist into hs (after hyst_reset).
 cudaError_t launch_k1_edges_u8(const uint8_t *in, int in_pitch, int w, int h, IntThresholds t,
                                const HystScratch &hs, HystImage img, cudaStream_t s, int band = 64);
-// The same for every image of a batch: a persistent grid of `ctas` one-warp CTAs
-// pops (image, strip, band) units from hdr->next_unit.
-cudaError_t launch_k1_edges_batch(const BatchImage *imgs, const CUtensorMap *tmaps, BatchHeader *hdr,
-                                  IntThresholds t, const HystScratch &hs, int band, int ctas, cudaStream_t s);
-// The batch kernel as a node of graph g.
-cudaError_t k1_add_batch_node(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, int band,
+// The same for every image of a batch, as a node of graph g: a persistent grid
+// of `ctas` one-warp CTAs pops (image, strip, band) units from hdr->next_unit.
+// tma_only: every image's input is TMA-readable (the kernel holds no direct-load path).
+cudaError_t k1_add_batch_node(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, int band, bool tma_only,
                               const BatchImage *imgs, const CUtensorMap *tmaps, BatchHeader *hdr, IntThresholds t,
                               const HystScratch &hs, int ctas, cudaGraphNode_t *out);
 
@@ -133,8 +133,14 @@ struct Repitch {
     const uint8_t *src;
     uint8_t *dst;        // 16-byte aligned, dst_pitch a multiple of 16
     int w, h, src_pitch, dst_pitch;
+    uint32_t task_base;  // in a list: tasks of the copies before this one
 };
 cudaError_t launch_repitch(const Repitch &c, cudaStream_t s);
+// Graph node copying list[0 .. hdr->nstage) (read when the node runs; tasks
+// counted by repitch_tasks, hdr->stage_tasks in all).
+uint32_t repitch_tasks(int w, int h);
+cudaError_t add_repitch_list_node(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, const Repitch *list,
+                                  const BatchHeader *hdr, cudaGraphNode_t *out);
 
 // ---------------------------------------------------------------- TMA (tma.cu)
 bool tma_usable(const void *base, int pitch);

@@ -81,6 +81,38 @@ __device__ __forceinline__ void load_row(const HystImage &im, int tx, int ty, in
     }
 }
 
+// Store 32 bytes (little-endian words wd[0..7]) at p, any alignment, with the
+// widest stores the alignment allows: two 16-byte stores when 16-byte aligned,
+// 8- or 4-byte words when 8- or 4-byte aligned, otherwise seven 4-byte words
+// funnel-shifted into place between a head and a tail of one byte and/or one
+// 16-bit store (at most 11 stores instead of 32).
+__device__ __forceinline__ void store32(uint8_t *p, const uint32_t (&wd)[8])
+{
+    const uintptr_t a = (uintptr_t)p;
+    const int r = (int)(a & 3);
+    if ((a & 15) == 0) {
+        reinterpret_cast<uint4 *>(p)[0] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+        reinterpret_cast<uint4 *>(p)[1] = make_uint4(wd[4], wd[5], wd[6], wd[7]);
+    } else if ((a & 7) == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) reinterpret_cast<uint2 *>(p)[k] = make_uint2(wd[2 * k], wd[2 * k + 1]);
+    } else if (r == 0) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) reinterpret_cast<uint32_t *>(p)[k] = wd[k];
+    } else {
+        // aligned word k of the destination (at p - r + 4k) holds data bytes 4k - r .. 4k - r + 3
+        uint32_t *base = reinterpret_cast<uint32_t *>(p - r);
+        const uint32_t sh = 8u * (uint32_t)(4 - r);
+#pragma unroll
+        for (int k = 1; k < 8; ++k) base[k] = __funnelshift_r(wd[k - 1], wd[k], sh);
+        // head: data bytes 0 .. 3 - r; tail: data bytes 32 - r .. 31
+        if (r & 1) p[0] = (uint8_t)wd[0];
+        if (r != 3) *reinterpret_cast<uint16_t *>(p + (r & 1)) = (uint16_t)(wd[0] >> (8 * (r & 1)));
+        if (r != 1) *reinterpret_cast<uint16_t *>(p + 32 - r) = (uint16_t)(wd[7] >> sh);
+        if (r & 1) p[31] = (uint8_t)(wd[7] >> 24);
+    }
+}
+
 // Write row `lane` of the tile as 255 where e is set, 0 elsewhere.
 __device__ __forceinline__ void store_row(const HystImage &im, int tx, int ty, int lane, uint32_t e)
 {
@@ -88,15 +120,14 @@ __device__ __forceinline__ void store_row(const HystImage &im, int tx, int ty, i
     if (y >= im.h) return;
     uint8_t *row = im.map + (int64_t)y * im.pitch + x0;
     int n = min(HT, im.w - x0);
-    if (n == HT && (((uintptr_t)row) & 15) == 0) {
-        uint4 a, b;
-        a.x = nibble_bytes(e); a.y = nibble_bytes(e >> 4); a.z = nibble_bytes(e >> 8); a.w = nibble_bytes(e >> 12);
-        b.x = nibble_bytes(e >> 16); b.y = nibble_bytes(e >> 20); b.z = nibble_bytes(e >> 24); b.w = nibble_bytes(e >> 28);
-        reinterpret_cast<uint4 *>(row)[0] = a;
-        reinterpret_cast<uint4 *>(row)[1] = b;
-    } else {
+    if (n < HT) {
         for (int i = 0; i < n; ++i) row[i] = ((e >> i) & 1) ? 255 : 0;
+        return;
     }
+    uint32_t wd[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) wd[k] = nibble_bytes(e >> (4 * k));
+    store32(row, wd);
 }
 
 __device__ __forceinline__ int find_image(const HystImage *imgs, int nimg, uint32_t t)

@@ -470,9 +470,8 @@ __device__ __forceinline__ void run_unit(const CUtensorMap *tmap, const Unit &U,
 #pragma unroll
             for (int q = 0; q < 8; ++q) wd[q] = nib01(c >> (4 * q)) + nib01(sgl >> (4 * q));
             uint8_t *dst = out + (int64_t)y * out_pitch + x;
-            if (x + 32 <= U.w && ((((uintptr_t)dst)) & 15) == 0) {
-                reinterpret_cast<uint4 *>(dst)[0] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
-                reinterpret_cast<uint4 *>(dst)[1] = make_uint4(wd[4], wd[5], wd[6], wd[7]);
+            if (x + 32 <= U.w) {
+                tile::store32(dst, wd);
             } else {
                 for (int b = 0; b < 32 && x + b < U.w; ++b) dst[b] = (uint8_t)((wd[b >> 2] >> (8 * (b & 3))) & 0xFF);
             }
@@ -529,7 +528,8 @@ k1_fused_kernel(const __grid_constant__ CUtensorMap tmap, const uint8_t *__restr
 }
 
 // A batch: a persistent grid pops (image, strip, band) units from a counter.
-template <int BAND>
+// PATH_TMA when every input is TMA-readable, else PATH_EITHER (chosen per image).
+template <int BAND, int PATH>
 __global__ void __launch_bounds__(THREADS, BAND == 64 ? 16 : 12)
 k1_fused_batch_kernel(const BatchImage *__restrict__ imgs, const CUtensorMap *__restrict__ tmaps,
                       BatchHeader *hdr, IntThresholds t, HystScratch hs)
@@ -562,7 +562,7 @@ k1_fused_batch_kernel(const BatchImage *__restrict__ imgs, const CUtensorMap *__
         U.sy = (int)(local / (uint32_t)B.nsx);
         U.X0 = U.sx * OUT_W;
         U.Y0 = U.sy * BAND;
-        U.tma = B.tma != 0;
+        U.tma = PATH == PATH_TMA || B.tma != 0;
         const HystImage img = B.img;
         if (U.tma && lane == 0) {
             // the descriptor was rewritten in global memory since the TMA unit may
@@ -570,8 +570,7 @@ k1_fused_batch_kernel(const BatchImage *__restrict__ imgs, const CUtensorMap *__
             asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&tmaps[lo]) : "memory");
         }
         __syncwarp();
-        run_unit<BAND, MODE_EDGES, PATH_EITHER>(&tmaps[lo], U, t, img.map, img.pitch, hs, img, &hs.state->error, S,
-                                                lane);
+        run_unit<BAND, MODE_EDGES, PATH>(&tmaps[lo], U, t, img.map, img.pitch, hs, img, &hs.state->error, S, lane);
     }
 }
 
@@ -614,21 +613,6 @@ cudaError_t launch_any(int band, const uint8_t *in, int in_pitch, int w, int h, 
     }
 }
 
-template <int BAND>
-cudaError_t launch_batch_band(const BatchImage *imgs, const CUtensorMap *tmaps, BatchHeader *hdr, IntThresholds t,
-                              const HystScratch &hs, int ctas, cudaStream_t s)
-{
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k1_fused_batch_kernel<BAND>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<BAND>));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    k1_fused_batch_kernel<BAND><<<ctas, THREADS, sizeof(Smem<BAND>), s>>>(imgs, tmaps, hdr, t, hs);
-    return cudaGetLastError();
-}
-
 }  // namespace
 
 bool k1_band_supported(int band) { return band == 64 || band == 160 || band == 256; }
@@ -657,28 +641,18 @@ cudaError_t launch_k1_edges_u8(const uint8_t *in, int in_pitch, int w, int h, In
     return launch_any<MODE_EDGES>(band, in, in_pitch, w, h, t, img.map, img.pitch, hs, img, &hs.state->error, s);
 }
 
-cudaError_t launch_k1_edges_batch(const BatchImage *imgs, const CUtensorMap *tmaps, BatchHeader *hdr, IntThresholds t,
-                                  const HystScratch &hs, int band, int ctas, cudaStream_t s)
-{
-    switch (band) {
-    case 160: return launch_batch_band<160>(imgs, tmaps, hdr, t, hs, ctas, s);
-    case 256: return launch_batch_band<256>(imgs, tmaps, hdr, t, hs, ctas, s);
-    default: return launch_batch_band<64>(imgs, tmaps, hdr, t, hs, ctas, s);
-    }
-}
-
-template <int BAND>
+template <int BAND, int PATH>
 cudaError_t add_batch_node_band(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, const BatchImage *imgs,
                                 const CUtensorMap *tmaps, BatchHeader *hdr, IntThresholds t, const HystScratch &hs,
                                 int ctas, cudaGraphNode_t *out)
 {
-    cudaError_t e = cudaFuncSetAttribute(k1_fused_batch_kernel<BAND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(Smem<BAND>));
+    cudaError_t e = cudaFuncSetAttribute(k1_fused_batch_kernel<BAND, PATH>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<BAND>));
     if (e != cudaSuccess) return e;
     HystScratch hs_copy = hs;
     void *args[] = {(void *)&imgs, (void *)&tmaps, (void *)&hdr, (void *)&t, (void *)&hs_copy};
     cudaKernelNodeParams kp = {};
-    kp.func = (void *)k1_fused_batch_kernel<BAND>;
+    kp.func = (void *)k1_fused_batch_kernel<BAND, PATH>;
     kp.gridDim = dim3(ctas);
     kp.blockDim = dim3(THREADS);
     kp.sharedMemBytes = sizeof(Smem<BAND>);
@@ -686,15 +660,25 @@ cudaError_t add_batch_node_band(cudaGraph_t g, const cudaGraphNode_t *deps, size
     return cudaGraphAddKernelNode(out, g, deps, ndeps, &kp);
 }
 
-cudaError_t k1_add_batch_node(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, int band,
+template <int PATH>
+cudaError_t add_batch_node_path(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, int band,
+                                const BatchImage *imgs, const CUtensorMap *tmaps, BatchHeader *hdr, IntThresholds t,
+                                const HystScratch &hs, int ctas, cudaGraphNode_t *out)
+{
+    switch (band) {
+    case 160: return add_batch_node_band<160, PATH>(g, deps, ndeps, imgs, tmaps, hdr, t, hs, ctas, out);
+    case 256: return add_batch_node_band<256, PATH>(g, deps, ndeps, imgs, tmaps, hdr, t, hs, ctas, out);
+    default: return add_batch_node_band<64, PATH>(g, deps, ndeps, imgs, tmaps, hdr, t, hs, ctas, out);
+    }
+}
+
+cudaError_t k1_add_batch_node(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, int band, bool tma_only,
                               const BatchImage *imgs, const CUtensorMap *tmaps, BatchHeader *hdr, IntThresholds t,
                               const HystScratch &hs, int ctas, cudaGraphNode_t *out)
 {
-    switch (band) {
-    case 160: return add_batch_node_band<160>(g, deps, ndeps, imgs, tmaps, hdr, t, hs, ctas, out);
-    case 256: return add_batch_node_band<256>(g, deps, ndeps, imgs, tmaps, hdr, t, hs, ctas, out);
-    default: return add_batch_node_band<64>(g, deps, ndeps, imgs, tmaps, hdr, t, hs, ctas, out);
-    }
+    if (tma_only)
+        return add_batch_node_path<PATH_TMA>(g, deps, ndeps, band, imgs, tmaps, hdr, t, hs, ctas, out);
+    return add_batch_node_path<PATH_EITHER>(g, deps, ndeps, band, imgs, tmaps, hdr, t, hs, ctas, out);
 }
 
 bool encode_k1_map(void *tmap_out, const uint8_t *in, int w, int h, int in_pitch)

@@ -144,6 +144,46 @@ def test_unaligned_input_base_and_pitch_are_staged():
         assert np.array_equal(o.cpu().numpy(), want)
 
 
+@pytest.mark.parametrize("direct", [0, 1])
+def test_repitch_every_base_offset_and_narrow_width(direct):
+    # repitching reads 16-byte granules funnel-shifted by the base offset, falling
+    # back to byte loads where a granule would leave the image's bytes: every
+    # offset 0..15, widths below, at and across one granule, pitches w..w+19
+    rng = np.random.default_rng(77)
+    cases = []
+    for k in range(48):
+        w = int([1, 3, 15, 16, 17, 31, 33, 47, 230, 449][k % 10])
+        h = int(rng.integers(1, 40))
+        off = k % 16
+        pitch = w + int(rng.integers(0, 20))
+        buf = np.zeros((h + 1) * pitch + 32, np.uint8)
+        img = synth.image(3000 + k, w, h, 4, 4, 6)
+        cases.append((img, buf, off, pitch))
+    ins, outs, wants = [], [], []
+    for img, buf, off, pitch in cases:
+        h, w = img.shape
+        d = dev(buf)
+        view = d[off:off + (h - 1) * pitch + w].as_strided((h, w), (pitch, 1))
+        view.copy_(dev(img))
+        ins.append(view)
+        outs.append(torch.full((h, w), 7, dtype=torch.uint8, device="cuda"))
+        wants.append(oracle.canny_u8(img))
+    total = sum(im.size for im, _, _, _ in cases)
+    with canny.Canny(total, 1) as c:
+        c.set_tuning(64, 12, direct)
+        c.run_batch(list(zip(ins, outs)))
+        torch.cuda.synchronize()
+        for o, want in zip(outs, wants):
+            assert np.array_equal(o.cpu().numpy(), want)
+    with canny.Canny(449, 40) as c:
+        c.set_tuning(64, 12, direct)
+        for i, o, want in zip(ins, outs, wants):
+            o.fill_(7)
+            c.run_pitched(i, o)
+            torch.cuda.synchronize()
+            assert np.array_equal(o.cpu().numpy(), want)
+
+
 def test_context_reuse_smaller_images_and_determinism():
     with canny.Canny(600, 400) as c:
         for (h, w, seed) in [(400, 600, 1), (17, 33, 2), (400, 600, 3), (1, 1, 4), (399, 599, 5)]:
@@ -549,18 +589,19 @@ def test_batch_many_uneven_images_two_calls():
                 assert np.array_equal(o, oracle.canny_u8(im))
 
 
-@pytest.mark.parametrize("band,ctas", [(64, 8), (160, 12), (256, 4)])
-def test_every_tuning_gives_identical_edges(band, ctas):
+@pytest.mark.parametrize("band,ctas,direct", [(64, 8, 0), (160, 12, 0), (256, 4, 0), (64, 16, 1), (160, 12, 1)])
+def test_every_tuning_gives_identical_edges(band, ctas, direct):
     imgs = [synth.image(900 + i, w, h, 8, 8, 10) for i, (h, w) in
             enumerate([(300, 500), (1, 70), (257, 33), (700, 449)])]
     total = sum(im.size for im in imgs)
     with canny.Canny(max(total, 700 * 700), 1) as c:
-        c.set_tuning(band, ctas)
+        c.set_tuning(band, ctas, direct)
+        assert canny.canny_get_tuning(c.ctx).direct_loads == direct
         outs, st = _batch_run(c, imgs)
         for im, o in zip(imgs, outs):
             assert np.array_equal(o, oracle.canny_u8(im))
     with canny.Canny(700, 700) as c:
-        c.set_tuning(band, ctas)
+        c.set_tuning(band, ctas, direct)
         for im in imgs:
             out, _ = run_int(im, ctx=c)
             assert np.array_equal(out, oracle.canny_u8(im))

@@ -57,6 +57,7 @@ constexpr int QCAP = UNROLL * 28 * LPX; // candidate pixels of one 3-row group, 
 constexpr int TILES_X = OUT_W / HT;
 constexpr int MW = OUT_W / 32;          // bitmask words per strip row
 static_assert((CH * BOX) % 128 == 0, "TMA stage buffers must stay 128-byte aligned");
+static_assert(UNROLL <= RING, "ring slots advance by at most one wrap per group");
 
 // Rows per unit. Each unit consumes a whole number of full mbarrier phase
 // cycles (NCH a multiple of 2 * STAGES), so a persistent CTA can run unit after
@@ -145,12 +146,14 @@ __device__ __forceinline__ float &pix(float2 (&p)[5], int k)
 
 // ---------------------------------------------------------------- candidate suppression
 // Step 3 + thresholds for one queued candidate pixel.
-// ybase: image row of the group's first queued row.
+// ybase: image row of the group's first queued row, sb: its strength ring slot.
 template <int BAND>
-__device__ __forceinline__ void suppress_pixel(Smem<BAND> &S, uint32_t entry, int ybase, int Y0, float hi2)
+__device__ __forceinline__ void suppress_pixel(Smem<BAND> &S, uint32_t entry, int sb, int ybase, int Y0, float hi2)
 {
-    const int y = ybase + (int)((entry >> 8) & 3u), p = (int)(entry & 255u);
-    const int sl = y % RING, su = (y + RING - 1) % RING, sd = (y + 1) % RING;
+    const int off = (int)((entry >> 8) & 3u), y = ybase + off, p = (int)(entry & 255u);
+    int sl = sb + off;
+    if (sl >= RING) sl -= RING;
+    const int su = sl == 0 ? RING - 1 : sl - 1, sd = sl == RING - 1 ? 0 : sl + 1;
     const float m = S.m2[sl][p];
     // all eight neighbour strengths at once, then pick by sector
     const float l = S.m2[sl][p - 1], r = S.m2[sl][p + 1];
@@ -236,6 +239,8 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint
         if (failed && lane == 0) atomicOr(err, 2u);
     };
 
+    // ring slot (row mod RING) of strength row r = Y0 - 7 + g, kept incrementally
+    int rsg = (((Y0 - 7) % RING) + RING) % RING;
     for (int g = 0; g < ITERS; g += UNROLL) {
 #pragma unroll
         for (int u = 0; u < UNROLL; ++u) {
@@ -380,7 +385,8 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint
                 }
             }
             // every row's strengths go to the ring (neighbours of later candidates)
-            const int rs = ((r % RING) + RING) % RING;
+            int rs = rsg + u;
+            if (rs >= RING) rs -= RING;
             float4 *mdst = reinterpret_cast<float4 *>(&S.m2[rs][LPX * lane]);
             mdst[0] = make_float4(m[0].x, m[1].x, m[2].x, m[3].x);
             mdst[1] = make_float4(m[0].y, m[1].y, m[2].y, m[3].y);
@@ -415,10 +421,13 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint
         // ---- Step 3 + thresholds for the queued pixels (their rows +-1 are in the ring)
         __syncwarp();
         const uint32_t n = S.qcount;
-        for (uint32_t j = lane; j < n; j += 32) suppress_pixel(S, S.queue[j], Y0 - 8 + g, Y0, hi2);
+        const int sb = rsg == 0 ? RING - 1 : rsg - 1;   // slot of row Y0 - 8 + g
+        for (uint32_t j = lane; j < n; j += 32) suppress_pixel(S, S.queue[j], sb, Y0 - 8 + g, Y0, hi2);
         __syncwarp();
         if (lane == 0) S.qcount = 0;
         __syncwarp();
+        rsg += UNROLL;
+        if (rsg >= RING) rsg -= RING;
     }
 }
 

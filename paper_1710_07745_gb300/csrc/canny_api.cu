@@ -25,6 +25,8 @@ struct canny_ctx {
     void *hyst_mem = nullptr;          // one allocation for the hysteresis scratch
     float *mag = nullptr;              // float path: strength after suppression
     float *d_max = nullptr;            // float path: the image's largest strength
+    void *fmaps = nullptr;             // float path: squared strengths + sectors (pass 1 -> pass 2)
+    size_t fmaps_cap = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int use_graph = 1;                 // 0 after a graph could not be built: host-driven passes
@@ -327,11 +329,26 @@ canny_status stage_input(canny_ctx *c, canny_image *im, cudaStream_t s)
 
 // Float path, Steps 1-4 up to the tile-local hysteresis: pass 1 finds the largest
 // squared strength, pass 2 recomputes the stencil and writes edges and tile state.
+// The float path's strength and sector maps for a w x h image. Growing them
+// drops the frame graphs, which hold the old buffer.
+bool ensure_fmaps(canny_ctx *c, int w, int h)
+{
+    const size_t need = k1f_map_bytes(w, h);
+    if (c->fmaps_cap >= need) return true;
+    drop_frame_graphs(c);
+    return ensure_stage(reinterpret_cast<uint8_t **>(&c->fmaps), &c->fmaps_cap, need);
+}
+
+// Float path, Steps 1-4 up to the tile-local hysteresis: pass 1 writes the
+// squared strengths and sectors and finds their maximum, pass 2 suppresses,
+// thresholds and fills the tiles from those maps.
 canny_status run_float_fused(canny_ctx *c, const canny_image *im, const HystImage &himg, cudaStream_t s)
 {
+    if (!ensure_fmaps(c, im->w, im->h)) return CANNY_ENOMEM;
     cudaError_t e = cudaMemsetAsync(c->d_max, 0, sizeof(float), s);
-    if (e == cudaSuccess) e = launch_k1f_max(im->d_in, im->in_pitch, im->w, im->h, c->fp, c->d_max, s);
-    if (e == cudaSuccess) e = launch_k1f_edges(im->d_in, im->in_pitch, im->w, im->h, c->fp, c->d_max, c->hs, himg, s);
+    if (e == cudaSuccess)
+        e = launch_k1f_strength(im->d_in, im->in_pitch, im->w, im->h, c->fp, c->d_max, c->fmaps, s);
+    if (e == cudaSuccess) e = launch_k1f_nms(c->fmaps, im->w, im->h, c->fp, c->d_max, c->hs, himg, s);
     return from_cuda(e);
 }
 
@@ -658,6 +675,7 @@ void canny_destroy(canny_ctx *c)
     cudaDeviceSynchronize();
     free_hyst(c);
     if (c->mag) cudaFree(c->mag);
+    if (c->fmaps) cudaFree(c->fmaps);
     if (c->d_max) cudaFree(c->d_max);
     if (c->d_host_in) cudaFree(c->d_host_in);
     if (c->d_host_out) cudaFree(c->d_host_out);
@@ -1057,6 +1075,8 @@ canny_status ensure_frames(canny_ctx *c, int w, int h)
     c->frame_w = w;
     c->frame_h = h;
     c->frame_pitch = pitch;
+    // the float path's maps exist before any frame graph captures their address
+    if (c->p.path != CANNY_PATH_INT && !ensure_fmaps(c, w, h)) return CANNY_ENOMEM;
     for (auto &f : c->fslots) {
         if (f.exec) continue;
         st = build_frame_graph(c, f);

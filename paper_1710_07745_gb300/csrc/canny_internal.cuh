@@ -155,14 +155,19 @@ cudaError_t launch_k1f_classify(const float *mag_nms, int mag_pitch, uint8_t *cl
                                 cudaStream_t s);
 
 // ---------------------------------------------------------------- launchers (k1_fused_f32.cu)
-// Float path pass 1: the image's largest squared strength, atomicMax'ed into
-// *d_smax (as float bits; the caller zeroes it first).
-cudaError_t launch_k1f_max(const uint8_t *in, int in_pitch, int w, int h, const FloatParams &fp, float *d_smax,
-                           cudaStream_t s);
-// Float path pass 2: Steps 1-4 up to the tile-local hysteresis with thresholds
-// relative to sqrt(*d_smax): edges into img.map, tile state into hs (after hyst_reset).
-cudaError_t launch_k1f_edges(const uint8_t *in, int in_pitch, int w, int h, const FloatParams &fp,
-                             const float *d_smax, const HystScratch &hs, HystImage img, cudaStream_t s);
+// Bytes of the float path's maps for a w x h image (squared strengths and
+// gradient sectors of whole 64 x 128 blocks).
+size_t k1f_map_bytes(int w, int h);
+// Float path pass 1: Steps 1-2 and the sector of Step 3 into maps (k1f_map_bytes
+// bytes, 16-byte aligned); the image's largest squared strength atomicMax'ed
+// into *d_smax (as float bits; the caller zeroes it first).
+cudaError_t launch_k1f_strength(const uint8_t *in, int in_pitch, int w, int h, const FloatParams &fp,
+                                float *d_smax, void *maps, cudaStream_t s);
+// Float path pass 2: Step 3 and the thresholds relative to sqrt(*d_smax) from the
+// maps, then the tile-local hysteresis: edges into img.map, tile state into hs
+// (after hyst_reset).
+cudaError_t launch_k1f_nms(const void *maps, int w, int h, const FloatParams &fp, const float *d_smax,
+                           const HystScratch &hs, HystImage img, cudaStream_t s);
 
 // ---------------------------------------------------------------- launchers (hysteresis.cu)
 // Local fill over all tiles of one image whose class map is already in img.map.

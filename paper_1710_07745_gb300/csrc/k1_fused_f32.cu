@@ -1,35 +1,37 @@
-// k1_fused_f32.cu -- the float32 variant of Steps 1-4 (paper Sec. 2.2.1) without a
-// stored strength image. The thresholds are fractions of the image's largest
-// strength, a grid-wide dependency, so the stencil runs twice over the input:
+// k1_fused_f32.cu -- the float32 variant of Steps 1-4 (paper Sec. 2.2.1). The
+// thresholds are fractions of the image's largest strength, a grid-wide
+// dependency, so the work splits into two passes:
 //
-//   pass 1 (k1f_max_kernel): Gaussian -> Sobel -> squared strength s = gx^2 + gy^2
-//     for every pixel, reduced to the image maximum smax (one atomicMax per CTA);
-//   pass 2 (k1f_edges_kernel): the same stencil again, then on the few pixels
-//     that can pass the low threshold: strength M = sqrt(s), direction sector,
-//     suppression, double threshold; then the tile flood fill of the hysteresis
-//     on 32 x 32 tiles and the 0/255 edge bytes, tile border masks and pending
+//   pass 1 (k1f_strength_kernel): Gaussian -> Sobel -> squared strength
+//     s = gx^2 + gy^2 and the gradient's sector for every pixel, written to a
+//     float map and a 2-bit sector map, and reduced to the image maximum smax
+//     (one atomicMax per CTA);
+//   pass 2 (k1f_nms_kernel): on the few pixels that can pass the low threshold,
+//     strength M = sqrt(s), suppression against the two neighbours the sector
+//     names, double threshold; then the tile flood fill of the hysteresis on
+//     32 x 32 tiles and the 0/255 edge bytes, tile border masks and pending
 //     bitmaps for the global passes.
 //
-// Each pass reads the input byte once; pass 2 writes the edge byte once. The
-// largest strength is Mmax = sqrt(smax) exactly: a correctly rounded square
-// root is monotonic, so the largest root is the root of the largest s.
+// Pass 1 reads the input byte and writes 4.25 bytes per pixel; pass 2 reads
+// those maps (with a 1-pixel ring) and writes the edge byte. The largest
+// strength is Mmax = sqrt(smax) exactly: a correctly rounded square root is
+// monotonic, so the largest root is the root of the largest s.
 //
 // Arithmetic follows the float32 definition operation by operation (no
 // contraction except where a product by 2 is exact): horizontal pass then
 // vertical pass, taps accumulated from the first, replicate border; Sobel
 // columns summed top to bottom; s = (gx*gx) + (gy*gy); M = sqrt_rn(s).
 //
-// A CTA of 256 threads covers a block of 64 rows x 128 columns (2 x 4 tiles)
-// and stages it in shared memory: input (as float, with a halo of R + 2 rows
-// and R + 2 columns rounded up to 16, R = ksize / 2; 16-byte vector loads
-// where the block lies inside the image), the horizontal pass, the smoothed
-// image S, the squared strengths (with a 1-pixel ring for the suppression).
-// Buffers alias once they are dead, so a 7-tap kernel needs 86 KB and two CTAs
-// fit on an SM. Work is done on pixel pairs that share their shared-memory
-// loads (the horizontal pass pairs two rows, the vertical pass and Sobel pair
-// two columns); the arithmetic itself is scalar and correctly rounded per
-// operation (__fmul_rn / __fadd_rn, and __fmaf_rn only where the product by 2
-// is exact).
+// A pass-1 CTA of 256 threads covers a block of 64 rows x 128 columns (2 x 4
+// tiles) and stages it in shared memory: input (as float, with a halo of R + 2
+// rows and R + 2 columns rounded up to 16, R = ksize / 2; 16-byte vector loads
+// where the block lies inside the image), the horizontal pass and the smoothed
+// image S. Buffers alias once they are dead, so a 7-tap kernel needs 86 KB and
+// two CTAs fit on an SM. Work is done on pixel pairs that share their
+// shared-memory loads (the horizontal pass pairs two rows, the vertical pass
+// and Sobel pair two columns); the arithmetic itself is scalar and correctly
+// rounded per operation (__fmul_rn / __fadd_rn, and __fmaf_rn only where the
+// product by 2 is exact).
 #include "hyst_tile.cuh"
 
 namespace canny {
@@ -101,51 +103,7 @@ __device__ __forceinline__ float2 tap_sum2(const FloatParams &fp, Load v)
     return acc;
 }
 
-// Sobel at the S entry (r, c) of a row-major S block with row stride sx, in the
-// definition's order; a + 2*b is formed as fma(2, b, a), which is the same
-// single rounding since 2*b is exact.
-__device__ __forceinline__ void sobel_at(const float *S, int sx, int r, int c, float &gx, float &gy)
-{
-    const float *u = S + (r - 1) * sx + c, *m = S + r * sx + c, *d = S + (r + 1) * sx + c;
-    float right = __fmaf_rn(2.f, m[1], u[1]);
-    right = fadd(right, d[1]);
-    float left = __fmaf_rn(2.f, m[-1], u[-1]);
-    left = fadd(left, d[-1]);
-    float down = __fmaf_rn(2.f, d[0], d[-1]);
-    down = fadd(down, d[1]);
-    float up = __fmaf_rn(2.f, u[0], u[-1]);
-    up = fadd(up, u[1]);
-    gx = fadd(right, -left);
-    gy = fadd(down, -up);
-}
-
 __device__ __forceinline__ float strength2(float gx, float gy) { return fadd(fmul(gx, gx), fmul(gy, gy)); }
-
-// Squared strengths of the pixel pair at S entries (r, c), (r, c + 1), c even:
-// the operations of sobel_at + strength2 on each pixel, sharing the loads.
-__device__ __forceinline__ float2 strength2_pair(const float *S, int sx, int r, int c)
-{
-    const float *u = S + (r - 1) * sx + c - 2, *m = S + r * sx + c - 2, *d = S + (r + 1) * sx + c - 2;
-    // columns c-2 .. c+3 of rows r-1, r, r+1 as aligned pairs
-    const float2 u0 = *reinterpret_cast<const float2 *>(u), u1 = *reinterpret_cast<const float2 *>(u + 2),
-                 u2 = *reinterpret_cast<const float2 *>(u + 4);
-    const float2 m0 = *reinterpret_cast<const float2 *>(m), m1 = *reinterpret_cast<const float2 *>(m + 2),
-                 m2 = *reinterpret_cast<const float2 *>(m + 4);
-    const float2 d0 = *reinterpret_cast<const float2 *>(d), d1 = *reinterpret_cast<const float2 *>(d + 2),
-                 d2 = *reinterpret_cast<const float2 *>(d + 4);
-    const float U[5] = {u0.y, u1.x, u1.y, u2.x, 0.f}, M[5] = {m0.y, m1.x, m1.y, m2.x, 0.f},
-                D[5] = {d0.y, d1.x, d1.y, d2.x, 0.f};    // columns c-1 .. c+2
-    float out[2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {                      // pixel at column c + i: index 1 + i
-        const float right = fadd(__fmaf_rn(2.f, M[2 + i], U[2 + i]), D[2 + i]);
-        const float left = fadd(__fmaf_rn(2.f, M[i], U[i]), D[i]);
-        const float down = fadd(__fmaf_rn(2.f, D[1 + i], D[i]), D[2 + i]);
-        const float up = fadd(__fmaf_rn(2.f, U[1 + i], U[i]), U[2 + i]);
-        out[i] = strength2(fadd(right, -left), fadd(down, -up));
-    }
-    return f2(out[0], out[1]);
-}
 
 // float(byte k of w), exactly: 2^23 + byte from a byte permute, minus 2^23.
 __device__ __forceinline__ float byte_f(uint32_t w, int k)
@@ -314,10 +272,67 @@ __device__ __forceinline__ void smooth_block(const uint8_t *__restrict__ in, int
     __syncthreads();
 }
 
+// Sector of the gradient (gx, gy), 2 bits: 0 H (left / right), 1 V (up / down),
+// 2 D (up-left / down-right), 3 A (down-left / up-right); tan 22.5 deg as a float.
+__device__ __forceinline__ uint32_t sector_of(float gx, float gy)
+{
+    const float t = 0.41421356f, ax = fabsf(gx), ay = fabsf(gy);
+    if (ay < fmul(ax, t)) return 0u;
+    if (ax < fmul(ay, t)) return 1u;
+    if ((gx > 0.f && gy > 0.f) || (gx < 0.f && gy < 0.f)) return 2u;
+    return 3u;
+}
+
+// Sobel (in the definition's order: columns summed top to bottom; a + 2 b
+// formed as fma(2, b, a), the same single rounding since 2 b is exact) and
+// squared strength of the pixel pair at S entries (r, c), (r, c + 1), c even,
+// sharing the loads; their sectors in bits 0-1 and 2-3 of *sec.
+__device__ __forceinline__ float2 strength_sector_pair(const float *S, int sx, int r, int c, uint32_t *sec)
+{
+    const float *u = S + (r - 1) * sx + c - 2, *m = S + r * sx + c - 2, *d = S + (r + 1) * sx + c - 2;
+    const float2 u0 = *reinterpret_cast<const float2 *>(u), u1 = *reinterpret_cast<const float2 *>(u + 2),
+                 u2 = *reinterpret_cast<const float2 *>(u + 4);
+    const float2 m0 = *reinterpret_cast<const float2 *>(m), m1 = *reinterpret_cast<const float2 *>(m + 2),
+                 m2 = *reinterpret_cast<const float2 *>(m + 4);
+    const float2 d0 = *reinterpret_cast<const float2 *>(d), d1 = *reinterpret_cast<const float2 *>(d + 2),
+                 d2 = *reinterpret_cast<const float2 *>(d + 4);
+    const float U[4] = {u0.y, u1.x, u1.y, u2.x}, M[4] = {m0.y, m1.x, m1.y, m2.x}, D[4] = {d0.y, d1.x, d1.y, d2.x};
+    float out[2];
+    uint32_t code = 0;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {                      // pixel at column c + i: index 1 + i
+        const float right = fadd(__fmaf_rn(2.f, M[2 + i], U[2 + i]), D[2 + i]);
+        const float left = fadd(__fmaf_rn(2.f, M[i], U[i]), D[i]);
+        const float down = fadd(__fmaf_rn(2.f, D[1 + i], D[i]), D[2 + i]);
+        const float up = fadd(__fmaf_rn(2.f, U[1 + i], U[i]), U[2 + i]);
+        const float gx = fadd(right, -left), gy = fadd(down, -up);
+        out[i] = strength2(gx, gy);
+        code |= sector_of(gx, gy) << (2 * i);
+    }
+    *sec = code;
+    return f2(out[0], out[1]);
+}
+
+// Layout of the pass-1 maps for a w x h image: whole blocks, mp floats a row
+// (a multiple of FB_W) and rows = a multiple of FB_H; the sector map holds
+// four pixels a byte (mp / 4 bytes a row). Pixels outside the image hold 0.
+struct MapLayout {
+    int mp, rows;
+};
+
+__host__ __device__ inline MapLayout map_layout(int w, int h)
+{
+    return MapLayout{(w + FB_W - 1) / FB_W * FB_W, (h + FB_H - 1) / FB_H * FB_H};
+}
+
 // ---------------------------------------------------------------- pass 1
+// Steps 1-2 and the sector of Step 3 for one block: squared strengths (0
+// outside the image) into smap, sectors into sect, block maximum atomicMax'ed
+// into *d_smax.
 template <int KS>
 __global__ void __launch_bounds__(FB_THREADS, 2)
-k1f_max_kernel(const uint8_t *__restrict__ in, int in_pitch, int w, int h, FloatParams fp, float *d_smax)
+k1f_strength_kernel(const uint8_t *__restrict__ in, int in_pitch, int w, int h, FloatParams fp, float *d_smax,
+                    float *__restrict__ smap, uint8_t *__restrict__ sect)
 {
     extern __shared__ __align__(16) float fsm[];
     const Geometry g = geometry(KS > 0 ? KS : fp.ksize);
@@ -325,15 +340,21 @@ k1f_max_kernel(const uint8_t *__restrict__ in, int in_pitch, int w, int h, Float
     const int x0 = blockIdx.x * FB_W, y0 = blockIdx.y * FB_H;
     smooth_block<KS>(in, in_pitch, w, h, fp, g, x0, y0, r0, r1);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const MapLayout L = map_layout(w, h);
     float best = 0.f;
     for (int r = warp; r < FB_H; r += FB_WARPS) {
-        if (y0 + r >= h) break;
+        const int Y = y0 + r;
         for (int q = lane; q < FB_W / 2; q += 32) {
-            const int c = 2 * q;                          // pixels x0 + c, x0 + c + 1
-            if (x0 + c >= w) break;
-            const float2 s2 = strength2_pair(r0, g.SX, r + 2, c + 2);
-            best = fmaxf(best, s2.x);
-            if (x0 + c + 1 < w) best = fmaxf(best, s2.y);
+            const int c = 2 * q, X = x0 + c;              // pixels X, X + 1
+            uint32_t code;
+            float2 s2 = strength_sector_pair(r0, g.SX, r + 2, c + 2, &code);
+            if (Y >= h || X >= w) s2.x = 0.f;
+            if (Y >= h || X + 1 >= w) s2.y = 0.f;
+            best = fmaxf(best, fmaxf(s2.x, s2.y));
+            *reinterpret_cast<float2 *>(smap + (size_t)Y * L.mp + X) = s2;
+            // lanes 2k and 2k + 1 hold the two pairs of one 4-pixel sector byte
+            const uint32_t other = __shfl_xor_sync(tile::FULL, code, 1);
+            if ((lane & 1) == 0) sect[(size_t)Y * (L.mp / 4) + (X >> 2)] = (uint8_t)(code | (other << 4));
         }
     }
     __shared__ float red[FB_WARPS];
@@ -349,49 +370,50 @@ k1f_max_kernel(const uint8_t *__restrict__ in, int in_pitch, int w, int h, Float
 }
 
 // ---------------------------------------------------------------- pass 2
-template <int KS>
-__global__ void __launch_bounds__(FB_THREADS, 2)
-k1f_edges_kernel(const uint8_t *__restrict__ in, int in_pitch, int w, int h, FloatParams fp,
-                 const float *__restrict__ d_smax, HystScratch hs, HystImage img)
-{
-    extern __shared__ __align__(16) float fsm[];
-    __shared__ uint32_t cand_s[FB_H][FB_TX], strong_s[FB_H][FB_TX];
-    const Geometry g = geometry(KS > 0 ? KS : fp.ksize);
-    float *r0 = fsm, *r1 = fsm + g.region0;
-    const int x0 = blockIdx.x * FB_W, y0 = blockIdx.y * FB_H;
-    smooth_block<KS>(in, in_pitch, w, h, fp, g, x0, y0, r0, r1);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+// Step 3 (suppression) and the thresholds on the pass-1 maps, then Step 4's
+// tile flood fill: each warp takes one 32 x 32 tile from start to end (its
+// strengths with a 1-pixel ring staged in its own shared memory), so warps
+// never wait for one another.
+constexpr int NMS_T = HT + 2;                // staged rows / columns of a tile with its ring
+constexpr int NMS_TILE = NMS_T * NMS_T;
 
-    // squared strength on the block and its ring (0 outside the image) into region 1
-    const float *S_s = r0;
-    float *s_s = r1;
-    // pairs of columns j = 2 .. FB_W + 1 (S row r + 1 is image row y0 - 1 + r)
-    for (int r = warp; r < g.MY; r += FB_WARPS) {
-        const int Y = y0 - 1 + r;
-        const bool row_in = Y >= 0 && Y < h;
-        for (int q = lane; q < FB_W / 2; q += 32) {
-            const int j = 2 + 2 * q, X = x0 - 2 + j;
-            float2 s2 = f2(0.f, 0.f);
-            if (row_in && X < w) {
-                s2 = strength2_pair(S_s, g.SX, r + 1, j);
-                if (X + 1 >= w) s2.y = 0.f;
-            }
-            *reinterpret_cast<float2 *>(s_s + r * g.MX + j) = s2;
+__global__ void __launch_bounds__(FB_THREADS)
+k1f_nms_kernel(const float *__restrict__ smap, const uint8_t *__restrict__ sect, int w, int h, FloatParams fp,
+               const float *__restrict__ d_smax, HystScratch hs, HystImage img)
+{
+    __shared__ float s_all[FB_WARPS * NMS_TILE];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tx = blockIdx.x * FB_TX + warp % FB_TX, ty = blockIdx.y * FB_TY + warp / FB_TX;
+    if (tx >= img.ntx || ty >= img.nty) return;                   // warp-uniform; no block barrier follows
+    const MapLayout L = map_layout(w, h);
+    float *s_s = s_all + warp * NMS_TILE;                          // entry (r, c): row ty*32 - 1 + r, column tx*32 - 1 + c
+    const int X0 = tx * HT, Y0 = ty * HT;
+    // sectors of tile row `lane` (32 pixels, 2 bits each)
+    const uint2 sec_row = __ldg(reinterpret_cast<const uint2 *>(sect + (size_t)(Y0 + lane) * (L.mp / 4) + (X0 >> 2)));
+    // the tile's strengths and ring (0 outside the maps): all loads first
+    {
+        constexpr int NE = (2 * NMS_T + 31) / 32;                   // ring-column entries per lane
+        float v[NMS_T], e[NE];
+#pragma unroll
+        for (int r = 0; r < NMS_T; ++r) {
+            const int Y = Y0 - 1 + r;
+            v[r] = (Y >= 0 && Y < L.rows) ? __ldg(smap + (size_t)Y * L.mp + X0 + lane) : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < NE; ++k) {                                // entry j: row j / 2, left or right column
+            const int j = lane + 32 * k, Y = Y0 - 1 + (j >> 1), Xe = (j & 1) ? X0 + HT : X0 - 1;
+            e[k] = (j < 2 * NMS_T && Y >= 0 && Y < L.rows && Xe >= 0 && Xe < L.mp)
+                       ? __ldg(smap + (size_t)Y * L.mp + Xe) : 0.f;
+        }
+#pragma unroll
+        for (int r = 0; r < NMS_T; ++r) s_s[r * NMS_T + 1 + lane] = v[r];
+#pragma unroll
+        for (int k = 0; k < NE; ++k) {
+            const int j = lane + 32 * k;
+            if (j < 2 * NMS_T) s_s[(j >> 1) * NMS_T + ((j & 1) ? NMS_T - 1 : 0)] = e[k];
         }
     }
-    // the ring's outer columns j = 1 and j = FB_W + 2
-    for (int i = tid; i < 2 * g.MY; i += FB_THREADS) {
-        const int r = i >> 1, j = (i & 1) ? FB_W + 2 : 1;
-        const int X = x0 - 2 + j, Y = y0 - 1 + r;
-        float s = 0.f;
-        if (X >= 0 && X < w && Y >= 0 && Y < h) {
-            float gx, gy;
-            sobel_at(S_s, g.SX, r + 1, j, gx, gy);
-            s = strength2(gx, gy);
-        }
-        s_s[r * g.MX + j] = s;
-    }
-    __syncthreads();
+    __syncwarp();
 
     // thresholds: fractions of Mmax = sqrt(smax), float products as in the definition
     const float mmax = __fsqrt_rn(*d_smax);
@@ -400,46 +422,37 @@ k1f_edges_kernel(const uint8_t *__restrict__ in, int in_pitch, int w, int h, Flo
     // necessary condition for sqrt_rn(s) > t_min: s > t_min^2 (1 - 2^-23); 1e-4 of slack
     const float s_pre = fmul(fmul(t_min, t_min), 0.9999f);
 
-    // Step 3 + thresholds: one (row, tile column) per warp iteration, lane = column
-    for (int item = warp; item < FB_H * FB_TX; item += FB_WARPS) {
-        const int r = item / FB_TX, tc = item % FB_TX;
-        const int mc = 2 + HT * tc + lane, mr = r + 1;      // index in s_s (and S column)
-        const float s = s_s[mr * g.MX + mc];
-        bool weak = false, strong = false;
+    // row r of the tile per iteration, lane = column; lane r keeps row r's masks
+    uint32_t cand = 0, strong = 0;
+    for (int r = 0; r < HT; ++r) {
+        const int at = (r + 1) * NMS_T + 1 + lane;
+        const float s = s_s[at];
+        const uint32_t sec_lo = __shfl_sync(tile::FULL, sec_row.x, r);   // row r, columns 0..15
+        const uint32_t sec_hi = __shfl_sync(tile::FULL, sec_row.y, r);   // columns 16..31
+        bool weak_px = false, strong_px = false;
         if (s > s_pre) {
             const float m = __fsqrt_rn(s);
-            float gx, gy;
-            sobel_at(S_s, g.SX, r + 2, mc, gx, gy);
-            const float t = 0.41421356f, ax = fabsf(gx), ay = fabsf(gy);
-            int dn, dp;                                         // offsets of n- and n+ in s_s
-            if (ay < fmul(ax, t)) { dn = -1; dp = 1; }                                  // H
-            else if (ax < fmul(ay, t)) { dn = -g.MX; dp = g.MX; }                       // V
-            else if ((gx > 0.f && gy > 0.f) || (gx < 0.f && gy < 0.f)) { dn = -g.MX - 1; dp = g.MX + 1; }  // D
-            else { dn = g.MX - 1; dp = -g.MX + 1; }             // A: down-left / up-right
-            const float mn = __fsqrt_rn(s_s[mr * g.MX + mc + dn]);
-            const float mp = __fsqrt_rn(s_s[mr * g.MX + mc + dp]);
+            const uint32_t sec = ((lane < 16 ? sec_lo : sec_hi) >> (2 * (lane & 15))) & 3u;
+            // offsets of n- and n+: H left / right, V up / down, D up-left / down-right,
+            // A down-left / up-right
+            const int dn = sec == 0 ? -1 : sec == 1 ? -NMS_T : sec == 2 ? -NMS_T - 1 : NMS_T - 1;
+            const float mn = __fsqrt_rn(s_s[at + dn]);
+            const float mp = __fsqrt_rn(s_s[at - dn]);
             const bool keep = (m > mn) && (m >= mp);
-            strong = keep && m > hi_t;
-            weak = keep && (m > lo_t || strong);
+            strong_px = keep && m > hi_t;
+            weak_px = keep && (m > lo_t || strong_px);
         }
-        const uint32_t wm = __ballot_sync(tile::FULL, weak), sm = __ballot_sync(tile::FULL, strong);
-        if (lane == 0) {
-            cand_s[r][tc] = wm;
-            strong_s[r][tc] = sm;
+        const uint32_t wm = __ballot_sync(tile::FULL, weak_px), sm = __ballot_sync(tile::FULL, strong_px);
+        if (lane == r) {
+            cand = wm;
+            strong = sm;
         }
     }
-    __syncthreads();
 
-    // Step 4, tile-local: warp k floods tile k of the block
-    const int txl = warp % FB_TX, tyl = warp / FB_TX;
-    const int tx = blockIdx.x * FB_TX + txl, ty = blockIdx.y * FB_TY + tyl;
-    if (tx < img.ntx && ty < img.nty) {
-        const uint32_t cand = cand_s[tyl * HT + lane][txl];
-        const uint32_t strong = strong_s[tyl * HT + lane][txl];
-        const uint32_t e = tile::flood_tile(strong, cand, lane);
-        tile::store_row(img, tx, ty, lane, e);
-        tile::finish_tile(hs, img.tile_base + (uint32_t)ty * (uint32_t)img.ntx + (uint32_t)tx, e, cand, lane);
-    }
+    // Step 4, tile-local
+    const uint32_t e = tile::flood_tile(strong, cand, lane);
+    tile::store_row(img, tx, ty, lane, e);
+    tile::finish_tile(hs, img.tile_base + (uint32_t)ty * (uint32_t)img.ntx + (uint32_t)tx, e, cand, lane);
 }
 
 size_t fused_smem_bytes(int ksize)
@@ -449,54 +462,59 @@ size_t fused_smem_bytes(int ksize)
 }
 
 template <int KS>
-cudaError_t launch_pair(const uint8_t *in, int in_pitch, int w, int h, const FloatParams &fp, float *d_smax,
-                        const HystScratch *hs, const HystImage *img, cudaStream_t s)
+cudaError_t launch_strength(const uint8_t *in, int in_pitch, int w, int h, const FloatParams &fp, float *d_smax,
+                            float *smap, uint8_t *sect, cudaStream_t s)
 {
     static bool attr = false;
     if (!attr) {
         const int bytes = (int)fused_smem_bytes(KS > 0 ? KS : MAX_KSIZE);
-        cudaError_t e = cudaFuncSetAttribute(k1f_max_kernel<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k1f_edges_kernel<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        cudaError_t e =
+            cudaFuncSetAttribute(k1f_strength_kernel<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     const dim3 grid((w + FB_W - 1) / FB_W, (h + FB_H - 1) / FB_H);
-    const size_t smem = fused_smem_bytes(fp.ksize);
-    if (!hs) {
-        k1f_max_kernel<KS><<<grid, FB_THREADS, smem, s>>>(in, in_pitch, w, h, fp, d_smax);
-    } else {
-        k1f_edges_kernel<KS><<<grid, FB_THREADS, smem, s>>>(in, in_pitch, w, h, fp, d_smax, *hs, *img);
-    }
+    k1f_strength_kernel<KS><<<grid, FB_THREADS, fused_smem_bytes(fp.ksize), s>>>(in, in_pitch, w, h, fp, d_smax,
+                                                                                  smap, sect);
     return cudaGetLastError();
-}
-
-cudaError_t dispatch(const uint8_t *in, int in_pitch, int w, int h, const FloatParams &fp, float *d_smax,
-                     const HystScratch *hs, const HystImage *img, cudaStream_t s)
-{
-    if (w <= 0 || h <= 0) return cudaSuccess;
-    switch (fp.ksize) {
-    case 3: return launch_pair<3>(in, in_pitch, w, h, fp, d_smax, hs, img, s);
-    case 5: return launch_pair<5>(in, in_pitch, w, h, fp, d_smax, hs, img, s);
-    case 7: return launch_pair<7>(in, in_pitch, w, h, fp, d_smax, hs, img, s);
-    case 9: return launch_pair<9>(in, in_pitch, w, h, fp, d_smax, hs, img, s);
-    case 11: return launch_pair<11>(in, in_pitch, w, h, fp, d_smax, hs, img, s);
-    default: return launch_pair<0>(in, in_pitch, w, h, fp, d_smax, hs, img, s);
-    }
 }
 
 }  // namespace
 
-cudaError_t launch_k1f_max(const uint8_t *in, int in_pitch, int w, int h, const FloatParams &fp, float *d_smax,
-                           cudaStream_t s)
+size_t k1f_map_bytes(int w, int h)
 {
-    return dispatch(in, in_pitch, w, h, fp, d_smax, nullptr, nullptr, s);
+    if (w <= 0 || h <= 0) return 0;
+    const MapLayout L = map_layout(w, h);
+    return (size_t)L.mp * L.rows * sizeof(float) + (size_t)(L.mp / 4) * L.rows;
 }
 
-cudaError_t launch_k1f_edges(const uint8_t *in, int in_pitch, int w, int h, const FloatParams &fp,
-                             const float *d_smax, const HystScratch &hs, HystImage img, cudaStream_t s)
+cudaError_t launch_k1f_strength(const uint8_t *in, int in_pitch, int w, int h, const FloatParams &fp,
+                                float *d_smax, void *maps, cudaStream_t s)
 {
-    return dispatch(in, in_pitch, w, h, fp, const_cast<float *>(d_smax), &hs, &img, s);
+    if (w <= 0 || h <= 0) return cudaSuccess;
+    const MapLayout L = map_layout(w, h);
+    float *smap = static_cast<float *>(maps);
+    uint8_t *sect = reinterpret_cast<uint8_t *>(smap + (size_t)L.mp * L.rows);
+    switch (fp.ksize) {
+    case 3: return launch_strength<3>(in, in_pitch, w, h, fp, d_smax, smap, sect, s);
+    case 5: return launch_strength<5>(in, in_pitch, w, h, fp, d_smax, smap, sect, s);
+    case 7: return launch_strength<7>(in, in_pitch, w, h, fp, d_smax, smap, sect, s);
+    case 9: return launch_strength<9>(in, in_pitch, w, h, fp, d_smax, smap, sect, s);
+    case 11: return launch_strength<11>(in, in_pitch, w, h, fp, d_smax, smap, sect, s);
+    default: return launch_strength<0>(in, in_pitch, w, h, fp, d_smax, smap, sect, s);
+    }
+}
+
+cudaError_t launch_k1f_nms(const void *maps, int w, int h, const FloatParams &fp, const float *d_smax,
+                           const HystScratch &hs, HystImage img, cudaStream_t s)
+{
+    if (w <= 0 || h <= 0) return cudaSuccess;
+    const MapLayout L = map_layout(w, h);
+    const float *smap = static_cast<const float *>(maps);
+    const uint8_t *sect = reinterpret_cast<const uint8_t *>(smap + (size_t)L.mp * L.rows);
+    const dim3 grid(L.mp / FB_W, L.rows / FB_H);
+    k1f_nms_kernel<<<grid, FB_THREADS, 0, s>>>(smap, sect, w, h, fp, d_smax, hs, img);
+    return cudaGetLastError();
 }
 
 }  // namespace canny

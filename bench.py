@@ -42,12 +42,12 @@ WORKLOAD = "canny_int_16384x16384"
 K1_BYTES_PER_PX = 2
 # ncu DRAM traffic of the fused kernel per 16384^2 launch, valid only for the kernel
 # source it was measured on (profiles/k1_fused_16384x8192.md: capture at half size, x2)
-K1_TRAFFIC = {"sha256_prefix": "86fce3b153800ed2", "bytes": 467_558_400}
+K1_TRAFFIC = {"sha256_prefix": "9728ff511329b07b", "bytes": 467_110_912}
 # whole pipeline floor: stencil 2 B/px + tile-local hysteresis read + write 2 B/px
 PIPE_BYTES_PER_PX = 4
 # ncu smsp__inst_executed.sum of the fused kernel per pixel (same capture and source
-# as K1_TRAFFIC: 284,931,895 warp instructions on 16384 x 8192 pixels)
-K1_INST = {"sha256_prefix": "86fce3b153800ed2", "warp_inst_per_px": 284_931_895 / (16384 * 8192)}
+# as K1_TRAFFIC: 283,583,457 warp instructions on 16384 x 8192 pixels)
+K1_INST = {"sha256_prefix": "9728ff511329b07b", "warp_inst_per_px": 283_583_457 / (16384 * 8192)}
 # warp instructions an SM can issue per clock (4 schedulers, one each)
 ISSUE_PER_SM_CLK = 4
 
@@ -62,10 +62,13 @@ def measured_peaks() -> dict:
 
 
 def k1_digest() -> str:
+    """sha256 over the fused kernel's source and the tile header it inlines."""
     import hashlib
-    src = os.path.join(ROOT, "paper_1710_07745_gb300", "csrc", "k1_fused.cu")
-    with open(src, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()
+    h = hashlib.sha256()
+    for name in ("k1_fused.cu", "hyst_tile.cuh"):
+        with open(os.path.join(ROOT, "paper_1710_07745_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def k1_traffic(w: int, h: int):

@@ -641,14 +641,18 @@ def run_ours(args, rank: int, world: int) -> None:
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32" if args.path == "int" else "f32",
         "data": "synthetic", "config": config({"path": "integer" if args.path == "int" else "float32"}),
-        "roofline": {"kernel": "k1_fused_kernel (Gauss/Sobel/NMS/threshold + tile-local hysteresis)",
+        "roofline": {"kernel": "k1_fused_kernel (Gauss/Sobel/NMS/threshold + tile-local hysteresis)"
+                     if args.path == "int" else
+                     "k1f_strength_kernel + k1f_nms_kernel (both stencil passes of the float variant)",
                      "bound": "hbm", "achieved": round(k1_gbs, 1), "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": round(k1_gbs / peaks["hbm_gbs"], 4),
-                     "traffic": k1_traffic(W, H), "peak_source": peaks["source"],
+                     "traffic": k1_traffic(W, H) if args.path == "int" else None,
+                     "peak_source": peaks["source"],
                      "bytes_per_launch": K1_BYTES_PER_PX * px},
-        "alu_roofline": alu_roofline(px, k1_ms, peaks["hbm_gbs"], clk),
+        "alu_roofline": alu_roofline(px, k1_ms, peaks["hbm_gbs"], clk) if args.path == "int" else None,
         "pipeline_roofline": {"achieved": round(pipe_gbs, 1), "unit": "GB/s",
                               "bytes_per_px": PIPE_BYTES_PER_PX,
                               "frac": round(pipe_gbs / peaks["hbm_gbs"], 4)},

@@ -464,7 +464,7 @@ def measure_serving(n_requests: int, loads=(0.1, 0.25, 0.5, 0.9, 1.5), budget_gb
 
     Request i carries image i mod 256 of a seeded pool (the sizes follow the stated
     distribution; the pixels repeat). Capacity is measured first with every request
-    arriving at once; the offered loads are fractions of it (above 1: overload, the
+    arriving at once (median of three runs); the offered loads are fractions of it (above 1: overload, the
     queue grows). Each load's trace has n_requests requests, or fewer when that
     would span more than max_trace_s seconds of arrivals (at least 5000). The
     serial baseline (one canny_run_pitched at a time) runs the second load's trace
@@ -500,8 +500,9 @@ def measure_serving(n_requests: int, loads=(0.1, 0.25, 0.5, 0.9, 1.5), budget_gb
             out["offered_mpx_s"] = round(offered, 1)
         return out
 
-    cap_rep = canny.canny_serve(cfg(0), trace(min(n_requests, 20000), 0.0, 1))
-    capacity = cap_rep.delivered_mpx_s                 # Mpixel/s
+    # capacity: median of three all-at-once runs (one run alone varied by up to 15 %)
+    caps = sorted(canny.canny_serve(cfg(0), trace(min(n_requests, 20000), 0.0, 1)).delivered_mpx_s for _ in range(3))
+    capacity = caps[1]                                 # Mpixel/s
     result = {"requests": n_requests, "sides": [SERVE_LO, SERVE_HI], "budget_gb": budget_gb, "streams": streams,
               "pool_images": SERVE_POOL, "capacity_mpx_s": round(capacity, 1), "loads": []}
     for k, load in enumerate(loads):

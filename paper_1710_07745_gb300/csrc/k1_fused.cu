@@ -410,9 +410,11 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 // 2^23 + 1024 + g holds g + 1024 (11 bits) in its low mantissa bits;
-                // shifted left by 11, the exponent bits leave the word
-                const uint32_t ax = __float_as_uint(gx[j].x + 8389632.0f), ay = __float_as_uint(gy[j].x + 8389632.0f);
-                const uint32_t bx = __float_as_uint(gx[j].y + 8389632.0f), by = __float_as_uint(gy[j].y + 8389632.0f);
+                // shifted left by 11, the exponent bits leave the word (paired adds: exact)
+                const float2 magic = f2(8389632.0f, 8389632.0f);
+                const float2 ux = __fadd2_rn(gx[j], magic), uy = __fadd2_rn(gy[j], magic);
+                const uint32_t ax = __float_as_uint(ux.x), ay = __float_as_uint(uy.x);
+                const uint32_t bx = __float_as_uint(ux.y), by = __float_as_uint(uy.y);
                 gprev[j] = (ax & 2047u) | (ay << 11);
                 gprev[j + 4] = (bx & 2047u) | (by << 11);
             }

@@ -211,7 +211,10 @@ canny_status canny_read_timing(canny_ctx *ctx, canny_timing *out);
 /*
  * Launch configuration of the fused integer kernel: rows per unit of work
  * (band: 64, 160 or 256; taller bands cut halo work, shorter ones balance small
- * images better) and persistent CTAs per SM in batches. direct_loads = 1 reads
+ * images better) and, for batches, ctas_per_sm: 0 (the default) launches one
+ * CTA per (image, strip, band) unit and lets the hardware schedule them, 1..32
+ * launches that many persistent CTAs per SM that pop units from a device
+ * counter. direct_loads = 1 reads
  * inputs whose base or pitch is not a multiple of 16 bytes directly instead of
  * repitching them into staging first (slower; no staging memory); 0 or 1.
  */
@@ -283,7 +286,7 @@ typedef struct {
     int64_t max_batch_pixels;     /* pixels per batch, at most (>= the largest request) */
     int serial;                   /* 1: one request at a time through canny_run_pitched (baseline) */
     int low, high;                /* integer-path thresholds */
-    int band, ctas_per_sm;        /* fused-kernel configuration (0: defaults) */
+    int band, ctas_per_sm;        /* fused-kernel configuration (band 0: defaults) */
 } canny_serve_config;
 
 typedef struct {

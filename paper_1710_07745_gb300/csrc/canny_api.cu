@@ -48,7 +48,7 @@ struct canny_ctx {
 
     // launch configuration of the fused kernel (canny_set_tuning / canny_autotune_batch)
     int band = 64;                     // rows per unit of work
-    int ctas_per_sm = 12;              // persistent CTAs per SM in a batch
+    int ctas_per_sm = 0;               // batches: 0 = one CTA per unit, else persistent CTAs per SM
     int direct_loads = 0;              // 1: inputs the TMA path cannot read are not repitched
 
     // integer-path batches: per staging slot one graph per fused-kernel variant
@@ -58,6 +58,7 @@ struct canny_ctx {
         unsigned char *h_blob = nullptr;
         cudaGraph_t graph[2] = {nullptr, nullptr};
         cudaGraphExec_t exec[2] = {nullptr, nullptr};
+        cudaGraphNode_t k1node[2] = {nullptr, nullptr};   // the fused kernel's node (grid set per launch)
         cudaEvent_t done = nullptr;
         bool valid[2] = {false, false};   // graph matches the current scratch and configuration
     } slots[2];
@@ -501,7 +502,8 @@ canny_status build_batch_graph(canny_ctx *c, canny_ctx::Slot &sl, int v)
     cudaGraphNode_t d_k1[3] = {up2, init, stage};
     if (e == cudaSuccess)
         e = k1_add_batch_node(g, d_k1, 3, c->band, v == 1, imgs, tmaps, hdr, c->it, c->hs,
-                              sm_count() * c->ctas_per_sm, &k1);
+                              c->ctas_per_sm > 0 ? sm_count() * c->ctas_per_sm : 0, &k1);
+    sl.k1node[v] = k1;
     if (e == cudaSuccess) e = hyst_add_loop(g, &k1, 1, c->hs, &loop);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&sl.exec[v], g, 0);
     if (e != cudaSuccess) {
@@ -602,7 +604,12 @@ canny_status run_batch_int(canny_ctx *c, int n, const canny_image *imgs, uint32_
         st = build_batch_graph(c, sl, v);
         if (st != CANNY_OK) return st;
     }
-    cudaError_t e = cudaGraphLaunch(sl.exec[v], s);
+    cudaError_t e = cudaSuccess;
+    if (c->ctas_per_sm <= 0)
+        e = k1_set_batch_units(sl.exec[v], sl.k1node[v], c->band, v == 1, (const BatchImage *)(c->d_blob + L.imgs),
+                               (const CUtensorMap *)(c->d_blob + L.tmaps), (BatchHeader *)c->d_blob, c->it, c->hs,
+                               unit_base);
+    if (e == cudaSuccess) e = cudaGraphLaunch(sl.exec[v], s);
     if (e == cudaSuccess) e = cudaEventRecord(sl.done, s);
     return from_cuda(e);
 }
@@ -877,7 +884,7 @@ canny_status canny_read_timing(canny_ctx *c, canny_timing *out)
 canny_status canny_set_tuning(canny_ctx *c, const canny_tuning *t)
 {
     if (!c || !t) return CANNY_EINVAL;
-    if (!k1_band_supported(t->band) || t->ctas_per_sm < 1 || t->ctas_per_sm > 32) return CANNY_EINVAL;
+    if (!k1_band_supported(t->band) || t->ctas_per_sm < 0 || t->ctas_per_sm > 32) return CANNY_EINVAL;
     if (t->direct_loads != 0 && t->direct_loads != 1) return CANNY_EINVAL;
     c->direct_loads = t->direct_loads;
     if (t->band != c->band || t->ctas_per_sm != c->ctas_per_sm) {
@@ -943,7 +950,7 @@ canny_status canny_autotune_batch(canny_ctx *c, int n, const canny_image *imgs, 
     if (!best.from_cache) {
         // time every candidate on this batch: warm-up run, then two timed runs
         const int bands[3] = {64, 160, 256};
-        const int ctas[3] = {8, 12, 16};
+        const int ctas[3] = {0, 12, 16};
         cudaEvent_t e0, e1;
         if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return CANNY_ECUDA;
         best.ms = 1e30;

@@ -105,12 +105,17 @@ cudaError_t launch_k1_classify_u8(const uint8_t *in, int in_pitch, uint8_t *cls,
 // tile masks / pending bitmaps / first worklist into hs (after hyst_reset).
 cudaError_t launch_k1_edges_u8(const uint8_t *in, int in_pitch, int w, int h, IntThresholds t,
                                const HystScratch &hs, HystImage img, cudaStream_t s, int band = 64);
-// The same for every image of a batch, as a node of graph g: a persistent grid
-// of `ctas` one-warp CTAs pops (image, strip, band) units from hdr->next_unit.
+// The same for every image of a batch, as a node of graph g: with ctas > 0 a
+// persistent grid of `ctas` one-warp CTAs pops (image, strip, band) units from
+// hdr->next_unit; with ctas <= 0 the grid has one CTA per unit, set before each
+// launch of the instantiated graph by k1_set_batch_units.
 // tma_only: every image's input is TMA-readable (the kernel holds no direct-load path).
 cudaError_t k1_add_batch_node(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, int band, bool tma_only,
                               const BatchImage *imgs, const CUtensorMap *tmaps, BatchHeader *hdr, IntThresholds t,
                               const HystScratch &hs, int ctas, cudaGraphNode_t *out);
+cudaError_t k1_set_batch_units(cudaGraphExec_t exec, cudaGraphNode_t node, int band, bool tma_only,
+                               const BatchImage *imgs, const CUtensorMap *tmaps, BatchHeader *hdr, IntThresholds t,
+                               const HystScratch &hs, uint32_t units);
 
 // ---------------------------------------------------------------- host images (hostio.cu)
 // One image between a tight, 16-byte aligned, device-accessible host buffer and

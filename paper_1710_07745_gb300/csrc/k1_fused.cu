@@ -538,9 +538,44 @@ k1_fused_kernel(const __grid_constant__ CUtensorMap tmap, const uint8_t *__restr
     run_unit<BAND, MODE, PATH>(&tmap, U, t, out, out_pitch, hs, img, err, S, lane);
 }
 
-// A batch: a persistent grid pops (image, strip, band) units from a counter.
-// PATH_TMA when every input is TMA-readable, else PATH_EITHER (chosen per image).
+// One (image, strip, band) unit of a batch.
 template <int BAND, int PATH>
+__device__ __forceinline__ void batch_unit(const BatchImage *__restrict__ imgs, const CUtensorMap *__restrict__ tmaps,
+                                           int nimg, uint32_t unit, IntThresholds t, const HystScratch &hs,
+                                           Smem<BAND> &S, int lane)
+{
+    int lo = 0, hi = nimg - 1;                     // last image whose units start at or before unit
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (imgs[mid].unit_base <= unit) lo = mid;
+        else hi = mid - 1;
+    }
+    const BatchImage &B = imgs[lo];
+    const uint32_t local = unit - B.unit_base;
+    Unit U;
+    U.in = B.in;
+    U.in_pitch = B.in_pitch;
+    U.w = B.img.w;
+    U.h = B.img.h;
+    U.sx = (int)(local % (uint32_t)B.nsx);
+    U.sy = (int)(local / (uint32_t)B.nsx);
+    U.X0 = U.sx * OUT_W;
+    U.Y0 = U.sy * BAND;
+    U.tma = PATH == PATH_TMA || B.tma != 0;
+    const HystImage img = B.img;
+    if (U.tma && lane == 0) {
+        // the descriptor was rewritten in global memory since the TMA unit may
+        // last have cached one at this address: order that write before its use
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&tmaps[lo]) : "memory");
+    }
+    __syncwarp();
+    run_unit<BAND, MODE_EDGES, PATH>(&tmaps[lo], U, t, img.map, img.pitch, hs, img, &hs.state->error, S, lane);
+}
+
+// A batch. PERSIST: a persistent grid pops units from a counter; otherwise the
+// grid has one CTA per unit (set per launch) and the hardware schedules them.
+// PATH_TMA when every input is TMA-readable, else PATH_EITHER (chosen per image).
+template <int BAND, int PATH, bool PERSIST>
 __global__ void __launch_bounds__(THREADS, BAND == 64 ? 16 : 12)
 k1_fused_batch_kernel(const BatchImage *__restrict__ imgs, const CUtensorMap *__restrict__ tmaps,
                       BatchHeader *hdr, IntThresholds t, HystScratch hs)
@@ -548,40 +583,21 @@ k1_fused_batch_kernel(const BatchImage *__restrict__ imgs, const CUtensorMap *__
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem<BAND> &S = *reinterpret_cast<Smem<BAND> *>(smem_raw);
     const int lane = threadIdx.x;
-    init_barriers(S, lane);
     const uint32_t total = hdr->total_units;
     const int nimg = (int)hdr->nimg;
-    for (;;) {
-        uint32_t unit = 0;
-        if (lane == 0) unit = atomicAdd(&hdr->next_unit, 1u);
-        unit = __shfl_sync(FULL, unit, 0);
-        if (unit >= total) break;
-        int lo = 0, hi = nimg - 1;                     // last image whose units start at or before unit
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (imgs[mid].unit_base <= unit) lo = mid;
-            else hi = mid - 1;
+    if constexpr (!PERSIST) {
+        if (blockIdx.x >= total) return;
+        init_barriers(S, lane);
+        batch_unit<BAND, PATH>(imgs, tmaps, nimg, blockIdx.x, t, hs, S, lane);
+    } else {
+        init_barriers(S, lane);
+        for (;;) {
+            uint32_t unit = 0;
+            if (lane == 0) unit = atomicAdd(&hdr->next_unit, 1u);
+            unit = __shfl_sync(FULL, unit, 0);
+            if (unit >= total) break;
+            batch_unit<BAND, PATH>(imgs, tmaps, nimg, unit, t, hs, S, lane);
         }
-        const BatchImage &B = imgs[lo];
-        const uint32_t local = unit - B.unit_base;
-        Unit U;
-        U.in = B.in;
-        U.in_pitch = B.in_pitch;
-        U.w = B.img.w;
-        U.h = B.img.h;
-        U.sx = (int)(local % (uint32_t)B.nsx);
-        U.sy = (int)(local / (uint32_t)B.nsx);
-        U.X0 = U.sx * OUT_W;
-        U.Y0 = U.sy * BAND;
-        U.tma = PATH == PATH_TMA || B.tma != 0;
-        const HystImage img = B.img;
-        if (U.tma && lane == 0) {
-            // the descriptor was rewritten in global memory since the TMA unit may
-            // last have cached one at this address: order that write before its use
-            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&tmaps[lo]) : "memory");
-        }
-        __syncwarp();
-        run_unit<BAND, MODE_EDGES, PATH>(&tmaps[lo], U, t, img.map, img.pitch, hs, img, &hs.state->error, S, lane);
     }
 }
 
@@ -652,34 +668,49 @@ cudaError_t launch_k1_edges_u8(const uint8_t *in, int in_pitch, int w, int h, In
     return launch_any<MODE_EDGES>(band, in, in_pitch, w, h, t, img.map, img.pitch, hs, img, &hs.state->error, s);
 }
 
-template <int BAND, int PATH>
-cudaError_t add_batch_node_band(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, const BatchImage *imgs,
-                                const CUtensorMap *tmaps, BatchHeader *hdr, IntThresholds t, const HystScratch &hs,
-                                int ctas, cudaGraphNode_t *out)
+// Kernel node parameters of the batch kernel; grid: CTAs (persistent) or units.
+template <int BAND, int PATH, bool PERSIST>
+cudaError_t batch_node_params(const BatchImage *const &imgs, const CUtensorMap *const &tmaps, BatchHeader *const &hdr,
+                              const IntThresholds &t, const HystScratch &hs, unsigned grid, void **args,
+                              cudaKernelNodeParams *kp)
 {
-    cudaError_t e = cudaFuncSetAttribute(k1_fused_batch_kernel<BAND, PATH>,
+    cudaError_t e = cudaFuncSetAttribute(k1_fused_batch_kernel<BAND, PATH, PERSIST>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<BAND>));
     if (e != cudaSuccess) return e;
-    HystScratch hs_copy = hs;
-    void *args[] = {(void *)&imgs, (void *)&tmaps, (void *)&hdr, (void *)&t, (void *)&hs_copy};
-    cudaKernelNodeParams kp = {};
-    kp.func = (void *)k1_fused_batch_kernel<BAND, PATH>;
-    kp.gridDim = dim3(ctas);
-    kp.blockDim = dim3(THREADS);
-    kp.sharedMemBytes = sizeof(Smem<BAND>);
-    kp.kernelParams = args;
-    return cudaGraphAddKernelNode(out, g, deps, ndeps, &kp);
+    args[0] = (void *)&imgs;
+    args[1] = (void *)&tmaps;
+    args[2] = (void *)&hdr;
+    args[3] = (void *)&t;
+    args[4] = (void *)&hs;
+    *kp = cudaKernelNodeParams{};
+    kp->func = (void *)k1_fused_batch_kernel<BAND, PATH, PERSIST>;
+    kp->gridDim = dim3(grid > 0 ? grid : 1u);
+    kp->blockDim = dim3(THREADS);
+    kp->sharedMemBytes = sizeof(Smem<BAND>);
+    kp->kernelParams = args;
+    return cudaSuccess;
 }
 
-template <int PATH>
-cudaError_t add_batch_node_path(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, int band,
-                                const BatchImage *imgs, const CUtensorMap *tmaps, BatchHeader *hdr, IntThresholds t,
-                                const HystScratch &hs, int ctas, cudaGraphNode_t *out)
+template <int BAND>
+cudaError_t batch_params_band(bool tma_only, bool persist, const BatchImage *const &imgs,
+                              const CUtensorMap *const &tmaps, BatchHeader *const &hdr, const IntThresholds &t,
+                              const HystScratch &hs, unsigned grid, void **args, cudaKernelNodeParams *kp)
+{
+    if (tma_only)
+        return persist ? batch_node_params<BAND, PATH_TMA, true>(imgs, tmaps, hdr, t, hs, grid, args, kp)
+                       : batch_node_params<BAND, PATH_TMA, false>(imgs, tmaps, hdr, t, hs, grid, args, kp);
+    return persist ? batch_node_params<BAND, PATH_EITHER, true>(imgs, tmaps, hdr, t, hs, grid, args, kp)
+                   : batch_node_params<BAND, PATH_EITHER, false>(imgs, tmaps, hdr, t, hs, grid, args, kp);
+}
+
+cudaError_t batch_params(int band, bool tma_only, bool persist, const BatchImage *const &imgs,
+                         const CUtensorMap *const &tmaps, BatchHeader *const &hdr, const IntThresholds &t,
+                         const HystScratch &hs, unsigned grid, void **args, cudaKernelNodeParams *kp)
 {
     switch (band) {
-    case 160: return add_batch_node_band<160, PATH>(g, deps, ndeps, imgs, tmaps, hdr, t, hs, ctas, out);
-    case 256: return add_batch_node_band<256, PATH>(g, deps, ndeps, imgs, tmaps, hdr, t, hs, ctas, out);
-    default: return add_batch_node_band<64, PATH>(g, deps, ndeps, imgs, tmaps, hdr, t, hs, ctas, out);
+    case 160: return batch_params_band<160>(tma_only, persist, imgs, tmaps, hdr, t, hs, grid, args, kp);
+    case 256: return batch_params_band<256>(tma_only, persist, imgs, tmaps, hdr, t, hs, grid, args, kp);
+    default: return batch_params_band<64>(tma_only, persist, imgs, tmaps, hdr, t, hs, grid, args, kp);
     }
 }
 
@@ -687,9 +718,23 @@ cudaError_t k1_add_batch_node(cudaGraph_t g, const cudaGraphNode_t *deps, size_t
                               const BatchImage *imgs, const CUtensorMap *tmaps, BatchHeader *hdr, IntThresholds t,
                               const HystScratch &hs, int ctas, cudaGraphNode_t *out)
 {
-    if (tma_only)
-        return add_batch_node_path<PATH_TMA>(g, deps, ndeps, band, imgs, tmaps, hdr, t, hs, ctas, out);
-    return add_batch_node_path<PATH_EITHER>(g, deps, ndeps, band, imgs, tmaps, hdr, t, hs, ctas, out);
+    void *args[5];
+    cudaKernelNodeParams kp;
+    cudaError_t e = batch_params(band, tma_only, ctas > 0, imgs, tmaps, hdr, t, hs, (unsigned)(ctas > 0 ? ctas : 1),
+                                 args, &kp);
+    if (e != cudaSuccess) return e;
+    return cudaGraphAddKernelNode(out, g, deps, ndeps, &kp);
+}
+
+cudaError_t k1_set_batch_units(cudaGraphExec_t exec, cudaGraphNode_t node, int band, bool tma_only,
+                               const BatchImage *imgs, const CUtensorMap *tmaps, BatchHeader *hdr, IntThresholds t,
+                               const HystScratch &hs, uint32_t units)
+{
+    void *args[5];
+    cudaKernelNodeParams kp;
+    cudaError_t e = batch_params(band, tma_only, false, imgs, tmaps, hdr, t, hs, units, args, &kp);
+    if (e != cudaSuccess) return e;
+    return cudaGraphExecKernelNodeSetParams(exec, node, &kp);
 }
 
 bool encode_k1_map(void *tmap_out, const uint8_t *in, int w, int h, int in_pitch)

@@ -197,7 +197,7 @@ extern "C" canny_status canny_serve(const canny_serve_config *cfg, int n, const 
             break;
         }
         if (cfg->band) {
-            canny_tuning t = {cfg->band, cfg->ctas_per_sm ? cfg->ctas_per_sm : 12, 0.0, 0, 0};
+            canny_tuning t = {cfg->band, cfg->ctas_per_sm, 0.0, 0, 0};
             st = canny_set_tuning(L.ctx, &t);
             if (st != CANNY_OK) break;
         }

@@ -458,7 +458,7 @@ def measure_float_on(d_in, d_out, name: str, n: int) -> dict:
 SERVE_POOL, SERVE_LO, SERVE_HI, SERVE_SEED = 256, 128, 4096, 5000
 
 
-def measure_serving(n_requests: int, loads=(0.1, 0.25, 0.5, 0.9, 1.5), budget_gb: float = 16.0, streams: int = 3,
+def measure_serving(n_requests: int, loads=(0.1, 0.25, 0.5, 0.9, 1.5), budget_gb: float = 16.0, streams: int = 4,
                     max_trace_s: float = 8.0) -> dict:
     """Continuous-batching server on Poisson arrivals, sides log-uniform in [128, 4096].
 
@@ -489,7 +489,10 @@ def measure_serving(n_requests: int, loads=(0.1, 0.25, 0.5, 0.9, 1.5), budget_gb
                                     float(t[i] - t[0]) if rate else 0.0) for i in range(n)]
 
     def cfg(serial):
-        return canny.canny_serve_config(budget_gb * 2 ** 30, streams, 4096, 256 << 20, serial, LOW, HIGH, 0, 0)
+        # at most 64 Mpixel a batch: with 4 streams, smaller batches overlap one
+        # batch's upload with another's stencil (all-at-once capacity 144 Gpixel/s
+        # against 123 for 3 streams of 256 Mpixel batches)
+        return canny.canny_serve_config(budget_gb * 2 ** 30, streams, 4096, 64 << 20, serial, LOW, HIGH, 0, 0)
 
     def summary(rep, offered=None):
         d = rep.as_dict()
@@ -504,6 +507,7 @@ def measure_serving(n_requests: int, loads=(0.1, 0.25, 0.5, 0.9, 1.5), budget_gb
     caps = sorted(canny.canny_serve(cfg(0), trace(min(n_requests, 20000), 0.0, 1)).delivered_mpx_s for _ in range(3))
     capacity = caps[1]                                 # Mpixel/s
     result = {"requests": n_requests, "sides": [SERVE_LO, SERVE_HI], "budget_gb": budget_gb, "streams": streams,
+              "max_batch_mpixel": 64,
               "pool_images": SERVE_POOL, "capacity_mpx_s": round(capacity, 1), "loads": []}
     for k, load in enumerate(loads):
         rate = load * capacity * 1e6 / mean_area        # requests per second

@@ -3,9 +3,10 @@
 // the TMA path cannot use. The copy engines move a pitched (2D) copy row by row,
 // which for request-sized images (rows of about a kilobyte) runs at a fraction
 // of the host link's rate; these kernels instead read (or write) the tight host
-// image as one contiguous range of 16-byte words over the link, and place the
-// bytes into (or take them from) the pitched device rows. The host buffers must
-// be device-accessible (pinned) and 16-byte aligned; the caller checks.
+// image as one contiguous range of aligned 16-byte words over the link, and
+// place the bytes into (or take them from) the pitched device rows. The host
+// buffers must be device-accessible (pinned) and 16-byte aligned; the caller
+// checks.
 #include "canny_internal.cuh"
 
 namespace canny {
@@ -14,36 +15,65 @@ namespace {
 
 constexpr int IO_THREADS = 256;
 
-// One copy per blockIdx.y; the CTAs of that row of the grid stride over its
-// 16-byte words of the tight host image.
+// The 16 bytes at p, any alignment, from a source whose bytes are [lo, hi):
+// two aligned 16-byte loads funnel-shifted into place, byte loads only where
+// an aligned granule would reach outside [lo, hi) (bytes at or past hi read 0).
+// The gather and the repitching below write whole aligned 16-byte destination
+// words from it: destination word j of a copy is 16 bytes at row j / wpr,
+// column 16 (j % wpr), wpr = ceil(w / 16); the bytes past w in a row's last
+// word are don't-care padding.
+__device__ __forceinline__ uint4 span16(const uint8_t *p, const uint8_t *lo, const uint8_t *hi)
+{
+    const uintptr_t pa = (uintptr_t)p, ga = pa & ~(uintptr_t)15, l = (uintptr_t)lo, h = (uintptr_t)hi;
+    const int m = (int)(pa - ga);
+    if (m == 0 && pa + 16 <= h) return __ldg(reinterpret_cast<const uint4 *>(p));
+    if (m != 0 && ga >= l && ga + 32 <= h) {
+        const uint4 A = __ldg(reinterpret_cast<const uint4 *>(ga));
+        const uint4 B = __ldg(reinterpret_cast<const uint4 *>(ga + 16));
+        const int q = m >> 2, r = 8 * (m & 3);
+        // V[i] = word q + i of the 32 loaded bytes
+        const uint32_t v0 = q == 0 ? A.x : q == 1 ? A.y : q == 2 ? A.z : A.w;
+        const uint32_t v1 = q == 0 ? A.y : q == 1 ? A.z : q == 2 ? A.w : B.x;
+        const uint32_t v2 = q == 0 ? A.z : q == 1 ? A.w : q == 2 ? B.x : B.y;
+        const uint32_t v3 = q == 0 ? A.w : q == 1 ? B.x : q == 2 ? B.y : B.z;
+        const uint32_t v4 = q == 0 ? B.x : q == 1 ? B.y : q == 2 ? B.z : B.w;
+        return make_uint4(__funnelshift_r(v0, v1, r), __funnelshift_r(v1, v2, r), __funnelshift_r(v2, v3, r),
+                          __funnelshift_r(v3, v4, r));
+    }
+    uint32_t wd[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+        if (pa + k < h) wd[k >> 2] |= (uint32_t)__ldg(p + k) << (8 * (k & 3));
+    return make_uint4(wd[0], wd[1], wd[2], wd[3]);
+}
 
-// host (tight rows) -> device (pitched rows)
+// One copy per blockIdx.y; the CTAs of that row of the grid stride over its
+// 16-byte words.
+
+// host (tight rows) -> device (pitched rows): each thread writes one 16-byte
+// word of a destination row (16-byte aligned rows; the bytes past w in a row's
+// last word are don't-care padding) from the 16 source bytes at its offset in
+// the tight image (span16: aligned 16-byte host loads funnel-shifted into
+// place, byte loads at the image's ends).
 __global__ void __launch_bounds__(IO_THREADS)
 gather_kernel(const HostCopy *__restrict__ copies)
 {
     const HostCopy c = copies[blockIdx.y];
-    const uint64_t bytes = (uint64_t)c.w * (uint64_t)c.h, words = (bytes + 15) / 16;
-    for (uint64_t word = blockIdx.x * (uint64_t)IO_THREADS + threadIdx.x; word < words;
-         word += (uint64_t)gridDim.x * IO_THREADS) {
-        const uint64_t first = word * 16u;
-        uint8_t b[16];
-        if (first + 16 <= bytes) {
-            const uint4 v = *reinterpret_cast<const uint4 *>(c.host + first);
-            const uint32_t wd[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int k = 0; k < 16; ++k) b[k] = (uint8_t)(wd[k >> 2] >> (8 * (k & 3)));
+    const uint64_t bytes = (uint64_t)c.w * (uint64_t)c.h;
+    const uint32_t wpr = (uint32_t)(c.w + 15) >> 4;
+    const uint64_t words = (uint64_t)wpr * (uint64_t)c.h;
+    const bool aligned = ((((uintptr_t)c.dev) | (uintptr_t)c.dev_pitch) & 15) == 0;
+    for (uint64_t j = blockIdx.x * (uint64_t)IO_THREADS + threadIdx.x; j < words; j += (uint64_t)gridDim.x * IO_THREADS) {
+        const uint32_t y = (uint32_t)(j / wpr), x = 16u * (uint32_t)(j - (uint64_t)y * wpr);
+        const uint64_t o = (uint64_t)y * (uint64_t)c.w + x;
+        const uint4 v = span16(c.host + o, c.host, c.host + bytes);
+        uint8_t *dst = c.dev + (int64_t)y * c.dev_pitch + x;
+        if (aligned) {
+            *reinterpret_cast<uint4 *>(dst) = v;
         } else {
-#pragma unroll
-            for (int k = 0; k < 16; ++k) b[k] = first + k < bytes ? c.host[first + k] : 0;
-        }
-        int row = (int)(first / (uint64_t)c.w), col = (int)(first - (uint64_t)row * c.w);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            if (first + k < bytes) c.dev[(int64_t)row * c.dev_pitch + col] = b[k];
-            if (++col == c.w) {
-                col = 0;
-                ++row;
-            }
+            const uint32_t wd[4] = {v.x, v.y, v.z, v.w};
+            const int n = min(16, c.w - (int)x);
+            for (int k = 0; k < n; ++k) dst[k] = (uint8_t)(wd[k >> 2] >> (8 * (k & 3)));
         }
     }
 }
@@ -103,37 +133,6 @@ dim3 io_grid(int n, uint64_t total_words)
     if (x > useful) x = useful;
     if (x < 1) x = 1;
     return dim3((unsigned)x, (unsigned)n);
-}
-
-// Repitching: destination word j of a copy (16 bytes at row j / wpr, column
-// 16 (j % wpr), wpr = ceil(w / 16)) gathers 16 source bytes from any
-// alignment: two aligned 16-byte loads funnel-shifted into place, byte loads
-// only where an aligned granule would reach outside the source's bytes
-// [src, src + (h - 1) src_pitch + w). The destination is always written whole
-// (bytes past w in a row's last word are don't-care padding).
-__device__ __forceinline__ uint4 span16(const uint8_t *p, const uint8_t *lo, const uint8_t *hi)
-{
-    const uintptr_t pa = (uintptr_t)p, ga = pa & ~(uintptr_t)15, l = (uintptr_t)lo, h = (uintptr_t)hi;
-    const int m = (int)(pa - ga);
-    if (m == 0 && pa + 16 <= h) return __ldg(reinterpret_cast<const uint4 *>(p));
-    if (m != 0 && ga >= l && ga + 32 <= h) {
-        const uint4 A = __ldg(reinterpret_cast<const uint4 *>(ga));
-        const uint4 B = __ldg(reinterpret_cast<const uint4 *>(ga + 16));
-        const int q = m >> 2, r = 8 * (m & 3);
-        // V[i] = word q + i of the 32 loaded bytes
-        const uint32_t v0 = q == 0 ? A.x : q == 1 ? A.y : q == 2 ? A.z : A.w;
-        const uint32_t v1 = q == 0 ? A.y : q == 1 ? A.z : q == 2 ? A.w : B.x;
-        const uint32_t v2 = q == 0 ? A.z : q == 1 ? A.w : q == 2 ? B.x : B.y;
-        const uint32_t v3 = q == 0 ? A.w : q == 1 ? B.x : q == 2 ? B.y : B.z;
-        const uint32_t v4 = q == 0 ? B.x : q == 1 ? B.y : q == 2 ? B.z : B.w;
-        return make_uint4(__funnelshift_r(v0, v1, r), __funnelshift_r(v1, v2, r), __funnelshift_r(v2, v3, r),
-                          __funnelshift_r(v3, v4, r));
-    }
-    uint32_t wd[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-    for (int k = 0; k < 16; ++k)
-        if (pa + k < h) wd[k >> 2] |= (uint32_t)__ldg(p + k) << (8 * (k & 3));
-    return make_uint4(wd[0], wd[1], wd[2], wd[3]);
 }
 
 __device__ __forceinline__ void repitch_word(const Repitch &c, uint64_t j)

@@ -124,17 +124,67 @@ __device__ __forceinline__ bool find_seeds(const HystScratch &hs, uint32_t t, in
     return (sd.top | sd.bot | sd.left | sd.right) != 0;
 }
 
+// The pending border words of t's neighbours that face t (the pixels an edge on
+// t's border would seed), as lane 0 read them at the start of a chase step.
+struct Facing {
+    uint32_t u, ul, ur, d, dl, dr, l, r;
+};
+
+// find_seeds for the tile a warp chases into, with every mask word read by lane
+// 0 alone: the same thread made this warp's earlier updates of those words (its
+// atomics in grow_tile), so it reads them back without a fence. Lane 0 also
+// reads the neighbours' facing pending words for grow_tile, in the same round
+// trip; the seeds are broadcast to every lane.
+__device__ __forceinline__ bool chase_seeds(const HystScratch &hs, uint32_t t, int nimg, TileSeeds &sd, int lane,
+                                            Facing &fp)
+{
+    sd.im = hs.imgs[find_image(hs.imgs, nimg, t)];
+    const HystImage &im = sd.im;
+    const uint32_t local = t - im.tile_base;
+    const int tx = (int)(local % (uint32_t)im.ntx), ty = (int)(local / (uint32_t)im.ntx);
+    sd.tx = tx;
+    sd.ty = ty;
+    uint32_t top = 0, bot = 0, left = 0, right = 0;
+    fp = Facing{0, 0, 0, 0, 0, 0, 0, 0};
+    if (lane == 0) {
+        const bool hasL = tx > 0, hasR = tx < im.ntx - 1, hasU = ty > 0, hasD = ty < im.nty - 1;
+        const uint32_t ntx = (uint32_t)im.ntx;
+        const TileMasks *M = hs.masks;
+        const TileMasks mu = masks_cg(&M[t]);
+        uint32_t eu = 0, eul = 0, eur = 0, ed = 0, edl = 0, edr = 0, el = 0, er = 0;
+        if (hasU) { eu = __ldcg(&M[t - ntx].edge_bottom); fp.u = __ldcg(&M[t - ntx].pend_bottom); }
+        if (hasU && hasL) { eul = __ldcg(&M[t - ntx - 1].edge_bottom); fp.ul = __ldcg(&M[t - ntx - 1].pend_bottom); }
+        if (hasU && hasR) { eur = __ldcg(&M[t - ntx + 1].edge_bottom); fp.ur = __ldcg(&M[t - ntx + 1].pend_bottom); }
+        if (hasD) { ed = __ldcg(&M[t + ntx].edge_top); fp.d = __ldcg(&M[t + ntx].pend_top); }
+        if (hasD && hasL) { edl = __ldcg(&M[t + ntx - 1].edge_top); fp.dl = __ldcg(&M[t + ntx - 1].pend_top); }
+        if (hasD && hasR) { edr = __ldcg(&M[t + ntx + 1].edge_top); fp.dr = __ldcg(&M[t + ntx + 1].pend_top); }
+        if (hasL) { el = __ldcg(&M[t - 1].edge_right); fp.l = __ldcg(&M[t - 1].pend_right); }
+        if (hasR) { er = __ldcg(&M[t + 1].edge_left); fp.r = __ldcg(&M[t + 1].pend_left); }
+        const uint32_t ring_top = eu | (eu << 1) | (eu >> 1) | (eul >> 31) | ((eur & 1u) << 31);
+        const uint32_t ring_bot = ed | (ed << 1) | (ed >> 1) | (edl >> 31) | ((edr & 1u) << 31);
+        top = ring_top & mu.pend_top;
+        bot = ring_bot & mu.pend_bottom;
+        left = (el | (el << 1) | (el >> 1)) & mu.pend_left;
+        right = (er | (er << 1) | (er >> 1)) & mu.pend_right;
+    }
+    sd.top = __shfl_sync(FULL, top, 0);
+    sd.bot = __shfl_sync(FULL, bot, 0);
+    sd.left = __shfl_sync(FULL, left, 0);
+    sd.right = __shfl_sync(FULL, right, 0);
+    return (sd.top | sd.bot | sd.left | sd.right) != 0;
+}
+
 // Tile t grows its seeds through its pending pixels (whole warp, lane = row).
 // Returns (in every lane) the mask of neighbours (NB_* bits) whose facing
-// border has pending pixels next to an edge this call added.
+// border has pending pixels next to an edge this call added, judged on the
+// facing words lane 0 read in chase_seeds (older words may hold pixels that
+// are no longer pending: that only costs a step that finds no seeds).
 __device__ __forceinline__ uint32_t grow_tile(const HystScratch &hs, uint32_t t, const TileSeeds &sd, int lane,
-                                              uint32_t p)
+                                              uint32_t p, const Facing &fp)
 {
     const HystImage &im = sd.im;
     const int tx = sd.tx, ty = sd.ty;
     const bool hasL = tx > 0, hasR = tx < im.ntx - 1, hasU = ty > 0, hasD = ty < im.nty - 1;
-    const uint32_t ntx = (uint32_t)im.ntx;
-    const TileMasks *M = hs.masks;
     const uint32_t s_top = sd.top, s_bot = sd.bot, s_left = sd.left, s_right = sd.right;
     uint32_t e0 = ((s_left >> lane) & 1u) | (((s_right >> lane) & 1u) << 31);
     if (lane == 0) e0 |= s_top;
@@ -171,33 +221,32 @@ __device__ __forceinline__ uint32_t grow_tile(const HystScratch &hs, uint32_t t,
         atomicAnd(&mt->pend_bottom, p_bot);
         atomicAnd(&mt->pend_left, p_left);
         atomicAnd(&mt->pend_right, p_right);
-        // Only a block-scope fence (this warp reads these masks again when it
-        // follows into a neighbour): a warp of another CTA working on a neighbour
-        // at the same time may miss these edges, but this warp checks that
-        // neighbour's pending border next and follows into it (a stale pending
-        // mask only has more bits), so no seed is lost; the end of the pass
-        // orders everything for the next one.
-        __threadfence_block();
-        // neighbours whose facing border has pending pixels next to a new edge
+        // No fence: this warp reads these masks again only through lane 0 (the
+        // thread that made these atomics) when it follows into a neighbour. A
+        // warp of another CTA working on a neighbour at the same time may miss
+        // these edges, but this warp checks that neighbour's pending border and
+        // follows into it (a stale pending word only has more bits), so no seed
+        // is lost; the end of the pass orders everything for the next one.
+        // Neighbours whose facing border has pending pixels next to a new edge:
         if (hasU && e_top) {
             uint32_t d = e_top | (e_top << 1) | (e_top >> 1);
-            if (__ldcg(&M[t - ntx].pend_bottom) & d) aff |= 1u << NB_U;
-            if (hasL && (e_top & 1u) && (__ldcg(&M[t - ntx - 1].pend_bottom) >> 31)) aff |= 1u << NB_UL;
-            if (hasR && (e_top >> 31) && (__ldcg(&M[t - ntx + 1].pend_bottom) & 1u)) aff |= 1u << NB_UR;
+            if (fp.u & d) aff |= 1u << NB_U;
+            if (hasL && (e_top & 1u) && (fp.ul >> 31)) aff |= 1u << NB_UL;
+            if (hasR && (e_top >> 31) && (fp.ur & 1u)) aff |= 1u << NB_UR;
         }
         if (hasD && e_bot) {
             uint32_t d = e_bot | (e_bot << 1) | (e_bot >> 1);
-            if (__ldcg(&M[t + ntx].pend_top) & d) aff |= 1u << NB_D;
-            if (hasL && (e_bot & 1u) && (__ldcg(&M[t + ntx - 1].pend_top) >> 31)) aff |= 1u << NB_DL;
-            if (hasR && (e_bot >> 31) && (__ldcg(&M[t + ntx + 1].pend_top) & 1u)) aff |= 1u << NB_DR;
+            if (fp.d & d) aff |= 1u << NB_D;
+            if (hasL && (e_bot & 1u) && (fp.dl >> 31)) aff |= 1u << NB_DL;
+            if (hasR && (e_bot >> 31) && (fp.dr & 1u)) aff |= 1u << NB_DR;
         }
         if (hasL && e_left) {
             uint32_t d = e_left | (e_left << 1) | (e_left >> 1);
-            if (__ldcg(&M[t - 1].pend_right) & d) aff |= 1u << NB_L;
+            if (fp.l & d) aff |= 1u << NB_L;
         }
         if (hasR && e_right) {
             uint32_t d = e_right | (e_right << 1) | (e_right >> 1);
-            if (__ldcg(&M[t + 1].pend_left) & d) aff |= 1u << NB_R;
+            if (fp.r & d) aff |= 1u << NB_R;
         }
     }
     return __shfl_sync(FULL, aff, 0);
@@ -247,10 +296,11 @@ hyst_global_kernel(HystScratch hs, int in_graph, cudaGraphConditionalHandle cond
             int sp = 0, budget = CHASE_BUDGET;
             for (;;) {
                 TileSeeds sd;
+                Facing fp;
                 uint32_t aff = 0, ntx = 0;
                 const uint32_t p_row = __ldcg(&hs.pend_bits[(size_t)t * HT + lane]);   // issued with the masks
-                if (find_seeds(hs, t, nimg, sd)) {
-                    aff = grow_tile(hs, t, sd, lane, p_row);
+                if (chase_seeds(hs, t, nimg, sd, lane, fp)) {
+                    aff = grow_tile(hs, t, sd, lane, p_row, fp);
                     ntx = (uint32_t)sd.im.ntx;
                 }
                 ++my_visits;

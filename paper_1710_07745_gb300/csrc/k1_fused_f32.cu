@@ -23,11 +23,12 @@
 // columns summed top to bottom; s = (gx*gx) + (gy*gy); M = sqrt_rn(s).
 //
 // A pass-1 CTA of 256 threads covers a block of 64 rows x 128 columns (2 x 4
-// tiles) and stages it in shared memory: input (as float, with a halo of R + 2
-// rows and R + 2 columns rounded up to 16, R = ksize / 2; 16-byte vector loads
-// where the block lies inside the image), the horizontal pass and the smoothed
-// image S. Buffers alias once they are dead, so a 7-tap kernel needs 86 KB and
-// two CTAs fit on an SM. Work is done on pixel pairs that share their
+// tiles) and stages it in shared memory: the horizontal pass and the smoothed
+// image S, and, for blocks at the image's left or right edge, the input (as
+// bytes, with a halo of R + 2 rows and R + 2 columns rounded up to 16, R =
+// ksize / 2; blocks inside the image run the horizontal pass from registers).
+// Buffers alias once they are dead, so a 7-tap kernel needs 73 KB and three
+// CTAs fit on an SM. Work is done on pixel pairs that share their
 // shared-memory loads (the horizontal pass pairs two rows, the vertical pass
 // and Sobel pair two columns); the arithmetic itself is scalar and correctly
 // rounded per operation (__fmul_rn / __fadd_rn, and __fmaf_rn only where the
@@ -50,7 +51,7 @@ struct Geometry {
     int SX, SY;                // smoothed image: columns x0-2 .. x0+FB_W+1, rows y0-2 .. y0+FB_H+1
     int MX, MY;                // squared strength with its ring, rows y0-1 .. y0+FB_H; column j is
                                // x0-2+j like S (the ring uses j = 1 .. FB_W+2), MX the row stride
-    int region0, region1;      // floats: input then S; horizontal pass then s
+    int region0, region1;      // floats: input bytes then S; horizontal pass
 };
 
 __host__ __device__ inline Geometry geometry(int ksize)
@@ -65,7 +66,8 @@ __host__ __device__ inline Geometry geometry(int ksize)
     g.SY = FB_H + 4;
     g.MX = FB_W + 4;
     g.MY = FB_H + 2;
-    const int a = g.IY * g.IX, b = g.SY * g.SX, c = g.IY * g.SX, d = g.MY * g.MX;
+    // the staged input is held as bytes (IY x IX of them) in the floats of region 0
+    const int a = (g.IY * g.IX + 3) / 4, b = g.SY * g.SX, c = g.IY * g.SX, d = g.MY * g.MX;
     g.region0 = a > b ? a : b;
     g.region1 = c > d ? c : d;
     return g;
@@ -142,12 +144,12 @@ __device__ __forceinline__ void hrow_regs(const uint8_t *row, int x0, int c0, co
 
 // Step 1's horizontal pass through a staged copy of the input (blocks at the
 // image's left or right edge, or inputs without 16-byte alignment): the input
-// block is staged as floats with clamped columns, then H is computed at the
+// block is staged as bytes with clamped columns, then H is computed at the
 // clamped columns, rows paired.
 template <int KS>
 __device__ __forceinline__ void staged_hpass(const uint8_t *__restrict__ in, int in_pitch, int w, int h,
                                              const FloatParams &fp, const Geometry &g, int x0, int y0,
-                                             float *I_s, float *H_s, bool aligned)
+                                             uint8_t *I_s, float *H_s, bool aligned)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ox = x0 - g.padx, oy = y0 - g.pady;
@@ -157,25 +159,12 @@ __device__ __forceinline__ void staged_hpass(const uint8_t *__restrict__ in, int
         for (int i = tid; i < g.IY * per_row; i += FB_THREADS) {
             const int r = i / per_row, j = i - r * per_row;
             const uint8_t *src = in + (int64_t)clampi(oy + r, 0, h - 1) * in_pitch + ox + 16 * j;
-            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(src));
-            const uint32_t wd[4] = {v.x, v.y, v.z, v.w};
-            float4 *dst = reinterpret_cast<float4 *>(I_s + r * g.IX + 16 * j);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                // float 2^23 + byte, minus 2^23: the byte's value, exactly
-                const float2 lo = __fadd2_rn(f2(__uint_as_float(__byte_perm(wd[q], 0x4B000000u, 0x7640u)),
-                                                __uint_as_float(__byte_perm(wd[q], 0x4B000000u, 0x7641u))),
-                                             f2(-8388608.f, -8388608.f));
-                const float2 hi = __fadd2_rn(f2(__uint_as_float(__byte_perm(wd[q], 0x4B000000u, 0x7642u)),
-                                                __uint_as_float(__byte_perm(wd[q], 0x4B000000u, 0x7643u))),
-                                             f2(-8388608.f, -8388608.f));
-                dst[q] = make_float4(lo.x, lo.y, hi.x, hi.y);
-            }
+            *reinterpret_cast<uint4 *>(I_s + r * g.IX + 16 * j) = __ldg(reinterpret_cast<const uint4 *>(src));
         }
     } else {
         for (int r = warp; r < g.IY; r += FB_WARPS) {
             const uint8_t *row = in + (int64_t)clampi(oy + r, 0, h - 1) * in_pitch;
-            for (int c = lane; c < g.IX; c += 32) I_s[r * g.IX + c] = (float)__ldg(row + clampi(ox + c, 0, w - 1));
+            for (int c = lane; c < g.IX; c += 32) I_s[r * g.IX + c] = __ldg(row + clampi(ox + c, 0, w - 1));
         }
     }
     __syncthreads();
@@ -184,9 +173,10 @@ __device__ __forceinline__ void staged_hpass(const uint8_t *__restrict__ in, int
         const int pairs = g.IY / 2;
         auto hpass = [&](int p, int c) {
             const int X = clampi(x0 - 2 + c, 0, w - 1);
-            const float *a = I_s + (2 * p) * g.IX + (X - g.R - ox);
-            const float *b = a + g.IX;
-            const float2 acc = tap_sum2<KS>(fp, [&](int k) { return f2(a[k], b[k]); });
+            const uint8_t *a = I_s + (2 * p) * g.IX + (X - g.R - ox);
+            const uint8_t *b = a + g.IX;
+            // a byte's value as a float is exact
+            const float2 acc = tap_sum2<KS>(fp, [&](int k) { return f2(__uint2float_rn(a[k]), __uint2float_rn(b[k])); });
             H_s[(2 * p) * g.SX + c] = acc.x;
             H_s[(2 * p + 1) * g.SX + c] = acc.y;
         };
@@ -207,7 +197,8 @@ __device__ __forceinline__ void smooth_block(const uint8_t *__restrict__ in, int
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int oy = y0 - g.pady;
-    float *I_s = r0, *H_s = r1;
+    uint8_t *I_s = reinterpret_cast<uint8_t *>(r0);
+    float *H_s = r1;
     // horizontal pass; the border is replicated by clamping (rows always,
     // columns only in blocks that reach past the image's left or right edge)
     const bool aligned = ((((uintptr_t)in) | (uintptr_t)in_pitch) & 15) == 0;
@@ -328,9 +319,10 @@ __host__ __device__ inline MapLayout map_layout(int w, int h)
 // ---------------------------------------------------------------- pass 1
 // Steps 1-2 and the sector of Step 3 for one block: squared strengths (0
 // outside the image) into smap, sectors into sect, block maximum atomicMax'ed
-// into *d_smax.
+// into *d_smax. With the input staged as bytes a 7- or 9-tap kernel's buffers
+// take at most 75 KB, so three CTAs fit on an SM.
 template <int KS>
-__global__ void __launch_bounds__(FB_THREADS, 2)
+__global__ void __launch_bounds__(FB_THREADS, 3)
 k1f_strength_kernel(const uint8_t *__restrict__ in, int in_pitch, int w, int h, FloatParams fp, float *d_smax,
                     float *__restrict__ smap, uint8_t *__restrict__ sect)
 {

@@ -226,6 +226,8 @@ uint32_t auto_max_passes(uint32_t ntiles)
 // Queue the global passes of the current run (after hyst_reset + local fill).
 canny_status run_global(canny_ctx *c, cudaStream_t s)
 {
+    // one cooperative launch runs every pass; else a graph while-loop; else the host loop
+    if (c->use_graph && hyst_coop_supported()) return from_cuda(launch_hyst_global_coop(c->hs, s));
     if (c->use_graph && c->exec) return from_cuda(cudaGraphLaunch(c->exec, s));
     // host-driven loop: one pass, read the control block, repeat
     for (;;) {

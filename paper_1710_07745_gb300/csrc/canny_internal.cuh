@@ -44,8 +44,9 @@ struct HystState {
     uint32_t pending_tiles;   // tiles with unresolved weak pixels after the local fill
     uint32_t ntiles;          // tiles in this run
     uint32_t nimg;            // images in this run
-    uint32_t keep_going;      // host-loop mode: 1 if another pass is needed
-    uint32_t pad[5];
+    uint32_t keep_going;      // 1 if another pass is needed
+    uint32_t bar_count, bar_gen;   // grid barrier of the cooperative multi-pass kernel
+    uint32_t pad[3];
 };
 
 struct HystScratch {
@@ -184,6 +185,10 @@ cudaError_t launch_hyst_local_batch(const HystScratch &hs, uint32_t ntiles, uint
 // (0 when not in a graph).
 cudaError_t launch_hyst_global_pass(const HystScratch &hs, int grid, bool in_graph,
                                     unsigned long long cond_handle, cudaStream_t s);
+// Every global pass in one cooperative launch (passes separated by a bounded
+// grid barrier): cudaErrorNotSupported when the device cannot hold the grid.
+bool hyst_coop_supported();
+cudaError_t launch_hyst_global_coop(const HystScratch &hs, cudaStream_t s);
 // Clear the worklist stamps and the control block before a run; for a single
 // image, also store its descriptor as image 0 (the global passes read it).
 cudaError_t hyst_reset(const HystScratch &hs, uint32_t ntiles, uint32_t nimg,

@@ -259,11 +259,12 @@ __device__ __forceinline__ uint32_t grow_tile(const HystScratch &hs, uint32_t t,
 // the stack cannot take is queued for the next pass. A tile may be visited by
 // two warps at a time: both only add edges, and each re-reads the masks, so the
 // result is the same.
-__global__ void __launch_bounds__(THREADS)
-hyst_global_kernel(HystScratch hs, int in_graph, cudaGraphConditionalHandle cond)
+// One pass (all CTAs of the grid). The last CTA to finish swaps the worklists,
+// counts the pass and sets keep_going (and, in a graph, the while-node's
+// condition).
+__device__ __forceinline__ void global_pass(const HystScratch &hs, int in_graph, cudaGraphConditionalHandle cond,
+                                            uint32_t (&stack)[WARPS][CHASE_STACK], uint32_t &visits)
 {
-    __shared__ uint32_t stack[WARPS][CHASE_STACK];
-    __shared__ uint32_t visits;
     HystState *st = hs.state;
     const uint32_t k = *(volatile uint32_t *)&st->pass;
     const uint32_t cur = k & 1u, nxt = cur ^ 1u;
@@ -284,7 +285,7 @@ hyst_global_kernel(HystScratch hs, int in_graph, cudaGraphConditionalHandle cond
         bool has = false;
         if (i < count) {
             TileSeeds sd;
-            mine = list[i];
+            mine = __ldcg(&list[i]);      // (a cooperative launch reuses L1 across passes)
             has = find_seeds(hs, mine, nimg, sd);
         }
         my_visits += (lane == 0) ? min(32u, count - base) : 0u;   // entries examined
@@ -344,6 +345,63 @@ hyst_global_kernel(HystScratch hs, int in_graph, cudaGraphConditionalHandle cond
             __threadfence();
             if (in_graph) cudaGraphSetConditional(cond, more ? 1u : 0u);
         }
+    }
+}
+
+__global__ void __launch_bounds__(THREADS)
+hyst_global_kernel(HystScratch hs, int in_graph, cudaGraphConditionalHandle cond)
+{
+    __shared__ uint32_t stack[WARPS][CHASE_STACK];
+    __shared__ uint32_t visits;
+    global_pass(hs, in_graph, cond, stack, visits);
+}
+
+// Grid-wide barrier of a cooperative launch (every CTA is resident): the last
+// CTA to arrive advances the generation. The wait is bounded; if it runs out,
+// error bit 1 is set and false returned in every thread of the CTA.
+constexpr uint32_t BARRIER_SPIN_LIMIT = 1u << 21;   // about a second
+
+__device__ __forceinline__ bool grid_barrier(HystState *st)
+{
+    __shared__ uint32_t ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t ok = 1;
+        const uint32_t gen = atomicAdd(&st->bar_gen, 0u);      // read before arriving
+        __threadfence();
+        if (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1) {
+            atomicExch(&st->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&st->bar_gen, 1u);
+        } else {
+            uint32_t n = 0;
+            while (atomicAdd(&st->bar_gen, 0u) == gen) {
+                if (++n > BARRIER_SPIN_LIMIT) {
+                    atomicOr(&st->error, 2u);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// All passes in one cooperative launch: pass, barrier, stop when the last CTA
+// of the pass found nothing more to do (or the pass cap was reached).
+__global__ void __launch_bounds__(THREADS)
+hyst_global_coop_kernel(HystScratch hs)
+{
+    __shared__ uint32_t stack[WARPS][CHASE_STACK];
+    __shared__ uint32_t visits;
+    for (;;) {
+        global_pass(hs, 0, cudaGraphConditionalHandle{}, stack, visits);
+        if (!grid_barrier(hs.state)) break;
+        if (!*(volatile uint32_t *)&hs.state->keep_going) break;
     }
 }
 
@@ -424,6 +482,31 @@ cudaError_t launch_hyst_global_pass(const HystScratch &hs, int grid, bool in_gra
     hyst_global_kernel<<<grid, THREADS, 0, s>>>(hs, in_graph ? 1 : 0,
                                                 (cudaGraphConditionalHandle)cond_handle);
     return cudaGetLastError();
+}
+
+bool hyst_coop_supported()
+{
+    static int ok = -1;
+    if (ok < 0) {
+        int dev = 0, coop = 0, per_sm = 0, sms = 0;
+        cudaGetDevice(&dev);
+        ok = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
+             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hyst_global_coop_kernel, THREADS, 0) ==
+                 cudaSuccess &&
+             (int64_t)per_sm * sms >= hyst_pass_grid();
+        cudaGetLastError();
+    }
+    return ok == 1;
+}
+
+cudaError_t launch_hyst_global_coop(const HystScratch &hs, cudaStream_t s)
+{
+    if (!hyst_coop_supported()) return cudaErrorNotSupported;
+    HystScratch hs_copy = hs;
+    void *args[] = {&hs_copy};
+    return cudaLaunchCooperativeKernel((void *)hyst_global_coop_kernel, dim3(hyst_pass_grid()), dim3(THREADS), args,
+                                       0, s);
 }
 
 // Append { while (cond) hyst_global_kernel } to graph g after the given nodes.

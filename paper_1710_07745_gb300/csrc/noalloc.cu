@@ -102,8 +102,16 @@ extern "C" canny_status canny_run_noalloc(const uint8_t *d_in, int in_pitch, uin
     if (e != cudaSuccess) return status_of(e);
     e = launch_k1_edges_u8(d_in, in_pitch, w, h, t, hs, im, s);
     if (e != cudaSuccess) return status_of(e);
-    // global passes driven from the host: one pass, read the control block, repeat
+    // global passes: one cooperative launch runs them all where the device allows,
+    // else they are driven from the host (one pass, read the control block, repeat)
     HystState st = {};
+    if (hyst_coop_supported()) {
+        e = launch_hyst_global_coop(hs, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&st, hs.state, sizeof(st), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return status_of(e);
+        return (st.error & 2u) ? CANNY_ECUDA : (st.error & 1u) ? CANNY_ENOCONVERGE : CANNY_OK;
+    }
     for (;;) {
         e = launch_hyst_global_pass(hs, hyst_pass_grid(), false, 0, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&st, hs.state, sizeof(st), cudaMemcpyDeviceToHost, s);

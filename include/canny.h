@@ -297,6 +297,7 @@ typedef struct {
     int64_t batches;
     double mean_batch_images;
     int64_t peak_bytes;           /* most arena bytes in use at once */
+    int64_t deferrals;            /* admissions put off because the arena had no room */
 } canny_serve_report;
 
 /*
@@ -308,11 +309,24 @@ typedef struct {
  * GPU. Each result equals the request's canny_run_pitched result. Writes the
  * per-request latencies (ms) to latency_ms if not NULL. Synchronous: returns
  * when every request has completed. The budget is allocated once per call.
+ * CANNY_EINVAL if a request's input and output buffers (16-byte pitched rows)
+ * alone exceed the budget; CANNY_ENOMEM if the budget or the streams' buffers
+ * cannot be allocated.
  */
 canny_status canny_serve(const canny_serve_config *cfg, int n, const canny_request *reqs, double *latency_ms,
                          canny_serve_report *out);
 
 /* Static, human-readable message for a status. */
+/*
+ * Test hook for failure detection (no GPU fault involved): the next
+ * device_allocations device or pinned-host allocations made by the library
+ * (contexts, scratch, staging, maps, serving budget) fail as if out of memory,
+ * and the next arena_allocations request admissions of canny_serve find no
+ * room (the request waits for the next attempt). Process-wide; counts >= 0
+ * replace the pending ones. CANNY_EINVAL for negative counts.
+ */
+canny_status canny_inject_alloc_failures(int device_allocations, int arena_allocations);
+
 const char *canny_strerror(canny_status s);
 
 #ifdef __cplusplus

@@ -75,7 +75,8 @@ class canny_serve_config(ctypes.Structure):
 class canny_serve_report(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_int64), ("wall_s", ctypes.c_double), ("delivered_mpx_s", ctypes.c_double),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
-                ("batches", ctypes.c_int64), ("mean_batch_images", ctypes.c_double), ("peak_bytes", ctypes.c_int64)]
+                ("batches", ctypes.c_int64), ("mean_batch_images", ctypes.c_double), ("peak_bytes", ctypes.c_int64),
+                ("deferrals", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -114,6 +115,7 @@ SIGNATURES = {
     "canny_run_noalloc": ([_P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                            ctypes.c_int, _P], ctypes.c_int),
     "canny_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    "canny_inject_alloc_failures": ([ctypes.c_int, ctypes.c_int], ctypes.c_int),
 }
 
 
@@ -137,6 +139,11 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                 fn.restype = res
             _lib = L
         return _lib
+
+
+def canny_inject_alloc_failures(device_allocations: int, arena_allocations: int = 0) -> None:
+    """Test hook: make the library's next allocations (and serving admissions) fail."""
+    _check(load().canny_inject_alloc_failures(device_allocations, arena_allocations), "canny_inject_alloc_failures")
 
 
 def strerror(status: int) -> str:

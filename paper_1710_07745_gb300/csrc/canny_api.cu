@@ -6,6 +6,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 #include <string>
 #include <unordered_map>
@@ -121,6 +122,17 @@ uint32_t tiles_of(int w, int h)
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Allocation failures injected by canny_inject_alloc_failures (test hook).
+std::atomic<int> g_fail_device{0}, g_fail_arena{0};
+
+bool take_failure(std::atomic<int> &n)
+{
+    int v = n.load();
+    while (v > 0)
+        if (n.compare_exchange_weak(v, v - 1)) return true;
+    return false;
+}
+
 // Frame graphs hold the scratch pointers and the band height: dropped with the batch graphs.
 void drop_frame_graphs(canny_ctx *c)
 {
@@ -188,7 +200,7 @@ canny_status ensure_hyst(canny_ctx *c, uint32_t max_tiles, uint32_t max_imgs)
     size_t off_state = align_up(off_lists + sizeof(uint32_t) * 2 * (size_t)max_tiles, 256);
     size_t total = align_up(off_state + sizeof(HystState), 256);
     void *mem = nullptr;
-    cudaError_t e = cudaMalloc(&mem, total);
+    cudaError_t e = dev_alloc(&mem, total);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return CANNY_ENOMEM;
@@ -267,7 +279,7 @@ canny_status run_stencil(canny_ctx *c, const canny_image *im, cudaStream_t s)
                                                im->w, im->h, c->it, &c->hs.state->error, s, c->band));
     if (!c->mag) {
         // the stored strength image is only needed for a class map of the float path
-        if (cudaMalloc((void **)&c->mag, sizeof(float) * (size_t)c->max_w * c->max_h) != cudaSuccess) {
+        if (dev_alloc((void **)&c->mag, sizeof(float) * (size_t)c->max_w * c->max_h) != cudaSuccess) {
             cudaGetLastError();
             return CANNY_ENOMEM;
         }
@@ -304,7 +316,7 @@ bool ensure_stage(uint8_t **buf, size_t *cap, size_t need)
     if (*buf) cudaFree(*buf);
     *buf = nullptr;
     *cap = 0;
-    if (cudaMalloc((void **)buf, need) != cudaSuccess) {
+    if (dev_alloc((void **)buf, need) != cudaSuccess) {
         cudaGetLastError();
         *buf = nullptr;
         return false;
@@ -451,9 +463,9 @@ canny_status ensure_blob(canny_ctx *c, uint32_t cap)
     }
     c->blob_cap = 0;
     const BlobLayout L = blob_layout(cap);
-    if (cudaMalloc((void **)&c->d_blob, L.dev_bytes) != cudaSuccess) { cudaGetLastError(); return CANNY_ENOMEM; }
+    if (dev_alloc((void **)&c->d_blob, L.dev_bytes) != cudaSuccess) { cudaGetLastError(); return CANNY_ENOMEM; }
     for (auto &sl : c->slots) {
-        if (cudaHostAlloc((void **)&sl.h_blob, L.host_bytes, cudaHostAllocDefault) != cudaSuccess) {
+        if (pinned_alloc((void **)&sl.h_blob, L.host_bytes) != cudaSuccess) {
             cudaGetLastError();
             return CANNY_ENOMEM;
         }
@@ -618,7 +630,39 @@ canny_status run_batch_int(canny_ctx *c, int n, const canny_image *imgs, uint32_
 
 }  // namespace
 
+namespace canny {
+
+cudaError_t dev_alloc(void **p, size_t bytes)
+{
+    if (take_failure(g_fail_device)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t pinned_alloc(void **p, size_t bytes)
+{
+    if (take_failure(g_fail_device)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaHostAlloc(p, bytes, cudaHostAllocDefault);
+}
+
+bool arena_failure_injected() { return take_failure(g_fail_arena); }
+
+}  // namespace canny
+
 extern "C" {
+
+canny_status canny_inject_alloc_failures(int device_allocations, int arena_allocations)
+{
+    if (device_allocations < 0 || arena_allocations < 0) return CANNY_EINVAL;
+    g_fail_device.store(device_allocations);
+    g_fail_arena.store(arena_allocations);
+    return CANNY_OK;
+}
 
 canny_status canny_params_default(canny_params *p)
 {
@@ -664,14 +708,14 @@ canny_status canny_create(int max_w, int max_h, const canny_params *p, canny_ctx
     }
     if (getenv("CANNY_NO_GRAPH")) c->use_graph = 0;
 
-    cudaError_t e = cudaHostAlloc((void **)&c->h_state, sizeof(HystState), cudaHostAllocDefault);
+    cudaError_t e = pinned_alloc((void **)&c->h_state, sizeof(HystState));
     if (e != cudaSuccess) { cudaGetLastError(); delete c; return CANNY_ENOMEM; }
     e = cudaEventCreateWithFlags(&c->staging_free, cudaEventDisableTiming);
     if (e != cudaSuccess) { cudaGetLastError(); canny_destroy(c); return from_cuda(e); }
     st = ensure_hyst(c, tiles_of(max_w, max_h), 1);
     if (st != CANNY_OK) { canny_destroy(c); return st; }
     if (p->path == CANNY_PATH_F32) {
-        e = cudaMalloc((void **)&c->d_max, sizeof(float));
+        e = dev_alloc((void **)&c->d_max, sizeof(float));
         if (e != cudaSuccess) { cudaGetLastError(); canny_destroy(c); return CANNY_ENOMEM; }
     }
     *out = c;
@@ -755,7 +799,7 @@ canny_status canny_run_batch(canny_ctx *c, int n, const canny_image *imgs, void 
         if (c->h_imgs) cudaFreeHost(c->h_imgs);
         c->h_imgs = nullptr;
         c->h_imgs_cap = 0;
-        if (cudaHostAlloc((void **)&c->h_imgs, sizeof(HystImage) * nimg, cudaHostAllocDefault) != cudaSuccess) {
+        if (pinned_alloc((void **)&c->h_imgs, sizeof(HystImage) * nimg) != cudaSuccess) {
             cudaGetLastError();
             return CANNY_ENOMEM;
         }
@@ -796,8 +840,8 @@ canny_status canny_run_host(canny_ctx *c, const uint8_t *h_in, int in_pitch, uin
     cudaStream_t s = (cudaStream_t)stream;
     size_t cap = (size_t)c->max_w * c->max_h;
     if (!c->d_host_in) {
-        if (cudaMalloc((void **)&c->d_host_in, cap) != cudaSuccess ||
-            cudaMalloc((void **)&c->d_host_out, cap) != cudaSuccess) {
+        if (dev_alloc((void **)&c->d_host_in, cap) != cudaSuccess ||
+            dev_alloc((void **)&c->d_host_out, cap) != cudaSuccess) {
             cudaGetLastError();
             return CANNY_ENOMEM;
         }
@@ -1014,7 +1058,7 @@ canny_status ensure_frame_streams(canny_ctx *c)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f.comp, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f.down, cudaEventDisableTiming);
     }
-    if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_frame_err, sizeof(uint32_t));
+    if (e == cudaSuccess) e = dev_alloc((void **)&c->d_frame_err, sizeof(uint32_t));
     if (e != cudaSuccess) {
         cudaGetLastError();
         return from_cuda(e);
@@ -1072,7 +1116,7 @@ canny_status ensure_frames(canny_ctx *c, int w, int h)
     if ((size_t)c->frame_pitch * (size_t)c->frame_h < need || !c->fslots[0].d_in) {
         free_frames(c);
         for (auto &f : c->fslots) {
-            if (cudaMalloc((void **)&f.d_in, need) != cudaSuccess || cudaMalloc((void **)&f.d_out, need) != cudaSuccess) {
+            if (dev_alloc((void **)&f.d_in, need) != cudaSuccess || dev_alloc((void **)&f.d_out, need) != cudaSuccess) {
                 cudaGetLastError();
                 free_frames(c);
                 return CANNY_ENOMEM;

@@ -148,6 +148,15 @@ uint32_t repitch_tasks(int w, int h);
 cudaError_t add_repitch_list_node(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, const Repitch *list,
                                   const BatchHeader *hdr, cudaGraphNode_t *out);
 
+// ---------------------------------------------------------------- allocation (canny_api.cu)
+// Every device and pinned-host allocation of the library goes through these, so
+// that canny_inject_alloc_failures can make the next ones fail (host side only).
+cudaError_t dev_alloc(void **p, size_t bytes);
+cudaError_t pinned_alloc(void **p, size_t bytes);
+// True (and one injected failure used up) if the serving arena's next request
+// allocation is to fail.
+bool arena_failure_injected();
+
 // ---------------------------------------------------------------- TMA (tma.cu)
 bool tma_usable(const void *base, int pitch);
 bool encode_u8_map(void *tmap_out, const void *base, int w, int h, int pitch, int box_w, int box_h);

@@ -32,7 +32,7 @@ public:
     bool init(size_t bytes)
     {
         bytes_ = bytes / 256 * 256;
-        if (cudaMalloc((void **)&base_, bytes_) != cudaSuccess) {
+        if (dev_alloc((void **)&base_, bytes_) != cudaSuccess) {
             cudaGetLastError();
             base_ = nullptr;
             return false;
@@ -46,6 +46,7 @@ public:
     }
     uint8_t *alloc(size_t n)
     {
+        if (arena_failure_injected()) return nullptr;
         n = (n + 255) / 256 * 256;
         for (auto it = free_.begin(); it != free_.end(); ++it) {
             if (it->second >= n) {
@@ -160,6 +161,9 @@ extern "C" canny_status canny_serve(const canny_serve_config *cfg, int n, const 
         const canny_request &r = reqs[i];
         if (r.w <= 0 || r.h <= 0 || !r.h_in || r.h_pitch < r.w || (r.h_out && r.out_pitch < r.w)) return CANNY_EINVAL;
         if (i > 0 && r.arrival_s < reqs[i - 1].arrival_s) return CANNY_EINVAL;   // arrival order
+        // input + output buffers (16-byte pitched, 256-byte granules) must fit the budget
+        const double need = 2.0 * (double)(((size_t)(r.w + 15) / 16 * 16 * (size_t)r.h + 255) / 256 * 256);
+        if (need > cfg->memory_budget_bytes) return CANNY_EINVAL;
         max_px = std::max<int64_t>(max_px, (int64_t)r.w * r.h);
         max_w = std::max(max_w, r.w);
         max_h = std::max(max_h, r.h);
@@ -190,8 +194,8 @@ extern "C" canny_status canny_serve(const canny_serve_config *cfg, int n, const 
                          : canny_create((int)std::min<int64_t>(cap, 1 << 30), 1, &p, &L.ctx);
         if (st != CANNY_OK) break;
         const size_t cbytes = sizeof(HostCopy) * 2 * (size_t)cfg->max_batch_images;
-        if (cudaHostAlloc((void **)&L.h_copies, cbytes, cudaHostAllocDefault) != cudaSuccess ||
-            cudaMalloc((void **)&L.d_copies, cbytes) != cudaSuccess) {
+        if (pinned_alloc((void **)&L.h_copies, cbytes) != cudaSuccess ||
+            dev_alloc((void **)&L.d_copies, cbytes) != cudaSuccess) {
             cudaGetLastError();
             st = CANNY_ENOMEM;
             break;
@@ -207,7 +211,7 @@ extern "C" canny_status canny_serve(const canny_serve_config *cfg, int n, const 
     std::deque<int> waiting;                 // arrived, not yet admitted
     std::vector<Admitted> admitted;          // admitted, not yet running
     int next = 0, done = 0;
-    int64_t batches = 0, batched_images = 0;
+    int64_t batches = 0, batched_images = 0, deferrals = 0;
     const auto t0 = Clock::now();
     auto now_s = [&]() { return std::chrono::duration<double>(Clock::now() - t0).count(); };
     double last_done = 0.0;
@@ -238,9 +242,9 @@ extern "C" canny_status canny_serve(const canny_serve_config *cfg, int n, const 
             const int pitch = (r.w + 15) / 16 * 16;
             const size_t bytes = (size_t)pitch * (size_t)r.h;
             uint8_t *in = arena.alloc(bytes);
-            if (!in) break;
+            if (!in) { ++deferrals; break; }
             uint8_t *o = arena.alloc(bytes);
-            if (!o) { arena.release(in, bytes); break; }
+            if (!o) { arena.release(in, bytes); ++deferrals; break; }
             admitted.push_back({waiting.front(), in, o, pitch, bytes});
             waiting.pop_front();
         }
@@ -313,6 +317,7 @@ extern "C" canny_status canny_serve(const canny_serve_config *cfg, int n, const 
     out->batches = batches;
     out->mean_batch_images = batches ? (double)batched_images / (double)batches : 0.0;
     out->peak_bytes = (int64_t)arena.peak();
+    out->deferrals = deferrals;
     if (latency_ms) std::copy(lat.begin(), lat.end(), latency_ms);
     return CANNY_OK;
 }

@@ -83,3 +83,10 @@ def test_create_rejects_bad_sizes_and_nulls(lib):
     assert lib.canny_run(None, None, None, None) == canny.CANNY_EINVAL
     assert lib.canny_get_stats(None, None) == canny.CANNY_EINVAL
     lib.canny_destroy(None)
+
+
+def test_inject_alloc_failures_rejects_negative_counts(lib):
+    from paper_1710_07745_gb300 import canny
+    assert lib.canny_inject_alloc_failures(-1, 0) == canny.CANNY_EINVAL
+    assert lib.canny_inject_alloc_failures(0, -2) == canny.CANNY_EINVAL
+    assert lib.canny_inject_alloc_failures(0, 0) == canny.CANNY_OK

@@ -318,14 +318,28 @@ canny_status canny_serve(const canny_serve_config *cfg, int n, const canny_reque
 
 /* Static, human-readable message for a status. */
 /*
- * Test hook for failure detection (no GPU fault involved): the next
- * device_allocations device or pinned-host allocations made by the library
- * (contexts, scratch, staging, maps, serving budget) fail as if out of memory,
- * and the next arena_allocations request admissions of canny_serve find no
- * room (the request waits for the next attempt). Process-wide; counts >= 0
- * replace the pending ones. CANNY_EINVAL for negative counts.
+ * Test hooks for failure detection, with no GPU fault involved. Counts of
+ * events that go wrong from now on (process-wide; each call replaces the
+ * pending counts; CANNY_EINVAL if one is negative):
+ *   device_allocations  the next device or pinned-host allocations made by the
+ *                       library (contexts, scratch, staging, maps, serving
+ *                       budget) fail as if out of memory;
+ *   arena_admissions    the next request admissions of canny_serve find no
+ *                       room in its budget (the request waits for the next
+ *                       attempt);
+ *   stalled_barriers    the next single-image runs start their global
+ *                       hysteresis passes with a grid barrier that can never
+ *                       complete: its bounded wait runs out (about a second)
+ *                       and the run reports CANNY_ECUDA through
+ *                       canny_get_stats; the context stays usable.
  */
-canny_status canny_inject_alloc_failures(int device_allocations, int arena_allocations);
+typedef struct {
+    int device_allocations;
+    int arena_admissions;
+    int stalled_barriers;
+} canny_fault_injection;
+
+canny_status canny_inject_faults(const canny_fault_injection *f);
 
 const char *canny_strerror(canny_status s);
 

@@ -72,6 +72,11 @@ class canny_serve_config(ctypes.Structure):
                 ("band", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
 
 
+class canny_fault_injection(ctypes.Structure):
+    _fields_ = [("device_allocations", ctypes.c_int), ("arena_admissions", ctypes.c_int),
+                ("stalled_barriers", ctypes.c_int)]
+
+
 class canny_serve_report(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_int64), ("wall_s", ctypes.c_double), ("delivered_mpx_s", ctypes.c_double),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
@@ -115,7 +120,7 @@ SIGNATURES = {
     "canny_run_noalloc": ([_P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                            ctypes.c_int, _P], ctypes.c_int),
     "canny_strerror": ([ctypes.c_int], ctypes.c_char_p),
-    "canny_inject_alloc_failures": ([ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "canny_inject_faults": ([ctypes.POINTER(canny_fault_injection)], ctypes.c_int),
 }
 
 
@@ -141,9 +146,11 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         return _lib
 
 
-def canny_inject_alloc_failures(device_allocations: int, arena_allocations: int = 0) -> None:
-    """Test hook: make the library's next allocations (and serving admissions) fail."""
-    _check(load().canny_inject_alloc_failures(device_allocations, arena_allocations), "canny_inject_alloc_failures")
+def canny_inject_faults(device_allocations: int = 0, arena_admissions: int = 0, stalled_barriers: int = 0) -> None:
+    """Test hook: make the library's next allocations, serving admissions or
+    single-image hysteresis barriers fail (see include/canny.h)."""
+    f = canny_fault_injection(device_allocations, arena_admissions, stalled_barriers)
+    _check(load().canny_inject_faults(ctypes.byref(f)), "canny_inject_faults")
 
 
 def strerror(status: int) -> str:

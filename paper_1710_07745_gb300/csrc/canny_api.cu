@@ -122,8 +122,8 @@ uint32_t tiles_of(int w, int h)
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-// Allocation failures injected by canny_inject_alloc_failures (test hook).
-std::atomic<int> g_fail_device{0}, g_fail_arena{0};
+// Failures injected by canny_inject_faults (test hooks).
+std::atomic<int> g_fail_device{0}, g_fail_arena{0}, g_fail_barrier{0};
 
 bool take_failure(std::atomic<int> &n)
 {
@@ -239,7 +239,12 @@ uint32_t auto_max_passes(uint32_t ntiles)
 canny_status run_global(canny_ctx *c, cudaStream_t s)
 {
     // one cooperative launch runs every pass; else a graph while-loop; else the host loop
-    if (c->use_graph && hyst_coop_supported()) return from_cuda(launch_hyst_global_coop(c->hs, s));
+    if (c->use_graph && hyst_coop_supported()) {
+        cudaError_t e = cudaSuccess;
+        if (take_failure(g_fail_barrier)) e = launch_hyst_phantom_arrival(c->hs, s);   // test hook
+        if (e == cudaSuccess) e = launch_hyst_global_coop(c->hs, s);
+        return from_cuda(e);
+    }
     if (c->use_graph && c->exec) return from_cuda(cudaGraphLaunch(c->exec, s));
     // host-driven loop: one pass, read the control block, repeat
     for (;;) {
@@ -656,11 +661,12 @@ bool arena_failure_injected() { return take_failure(g_fail_arena); }
 
 extern "C" {
 
-canny_status canny_inject_alloc_failures(int device_allocations, int arena_allocations)
+canny_status canny_inject_faults(const canny_fault_injection *f)
 {
-    if (device_allocations < 0 || arena_allocations < 0) return CANNY_EINVAL;
-    g_fail_device.store(device_allocations);
-    g_fail_arena.store(arena_allocations);
+    if (!f || f->device_allocations < 0 || f->arena_admissions < 0 || f->stalled_barriers < 0) return CANNY_EINVAL;
+    g_fail_device.store(f->device_allocations);
+    g_fail_arena.store(f->arena_admissions);
+    g_fail_barrier.store(f->stalled_barriers);
     return CANNY_OK;
 }
 

@@ -150,7 +150,7 @@ cudaError_t add_repitch_list_node(cudaGraph_t g, const cudaGraphNode_t *deps, si
 
 // ---------------------------------------------------------------- allocation (canny_api.cu)
 // Every device and pinned-host allocation of the library goes through these, so
-// that canny_inject_alloc_failures can make the next ones fail (host side only).
+// that canny_inject_faults can make the next ones fail (host side only).
 cudaError_t dev_alloc(void **p, size_t bytes);
 cudaError_t pinned_alloc(void **p, size_t bytes);
 // True (and one injected failure used up) if the serving arena's next request
@@ -198,6 +198,9 @@ cudaError_t launch_hyst_global_pass(const HystScratch &hs, int grid, bool in_gra
 // grid barrier): cudaErrorNotSupported when the device cannot hold the grid.
 bool hyst_coop_supported();
 cudaError_t launch_hyst_global_coop(const HystScratch &hs, cudaStream_t s);
+// Test hook: barrier arrivals that no CTA makes, so the next cooperative
+// launch's barrier never completes and its bounded wait runs out.
+cudaError_t launch_hyst_phantom_arrival(const HystScratch &hs, cudaStream_t s);
 // Clear the worklist stamps and the control block before a run; for a single
 // image, also store its descriptor as image 0 (the global passes read it).
 cudaError_t hyst_reset(const HystScratch &hs, uint32_t ntiles, uint32_t nimg,

@@ -500,6 +500,18 @@ bool hyst_coop_supported()
     return ok == 1;
 }
 
+namespace {
+// Test hook: arrivals at the cooperative passes' grid barrier that no CTA
+// makes, more than any grid has CTAs, so no arrival ever completes the barrier.
+__global__ void hyst_phantom_arrival_kernel(HystState *st) { atomicAdd(&st->bar_count, 1u << 30); }
+}  // namespace
+
+cudaError_t launch_hyst_phantom_arrival(const HystScratch &hs, cudaStream_t s)
+{
+    hyst_phantom_arrival_kernel<<<1, 1, 0, s>>>(hs.state);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_hyst_global_coop(const HystScratch &hs, cudaStream_t s)
 {
     if (!hyst_coop_supported()) return cudaErrorNotSupported;

@@ -216,7 +216,9 @@ canny_status ensure_hyst(canny_ctx *c, uint32_t max_tiles, uint32_t max_imgs)
     c->hs.max_tiles = max_tiles;
     c->hs.max_imgs = max_imgs;
     if (cudaMemset(c->hs.state, 0, sizeof(HystState)) != cudaSuccess) return CANNY_ECUDA;
-    if (c->use_graph) {
+    // (single images run their passes in one cooperative launch where the device
+    // allows; the graph while-loop is the fallback)
+    if (c->use_graph && !hyst_coop_supported()) {
         if (hyst_build_graph(c->hs, &c->graph, &c->exec) != cudaSuccess) {
             cudaGetLastError();
             c->use_graph = 0;

@@ -245,9 +245,13 @@ canny_status run_global(canny_ctx *c, cudaStream_t s)
         cudaError_t e = cudaSuccess;
         if (take_failure(g_fail_barrier)) e = launch_hyst_phantom_arrival(c->hs, s);   // test hook
         if (e == cudaSuccess) e = launch_hyst_global_coop(c->hs, s);
-        return from_cuda(e);
+        // a device shared with other work (fewer SMs than at start-up) may refuse
+        // the grid: then the passes are driven from the host below
+        if (e != cudaErrorCooperativeLaunchTooLarge) return from_cuda(e);
+        cudaGetLastError();
+    } else if (c->use_graph && c->exec) {
+        return from_cuda(cudaGraphLaunch(c->exec, s));
     }
-    if (c->use_graph && c->exec) return from_cuda(cudaGraphLaunch(c->exec, s));
     // host-driven loop: one pass, read the control block, repeat
     for (;;) {
         cudaError_t e = launch_hyst_global_pass(c->hs, hyst_pass_grid(), false, 0, s);

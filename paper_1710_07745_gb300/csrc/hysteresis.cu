@@ -15,8 +15,10 @@
 //                facing border gained edges next to its pending pixels is
 //                followed at once by the same warp, or queued for the next pass
 //                when the warp's budget runs out. Passes repeat until the
-//                worklist is empty; a CUDA-graph while-node drives the loop, its
-//                condition set by the last CTA of each pass.
+//                worklist is empty, decided by the last CTA of each pass: for a
+//                single image all passes run in one cooperative launch (a
+//                bounded grid barrier between them); inside the batch and
+//                frame graphs a CUDA-graph while-node drives the loop.
 // Pending pixels live only in a compact bitmap, so the map never holds a value
 // other than 0/255 and no clean-up sweep is needed.
 #include "hyst_tile.cuh"

@@ -368,14 +368,16 @@ k1f_strength_kernel(const uint8_t *__restrict__ in, int in_pitch, int w, int h, 
 // never wait for one another.
 constexpr int NMS_T = HT + 2;                // staged rows / columns of a tile with its ring
 constexpr int NMS_TILE = NMS_T * NMS_T;
+constexpr int NMS_WARPS = 2;                 // tiles (side by side) per CTA: small CTAs free their
+                                             // slots soon after their own tiles are done
 
-__global__ void __launch_bounds__(FB_THREADS)
+__global__ void __launch_bounds__(NMS_WARPS * 32)
 k1f_nms_kernel(const float *__restrict__ smap, const uint8_t *__restrict__ sect, int w, int h, FloatParams fp,
                const float *__restrict__ d_smax, HystScratch hs, HystImage img)
 {
-    __shared__ float s_all[FB_WARPS * NMS_TILE];
+    __shared__ float s_all[NMS_WARPS * NMS_TILE];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tx = blockIdx.x * FB_TX + warp % FB_TX, ty = blockIdx.y * FB_TY + warp / FB_TX;
+    const int tx = blockIdx.x * NMS_WARPS + warp, ty = blockIdx.y;
     if (tx >= img.ntx || ty >= img.nty) return;                   // warp-uniform; no block barrier follows
     const MapLayout L = map_layout(w, h);
     float *s_s = s_all + warp * NMS_TILE;                          // entry (r, c): row ty*32 - 1 + r, column tx*32 - 1 + c
@@ -504,8 +506,8 @@ cudaError_t launch_k1f_nms(const void *maps, int w, int h, const FloatParams &fp
     const MapLayout L = map_layout(w, h);
     const float *smap = static_cast<const float *>(maps);
     const uint8_t *sect = reinterpret_cast<const uint8_t *>(smap + (size_t)L.mp * L.rows);
-    const dim3 grid(L.mp / FB_W, L.rows / FB_H);
-    k1f_nms_kernel<<<grid, FB_THREADS, 0, s>>>(smap, sect, w, h, fp, d_smax, hs, img);
+    const dim3 grid(L.mp / (HT * NMS_WARPS), L.rows / HT);
+    k1f_nms_kernel<<<grid, NMS_WARPS * 32, 0, s>>>(smap, sect, w, h, fp, d_smax, hs, img);
     return cudaGetLastError();
 }
 

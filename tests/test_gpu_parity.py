@@ -742,3 +742,32 @@ def test_batch_tma_inputs_rewritten_between_calls():
             assert st["status"] == canny.CANNY_OK
             for im, o in zip(imgs, outs):
                 assert np.array_equal(o, oracle.canny_u8(im))
+
+
+@pytest.mark.parametrize("seed", [11, 12, 13])
+def test_random_sizes_offsets_and_pitches_match_the_oracle(seed):
+    # random widths 1..2999 and heights 1..599, input and output views at any
+    # byte offset and with padded pitches (staging, unaligned stores, ragged
+    # strips and bands), the float path on every third case
+    rng = np.random.default_rng(seed)
+    with canny.Canny(3000, 600) as ci, canny.Canny(3000, 600, path=canny.CANNY_PATH_F32, low=0.1, high=0.3) as cf:
+        for k in range(50):
+            w, h = int(rng.integers(1, 3000)), int(rng.integers(1, 600))
+            img = synth.image(int(rng.integers(0, 1 << 30)), w, h, int(rng.integers(1, 40)), int(rng.integers(1, 40)),
+                              int(rng.integers(0, 16)))
+            views = []
+            for _ in range(2):
+                off, pitch = int(rng.integers(0, 16)), w + int(rng.integers(0, 40))
+                buf = torch.full((off + h * pitch + 64,), 7, dtype=torch.uint8, device="cuda")
+                views.append(buf[off:off + (h - 1) * pitch + w].as_strided((h, w), (pitch, 1)))
+            src, dst = views
+            src.copy_(dev(img))
+            ci.run_pitched(src, dst)
+            torch.cuda.synchronize()
+            assert ci.stats()["status"] == canny.CANNY_OK
+            assert np.array_equal(dst.cpu().numpy(), oracle.canny_u8(img)), (w, h)
+            if k % 3 == 0 and w * h <= 400000:
+                dst.fill_(7)
+                cf.run_pitched(src, dst)
+                torch.cuda.synchronize()
+                assert np.array_equal(dst.cpu().numpy(), oracle.canny_f32(img, 1.4, 7, 0.1, 0.3)), (w, h)

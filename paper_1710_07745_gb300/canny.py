@@ -146,6 +146,24 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         return _lib
 
 
+_checked = None
+
+
+def load_checked() -> ctypes.CDLL:
+    """Load the checked build (-DCANNY_CHECKS: device-side bounds checks that set
+    error bit 3, reported as CANNY_ECUDA, instead of faulting), building it first."""
+    global _checked
+    with _lock:
+        if _checked is None:
+            L = ctypes.CDLL(_build.build(checks=True))
+            for name, (args, res) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _checked = L
+        return _checked
+
+
 def canny_inject_faults(device_allocations: int = 0, arena_admissions: int = 0, stalled_barriers: int = 0) -> None:
     """Test hook: make the library's next allocations, serving admissions or
     single-image hysteresis barriers fail (see include/canny.h)."""

@@ -868,7 +868,7 @@ canny_status canny_run_host(canny_ctx *c, const uint8_t *h_in, int in_pitch, uin
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return from_cuda(e);
     const HystState *hst = (const HystState *)c->h_state;
-    return (hst->error & 2u) ? CANNY_ECUDA : (hst->error & 1u) ? CANNY_ENOCONVERGE : CANNY_OK;
+    return (hst->error & 10u) ? CANNY_ECUDA : (hst->error & 1u) ? CANNY_ENOCONVERGE : CANNY_OK;
 }
 
 canny_status canny_hysteresis(canny_ctx *c, const canny_image *img, void *stream)
@@ -1205,7 +1205,7 @@ canny_status canny_run_frames(canny_ctx *c, int n, const uint8_t *const *h_in, i
     c->last.tiles = ntiles;
     c->last_stream = s;
     const uint32_t err = c->h_state[0];
-    return (err & 2u) ? CANNY_ECUDA : (err & 1u) ? CANNY_ENOCONVERGE : CANNY_OK;
+    return (err & 10u) ? CANNY_ECUDA : (err & 1u) ? CANNY_ENOCONVERGE : CANNY_OK;
 }
 
 canny_status canny_get_stats(canny_ctx *c, canny_stats *out)
@@ -1224,7 +1224,7 @@ canny_status canny_get_stats(canny_ctx *c, canny_stats *out)
     out->hyst_passes = st->pass;
     out->hyst_tiles_visited = st->visited;
     out->pending_tiles = st->pending_tiles;
-    out->status = (st->error & 2u) ? CANNY_ECUDA : (st->error & 1u) ? CANNY_ENOCONVERGE : CANNY_OK;
+    out->status = (st->error & 10u) ? CANNY_ECUDA : (st->error & 1u) ? CANNY_ENOCONVERGE : CANNY_OK;
     return CANNY_OK;
 }
 

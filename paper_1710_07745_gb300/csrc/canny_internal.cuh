@@ -34,12 +34,22 @@ struct TileMasks {
 };
 
 // Device-side control block of one run's hysteresis.
+// Checked builds (-DCANNY_CHECKS, in place of a sanitizer): device-side bounds
+// checks that record a failure in the run's error word (bit 3) and skip the
+// access. In normal builds a check is the constant true and compiles away.
+#ifdef CANNY_CHECKS
+#define CANNY_CHECK(cond, errp) ((cond) ? true : (atomicOr((errp), 8u), false))
+#else
+#define CANNY_CHECK(cond, errp) true
+#endif
+
 struct HystState {
     uint32_t list_count[2];   // sizes of the two worklists
     uint32_t done_ctas;       // CTAs finished in the current global pass
     uint32_t pass;            // global passes completed
     uint32_t max_passes;      // cap
-    uint32_t error;           // bit 0: cap reached with work left; bit 1: a pipeline wait ran out
+    uint32_t error;           // bit 0: cap reached with work left; bit 1: a pipeline wait ran out;
+                              // bit 3: a bounds check of a checked build failed
     uint32_t visited;         // tile visits summed over passes
     uint32_t pending_tiles;   // tiles with unresolved weak pixels after the local fill
     uint32_t ntiles;          // tiles in this run

@@ -145,7 +145,8 @@ __device__ __forceinline__ void push(const HystScratch &hs, uint32_t list, uint3
 {
     if (atomicMax(&hs.stamp[tile], stamp) < stamp) {
         uint32_t idx = atomicAdd(&hs.state->list_count[list], 1u);
-        hs.lists[(size_t)list * hs.max_tiles + idx] = tile;
+        if (CANNY_CHECK(idx < hs.max_tiles && tile < hs.max_tiles, &hs.state->error))
+            hs.lists[(size_t)list * hs.max_tiles + idx] = tile;
     }
 }
 
@@ -166,6 +167,7 @@ __device__ __forceinline__ void finish_tile(const HystScratch &hs, uint32_t t, u
     m.pend_left = __ballot_sync(FULL, pend & 1u);
     m.pend_right = __ballot_sync(FULL, pend >> 31);
     const bool any_pend = __any_sync(FULL, pend != 0);
+    if (!CANNY_CHECK(t < hs.max_tiles, &hs.state->error)) return;
     if (any_pend) hs.pend_bits[(size_t)t * HT + lane] = pend;
     if (lane == 0) {
         hs.masks[t] = m;
@@ -175,7 +177,10 @@ __device__ __forceinline__ void finish_tile(const HystScratch &hs, uint32_t t, u
         // 1 = queued for pass 0, 0 = not queued
         const bool queue = (m.pend_top | m.pend_bottom | m.pend_left | m.pend_right) != 0;
         hs.stamp[t] = queue ? 1u : 0u;
-        if (queue) hs.lists[atomicAdd(&hs.state->list_count[0], 1u)] = t;
+        if (queue) {
+            const uint32_t i = atomicAdd(&hs.state->list_count[0], 1u);
+            if (CANNY_CHECK(i < hs.max_tiles, &hs.state->error)) hs.lists[i] = t;
+        }
     }
 }
 

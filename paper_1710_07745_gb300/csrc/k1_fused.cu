@@ -148,7 +148,8 @@ __device__ __forceinline__ float &pix(float2 (&p)[5], int k)
 // Step 3 + thresholds for one queued candidate pixel.
 // ybase: image row of the group's first queued row, sb: its strength ring slot.
 template <int BAND>
-__device__ __forceinline__ void suppress_pixel(Smem<BAND> &S, uint32_t entry, int sb, int ybase, int Y0, float hi2)
+__device__ __forceinline__ void suppress_pixel(Smem<BAND> &S, uint32_t entry, int sb, int ybase, int Y0, float hi2,
+                                               uint32_t *err)
 {
     const int off = (int)((entry >> 8) & 3u), y = ybase + off, p = (int)(entry & 255u);
     int sl = sb + off;
@@ -168,6 +169,7 @@ __device__ __forceinline__ void suppress_pixel(Smem<BAND> &S, uint32_t entry, in
     const float mp = hz ? r : vt ? dc : dg ? dr : ur;
     if (m > mn && m >= mp) {
         const int col = p - LPX, row = y - Y0;
+        if (!CANNY_CHECK(row >= 0 && row < BAND && col >= 0 && col < OUT_W, err)) return;
         atomicOr(&S.cand[row][col >> 5], 1u << (col & 31));
         if (m > hi2) atomicOr(&S.strong[row][col >> 5], 1u << (col & 31));
     }
@@ -397,7 +399,8 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint
 #pragma unroll
                 for (int k = 0; k < LPX; ++k)      // static indices keep gprev in registers
                     if ((cm_prev >> k) & 1u)
-                        S.queue[idx++] = (uint32_t)(LPX * lane + k) | ((uint32_t)u << 8) | (gprev[k] << 10);
+                        if (CANNY_CHECK(idx < QCAP, err))
+                            S.queue[idx++] = (uint32_t)(LPX * lane + k) | ((uint32_t)u << 8) | (gprev[k] << 10);
             }
             // which pixels are candidates, and their gradients for the sector test (computed
             // for every lane without a branch: nearly every row has a candidate somewhere)
@@ -424,7 +427,8 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint
         __syncwarp();
         const uint32_t n = S.qcount;
         const int sb = rsg == 0 ? RING - 1 : rsg - 1;   // slot of row Y0 - 8 + g
-        for (uint32_t j = lane; j < n; j += 32) suppress_pixel(S, S.queue[j], sb, Y0 - 8 + g, Y0, hi2);
+        for (uint32_t j = lane; j < n && CANNY_CHECK(j < QCAP, err); j += 32)
+            suppress_pixel(S, S.queue[j], sb, Y0 - 8 + g, Y0, hi2, err);
         __syncwarp();
         if (lane == 0) S.qcount = 0;
         __syncwarp();

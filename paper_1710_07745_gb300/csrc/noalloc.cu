@@ -110,7 +110,7 @@ extern "C" canny_status canny_run_noalloc(const uint8_t *d_in, int in_pitch, uin
         if (e == cudaSuccess) e = cudaMemcpyAsync(&st, hs.state, sizeof(st), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return status_of(e);
-        return (st.error & 2u) ? CANNY_ECUDA : (st.error & 1u) ? CANNY_ENOCONVERGE : CANNY_OK;
+        return (st.error & 10u) ? CANNY_ECUDA : (st.error & 1u) ? CANNY_ENOCONVERGE : CANNY_OK;
     }
     for (;;) {
         e = launch_hyst_global_pass(hs, hyst_pass_grid(), false, 0, s);
@@ -119,5 +119,5 @@ extern "C" canny_status canny_run_noalloc(const uint8_t *d_in, int in_pitch, uin
         if (e != cudaSuccess) return status_of(e);
         if (!st.keep_going) break;
     }
-    return (st.error & 2u) ? CANNY_ECUDA : (st.error & 1u) ? CANNY_ENOCONVERGE : CANNY_OK;
+    return (st.error & 10u) ? CANNY_ECUDA : (st.error & 1u) ? CANNY_ENOCONVERGE : CANNY_OK;
 }

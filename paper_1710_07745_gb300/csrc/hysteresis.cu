@@ -270,7 +270,8 @@ __device__ __forceinline__ void global_pass(const HystScratch &hs, int in_graph,
     HystState *st = hs.state;
     const uint32_t k = *(volatile uint32_t *)&st->pass;
     const uint32_t cur = k & 1u, nxt = cur ^ 1u;
-    const uint32_t count = *(volatile uint32_t *)&st->list_count[cur];
+    uint32_t count = *(volatile uint32_t *)&st->list_count[cur];
+    if (!CANNY_CHECK(count <= hs.max_tiles, &st->error)) count = hs.max_tiles;
     const int nimg = (int)st->nimg;
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const uint32_t warp = (blockIdx.x * THREADS + threadIdx.x) >> 5;
@@ -288,7 +289,7 @@ __device__ __forceinline__ void global_pass(const HystScratch &hs, int in_graph,
         if (i < count) {
             TileSeeds sd;
             mine = __ldcg(&list[i]);      // (a cooperative launch reuses L1 across passes)
-            has = find_seeds(hs, mine, nimg, sd);
+            has = CANNY_CHECK(mine < hs.max_tiles, &st->error) && find_seeds(hs, mine, nimg, sd);
         }
         my_visits += (lane == 0) ? min(32u, count - base) : 0u;   // entries examined
         uint32_t todo = __ballot_sync(FULL, has);
@@ -301,6 +302,7 @@ __device__ __forceinline__ void global_pass(const HystScratch &hs, int in_graph,
                 TileSeeds sd;
                 Facing fp;
                 uint32_t aff = 0, ntx = 0;
+                if (!CANNY_CHECK(t < hs.max_tiles, &st->error)) break;
                 const uint32_t p_row = __ldcg(&hs.pend_bits[(size_t)t * HT + lane]);   // issued with the masks
                 if (chase_seeds(hs, t, nimg, sd, lane, fp)) {
                     aff = grow_tile(hs, t, sd, lane, p_row, fp);

@@ -53,6 +53,7 @@ constexpr int STAGES = 2;               // chunks in flight: 6 rows ahead
 constexpr int BOX = 256;                // TMA box width: columns X0-16 .. X0+239
 constexpr uint32_t CHUNK_BYTES = BOX * CH;
 constexpr int RING = 5;                 // rows of strengths kept
+constexpr int SRING = 6;                // rows of smoothed bytes kept
 constexpr int QCAP = UNROLL * 28 * LPX; // candidate pixels of one 3-row group, at most
 constexpr int TILES_X = OUT_W / HT;
 constexpr int MW = OUT_W / 32;          // bitmask words per strip row
@@ -80,7 +81,8 @@ template <int BAND>
 struct alignas(128) Smem {
     uint8_t in[STAGES][CH * BOX];        // TMA destinations, 128-byte aligned
     float m2[RING][256];                 // strengths of the last rows, by row mod RING
-    uint32_t queue[QCAP];                // pixel | row in group << 8 | (gx + 1024) << 10 | (gy + 1024) << 21
+    uint8_t srow[SRING][256];            // smoothed bytes of the last rows, by row mod SRING
+    uint16_t queue[QCAP];                // pixel | row in group << 8
     uint32_t cand[BAND][MW];             // class >= 1 (weak or strong), bit = column
     uint32_t strong[BAND][MW];           // class == 2
     uint32_t qcount;
@@ -146,21 +148,39 @@ __device__ __forceinline__ float &pix(float2 (&p)[5], int k)
 
 // ---------------------------------------------------------------- candidate suppression
 // Step 3 + thresholds for one queued candidate pixel.
-// ybase: image row of the group's first queued row, sb: its strength ring slot.
+// ybase: image row of the group's first queued row, sb: its strength ring slot,
+// tb: the smoothed-row ring slot of the row above it (row ybase - 1).
+// The pixel's Sobel gradients are computed again from the smoothed rows (the
+// same exact integers the stencil formed in floats), with the replicate border
+// taken by clamping the neighbour row and column to the image.
 template <int BAND>
-__device__ __forceinline__ void suppress_pixel(Smem<BAND> &S, uint32_t entry, int sb, int ybase, int Y0, float hi2,
-                                               uint32_t *err)
+__device__ __forceinline__ void suppress_pixel(Smem<BAND> &S, uint32_t entry, int sb, int tb, int ybase, int Y0,
+                                               int X0, int w, int h, float hi2, uint32_t *err)
 {
     const int off = (int)((entry >> 8) & 3u), y = ybase + off, p = (int)(entry & 255u);
     int sl = sb + off;
     if (sl >= RING) sl -= RING;
     const int su = sl == 0 ? RING - 1 : sl - 1, sd = sl == RING - 1 ? 0 : sl + 1;
+    int tu = tb + off;
+    if (tu >= SRING) tu -= SRING;
+    int tc = tu + 1;
+    if (tc >= SRING) tc -= SRING;
+    int td = tc + 1;
+    if (td >= SRING) td -= SRING;
+    if (y == 0) tu = tc;                               // S(x, -1) = S(x, 0)
+    if (y == h - 1) td = tc;                           // S(x, h) = S(x, h - 1)
+    const int c = X0 - LPX + p;                        // image column
+    const int pl = c > 0 ? p - 1 : p, pr = c < w - 1 ? p + 1 : p;
+    const int s_ul = S.srow[tu][pl], s_uc = S.srow[tu][p], s_ur = S.srow[tu][pr];
+    const int s_l = S.srow[tc][pl], s_r = S.srow[tc][pr];
+    const int s_dl = S.srow[td][pl], s_dc = S.srow[td][p], s_dr = S.srow[td][pr];
+    const int gx = (s_ur + 2 * s_r + s_dr) - (s_ul + 2 * s_l + s_dl);
+    const int gy = (s_dl + 2 * s_dc + s_dr) - (s_ul + 2 * s_uc + s_ur);
     const float m = S.m2[sl][p];
     // all eight neighbour strengths at once, then pick by sector
     const float l = S.m2[sl][p - 1], r = S.m2[sl][p + 1];
     const float ul = S.m2[su][p - 1], uc = S.m2[su][p], ur = S.m2[su][p + 1];
     const float dl = S.m2[sd][p - 1], dc = S.m2[sd][p], dr = S.m2[sd][p + 1];
-    const int gx = (int)((entry >> 10) & 2047u) - 1024, gy = (int)(entry >> 21) - 1024;
     const int ax = abs(gx), ay = abs(gy);
     const bool hz = ay * 32768 < ax * 13573;           // H: left / right
     const bool vt = ax * 32768 < ay * 13573;           // V: up / down
@@ -199,9 +219,6 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint
         for (int j = 0; j < 5; ++j) Sp[a][j] = f2(0.f, 0.f);
     }
     uint32_t cm_prev = 0;                     // candidate pixels of the previous row
-    uint32_t gprev[LPX];                      // their gradients, (gx + 1024) | (gy + 1024) << 11
-#pragma unroll
-    for (int k = 0; k < LPX; ++k) gprev[k] = 0;
     uint32_t last0 = 0, last1 = 0;            // words of input row h-1, for rows below the image
     uint32_t pf0[UNROLL], pf1[UNROLL];        // direct-load prefetch
 
@@ -241,8 +258,10 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint
         if (failed && lane == 0) atomicOr(err, 2u);
     };
 
-    // ring slot (row mod RING) of strength row r = Y0 - 7 + g, kept incrementally
+    // ring slot (row mod RING) of strength row r = Y0 - 7 + g, kept incrementally,
+    // and slot (row mod SRING) of smoothed row Y0 - 6 + g (it alternates: g steps by 3)
     int rsg = (((Y0 - 7) % RING) + RING) % RING;
+    int tsg = (((Y0 - 6) % SRING) + SRING) % SRING;
     for (int g = 0; g < ITERS; g += UNROLL) {
 #pragma unroll
         for (int u = 0; u < UNROLL; ++u) {
@@ -336,6 +355,12 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint
             Sp[a][2] = __fadd2_rn(f2(sbyte(he0, 3), sbyte(he1, 3)), unbias);   // (S2, S6)
             Sp[a][3] = __fadd2_rn(f2(sbyte(ho0, 3), sbyte(ho1, 3)), unbias);   // (S3, S7)
             Sp[a][4] = f2(__shfl_up_sync(FULL, Sp[a][3].y, 1), __shfl_down_sync(FULL, Sp[a][0].x, 1));
+            {   // the row's smoothed bytes, for the candidates' gradients
+                int ts = tsg + u;
+                if (ts >= SRING) ts -= SRING;
+                *reinterpret_cast<uint2 *>(&S.srow[ts][LPX * lane]) =
+                    make_uint2(perm(he0, ho0, 0x7351u), perm(he1, ho1, 0x7351u));
+            }
             if (border) {
                 // replicate border on S: S(-1) = S(0), S(x >= w) = S(w - 1)
                 if (xl == 0) Sp[a][4].x = Sp[a][0].x;
@@ -400,26 +425,14 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint
                 for (int k = 0; k < LPX; ++k)      // static indices keep gprev in registers
                     if ((cm_prev >> k) & 1u)
                         if (CANNY_CHECK(idx < QCAP, err))
-                            S.queue[idx++] = (uint32_t)(LPX * lane + k) | ((uint32_t)u << 8) | (gprev[k] << 10);
+                            S.queue[idx++] = (uint16_t)((LPX * lane + k) | (u << 8));
             }
-            // which pixels are candidates, and their gradients for the sector test (computed
-            // for every lane without a branch: nearly every row has a candidate somewhere)
+            // which pixels are candidates
             uint32_t cm = 0;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 cm |= (m[j].x > lo2 ? 1u : 0u) << j;
                 cm |= (m[j].y > lo2 ? 1u : 0u) << (j + 4);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                // 2^23 + 1024 + g holds g + 1024 (11 bits) in its low mantissa bits;
-                // shifted left by 11, the exponent bits leave the word (paired adds: exact)
-                const float2 magic = f2(8389632.0f, 8389632.0f);
-                const float2 ux = __fadd2_rn(gx[j], magic), uy = __fadd2_rn(gy[j], magic);
-                const uint32_t ax = __float_as_uint(ux.x), ay = __float_as_uint(uy.x);
-                const uint32_t bx = __float_as_uint(ux.y), by = __float_as_uint(uy.y);
-                gprev[j] = (ax & 2047u) | (ay << 11);
-                gprev[j + 4] = (bx & 2047u) | (by << 11);
             }
             cm_prev = out_lane ? cm : 0u;
         }
@@ -427,13 +440,15 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint
         __syncwarp();
         const uint32_t n = S.qcount;
         const int sb = rsg == 0 ? RING - 1 : rsg - 1;   // slot of row Y0 - 8 + g
+        const int tb = tsg >= 3 ? tsg - 3 : tsg + 3;    // slot of row Y0 - 9 + g
         for (uint32_t j = lane; j < n && CANNY_CHECK(j < QCAP, err); j += 32)
-            suppress_pixel(S, S.queue[j], sb, Y0 - 8 + g, Y0, hi2, err);
+            suppress_pixel(S, S.queue[j], sb, tb, Y0 - 8 + g, Y0, X0, w, h, hi2, err);
         __syncwarp();
         if (lane == 0) S.qcount = 0;
         __syncwarp();
         rsg += UNROLL;
         if (rsg >= RING) rsg -= RING;
+        tsg = tsg >= 3 ? tsg - 3 : tsg + 3;
     }
 }
 

@@ -153,7 +153,7 @@ __device__ __forceinline__ float &pix(float2 (&p)[5], int k)
 // The pixel's Sobel gradients are computed again from the smoothed rows (the
 // same exact integers the stencil formed in floats), with the replicate border
 // taken by clamping the neighbour row and column to the image.
-template <int BAND>
+template <int BAND, bool INTERIOR>
 __device__ __forceinline__ void suppress_pixel(Smem<BAND> &S, uint32_t entry, int sb, int tb, int ybase, int Y0,
                                                int X0, int w, int h, float hi2, uint32_t *err)
 {
@@ -167,10 +167,10 @@ __device__ __forceinline__ void suppress_pixel(Smem<BAND> &S, uint32_t entry, in
     if (tc >= SRING) tc -= SRING;
     int td = tc + 1;
     if (td >= SRING) td -= SRING;
-    if (y == 0) tu = tc;                               // S(x, -1) = S(x, 0)
-    if (y == h - 1) td = tc;                           // S(x, h) = S(x, h - 1)
+    if (!INTERIOR && y == 0) tu = tc;                  // S(x, -1) = S(x, 0)
+    if (!INTERIOR && y == h - 1) td = tc;              // S(x, h) = S(x, h - 1)
     const int c = X0 - LPX + p;                        // image column
-    const int pl = c > 0 ? p - 1 : p, pr = c < w - 1 ? p + 1 : p;
+    const int pl = INTERIOR || c > 0 ? p - 1 : p, pr = INTERIOR || c < w - 1 ? p + 1 : p;
     const int s_ul = S.srow[tu][pl], s_uc = S.srow[tu][p], s_ur = S.srow[tu][pr];
     const int s_l = S.srow[tc][pl], s_r = S.srow[tc][pr];
     const int s_dl = S.srow[td][pl], s_dc = S.srow[td][p], s_dr = S.srow[td][pr];
@@ -196,14 +196,17 @@ __device__ __forceinline__ void suppress_pixel(Smem<BAND> &S, uint32_t entry, in
 }
 
 // ---------------------------------------------------------------- phase 1
-template <bool TMA, int BAND>
+// INTERIOR: every input row Y0 - 4 .. Y0 + BAND + 4 lies inside the image and
+// every lane's columns (and their halos) too, so the border and row-range
+// checks are compiled out.
+template <bool TMA, int BAND, bool INTERIOR>
 __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint8_t *__restrict__ in,
                                              int in_pitch, int w, int h, IntThresholds t, Smem<BAND> &S, int lane,
                                              int X0, int Y0, uint32_t *err)
 {
     constexpr int ITERS = Band<BAND>::ITERS, NCH = Band<BAND>::NCH;
     const int xl = X0 - LPX + LPX * lane;     // image column of the lane's first pixel
-    const bool border = xl <= 0 || xl + LPX >= w;
+    const bool border = !INTERIOR && (xl <= 0 || xl + LPX >= w);
     const bool out_lane = lane >= 1 && lane <= 28 && xl < w;
     const int last = w - 1 - xl;               // index of the lane's last in-image pixel
     const float lo2 = (float)min(t.lo2, 1 << 24), hi2 = (float)min(t.hi2, 1 << 24);
@@ -223,7 +226,7 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint
     uint32_t pf0[UNROLL], pf1[UNROLL];        // direct-load prefetch
 
     auto direct_load = [&](int y, uint32_t &w0, uint32_t &w1) {
-        const uint8_t *row = in + (int64_t)clampi(y, 0, h - 1) * in_pitch;
+        const uint8_t *row = in + (int64_t)(INTERIOR ? y : clampi(y, 0, h - 1)) * in_pitch;
         if (direct_fast) {
             uint2 v = __ldg(reinterpret_cast<const uint2 *>(row + xl));
             w0 = v.x;
@@ -277,14 +280,15 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint
                 const int c = g / CH, off = u, slot = c % STAGES;
                 if (off == 0) {
                     wait_chunk(c);
-                    if (yin < 0) wait_chunk(4 / CH);   // top band: row 0 is in that chunk
+                    if (!INTERIOR && yin < 0) wait_chunk(4 / CH);   // top band: row 0 is in that chunk
                 }
-                if (yin >= h) {
+                if (!INTERIOR && yin >= h) {
                     w0 = last0;
                     w1 = last1;
                 } else {
                     // rows above the image repeat row 0, which sits in chunk 1 (yin = -4..-2) or 0
-                    const uint8_t *row = yin < 0 ? &S.in[(4 / CH) % STAGES][(4 % CH) * BOX] : &S.in[slot][off * BOX];
+                    const uint8_t *row = !INTERIOR && yin < 0 ? &S.in[(4 / CH) % STAGES][(4 % CH) * BOX]
+                                                              : &S.in[slot][off * BOX];
                     if (!border) {
                         const uint2 v = *reinterpret_cast<const uint2 *>(row + soff);
                         w0 = v.x;
@@ -297,7 +301,7 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint
                         w0 = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
                         w1 = b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24);
                     }
-                    if (yin == h - 1) {
+                    if (!INTERIOR && yin == h - 1) {
                         last0 = w0;
                         last1 = w1;
                     }
@@ -372,7 +376,8 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint
                     for (int k = -1; k <= LPX; ++k) if (k > last) pix(Sp[a], k) = sl;
                 }
             }
-            if (s == 0) {                        // S(-1) = S(0)
+            if (INTERIOR) {
+            } else if (s == 0) {                 // S(-1) = S(0)
 #pragma unroll
                 for (int j = 0; j < 5; ++j) Sp[am1][j] = Sp[a][j];
             } else if (s >= h) {                 // S(h) = S(h - 1)
@@ -401,7 +406,7 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint
                 gy[j] = __fadd2_rn(__ffma2_rn(E[j], two, el), er);
                 m[j] = __ffma2_rn(gx[j], gx[j], __fmul2_rn(gy[j], gy[j]));
             }
-            if (r < 0 || r >= h) {
+            if (!INTERIOR && (r < 0 || r >= h)) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) m[j] = f2(0.f, 0.f);
             } else if (border) {
@@ -442,7 +447,7 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint
         const int sb = rsg == 0 ? RING - 1 : rsg - 1;   // slot of row Y0 - 8 + g
         const int tb = tsg >= 3 ? tsg - 3 : tsg + 3;    // slot of row Y0 - 9 + g
         for (uint32_t j = lane; j < n && CANNY_CHECK(j < QCAP, err); j += 32)
-            suppress_pixel(S, S.queue[j], sb, tb, Y0 - 8 + g, Y0, X0, w, h, hi2, err);
+            suppress_pixel<BAND, INTERIOR>(S, S.queue[j], sb, tb, Y0 - 8 + g, Y0, X0, w, h, hi2, err);
         __syncwarp();
         if (lane == 0) S.qcount = 0;
         __syncwarp();
@@ -461,12 +466,24 @@ struct Unit {
     bool tma;
 };
 
+// A unit away from every image border: input rows Y0 - 4 .. Y0 + BAND + 4 and
+// the columns of all 32 lanes with their halos (X0 - 16 .. X0 + 247) in the image.
+template <int BAND>
+__device__ __forceinline__ bool interior_unit(const Unit &U)
+{
+    return U.X0 >= 16 && U.X0 + 248 <= U.w && U.Y0 >= 4 && U.Y0 + BAND + 4 < U.h;
+}
+
 // PATH: 0 = per unit (U.tma), 1 = TMA only, 2 = direct loads only. A kernel that
 // holds one path only is compiled for that path alone (no register pressure
 // from the other).
 enum { PATH_EITHER = 0, PATH_TMA = 1, PATH_DIRECT = 2 };
 
-template <int BAND, int MODE, int PATH>
+// SPLIT: interior units take the stencil compiled without border checks. The
+// batch kernel, whose units are mostly border units of small images, holds the
+// general stencil alone (two copies of the loop in one kernel cost it more in
+// instruction fetch than the interior units gain).
+template <int BAND, int MODE, int PATH, bool SPLIT>
 __device__ __forceinline__ void run_unit(const CUtensorMap *tmap, const Unit &U, IntThresholds t, uint8_t *out,
                                          int out_pitch, const HystScratch &hs, const HystImage &img, uint32_t *err,
                                          Smem<BAND> &S, int lane)
@@ -481,11 +498,19 @@ __device__ __forceinline__ void run_unit(const CUtensorMap *tmap, const Unit &U,
     if (PATH == PATH_TMA || (PATH == PATH_EITHER && U.tma)) {
         // the previous unit's reads of the stage buffers are done before TMA reuses them
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        if constexpr (PATH != PATH_DIRECT)
-            stencil_band<true, BAND>(tmap, U.in, U.in_pitch, U.w, U.h, t, S, lane, U.X0, U.Y0, err);
+        if constexpr (PATH != PATH_DIRECT) {
+            if (SPLIT && interior_unit<BAND>(U))
+                stencil_band<true, BAND, true>(tmap, U.in, U.in_pitch, U.w, U.h, t, S, lane, U.X0, U.Y0, err);
+            else
+                stencil_band<true, BAND, false>(tmap, U.in, U.in_pitch, U.w, U.h, t, S, lane, U.X0, U.Y0, err);
+        }
     } else {
-        if constexpr (PATH != PATH_TMA)
-            stencil_band<false, BAND>(tmap, U.in, U.in_pitch, U.w, U.h, t, S, lane, U.X0, U.Y0, err);
+        if constexpr (PATH != PATH_TMA) {
+            if (SPLIT && interior_unit<BAND>(U))
+                stencil_band<false, BAND, true>(tmap, U.in, U.in_pitch, U.w, U.h, t, S, lane, U.X0, U.Y0, err);
+            else
+                stencil_band<false, BAND, false>(tmap, U.in, U.in_pitch, U.w, U.h, t, S, lane, U.X0, U.Y0, err);
+        }
     }
     __syncwarp();
 
@@ -533,7 +558,7 @@ __device__ __forceinline__ void init_barriers(Smem<BAND> &S, int lane)
 }
 
 // ---------------------------------------------------------------- kernels
-// One image: one CTA per unit (blockIdx.x = strip, blockIdx.y = band).
+// One image: one CTA per unit (blockIdx.x = strip, blockIdx.y = band, reordered).
 template <int BAND, int MODE, int PATH>
 __global__ void __launch_bounds__(THREADS, BAND == 64 ? 16 : 12)
 k1_fused_kernel(const __grid_constant__ CUtensorMap tmap, const uint8_t *__restrict__ in, int in_pitch,
@@ -550,11 +575,14 @@ k1_fused_kernel(const __grid_constant__ CUtensorMap tmap, const uint8_t *__restr
     U.w = w;
     U.h = h;
     U.sx = blockIdx.x;
-    U.sy = blockIdx.y;
+    // the bottom band row (border units, the slower stencil) starts right after
+    // the top one instead of in the last wave: bands 0, nb - 1, 1, 2, ..., nb - 2
+    const int nb = (int)gridDim.y, by = (int)blockIdx.y;
+    U.sy = by == 0 || nb < 3 ? by : (by == 1 ? nb - 1 : by - 1);
     U.X0 = U.sx * OUT_W;
     U.Y0 = U.sy * BAND;
     U.tma = PATH == PATH_TMA;
-    run_unit<BAND, MODE, PATH>(&tmap, U, t, out, out_pitch, hs, img, err, S, lane);
+    run_unit<BAND, MODE, PATH, true>(&tmap, U, t, out, out_pitch, hs, img, err, S, lane);
 }
 
 // One (image, strip, band) unit of a batch.
@@ -588,7 +616,7 @@ __device__ __forceinline__ void batch_unit(const BatchImage *__restrict__ imgs, 
         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&tmaps[lo]) : "memory");
     }
     __syncwarp();
-    run_unit<BAND, MODE_EDGES, PATH>(&tmaps[lo], U, t, img.map, img.pitch, hs, img, &hs.state->error, S, lane);
+    run_unit<BAND, MODE_EDGES, PATH, false>(&tmaps[lo], U, t, img.map, img.pitch, hs, img, &hs.state->error, S, lane);
 }
 
 // A batch. PERSIST: a persistent grid pops units from a counter; otherwise the

@@ -66,6 +66,21 @@ def test_small_workload_bit_exact():
     assert np.array_equal(cls, oracle.classify_u8(img))
 
 
+# Sizes at the edge of the interior test: a unit (strip X0 = 224 k, band
+# Y0 = 64 j) runs the stencil without border checks only when X0 >= 16,
+# X0 + 248 <= w, Y0 >= 4 and Y0 + 68 < h. Each size puts one strip or band
+# exactly on either side of that line; all must stay bit-exact.
+@pytest.mark.parametrize("h,w", [(132, 472), (133, 472), (132, 471), (133, 473), (197, 696), (196, 697),
+                                 (261, 920), (260, 919), (69, 248), (68, 247)])
+def test_interior_unit_boundaries(h, w):
+    img = blocky_image(h * 3 + w, h, w)
+    out, st = run_int(img)
+    assert st["status"] == canny.CANNY_OK
+    assert np.array_equal(out, oracle.canny_u8(img))
+    cls, _ = run_int(img, stage="classify")
+    assert np.array_equal(cls, oracle.classify_u8(img))
+
+
 def test_medium_workload_bit_exact():
     img = synth.medium()
     out, st = run_int(img)

@@ -42,12 +42,12 @@ WORKLOAD = "canny_int_16384x16384"
 K1_BYTES_PER_PX = 2
 # ncu DRAM traffic of the fused kernel per 16384^2 launch, valid only for the kernel
 # source it was measured on (profiles/k1_fused_16384x8192.md: capture at half size, x2)
-K1_TRAFFIC = {"sha256_prefix": "944c11edeb873e7c", "bytes": 467_559_424}
+K1_TRAFFIC = {"sha256_prefix": "e9deaa80b2807105", "bytes": 467_559_424}
 # whole pipeline floor: stencil 2 B/px + tile-local hysteresis read + write 2 B/px
 PIPE_BYTES_PER_PX = 4
 # ncu smsp__inst_executed.sum of the fused kernel per pixel (same capture and source
 # as K1_TRAFFIC: 278,582,223 warp instructions on 16384 x 8192 pixels)
-K1_INST = {"sha256_prefix": "944c11edeb873e7c", "warp_inst_per_px": 202_902_579 / (16384 * 8192)}
+K1_INST = {"sha256_prefix": "e9deaa80b2807105", "warp_inst_per_px": 202_902_579 / (16384 * 8192)}
 # warp instructions an SM can issue per clock (4 schedulers, one each)
 ISSUE_PER_SM_CLK = 4
 

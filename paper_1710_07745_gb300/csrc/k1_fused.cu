@@ -19,15 +19,18 @@
 //     2^23) and Sobel (column sums and row differences) and the squared
 //     strength run in packed float2 arithmetic (__ffma2_rn etc.); every value
 //     is an integer below 2^24, so the result is exact;
-//   - every row's strengths go to a 5-row ring in shared memory. Only ~2% of
-//     pixels exceed the low threshold: their lanes keep the row's gradients in
-//     registers and, one row later, queue one entry per such pixel holding its
-//     column, row and gradients; after every 3 rows the lanes share the queued
-//     pixels (one each) and run the sector test and the suppression for them
-//     alone, setting bits in the strip's weak/strong row bitmasks. A
-//     non-candidate neighbour is at most the low threshold, below any
-//     candidate, so its stored strength decides nothing.
-// Shared memory stays under 13 KB per CTA and registers at 128 per thread, so
+//   - every row's strengths go to a 5-row ring and its smoothed bytes to a
+//     6-row ring in shared memory. Only ~2% of pixels exceed the low
+//     threshold: one row later their lanes queue one 16-bit entry per such
+//     pixel (column, row); after every 3 rows the lanes share the queued
+//     pixels (one each), form their Sobel gradients again from the smoothed
+//     rows, and run the sector test and the suppression for them alone,
+//     setting bits in the strip's weak/strong row bitmasks. A non-candidate
+//     neighbour is at most the low threshold, below any candidate, so its
+//     stored strength decides nothing.
+//   - units away from every image border run a copy of the band loop
+//     compiled without the border and row-range tests.
+// Shared memory stays at 13.2 KB per CTA and registers at 128 per thread, so
 // 16 one-warp CTAs fit on an SM.
 // Phase 2: either the class map is written from the bitmasks (canny_classify),
 // or the warp runs the tile flood fill of the hysteresis on them and writes

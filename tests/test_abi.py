@@ -43,6 +43,15 @@ def test_library_exports_every_declared_symbol(lib):
         assert sym in canny.SIGNATURES, sym
 
 
+def test_checked_build_exports_the_same_symbols():
+    # the -DCANNY_CHECKS library (device bounds checks) is a drop-in copy of the ABI
+    from paper_1710_07745_gb300 import canny
+    checked = canny.load_checked()
+    for sym in _declared_symbols(os.path.join(ROOT, "include", "canny.h")):
+        assert hasattr(checked, sym), f"{sym} not exported by the checked build"
+    assert checked.canny_strerror(canny.CANNY_OK) == canny.load().canny_strerror(canny.CANNY_OK)
+
+
 def test_strerror_and_defaults(lib):
     from paper_1710_07745_gb300 import canny
     assert canny.strerror(canny.CANNY_OK) == "ok"

@@ -696,11 +696,12 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
-    rank, world = dist_init(args.gpus)
     if args.impl == "reference":
-        run_reference(args, rank, world)
-    else:
-        run_ours(args, rank, world)
+        # the oracle runs on rank 0 alone and exchanges nothing: no process group
+        run_reference(args, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")))
+        return
+    rank, world = dist_init(args.gpus)
+    run_ours(args, rank, world)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -53,7 +53,7 @@ def serpentine(n, gap=32):
 
 
 @pytest.mark.parametrize("h,w", [(1, 1), (1, 300), (300, 1), (3, 3), (17, 5), (31, 33), (64, 224), (65, 225),
-                                 (200, 301), (129, 450)])
+                                 (200, 301), (129, 450), (300, 700), (520, 1000)])   # the last two hold interior units
 def test_checked_build_integer_and_float_sizes(lib, h, w):
     img = synth.image(h * 7 + w, w, h, 4, 4, 10)
     for path in (canny.CANNY_PATH_INT, canny.CANNY_PATH_F32):

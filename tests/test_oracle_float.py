@@ -97,3 +97,64 @@ def test_float_thresholds_relative_to_max():
     assert (M[cls == 2] > np.float32(0.3) * np.float32(mmax)).all()
     assert (M[cls == 1] > np.float32(0.1) * np.float32(mmax)).all()
     assert e[:, :9].max() == 0  # the faint blob is not an edge
+
+
+# ---------------------------------------------------------------- sector pins (Step 2 direction, Step 3)
+H, V, D, A = oracle.SECTOR_H, oracle.SECTOR_V, oracle.SECTOR_D, oracle.SECTOR_A
+
+
+@pytest.mark.parametrize("gx,gy,want", [
+    (100.0, 0.0, H), (-100.0, 3.0, H), (0.25, -0.1, H),
+    (0.0, 100.0, V), (5.0, -100.0, V), (-0.1, 0.3, V),
+    (100.0, 100.0, D), (-7.0, -7.0, D), (0.5, 0.5, D), (-3.5, -2.0, D),
+    (100.0, -100.0, A), (-7.0, 7.0, A), (2.5, -2.5, A), (-2.0, 3.5, A),
+])
+def test_sector_f_examples(gx, gy, want):
+    """One example per sector and sign pattern: D is the diagonal where Gx and
+    Gy share a sign (the gradient points down-right or up-left, y downward),
+    A the other one."""
+    assert oracle.sector_f(gx, gy) == want
+
+
+def test_sector_f_agrees_with_exact_boundary():
+    """Away from a 1e-6 relative band around tan(22.5 deg) = sqrt(2) - 1, the
+    float sector is the exact one: H iff (ax + ay)^2 < 2 ax^2, V iff
+    (ax + ay)^2 < 2 ay^2, else D when Gx Gy > 0, A otherwise. float32 inputs
+    in [2^-8, 1020] make every float64 operation here exact."""
+    rng = np.random.default_rng(7)
+    g = rng.uniform(-1020, 1020, (400000, 2)).astype(np.float32)
+    r = np.arange(-40, 41, dtype=np.float32) * np.float32(0.75)
+    gg = np.stack(np.meshgrid(r, r), -1).reshape(-1, 2)
+    g = np.concatenate([g, gg])
+    g = g[(np.abs(g) >= 2.0 ** -8).all(1)]
+    gx, gy = g[:, 0].astype(np.float64), g[:, 1].astype(np.float64)
+    ax, ay = np.abs(gx), np.abs(gy)
+    t = np.sqrt(2.0) - 1.0
+    ok = (np.abs(ay - ax * t) > 1e-6 * ax) & (np.abs(ax - ay * t) > 1e-6 * ay)
+    assert ok.mean() > 0.999
+    gx, gy, ax, ay = gx[ok], gy[ok], ax[ok], ay[ok]
+    exact = np.where((ax + ay) ** 2 < 2 * ax ** 2, H,
+                     np.where((ax + ay) ** 2 < 2 * ay ** 2, V, np.where(gx * gy > 0, D, A)))
+    got = np.array([oracle.sector_f(a, b) for a, b in zip(gx.astype(np.float32), gy.astype(np.float32))])
+    assert np.array_equal(got, exact)
+    assert {H, V, D, A} <= set(got.tolist())
+
+
+@pytest.mark.parametrize("anti", [False, True])
+def test_float_diagonal_step_gives_the_two_central_diagonals(anti):
+    """I = 224 where x + y >= n (or x >= y for the anti-diagonal step), else 32.
+    The gradient lies in sector D (A), which compares pixels two diagonals
+    apart across the step, so the two diagonals nearest the step both survive;
+    the other diagonal sector would compare along the step and keep at most
+    one pixel of it."""
+    n = 40
+    y, x = np.mgrid[0:n, 0:n]
+    key = (x - y) if anti else (x + y)
+    edge_at = 0 if anti else n
+    img = np.where(key >= edge_at, 224, 32).astype(np.uint8)
+    e = oracle.canny_f32(img) == 255
+    inner, k = e[6:n - 6, 6:n - 6], key[6:n - 6, 6:n - 6]
+    assert np.array_equal(inner, (k == edge_at - 1) | (k == edge_at))
+    gx, gy = oracle.sobel_f32(oracle.gauss_f32(img))
+    px = (20, 20) if anti else (20, 19)
+    assert oracle.sector_f(gx[px], gy[px]) == (A if anti else D)

@@ -3,40 +3,41 @@
 // suppression -> double threshold -> tile-local hysteresis. The image is read
 // once and the edge map written once; the class map never leaves the SM.
 //
-// A CTA is one warp. Its unit of work is a strip of 224 columns x BAND rows
-// (BAND = 64, 160 or 256: 7 x BAND/32 hysteresis tiles); lane L handles the 8
-// pixels starting at column X0 - 8 + 8L, lanes 1..28 give the output, lanes 0
-// and 29 serve halos, lanes 30 and 31 idle along. One image: one CTA per unit.
-// A batch: a persistent grid pops units of all images from a device counter.
-//
-// Phase 1, sliding down the BAND rows (plus a 4-row halo each side):
-//   - TMA loads the strip's input rows (256 bytes from X0 - 16) in chunks of
-//     3 rows into a 2-stage shared-memory ring, one mbarrier per stage;
-//   - the binomial Gaussian runs on pairs of 16-bit lanes (vertical: a cascade
-//     of four pairwise sums; horizontal: packed words with the +128 rounding
-//     folded in); neighbour lanes trade halo values by shuffles;
-//   - the smoothed bytes become floats S (2^23 + S from a byte permute, minus
-//     2^23) and Sobel (column sums and row differences) and the squared
-//     strength run in packed float2 arithmetic (__ffma2_rn etc.); every value
-//     is an integer below 2^24, so the result is exact;
-//   - every row's strengths go to a 5-row ring and its smoothed bytes to a
-//     6-row ring in shared memory. Only ~2% of pixels exceed the low
-//     threshold: one row later their lanes queue one 16-bit entry per such
-//     pixel (column, row); after every 3 rows the lanes share the queued
-//     pixels (one each), form their Sobel gradients again from the smoothed
-//     rows, and run the sector test and the suppression for them alone,
-//     setting bits in the strip's weak/strong row bitmasks. A non-candidate
-//     neighbour is at most the low threshold, below any candidate, so its
-//     stored strength decides nothing.
-//   - units away from every image border run a copy of the band loop
-//     compiled without the border and row-range tests.
-// Shared memory stays at 13.2 KB per CTA and registers at 128 per thread, so
-// 16 one-warp CTAs fit on an SM.
-// Phase 2: either the class map is written from the bitmasks (canny_classify),
-// or the warp runs the tile flood fill of the hysteresis on them and writes
-// 255/0 edge bytes plus the tile border masks and pending bitmaps that the
-// global passes need.
+// A CTA is one warp. Its unit of work is a strip of 480 columns x BAND rows
+// (15 x BAND/32 hysteresis tiles). Lane L owns the 16 pixels starting at
+// column X0 - 16 + 16 L; lanes 1..30 give the output, lanes 0 and 31 supply
+// the halo columns. The warp slides down the BAND rows plus a 4-row halo on
+// each side, four rows per group:
+//   - TMA stages the strip's input rows (512 bytes from X0 - 16, as two
+//     256-byte boxes) three rows per chunk into a 2-stage ring, one mbarrier
+//     per stage;
+//   - Step 1, binomial 5x5: a lane's 16 bytes become eight 16-bit pairs
+//     E_k = (x_4k, x_4k+2), O_k = (x_4k+1, x_4k+3); the vertical pass is
+//     (1,2,1) applied twice, the horizontal pass weights shifted pairs (+128
+//     rounding folded in), all in integer SWAR. Every row-to-row state (the
+//     two vertical stages, Sobel's Dx and T) spans two rows, so with three
+//     rows per group the registers rotate without copies;
+//   - Step 2, Sobel: the smoothed bytes S become fp16 pairs 1024 + S by one
+//     byte permute; every Sobel sum is an integer of magnitude below 2048,
+//     which fp16 holds exactly, so Gx and Gy are exact;
+//   - candidates: Gx^2 + Gy^2 is compared with the low threshold in fp16
+//     with a margin that makes the test a necessary condition (a pixel above
+//     the threshold is always flagged; a few below it may be), giving 16
+//     flags per lane and row;
+//   - every row's exact Gx, Gy go to a 5-row shared ring; after each group the
+//     warp deals the flagged pixels of three rows out to its lanes (a prefix
+//     sum over the lanes' flag counts), and each lane runs the exact Step 3
+//     for its pixel: fp32 strength (exact), the Q15 sector test, suppression
+//     against the two neighbours its sector names, and the Step 4
+//     thresholds, setting bits in the tile row's weak/strong bitmasks;
+//   - after every 32 rows the warp runs the tile flood fill of the
+//     hysteresis on the 15 tiles of that tile row and writes 255/0 edge bytes
+//     plus the tile border masks and pending bitmaps that the global passes
+//     need (or, for canny_classify, the class bytes).
+// Units away from every image border run a copy of the band loop compiled
+// without the border and row-range tests.
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <string.h>
 
 #include "hyst_tile.cuh"
@@ -47,49 +48,45 @@ namespace {
 
 using tile::FULL;
 
-constexpr int LPX = 8;                  // pixels per lane per row
+constexpr int LPX = 16;                 // pixels per lane per row
 constexpr int THREADS = 32;             // one warp per CTA
-constexpr int OUT_W = 28 * LPX;         // 224 output columns (lanes 1..28) = 7 hysteresis tiles
-constexpr int UNROLL = 3;               // period of the 3-row windows
-constexpr int CH = UNROLL;              // input rows per TMA chunk (one chunk per unrolled group)
-constexpr int STAGES = 2;               // chunks in flight: 6 rows ahead
-constexpr int BOX = 256;                // TMA box width: columns X0-16 .. X0+239
-constexpr uint32_t CHUNK_BYTES = BOX * CH;
-constexpr int RING = 5;                 // rows of strengths kept
-constexpr int SRING = 6;                // rows of smoothed bytes kept
-constexpr int QCAP = UNROLL * 28 * LPX; // candidate pixels of one 3-row group, at most
+constexpr int OUT_LANES = 30;           // lanes 1..30 give the output
+constexpr int OUT_W = OUT_LANES * LPX;  // 480 output columns = 15 hysteresis tiles
 constexpr int TILES_X = OUT_W / HT;
-constexpr int MW = OUT_W / 32;          // bitmask words per strip row
-static_assert((CH * BOX) % 128 == 0, "TMA stage buffers must stay 128-byte aligned");
-static_assert(UNROLL <= RING, "ring slots advance by at most one wrap per group");
+constexpr int ROWB = THREADS * LPX;     // 512 staged bytes per row: columns X0-16 .. X0+495
+constexpr int BOX = 256;                // TMA box width (the hardware limit): two boxes per row
+constexpr int U = 3;                    // rows per group = input rows per TMA chunk
+constexpr int CH = U;
+constexpr int STAGES = 2;               // chunks in flight: 6 rows ahead
+constexpr int GRING = U + 2;            // gradient rows kept: a group's candidate rows +-1
+constexpr int CROWS = HT + U - 1;       // rows of class bitmasks: a tile row plus a group's overhang
+constexpr int GHALF = THREADS * 16;     // bytes of one gradient half-row (E or O pairs of all lanes)
+constexpr int GROW = 4 * GHALF;         // one gradient row: Gx E, Gx O, Gy E, Gy O
+constexpr uint32_t CHUNK_BYTES = ROWB * CH;
+static_assert(OUT_W % HT == 0, "strips hold whole tiles");
 
-// Rows per unit. Each unit consumes a whole number of full mbarrier phase
-// cycles (NCH a multiple of 2 * STAGES), so a persistent CTA can run unit after
-// unit on the same barriers.
+// Rows per unit: input rows Y0-4 .. Y0+BAND+3 in groups of U.
 template <int BAND>
 struct Band {
-    static constexpr int ITERS = BAND + 8;          // input rows Y0-4 .. Y0+BAND+3
-    static constexpr int NCH = ITERS / CH;          // chunks per unit
+    static constexpr int ITERS = BAND + 8;
+    static constexpr int GROUPS = ITERS / U;
     static constexpr int TILES_Y = BAND / HT;
-    static_assert(BAND % HT == 0 && ITERS % UNROLL == 0 && NCH % (2 * STAGES) == 0, "bad band height");
+    static_assert(BAND % HT == 0 && ITERS % U == 0 && GROUPS % STAGES == 0, "bad band height");
 };
 
-constexpr uint32_t MAGIC = 0x4B000000u;             // float 2^23
 constexpr uint32_t BIAS = 0x00800080u;              // +128 in both 16-bit lanes
+constexpr uint32_t H1024 = 0x64006400u;             // fp16 1024 in both halves (exponent byte 0x64)
+constexpr uint32_t HTWO = 0x40004000u;              // fp16 2.0
+constexpr uint32_t HM3072 = 0xEA00EA00u;            // fp16 -3072
 constexpr uint32_t WAIT_LIMIT = 1u << 22;           // bounded mbarrier waits
 
 enum { MODE_CLASSMAP = 0, MODE_EDGES = 1 };
 
-template <int BAND>
-struct alignas(128) Smem {
-    uint8_t in[STAGES][CH * BOX];        // TMA destinations, 128-byte aligned
-    float m2[RING][256];                 // strengths of the last rows, by row mod RING
-    uint8_t srow[SRING][256];            // smoothed bytes of the last rows, by row mod SRING
-    uint16_t queue[QCAP];                // pixel | row in group << 8
-    uint32_t cand[BAND][MW];             // class >= 1 (weak or strong), bit = column
-    uint32_t strong[BAND][MW];           // class == 2
-    uint32_t qcount;
-    uint32_t pad;
+struct Smem {                            // at the 128-byte aligned start of dynamic shared memory
+    uint8_t in[STAGES][2][CH][BOX];      // TMA destinations: [stage][box][row][column]
+    uint8_t g[GRING][GROW];              // exact Gx, Gy (fp16) of the last rows, by row mod GRING
+    uint32_t cand[CROWS][TILES_X];       // class >= 1 by (row - Y0) mod CROWS, bit = column
+    uint32_t strong[CROWS][TILES_X];     // class == 2
     unsigned long long full[STAGES];     // mbarriers of the input ring
 };
 
@@ -129,334 +126,107 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
 
 __device__ __forceinline__ uint32_t perm(uint32_t a, uint32_t b, uint32_t sel) { return __byte_perm(a, b, sel); }
 
-// float 2^23 + (byte k of w)
-__device__ __forceinline__ float sbyte(uint32_t w, int k)
+// fp16x2 arithmetic on raw bits, round to nearest (every use here is exact
+// except the candidate test, whose margin covers its rounding); the intrinsics
+// let constant operands be encoded as immediates
+__device__ __forceinline__ __half2 as_h2(uint32_t u)
 {
-    return __uint_as_float(perm(w, MAGIC, 0x7540u | (uint32_t)k));
+    __half2 h;
+    memcpy(&h, &u, 4);
+    return h;
+}
+__device__ __forceinline__ uint32_t as_u32(__half2 h)
+{
+    uint32_t u;
+    memcpy(&u, &h, 4);
+    return u;
+}
+__device__ __forceinline__ uint32_t hadd2(uint32_t a, uint32_t b) { return as_u32(__hadd2(as_h2(a), as_h2(b))); }
+__device__ __forceinline__ uint32_t hsub2(uint32_t a, uint32_t b) { return as_u32(__hsub2(as_h2(a), as_h2(b))); }
+__device__ __forceinline__ uint32_t hfma2(uint32_t a, uint32_t b, uint32_t c)
+{
+    return as_u32(__hfma2(as_h2(a), as_h2(b), as_h2(c)));
 }
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
 
-__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.f, -1.f), a); }
-
 // 4 bytes of value 0/1 from the low 4 bits of t
 __device__ __forceinline__ uint32_t nib01(uint32_t t) { return ((t & 0xFu) * 0x00204081u) & 0x01010101u; }
 
-// Pixel k in [-1, 8] of a row held as pairs p[j] = (x_j, x_{j+4}), p[4] = (x_-1, x_8).
-__device__ __forceinline__ float &pix(float2 (&p)[5], int k)
+// Half p (0..15) of a lane's pixels held as E_k = (4k, 4k+2), O_k = (4k+1, 4k+3).
+__device__ __forceinline__ uint32_t get_px(const uint32_t (&E)[4], const uint32_t (&O)[4], int p)
 {
-    return k < 0 ? p[4].x : (k > 7 ? p[4].y : (k < 4 ? p[k].x : p[k - 4].y));
+    const uint32_t w = (p & 1) ? O[p >> 2] : E[p >> 2];
+    return (p & 2) ? (w >> 16) : (w & 0xFFFFu);
+}
+__device__ __forceinline__ void set_px(uint32_t (&E)[4], uint32_t (&O)[4], int p, uint32_t v)
+{
+    uint32_t &w = (p & 1) ? O[p >> 2] : E[p >> 2];
+    w = (p & 2) ? ((w & 0xFFFFu) | (v << 16)) : ((w & 0xFFFF0000u) | v);
 }
 
-// ---------------------------------------------------------------- candidate suppression
-// Step 3 + thresholds for one queued candidate pixel.
-// ybase: image row of the group's first queued row, sb: its strength ring slot,
-// tb: the smoothed-row ring slot of the row above it (row ybase - 1).
-// The pixel's Sobel gradients are computed again from the smoothed rows (the
-// same exact integers the stencil formed in floats), with the replicate border
-// taken by clamping the neighbour row and column to the image.
-template <int BAND, bool INTERIOR>
-__device__ __forceinline__ void suppress_pixel(Smem<BAND> &S, uint32_t entry, int sb, int tb, int ybase, int Y0,
-                                               int X0, int w, int h, float hi2, uint32_t *err)
+// Position of the k-th (0-based) set bit of m; m's set bits lie in bits 4..7 of its bytes.
+__device__ __forceinline__ uint32_t nth_flag(uint32_t m, uint32_t k)
 {
-    const int off = (int)((entry >> 8) & 3u), y = ybase + off, p = (int)(entry & 255u);
-    int sl = sb + off;
-    if (sl >= RING) sl -= RING;
-    const int su = sl == 0 ? RING - 1 : sl - 1, sd = sl == RING - 1 ? 0 : sl + 1;
-    int tu = tb + off;
-    if (tu >= SRING) tu -= SRING;
-    int tc = tu + 1;
-    if (tc >= SRING) tc -= SRING;
-    int td = tc + 1;
-    if (td >= SRING) td -= SRING;
-    if (!INTERIOR && y == 0) tu = tc;                  // S(x, -1) = S(x, 0)
-    if (!INTERIOR && y == h - 1) td = tc;              // S(x, h) = S(x, h - 1)
-    const int c = X0 - LPX + p;                        // image column
-    const int pl = INTERIOR || c > 0 ? p - 1 : p, pr = INTERIOR || c < w - 1 ? p + 1 : p;
-    const int s_ul = S.srow[tu][pl], s_uc = S.srow[tu][p], s_ur = S.srow[tu][pr];
-    const int s_l = S.srow[tc][pl], s_r = S.srow[tc][pr];
-    const int s_dl = S.srow[td][pl], s_dc = S.srow[td][p], s_dr = S.srow[td][pr];
-    const int gx = (s_ur + 2 * s_r + s_dr) - (s_ul + 2 * s_l + s_dl);
-    const int gy = (s_dl + 2 * s_dc + s_dr) - (s_ul + 2 * s_uc + s_ur);
-    const float m = S.m2[sl][p];
-    // all eight neighbour strengths at once, then pick by sector
-    const float l = S.m2[sl][p - 1], r = S.m2[sl][p + 1];
-    const float ul = S.m2[su][p - 1], uc = S.m2[su][p], ur = S.m2[su][p + 1];
-    const float dl = S.m2[sd][p - 1], dc = S.m2[sd][p], dr = S.m2[sd][p + 1];
-    const int ax = abs(gx), ay = abs(gy);
-    const bool hz = ay * 32768 < ax * 13573;           // H: left / right
-    const bool vt = ax * 32768 < ay * 13573;           // V: up / down
-    const bool dg = gx * gy > 0;                       // D: up-left / down-right, else A
-    const float mn = hz ? l : vt ? uc : dg ? ul : dl;  // A: down-left / up-right
-    const float mp = hz ? r : vt ? dc : dg ? dr : ur;
+    uint32_t pos = 0, c = __popc(m & 0xFFFFu);
+    if (k >= c) { k -= c; m >>= 16; pos = 16; }
+    c = __popc(m & 0xFFu);
+    if (k >= c) { k -= c; m >>= 8; pos += 8; }
+    m >>= 4;
+    pos += 4;
+    c = __popc(m & 0x3u);
+    if (k >= c) { k -= c; m >>= 2; pos += 2; }
+    if (k >= (m & 1u)) pos += 1;
+    return pos;
+}
+
+// Lane-local pixel (0..15) of flag bit b: bit 7 - q of byte B of the flag word
+// is the flag of pixel 4q + B.
+__device__ __forceinline__ int flag_px(uint32_t b) { return 4 * (7 - (int)(b & 7u)) + (int)(b >> 3); }
+
+// Byte offset, inside a gradient row, of the Gx value of staged column col (0..511):
+// lane col / 16 at 16 col / 16 bytes, pair col / 4 mod 4 at 4 times that, high
+// half if bit 1 of col is set, the O half-row (+GHALF) if bit 0 is set; together
+// that is col with bit 0 moved to bit 9.
+__device__ __forceinline__ int gcol_off(int col) { return (col & ~1) + (col & 1) * GHALF; }
+
+__device__ __forceinline__ float gload(const uint8_t *p)
+{
+    return __half2float(__ushort_as_half(*reinterpret_cast<const unsigned short *>(p)));
+}
+
+// Exact Gx^2 + Gy^2 at a gradient-row byte offset (0 outside the image).
+__device__ __forceinline__ float gstrength(const uint8_t *p)
+{
+    const float x = gload(p), y = gload(p + 2 * GHALF);
+    return fmaf(x, x, y * y);
+}
+
+// ---------------------------------------------------------------- Step 3 for one flagged pixel
+// rowc, rowu, rowd: gradient rows of the pixel's row and the rows above and below;
+// col: staged column (lanes 1..30). The flag is a necessary condition; the exact
+// strength decides here.
+__device__ __forceinline__ void suppress_pixel(Smem &S, int col, const uint8_t *rowc, const uint8_t *rowu,
+                                               const uint8_t *rowd, int trow, float lo2, float hi2, uint32_t *err)
+{
+    const int off = gcol_off(col);
+    const float gx = gload(rowc + off), gy = gload(rowc + off + 2 * GHALF);
+    const float m = fmaf(gx, gx, gy * gy);             // exact: integers below 2^24
+    if (!(m > lo2)) return;
+    const float ax = fabsf(gx), ay = fabsf(gy);
+    const bool hz = ay * 32768.f < ax * 13573.f;       // H: left / right (both products exact)
+    const bool vt = ax * 32768.f < ay * 13573.f;       // V: up / down
+    const bool dg = gx * gy > 0.f;                     // D: up-left / down-right, else A: down-left / up-right
+    const int dxn = vt ? 0 : -1;                       // negative-side neighbour (dxn, dyn), positive (-dxn, -dyn)
+    const uint8_t *rn = hz ? rowc : (vt || dg ? rowu : rowd);
+    const uint8_t *rp = hz ? rowc : (vt || dg ? rowd : rowu);
+    const float mn = gstrength(rn + gcol_off(col + dxn));
+    const float mp = gstrength(rp + gcol_off(col - dxn));
     if (m > mn && m >= mp) {
-        const int col = p - LPX, row = y - Y0;
-        if (!CANNY_CHECK(row >= 0 && row < BAND && col >= 0 && col < OUT_W, err)) return;
-        atomicOr(&S.cand[row][col >> 5], 1u << (col & 31));
-        if (m > hi2) atomicOr(&S.strong[row][col >> 5], 1u << (col & 31));
-    }
-}
-
-// ---------------------------------------------------------------- phase 1
-// INTERIOR: every input row Y0 - 4 .. Y0 + BAND + 4 lies inside the image and
-// every lane's columns (and their halos) too, so the border and row-range
-// checks are compiled out.
-template <bool TMA, int BAND, bool INTERIOR>
-__device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const uint8_t *__restrict__ in,
-                                             int in_pitch, int w, int h, IntThresholds t, Smem<BAND> &S, int lane,
-                                             int X0, int Y0, uint32_t *err)
-{
-    constexpr int ITERS = Band<BAND>::ITERS, NCH = Band<BAND>::NCH;
-    const int xl = X0 - LPX + LPX * lane;     // image column of the lane's first pixel
-    const bool border = !INTERIOR && (xl <= 0 || xl + LPX >= w);
-    const bool out_lane = lane >= 1 && lane <= 28 && xl < w;
-    const int last = w - 1 - xl;               // index of the lane's last in-image pixel
-    const float lo2 = (float)min(t.lo2, 1 << 24), hi2 = (float)min(t.hi2, 1 << 24);
-    const bool direct_fast = !TMA && xl >= 0 && xl + LPX <= w &&
-                             ((((uintptr_t)in) | (uintptr_t)in_pitch | (uintptr_t)xl) & 7) == 0;
-    const int soff = min(LPX + LPX * lane, BOX - LPX);   // lane's bytes in a staged row
-
-    uint32_t rp[4] = {0, 0, 0, 0}, p1[4] = {0, 0, 0, 0}, p2[4] = {0, 0, 0, 0}, p3[4] = {0, 0, 0, 0};
-    float2 Sp[3][5];      // S by row slot (row mod 3), pairs (x_j, x_j+4), halo (x_-1, x_8)
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-#pragma unroll
-        for (int j = 0; j < 5; ++j) Sp[a][j] = f2(0.f, 0.f);
-    }
-    uint32_t cm_prev = 0;                     // candidate pixels of the previous row
-    uint32_t last0 = 0, last1 = 0;            // words of input row h-1, for rows below the image
-    uint32_t pf0[UNROLL], pf1[UNROLL];        // direct-load prefetch
-
-    auto direct_load = [&](int y, uint32_t &w0, uint32_t &w1) {
-        const uint8_t *row = in + (int64_t)(INTERIOR ? y : clampi(y, 0, h - 1)) * in_pitch;
-        if (direct_fast) {
-            uint2 v = __ldg(reinterpret_cast<const uint2 *>(row + xl));
-            w0 = v.x;
-            w1 = v.y;
-        } else {
-            uint32_t b[LPX];
-#pragma unroll
-            for (int k = 0; k < LPX; ++k) b[k] = __ldg(row + clampi(xl + k, 0, w - 1));
-            w0 = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
-            w1 = b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24);
-        }
-    };
-    auto issue_chunk = [&](int c) {           // lane 0 only
-        const int slot = c % STAGES;
-        mbar_expect_tx(&S.full[slot], CHUNK_BYTES);
-        tma_load_2d(&S.in[slot][0], tmap, X0 - 16, Y0 - 4 + c * CH, &S.full[slot]);
-    };
-
-    if (TMA) {
-        if (lane == 0)
-            for (int c = 0; c < STAGES && c < NCH; ++c) issue_chunk(c);
-    } else {
-#pragma unroll
-        for (int u = 0; u < UNROLL; ++u) direct_load(Y0 - 4 + u, pf0[u], pf1[u]);
-    }
-    bool failed = false;
-    auto wait_chunk = [&](int c) {
-        if (failed) return;
-        uint32_t n = 0;
-        while (!mbar_try_wait(&S.full[c % STAGES], (uint32_t)(c / STAGES) & 1u))
-            if (++n > WAIT_LIMIT) { failed = true; break; }
-        if (failed && lane == 0) atomicOr(err, 2u);
-    };
-
-    // ring slot (row mod RING) of strength row r = Y0 - 7 + g, kept incrementally,
-    // and slot (row mod SRING) of smoothed row Y0 - 6 + g (it alternates: g steps by 3)
-    int rsg = (((Y0 - 7) % RING) + RING) % RING;
-    int tsg = (((Y0 - 6) % SRING) + SRING) % SRING;
-    for (int g = 0; g < ITERS; g += UNROLL) {
-#pragma unroll
-        for (int u = 0; u < UNROLL; ++u) {
-            const int i = g + u;
-            const int yin = Y0 - 4 + i;          // input row of this iteration
-            const int s = yin - 2;               // smoothed row completed now
-            const int a = u % 3;                 // slot of row s
-            const int am1 = (u + 2) % 3, am2 = (u + 1) % 3;
-
-            // ---- the lane's 8 input bytes of row clamp(yin)
-            uint32_t w0, w1;
-            if (TMA) {
-                const int c = g / CH, off = u, slot = c % STAGES;
-                if (off == 0) {
-                    wait_chunk(c);
-                    if (!INTERIOR && yin < 0) wait_chunk(4 / CH);   // top band: row 0 is in that chunk
-                }
-                if (!INTERIOR && yin >= h) {
-                    w0 = last0;
-                    w1 = last1;
-                } else {
-                    // rows above the image repeat row 0, which sits in chunk 1 (yin = -4..-2) or 0
-                    const uint8_t *row = !INTERIOR && yin < 0 ? &S.in[(4 / CH) % STAGES][(4 % CH) * BOX]
-                                                              : &S.in[slot][off * BOX];
-                    if (!border) {
-                        const uint2 v = *reinterpret_cast<const uint2 *>(row + soff);
-                        w0 = v.x;
-                        w1 = v.y;
-                    } else {
-                        uint32_t b[LPX];
-#pragma unroll
-                        for (int k = 0; k < LPX; ++k)
-                            b[k] = row[clampi(clampi(xl + k, 0, w - 1) - (X0 - 16), 0, BOX - 1)];
-                        w0 = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
-                        w1 = b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24);
-                    }
-                    if (!INTERIOR && yin == h - 1) {
-                        last0 = w0;
-                        last1 = w1;
-                    }
-                }
-                if (off == CH - 1) {             // chunk consumed: refill its stage
-                    __syncwarp();
-                    if (lane == 0 && c + STAGES < NCH && !failed) {
-                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        issue_chunk(c + STAGES);
-                    }
-                }
-            } else {
-                w0 = pf0[u];
-                w1 = pf1[u];
-                if (i + UNROLL < ITERS) direct_load(yin + UNROLL, pf0[u], pf1[u]);
-            }
-
-            // ---- Step 1: vertical binomial cascade
-            uint32_t q[4];
-            q[0] = perm(w0, 0, 0x4240u);   // pixels (0, 2)
-            q[1] = perm(w0, 0, 0x4341u);   // pixels (1, 3)
-            q[2] = perm(w1, 0, 0x4240u);   // pixels (4, 6)
-            q[3] = perm(w1, 0, 0x4341u);   // pixels (5, 7)
-            uint32_t v[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const uint32_t n1 = rp[k] + q[k];
-                const uint32_t n2 = p1[k] + n1;
-                const uint32_t n3 = p2[k] + n2;
-                v[k] = p3[k] + n3;
-                rp[k] = q[k];
-                p1[k] = n1;
-                p2[k] = n2;
-                p3[k] = n3;
-            }
-            if (i < 4) continue;                 // cascade still filling (warp-uniform)
-
-            // ---- Step 1: horizontal binomial on the packed vertical sums
-            const uint32_t Lh = __shfl_up_sync(FULL, perm(v[2], v[3], 0x7632u), 1);   // (V-2, V-1)
-            const uint32_t Rh = __shfl_down_sync(FULL, perm(v[0], v[1], 0x5410u), 1); // (V8, V9)
-            const uint32_t A = perm(Lh, v[0], 0x5410u);   // (V-2, V0)
-            const uint32_t B = perm(Lh, v[1], 0x5432u);   // (V-1, V1)
-            const uint32_t C = perm(v[0], v[2], 0x5432u); // (V2, V4)
-            const uint32_t D = perm(v[1], v[3], 0x5432u); // (V3, V5)
-            const uint32_t F = perm(v[2], Rh, 0x5432u);   // (V6, V8)
-            const uint32_t G = perm(v[3], Rh, 0x7632u);   // (V7, V9)
-            const uint32_t he0 = A + C + BIAS + 4u * (B + v[1]) + 6u * v[0];   // (h0, h2)
-            const uint32_t ho0 = B + D + BIAS + 4u * (v[0] + C) + 6u * v[1];   // (h1, h3)
-            const uint32_t he1 = C + F + BIAS + 4u * (D + v[3]) + 6u * v[2];   // (h4, h6)
-            const uint32_t ho1 = D + G + BIAS + 4u * (v[2] + F) + 6u * v[3];   // (h5, h7)
-            // S as floats: 2^23 + byte from a byte permute, minus 2^23 (exact)
-            const float2 unbias = f2(-8388608.f, -8388608.f);
-            Sp[a][0] = __fadd2_rn(f2(sbyte(he0, 1), sbyte(he1, 1)), unbias);   // (S0, S4)
-            Sp[a][1] = __fadd2_rn(f2(sbyte(ho0, 1), sbyte(ho1, 1)), unbias);   // (S1, S5)
-            Sp[a][2] = __fadd2_rn(f2(sbyte(he0, 3), sbyte(he1, 3)), unbias);   // (S2, S6)
-            Sp[a][3] = __fadd2_rn(f2(sbyte(ho0, 3), sbyte(ho1, 3)), unbias);   // (S3, S7)
-            Sp[a][4] = f2(__shfl_up_sync(FULL, Sp[a][3].y, 1), __shfl_down_sync(FULL, Sp[a][0].x, 1));
-            {   // the row's smoothed bytes, for the candidates' gradients
-                int ts = tsg + u;
-                if (ts >= SRING) ts -= SRING;
-                *reinterpret_cast<uint2 *>(&S.srow[ts][LPX * lane]) =
-                    make_uint2(perm(he0, ho0, 0x7351u), perm(he1, ho1, 0x7351u));
-            }
-            if (border) {
-                // replicate border on S: S(-1) = S(0), S(x >= w) = S(w - 1)
-                if (xl == 0) Sp[a][4].x = Sp[a][0].x;
-                if (last < LPX + 1) {
-                    float sl = Sp[a][4].x;
-#pragma unroll
-                    for (int k = -1; k <= LPX; ++k) if (k == last) sl = pix(Sp[a], k);
-#pragma unroll
-                    for (int k = -1; k <= LPX; ++k) if (k > last) pix(Sp[a], k) = sl;
-                }
-            }
-            if (INTERIOR) {
-            } else if (s == 0) {                 // S(-1) = S(0)
-#pragma unroll
-                for (int j = 0; j < 5; ++j) Sp[am1][j] = Sp[a][j];
-            } else if (s >= h) {                 // S(h) = S(h - 1)
-#pragma unroll
-                for (int j = 0; j < 5; ++j) Sp[a][j] = Sp[am1][j];
-            }
-            if (i < 6) continue;
-
-            // ---- Step 2: Sobel and strength of row r = s-1 (slots am2, am1, a = rows r-1, r, r+1)
-            const int r = s - 1;
-            float2 E[5], CS[5];
-            const float2 two = f2(2.f, 2.f);
-#pragma unroll
-            for (int j = 0; j < 5; ++j) {
-                E[j] = sub2(Sp[a][j], Sp[am2][j]);                                     // S(r+1) - S(r-1)
-                CS[j] = __fadd2_rn(__ffma2_rn(Sp[am1][j], two, Sp[am2][j]), Sp[a][j]);  // column sums (<= 1020)
-            }
-            float2 gx[4], gy[4], m[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const float2 cl = j > 0 ? CS[j - 1] : f2(CS[4].x, CS[3].x);   // column sum at x-1
-                const float2 cr = j < 3 ? CS[j + 1] : f2(CS[0].y, CS[4].y);   // column sum at x+1
-                gx[j] = sub2(cr, cl);
-                const float2 el = j > 0 ? E[j - 1] : f2(E[4].x, E[3].x);   // E(x-1)
-                const float2 er = j < 3 ? E[j + 1] : f2(E[0].y, E[4].y);   // E(x+1)
-                gy[j] = __fadd2_rn(__ffma2_rn(E[j], two, el), er);
-                m[j] = __ffma2_rn(gx[j], gx[j], __fmul2_rn(gy[j], gy[j]));
-            }
-            if (!INTERIOR && (r < 0 || r >= h)) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) m[j] = f2(0.f, 0.f);
-            } else if (border) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    if (xl + j < 0 || j > last) m[j].x = 0.f;
-                    if (xl + j + 4 < 0 || j + 4 > last) m[j].y = 0.f;
-                }
-            }
-            // every row's strengths go to the ring (neighbours of later candidates)
-            int rs = rsg + u;
-            if (rs >= RING) rs -= RING;
-            float4 *mdst = reinterpret_cast<float4 *>(&S.m2[rs][LPX * lane]);
-            mdst[0] = make_float4(m[0].x, m[1].x, m[2].x, m[3].x);
-            mdst[1] = make_float4(m[0].y, m[1].y, m[2].y, m[3].y);
-            // queue the previous row's candidates now that its lower neighbour row exists
-            // (row offset u within this group's queued rows Y0 - 8 + g .. Y0 - 6 + g)
-            if (cm_prev && r - 1 >= Y0 && r - 1 < Y0 + BAND) {
-                uint32_t idx = atomicAdd(&S.qcount, (uint32_t)__popc(cm_prev));
-#pragma unroll
-                for (int k = 0; k < LPX; ++k)      // static indices keep gprev in registers
-                    if ((cm_prev >> k) & 1u)
-                        if (CANNY_CHECK(idx < QCAP, err))
-                            S.queue[idx++] = (uint16_t)((LPX * lane + k) | (u << 8));
-            }
-            // which pixels are candidates
-            uint32_t cm = 0;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                cm |= (m[j].x > lo2 ? 1u : 0u) << j;
-                cm |= (m[j].y > lo2 ? 1u : 0u) << (j + 4);
-            }
-            cm_prev = out_lane ? cm : 0u;
-        }
-        // ---- Step 3 + thresholds for the queued pixels (their rows +-1 are in the ring)
-        __syncwarp();
-        const uint32_t n = S.qcount;
-        const int sb = rsg == 0 ? RING - 1 : rsg - 1;   // slot of row Y0 - 8 + g
-        const int tb = tsg >= 3 ? tsg - 3 : tsg + 3;    // slot of row Y0 - 9 + g
-        for (uint32_t j = lane; j < n && CANNY_CHECK(j < QCAP, err); j += 32)
-            suppress_pixel<BAND, INTERIOR>(S, S.queue[j], sb, tb, Y0 - 8 + g, Y0, X0, w, h, hi2, err);
-        __syncwarp();
-        if (lane == 0) S.qcount = 0;
-        __syncwarp();
-        rsg += UNROLL;
-        if (rsg >= RING) rsg -= RING;
-        tsg = tsg >= 3 ? tsg - 3 : tsg + 3;
+        const int oc = col - LPX;                      // output column in the strip
+        if (!CANNY_CHECK(oc >= 0 && oc < OUT_W && trow >= 0 && trow < CROWS, err)) return;
+        atomicOr(&S.cand[trow][oc >> 5], 1u << (oc & 31));
+        if (m > hi2) atomicOr(&S.strong[trow][oc >> 5], 1u << (oc & 31));
     }
 }
 
@@ -469,12 +239,397 @@ struct Unit {
     bool tma;
 };
 
-// A unit away from every image border: input rows Y0 - 4 .. Y0 + BAND + 4 and
-// the columns of all 32 lanes with their halos (X0 - 16 .. X0 + 247) in the image.
-template <int BAND>
-__device__ __forceinline__ bool interior_unit(const Unit &U)
+// Where a unit's results go.
+struct Out {
+    uint8_t *map;              // class map (MODE_CLASSMAP) or edge map
+    int pitch;
+    HystScratch hs;
+    HystImage img;
+};
+
+// The tile row t (32 rows) of the unit is classified: flood its 15 tiles and write
+// edges and tile state, or write the class bytes; then clear the bitmask rows.
+// Row y of the tile row sits in bitmask row (32 t + y) mod CROWS.
+template <int BAND, int MODE>
+__device__ __forceinline__ void finish_tile_row(Smem &S, const Unit &U_, const Out &O, int t, int lane)
 {
-    return U.X0 >= 16 && U.X0 + 248 <= U.w && U.Y0 >= 4 && U.Y0 + BAND + 4 < U.h;
+    __syncwarp();
+    const int brow = (HT * t + lane) % CROWS;
+    if (MODE == MODE_CLASSMAP) {
+        const int y = U_.Y0 + t * HT + lane;
+#pragma unroll 1
+        for (int txl = 0; txl < TILES_X; ++txl) {
+            const int x = U_.X0 + HT * txl;
+            const uint32_t c = S.cand[brow][txl], sg = S.strong[brow][txl];
+            S.cand[brow][txl] = 0u;
+            S.strong[brow][txl] = 0u;
+            if (y >= U_.h || x >= U_.w) continue;
+            uint32_t wd[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) wd[q] = nib01(c >> (4 * q)) + nib01(sg >> (4 * q));
+            uint8_t *dst = O.map + (int64_t)y * O.pitch + x;
+            if (x + 32 <= U_.w) {
+                tile::store32(dst, wd);
+            } else {
+                for (int b = 0; b < 32 && x + b < U_.w; ++b) dst[b] = (uint8_t)((wd[b >> 2] >> (8 * (b & 3))) & 0xFF);
+            }
+        }
+    } else {
+        constexpr int TILES_Y = Band<BAND>::TILES_Y;
+        const int ty = U_.sy * TILES_Y + t;
+        if (ty >= O.img.nty) {
+            for (int txl = 0; txl < TILES_X; ++txl) S.cand[brow][txl] = S.strong[brow][txl] = 0u;
+            __syncwarp();
+            return;
+        }
+        // a tile row of whole tiles in 16-byte aligned output rows: empty tiles take two zero stores a row
+        const int y = ty * HT + lane;
+        const bool fast = ((((uintptr_t)O.img.map) | (uintptr_t)O.img.pitch) & 15) == 0 && (ty + 1) * HT <= O.img.h;
+        uint8_t *orow = O.img.map + (int64_t)min(y, O.img.h - 1) * O.img.pitch;
+#pragma unroll 1
+        for (int txl = 0; txl < TILES_X; ++txl) {
+            const int tx = U_.sx * TILES_X + txl;
+            const uint32_t cand = S.cand[brow][txl], strong = S.strong[brow][txl];
+            S.cand[brow][txl] = 0u;
+            S.strong[brow][txl] = 0u;
+            if (tx >= O.img.ntx) continue;                              // warp-uniform
+            const uint32_t tid = O.img.tile_base + (uint32_t)ty * (uint32_t)O.img.ntx + (uint32_t)tx;
+            if (!__any_sync(FULL, cand != 0u)) {
+                // nothing above the low threshold: zeros, empty border masks, not queued
+                if (fast && (tx + 1) * HT <= O.img.w) {
+                    uint4 *p = reinterpret_cast<uint4 *>(orow + tx * HT);
+                    p[0] = make_uint4(0u, 0u, 0u, 0u);
+                    p[1] = make_uint4(0u, 0u, 0u, 0u);
+                } else {
+                    tile::store_row(O.img, tx, ty, lane, 0u);
+                }
+                if (lane == 0 && CANNY_CHECK(tid < O.hs.max_tiles, &O.hs.state->error)) {
+                    O.hs.masks[tid] = TileMasks{};
+                    O.hs.stamp[tid] = 0u;
+                }
+                continue;
+            }
+            // every candidate strong: nothing to grow
+            const uint32_t e = __all_sync(FULL, cand == strong) ? cand : tile::flood_tile(strong, cand, lane);
+            tile::store_row(O.img, tx, ty, lane, e);
+            tile::finish_tile(O.hs, tid, e, cand, lane);
+        }
+    }
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------- the band loop
+// INTERIOR: every input row Y0 - 4 .. Y0 + BAND + 3 lies inside the image and
+// every lane's columns too, so the border and row-range checks are compiled out.
+template <bool TMA, int BAND, bool INTERIOR, int MODE>
+__device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const Unit &U_, IntThresholds t, const Out &O,
+                                             Smem &S, int lane, uint32_t pbase, uint32_t *err)
+{
+    constexpr int GROUPS = Band<BAND>::GROUPS;
+    const int w = U_.w, h = U_.h, X0 = U_.X0, Y0 = U_.Y0;
+    const int xl = X0 - LPX + LPX * lane;       // image column of the lane's first pixel
+    const bool border = !INTERIOR && (xl < 0 || xl + LPX > w);
+    const bool out_lane = lane >= 1 && lane <= OUT_LANES;
+    const int e_last = w - 1 - xl;               // lane pixel holding column w - 1 (if 0..15)
+    const float lo2 = (float)min(t.lo2, 1 << 24), hi2 = (float)min(t.hi2, 1 << 24);
+    // candidate test threshold: largest fp16 at most lo2 (1 - 2^-9) - 1, in [0.5, 65504]
+    uint32_t negL;
+    {
+        const float L = fminf(fmaxf((float)t.lo2 * (1.f - 1.f / 512.f) - 1.f, 0.5f), 65504.f);
+        const uint32_t hb = (uint32_t)__half_as_ushort(__float2half_rd(L)) | 0x8000u;   // -L'
+        negL = hb | (hb << 16);
+    }
+
+    // Row state as 3-slot rings indexed by iteration mod 3 (= u: a group is 3 rows),
+    // so no value is ever copied: input rows (pairs E_0..3, O_0..3), first-stage
+    // vertical sums a, and Sobel's Dx and T of the smoothed rows.
+    static_assert(U == 3, "the row rings below have 3 slots");
+    uint32_t rq[3][8], ra[3][8], dx[3][8], tb[3][8];
+#pragma unroll
+    for (int z = 0; z < 3; ++z)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) rq[z][j] = ra[z][j] = dx[z][j] = tb[z][j] = 0u;
+    uint32_t last[4] = {0u, 0u, 0u, 0u};         // words of input row h-1, for rows below the image
+    uint32_t mk[U] = {};                         // flag words of a group's candidate rows
+    uint32_t carry = 0u;
+    int next_tile = 0;                           // next tile row to finish
+
+    auto issue_chunk = [&](int c) {              // lane 0 only
+        const int slot = c % STAGES;
+        const int y = Y0 - 4 + c * CH;
+        mbar_expect_tx(&S.full[slot], CHUNK_BYTES);
+        tma_load_2d(&S.in[slot][0][0][0], tmap, X0 - LPX, y, &S.full[slot]);
+        tma_load_2d(&S.in[slot][1][0][0], tmap, X0 - LPX + BOX, y, &S.full[slot]);
+    };
+    bool failed = false;
+    auto wait_chunk = [&](int c) {
+        if (failed) return;
+        uint32_t n = 0;
+        const uint32_t parity = ((uint32_t)(c / STAGES) + pbase) & 1u;
+        while (!mbar_try_wait(&S.full[c % STAGES], parity))
+            if (++n > WAIT_LIMIT) { failed = true; break; }
+        if (failed && lane == 0) atomicOr(err, 2u);
+    };
+    if (TMA && lane == 0)
+        for (int c = 0; c < STAGES && c < GROUPS; ++c) issue_chunk(c);
+
+    // rows above the image repeat row 0: input row index 4 = chunk 4 / CH, row 4 % CH
+    constexpr int ROW0_CHUNK = 4 / CH, ROW0_OFF = 4 % CH;
+    static_assert(ROW0_CHUNK < STAGES, "row 0 of the top band must be in flight with chunk 0");
+    int gsl = 0;                                  // gradient-ring slot of the next Sobel row
+#pragma unroll 1
+    for (int g = 0; g < GROUPS; ++g) {
+        if (TMA) {
+            wait_chunk(g);
+            if (!INTERIOR && Y0 == 0 && g < ROW0_CHUNK) wait_chunk(ROW0_CHUNK);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = g * U + u;
+            const int yin = Y0 - 4 + i;           // input row of this iteration
+            const int s = yin - 2;                // smoothed row completed now
+            const int r = s - 1;                  // Sobel row completed now
+
+            // ---- the lane's 16 input bytes of row clamp(yin)
+            uint32_t wd[4];
+            if (!INTERIOR && yin >= h) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) wd[k] = last[k];
+            } else if (TMA) {
+                const bool above = !INTERIOR && yin < 0;
+                const int slot = above ? ROW0_CHUNK % STAGES : g % STAGES, ru = above ? ROW0_OFF : u;
+                if (!border) {
+                    const uint4 v = *reinterpret_cast<const uint4 *>(&S.in[slot][lane >> 4][ru][(lane & 15) * LPX]);
+                    wd[0] = v.x; wd[1] = v.y; wd[2] = v.z; wd[3] = v.w;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        uint32_t b[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int col = clampi(xl + 4 * k + e, 0, w - 1) - (X0 - LPX);
+                            b[e] = S.in[slot][col >> 8][ru][col & 255];
+                        }
+                        wd[k] = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
+                    }
+                }
+            } else {
+                const uint8_t *rowp = U_.in + (int64_t)(INTERIOR ? yin : clampi(yin, 0, h - 1)) * U_.in_pitch;
+                if (!border && ((((uintptr_t)(rowp + xl)) & 15) == 0)) {
+                    const uint4 v = __ldg(reinterpret_cast<const uint4 *>(rowp + xl));
+                    wd[0] = v.x; wd[1] = v.y; wd[2] = v.z; wd[3] = v.w;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        uint32_t b[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) b[e] = __ldg(rowp + clampi(xl + 4 * k + e, 0, w - 1));
+                        wd[k] = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
+                    }
+                }
+            }
+            if (!INTERIOR && yin == h - 1) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) last[k] = wd[k];
+            }
+
+            // ---- Step 1, vertical: (1,2,1) on input rows -> a(yin-1), on a -> V(yin-2)
+            const int z0 = u, z1 = (u + 2) % 3, z2 = (u + 1) % 3;       // slots of iterations i, i-1, i-2
+            uint32_t v[8];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                rq[z0][k] = perm(wd[k], 0u, 0x4240u);
+                rq[z0][k + 4] = perm(wd[k], 0u, 0x4341u);
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                ra[z0][j] = rq[z2][j] + 2u * rq[z1][j] + rq[z0][j];        // <= 1020 per 16-bit lane
+                v[j] = ra[z2][j] + 2u * ra[z1][j] + ra[z0][j];             // <= 4080
+            }
+            if (i < 4) continue;                  // vertical window still filling (warp-uniform)
+
+            // ---- Step 1, horizontal binomial; V(x) pairs E = v[0..3], O = v[4..7]
+            const uint32_t Rh = __shfl_down_sync(FULL, perm(v[0], v[4], 0x5410u), 1);   // (V16, V17)
+            const uint32_t Lh = __shfl_up_sync(FULL, perm(v[3], v[7], 0x7632u), 1);     // (V-2, V-1)
+            uint32_t SE[4], SO[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t A = k ? perm(v[k - 1], v[k], 0x5432u) : perm(Lh, v[0], 0x5410u);      // (V4k-2, V4k)
+                const uint32_t B = k ? perm(v[k + 3], v[k + 4], 0x5432u) : perm(Lh, v[4], 0x5432u);  // (V4k-1, V4k+1)
+                const uint32_t C = k < 3 ? perm(v[k], v[k + 1], 0x5432u) : perm(v[3], Rh, 0x5432u);  // (V4k+2, V4k+4)
+                const uint32_t D = k < 3 ? perm(v[k + 4], v[k + 5], 0x5432u) : perm(v[7], Rh, 0x7632u); // (V4k+3, V4k+5)
+                const uint32_t he = A + C + BIAS + 4u * (B + v[k + 4]) + 6u * v[k];   // (h4k, h4k+2)
+                const uint32_t ho = B + D + BIAS + 4u * (v[k] + C) + 6u * v[k + 4];   // (h4k+1, h4k+3)
+                // S = h >> 8 as fp16 1024 + S: the high byte of each lane under exponent byte 0x64
+                SE[k] = perm(he, H1024, 0x7351u);
+                SO[k] = perm(ho, H1024, 0x7351u);
+            }
+            // replicate border on S at the right image edge: S(w) = S(w - 1)
+            if (border && e_last >= 0 && e_last < LPX - 1) {
+#pragma unroll
+                for (int p = 0; p < LPX - 1; ++p)
+                    if (p == e_last) set_px(SE, SO, p + 1, get_px(SE, SO, p));
+            }
+
+            // ---- Step 2: Sobel. Dx = S(x+1) - S(x-1); T = S(x-1) + 2 S(x) + S(x+1) + 1024
+            const uint32_t SLw = __shfl_up_sync(FULL, SO[3], 1);    // left lane's (S13, S15): hi = S(-1)
+            const uint32_t SRw = __shfl_down_sync(FULL, SE[0], 1);  // right lane's (S0, S2): lo = S(16)
+            uint32_t DX[8], TB[8];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                uint32_t SB = k ? perm(SO[k - 1], SO[k], 0x5432u) : perm(SLw, SO[0], 0x5432u);   // (S4k-1, S4k+1)
+                uint32_t SC = k < 3 ? perm(SE[k], SE[k + 1], 0x5432u) : perm(SE[3], SRw, 0x5432u); // (S4k+2, S4k+4)
+                if (!INTERIOR) {
+                    if (k == 0 && xl == 0) SB = perm(SE[0], SO[0], 0x5410u);               // S(-1) = S(0)
+                    if (k == 3 && e_last == LPX - 1) SC = perm(SE[3], SO[3], 0x7632u);     // S(w) = S(w-1)
+                }
+                dx[z0][k] = hsub2(SO[k], SB);
+                dx[z0][k + 4] = hsub2(SC, SE[k]);
+                tb[z0][k] = hadd2(hadd2(hfma2(SE[k], HTWO, HM3072), SB), SO[k]);
+                tb[z0][k + 4] = hadd2(hadd2(hfma2(SO[k], HTWO, HM3072), SE[k]), SC);
+            }
+            if (!INTERIOR && s == h) {            // S(h) = S(h - 1)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) { dx[z0][j] = dx[z1][j]; tb[z0][j] = tb[z1][j]; }
+            }
+            uint32_t gx[8], gy[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                gx[j] = hadd2(hfma2(dx[z1][j], HTWO, dx[z2][j]), dx[z0][j]);   // Dx(r-1) + 2 Dx(r) + Dx(r+1)
+                gy[j] = hsub2(tb[z0][j], tb[z2][j]);                           // T(r+1) - T(r-1)
+            }
+            if (!INTERIOR && s == 0) {            // S(-1) = S(0) for the next row's Sobel
+#pragma unroll
+                for (int j = 0; j < 8; ++j) { dx[z1][j] = dx[z0][j]; tb[z1][j] = tb[z0][j]; }
+            }
+            if (i < 6) continue;                  // Sobel rows start at Y0 - 1 (warp-uniform)
+
+            // ---- outside the image the strengths are 0
+            if (!INTERIOR) {
+                if (r < 0 || r >= h) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) gx[j] = gy[j] = 0u;
+                } else if (border) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int p0 = 4 * (j & 3) + (j >> 2), p1 = p0 + 2;   // pixels of pair j
+                        const uint32_t keep = (xl + p0 >= 0 && p0 <= e_last ? 0x0000FFFFu : 0u) |
+                                              (xl + p1 >= 0 && p1 <= e_last ? 0xFFFF0000u : 0u);
+                        gx[j] &= keep;
+                        gy[j] &= keep;
+                    }
+                }
+            }
+            uint8_t *grow = S.g[gsl];
+            *reinterpret_cast<uint4 *>(grow + 0 * GHALF + lane * 16) = make_uint4(gx[0], gx[1], gx[2], gx[3]);
+            *reinterpret_cast<uint4 *>(grow + 1 * GHALF + lane * 16) = make_uint4(gx[4], gx[5], gx[6], gx[7]);
+            *reinterpret_cast<uint4 *>(grow + 2 * GHALF + lane * 16) = make_uint4(gy[0], gy[1], gy[2], gy[3]);
+            *reinterpret_cast<uint4 *>(grow + 3 * GHALF + lane * 16) = make_uint4(gy[4], gy[5], gy[6], gy[7]);
+            gsl = gsl == GRING - 1 ? 0 : gsl + 1;
+
+            // ---- candidates: Gx^2 + Gy^2 - L' >= 0 in fp16 (sign bit clear)
+            uint32_t acc = 0u;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t de = hfma2(gx[k], gx[k], hfma2(gy[k], gy[k], negL));
+                const uint32_t dd = hfma2(gx[k + 4], gx[k + 4], hfma2(gy[k + 4], gy[k + 4], negL));
+                const uint32_t wq = perm(de, dd, 0x7351u);   // sign bytes of pixels 4k, 4k+1, 4k+2, 4k+3
+                if (k == 0) acc = wq;
+                else {
+                    const uint32_t sel = (0xFF00u >> k) & 0xFFu;
+                    const uint32_t c = sel * 0x01010101u;    // bits 7 .. 8-k of each byte keep acc
+                    acc = (acc & c) | ((wq >> k) & ~c);
+                }
+            }
+            uint32_t m = ~acc & 0xF0F0F0F0u;
+            const bool in_band = INTERIOR ? (i >= 7 && i < BAND + 7) : (i >= 7 && i < BAND + 7 && r < h);
+            if (!in_band || !out_lane) m = 0u;
+            if (u < U - 1) mk[u + 1] = m;
+            else carry = m;
+        }
+
+        // ---- refill the stage this group consumed
+        if (TMA) {
+            __syncwarp();
+            if (lane == 0 && g + STAGES < GROUPS && !failed) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue_chunk(g + STAGES);
+            }
+        }
+
+        // ---- Step 3 + thresholds for the flagged pixels of rows R .. R+U-1 (R = Y0 + U g - 8)
+        const int R = Y0 + U * g - 8;
+        __syncwarp();
+        uint32_t anyf = 0u;
+#pragma unroll
+        for (int rr = 0; rr < U; ++rr) anyf |= mk[rr];
+        if (g >= 2 && __any_sync(FULL, anyf != 0u)) {
+            // ring slot of row R: rows Y0-1+k sit in slot k mod GRING and gsl follows row R+U
+            const int slotR = gsl == GRING - 1 ? 0 : gsl + 1;
+            uint32_t pre[U];                      // flags of this lane in rows before rr, inclusive of rr
+            uint32_t cnt = 0u;
+#pragma unroll
+            for (int rr = 0; rr < U; ++rr) {
+                pre[rr] = (rr ? pre[rr - 1] : 0u) + __popc(mk[rr]);
+                if (rr < U - 1) cnt |= pre[rr] << (8 * rr);
+            }
+            const uint32_t cl = pre[U - 1];
+            uint32_t incl = cl;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t o = __shfl_up_sync(FULL, incl, d);
+                if (lane >= d) incl += o;
+            }
+            const uint32_t n = __shfl_sync(FULL, incl, 31);
+#pragma unroll 1
+            for (uint32_t base = 0; base < n; base += 32) {
+                // flagged pixel j of the warp (in lane, row, pixel order) goes to lane j - base;
+                // its owner is the first lane whose inclusive count exceeds j
+                const uint32_t j = base + lane;
+                int own = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1)
+                    if (__shfl_sync(FULL, incl, own + step - 1) <= j) own += step;
+                const uint32_t o_excl = __shfl_sync(FULL, incl - cl, own);
+                const uint32_t o_cnt = __shfl_sync(FULL, cnt, own);
+                uint32_t om[U];
+#pragma unroll
+                for (int rr = 0; rr < U; ++rr) om[rr] = __shfl_sync(FULL, mk[rr], own);
+                if (j < n) {
+                    uint32_t k = j - o_excl, mw = om[0], kbase = 0u;
+                    int rr = 0;
+#pragma unroll
+                    for (int q = 1; q < U; ++q) {
+                        const uint32_t bq = (o_cnt >> (8 * (q - 1))) & 255u;
+                        if (k >= bq) { rr = q; mw = om[q]; kbase = bq; }
+                    }
+                    const int col = own * LPX + flag_px(nth_flag(mw, k - kbase));
+                    int sc = slotR + rr;
+                    if (sc >= GRING) sc -= GRING;
+                    const int su = sc == 0 ? GRING - 1 : sc - 1, sd = sc == GRING - 1 ? 0 : sc + 1;
+                    suppress_pixel(S, col, S.g[sc], S.g[su], S.g[sd], (R + rr - Y0) % CROWS, lo2, hi2, err);
+                }
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int rr = 0; rr < U - 1; ++rr) mk[rr] = 0u;
+        mk[0] = carry;
+
+        // ---- Step 4, tile-local: once the last row of a tile row is classified
+        if (next_tile < Band<BAND>::TILES_Y && R + U - 1 >= Y0 + HT * next_tile + HT - 1) {
+            finish_tile_row<BAND, MODE>(S, U_, O, next_tile, lane);
+            ++next_tile;
+        }
+    }
+}
+
+// A unit away from every image border: input rows Y0 - 4 .. Y0 + BAND + 3 and
+// the columns of all 32 lanes (X0 - 16 .. X0 + 495) in the image.
+template <int BAND>
+__device__ __forceinline__ bool interior_unit(const Unit &U_)
+{
+    return U_.X0 >= LPX && U_.X0 + OUT_W + LPX <= U_.w && U_.Y0 >= 4 && U_.Y0 + BAND + 4 <= U_.h;
 }
 
 // PATH: 0 = per unit (U.tma), 1 = TMA only, 2 = direct loads only. A kernel that
@@ -484,74 +639,37 @@ enum { PATH_EITHER = 0, PATH_TMA = 1, PATH_DIRECT = 2 };
 
 // SPLIT: interior units take the stencil compiled without border checks. The
 // batch kernel, whose units are mostly border units of small images, holds the
-// general stencil alone (two copies of the loop in one kernel cost it more in
-// instruction fetch than the interior units gain).
+// general stencil alone.
 template <int BAND, int MODE, int PATH, bool SPLIT>
-__device__ __forceinline__ void run_unit(const CUtensorMap *tmap, const Unit &U, IntThresholds t, uint8_t *out,
-                                         int out_pitch, const HystScratch &hs, const HystImage &img, uint32_t *err,
-                                         Smem<BAND> &S, int lane)
+__device__ __forceinline__ void run_unit(const CUtensorMap *tmap, const Unit &U_, IntThresholds t, const Out &O,
+                                         uint32_t pbase, uint32_t *err, Smem &S, int lane)
 {
-    constexpr int TILES_Y = Band<BAND>::TILES_Y;
-    for (int k = lane; k < BAND * MW; k += THREADS) {
+    for (int k = lane; k < CROWS * TILES_X; k += THREADS) {
         (&S.cand[0][0])[k] = 0u;
         (&S.strong[0][0])[k] = 0u;
     }
-    if (lane == 0) S.qcount = 0;
     __syncwarp();
-    if (PATH == PATH_TMA || (PATH == PATH_EITHER && U.tma)) {
+    if (PATH == PATH_TMA || (PATH == PATH_EITHER && U_.tma)) {
         // the previous unit's reads of the stage buffers are done before TMA reuses them
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         if constexpr (PATH != PATH_DIRECT) {
-            if (SPLIT && interior_unit<BAND>(U))
-                stencil_band<true, BAND, true>(tmap, U.in, U.in_pitch, U.w, U.h, t, S, lane, U.X0, U.Y0, err);
+            if (SPLIT && interior_unit<BAND>(U_))
+                stencil_band<true, BAND, true, MODE>(tmap, U_, t, O, S, lane, pbase, err);
             else
-                stencil_band<true, BAND, false>(tmap, U.in, U.in_pitch, U.w, U.h, t, S, lane, U.X0, U.Y0, err);
+                stencil_band<true, BAND, false, MODE>(tmap, U_, t, O, S, lane, pbase, err);
         }
     } else {
         if constexpr (PATH != PATH_TMA) {
-            if (SPLIT && interior_unit<BAND>(U))
-                stencil_band<false, BAND, true>(tmap, U.in, U.in_pitch, U.w, U.h, t, S, lane, U.X0, U.Y0, err);
+            if (SPLIT && interior_unit<BAND>(U_))
+                stencil_band<false, BAND, true, MODE>(tmap, U_, t, O, S, lane, pbase, err);
             else
-                stencil_band<false, BAND, false>(tmap, U.in, U.in_pitch, U.w, U.h, t, S, lane, U.X0, U.Y0, err);
-        }
-    }
-    __syncwarp();
-
-    if (MODE == MODE_CLASSMAP) {
-        // class byte = weak bit + strong bit
-        for (int k = lane; k < BAND * MW; k += THREADS) {
-            const int row = k / MW, wj = k % MW;
-            const int y = U.Y0 + row, x = U.X0 + 32 * wj;
-            if (y >= U.h || x >= U.w) continue;
-            const uint32_t c = S.cand[row][wj], sgl = S.strong[row][wj];
-            uint32_t wd[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) wd[q] = nib01(c >> (4 * q)) + nib01(sgl >> (4 * q));
-            uint8_t *dst = out + (int64_t)y * out_pitch + x;
-            if (x + 32 <= U.w) {
-                tile::store32(dst, wd);
-            } else {
-                for (int b = 0; b < 32 && x + b < U.w; ++b) dst[b] = (uint8_t)((wd[b >> 2] >> (8 * (b & 3))) & 0xFF);
-            }
-        }
-    } else {
-        // Step 4, tile-local: flood fill each of the unit's 7 x BAND/32 tiles from its bitmasks
-        for (int tl = 0; tl < TILES_X * TILES_Y; ++tl) {
-            const int txl = tl % TILES_X, tyl = tl / TILES_X;
-            const int tx = U.sx * TILES_X + txl, ty = U.sy * TILES_Y + tyl;
-            if (tx >= img.ntx || ty >= img.nty) continue;         // warp-uniform
-            const uint32_t cand = S.cand[tyl * HT + lane][txl];
-            const uint32_t strong = S.strong[tyl * HT + lane][txl];
-            const uint32_t e = tile::flood_tile(strong, cand, lane);
-            tile::store_row(img, tx, ty, lane, e);
-            tile::finish_tile(hs, img.tile_base + (uint32_t)ty * (uint32_t)img.ntx + (uint32_t)tx, e, cand, lane);
+                stencil_band<false, BAND, false, MODE>(tmap, U_, t, O, S, lane, pbase, err);
         }
     }
     __syncwarp();
 }
 
-template <int BAND>
-__device__ __forceinline__ void init_barriers(Smem<BAND> &S, int lane)
+__device__ __forceinline__ void init_barriers(Smem &S, int lane)
 {
     if (lane == 0) {
         for (int k = 0; k < STAGES; ++k) mbar_init(&S.full[k], 1);
@@ -563,36 +681,41 @@ __device__ __forceinline__ void init_barriers(Smem<BAND> &S, int lane)
 // ---------------------------------------------------------------- kernels
 // One image: one CTA per unit (blockIdx.x = strip, blockIdx.y = band, reordered).
 template <int BAND, int MODE, int PATH>
-__global__ void __launch_bounds__(THREADS, BAND == 64 ? 16 : 12)
+__global__ void __launch_bounds__(THREADS, 12)
 k1_fused_kernel(const __grid_constant__ CUtensorMap tmap, const uint8_t *__restrict__ in, int in_pitch,
                 int w, int h, IntThresholds t, uint8_t *__restrict__ out, int out_pitch,
                 HystScratch hs, HystImage img, uint32_t *err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    Smem<BAND> &S = *reinterpret_cast<Smem<BAND> *>(smem_raw);
+    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
     const int lane = threadIdx.x;
     init_barriers(S, lane);
-    Unit U;
-    U.in = in;
-    U.in_pitch = in_pitch;
-    U.w = w;
-    U.h = h;
-    U.sx = blockIdx.x;
+    Unit U_;
+    U_.in = in;
+    U_.in_pitch = in_pitch;
+    U_.w = w;
+    U_.h = h;
+    U_.sx = blockIdx.x;
     // the bottom band row (border units, the slower stencil) starts right after
     // the top one instead of in the last wave: bands 0, nb - 1, 1, 2, ..., nb - 2
     const int nb = (int)gridDim.y, by = (int)blockIdx.y;
-    U.sy = by == 0 || nb < 3 ? by : (by == 1 ? nb - 1 : by - 1);
-    U.X0 = U.sx * OUT_W;
-    U.Y0 = U.sy * BAND;
-    U.tma = PATH == PATH_TMA;
-    run_unit<BAND, MODE, PATH, true>(&tmap, U, t, out, out_pitch, hs, img, err, S, lane);
+    U_.sy = by == 0 || nb < 3 ? by : (by == 1 ? nb - 1 : by - 1);
+    U_.X0 = U_.sx * OUT_W;
+    U_.Y0 = U_.sy * BAND;
+    U_.tma = PATH == PATH_TMA;
+    Out O;
+    O.map = out;
+    O.pitch = out_pitch;
+    O.hs = hs;
+    O.img = img;
+    run_unit<BAND, MODE, PATH, true>(&tmap, U_, t, O, 0u, err, S, lane);
 }
 
 // One (image, strip, band) unit of a batch.
 template <int BAND, int PATH>
 __device__ __forceinline__ void batch_unit(const BatchImage *__restrict__ imgs, const CUtensorMap *__restrict__ tmaps,
                                            int nimg, uint32_t unit, IntThresholds t, const HystScratch &hs,
-                                           Smem<BAND> &S, int lane)
+                                           uint32_t pbase, Smem &S, int lane)
 {
     int lo = 0, hi = nimg - 1;                     // last image whose units start at or before unit
     while (lo < hi) {
@@ -602,51 +725,65 @@ __device__ __forceinline__ void batch_unit(const BatchImage *__restrict__ imgs, 
     }
     const BatchImage &B = imgs[lo];
     const uint32_t local = unit - B.unit_base;
-    Unit U;
-    U.in = B.in;
-    U.in_pitch = B.in_pitch;
-    U.w = B.img.w;
-    U.h = B.img.h;
-    U.sx = (int)(local % (uint32_t)B.nsx);
-    U.sy = (int)(local / (uint32_t)B.nsx);
-    U.X0 = U.sx * OUT_W;
-    U.Y0 = U.sy * BAND;
-    U.tma = PATH == PATH_TMA || B.tma != 0;
-    const HystImage img = B.img;
-    if (U.tma && lane == 0) {
+    Unit U_;
+    U_.in = B.in;
+    U_.in_pitch = B.in_pitch;
+    U_.w = B.img.w;
+    U_.h = B.img.h;
+    U_.sx = (int)(local % (uint32_t)B.nsx);
+    U_.sy = (int)(local / (uint32_t)B.nsx);
+    U_.X0 = U_.sx * OUT_W;
+    U_.Y0 = U_.sy * BAND;
+    U_.tma = PATH == PATH_TMA || B.tma != 0;
+    Out O;
+    O.img = B.img;
+    O.map = O.img.map;
+    O.pitch = O.img.pitch;
+    O.hs = hs;
+    if (U_.tma && lane == 0) {
         // the descriptor was rewritten in global memory since the TMA unit may
         // last have cached one at this address: order that write before its use
         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&tmaps[lo]) : "memory");
     }
     __syncwarp();
-    run_unit<BAND, MODE_EDGES, PATH, false>(&tmaps[lo], U, t, img.map, img.pitch, hs, img, &hs.state->error, S, lane);
+    run_unit<BAND, MODE_EDGES, PATH, false>(&tmaps[lo], U_, t, O, pbase, &hs.state->error, S, lane);
 }
 
 // A batch. PERSIST: a persistent grid pops units from a counter; otherwise the
 // grid has one CTA per unit (set per launch) and the hardware schedules them.
 // PATH_TMA when every input is TMA-readable, else PATH_EITHER (chosen per image).
 template <int BAND, int PATH, bool PERSIST>
-__global__ void __launch_bounds__(THREADS, BAND == 64 ? 16 : 12)
+__global__ void __launch_bounds__(THREADS, 12)
 k1_fused_batch_kernel(const BatchImage *__restrict__ imgs, const CUtensorMap *__restrict__ tmaps,
                       BatchHeader *hdr, IntThresholds t, HystScratch hs)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    Smem<BAND> &S = *reinterpret_cast<Smem<BAND> *>(smem_raw);
+    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
     const int lane = threadIdx.x;
     const uint32_t total = hdr->total_units;
     const int nimg = (int)hdr->nimg;
     if constexpr (!PERSIST) {
         if (blockIdx.x >= total) return;
         init_barriers(S, lane);
-        batch_unit<BAND, PATH>(imgs, tmaps, nimg, blockIdx.x, t, hs, S, lane);
+        batch_unit<BAND, PATH>(imgs, tmaps, nimg, blockIdx.x, t, hs, 0u, S, lane);
     } else {
         init_barriers(S, lane);
+        // each stage completes GROUPS / STAGES phases per TMA unit: track the parity
+        uint32_t pbase = 0u;
         for (;;) {
             uint32_t unit = 0;
             if (lane == 0) unit = atomicAdd(&hdr->next_unit, 1u);
             unit = __shfl_sync(FULL, unit, 0);
             if (unit >= total) break;
-            batch_unit<BAND, PATH>(imgs, tmaps, nimg, unit, t, hs, S, lane);
+            batch_unit<BAND, PATH>(imgs, tmaps, nimg, unit, t, hs, pbase, S, lane);
+            // a direct-load unit leaves the barriers untouched; the image decides
+            int lo = 0, hi = nimg - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (imgs[mid].unit_base <= unit) lo = mid;
+                else hi = mid - 1;
+            }
+            if (PATH == PATH_TMA || imgs[lo].tma != 0) pbase ^= (uint32_t)((Band<BAND>::GROUPS / STAGES) & 1);
         }
     }
 }
@@ -659,19 +796,19 @@ cudaError_t launch_single(const CUtensorMap &tmap, bool tma, const uint8_t *in, 
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k1_fused_kernel<BAND, MODE, PATH_TMA>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<BAND>));
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k1_fused_kernel<BAND, MODE, PATH_DIRECT>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<BAND>));
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
         if (e != cudaSuccess) return e;
         attr = true;
     }
     dim3 grid((w + OUT_W - 1) / OUT_W, (h + BAND - 1) / BAND);
     if (tma)
-        k1_fused_kernel<BAND, MODE, PATH_TMA><<<grid, THREADS, sizeof(Smem<BAND>), s>>>(
+        k1_fused_kernel<BAND, MODE, PATH_TMA><<<grid, THREADS, sizeof(Smem), s>>>(
             tmap, in, in_pitch, w, h, t, out, out_pitch, hs, img, err);
     else
-        k1_fused_kernel<BAND, MODE, PATH_DIRECT><<<grid, THREADS, sizeof(Smem<BAND>), s>>>(
+        k1_fused_kernel<BAND, MODE, PATH_DIRECT><<<grid, THREADS, sizeof(Smem), s>>>(
             tmap, in, in_pitch, w, h, t, out, out_pitch, hs, img, err);
     return cudaGetLastError();
 }
@@ -725,7 +862,7 @@ cudaError_t batch_node_params(const BatchImage *const &imgs, const CUtensorMap *
                               cudaKernelNodeParams *kp)
 {
     cudaError_t e = cudaFuncSetAttribute(k1_fused_batch_kernel<BAND, PATH, PERSIST>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<BAND>));
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
     if (e != cudaSuccess) return e;
     args[0] = (void *)&imgs;
     args[1] = (void *)&tmaps;
@@ -736,7 +873,7 @@ cudaError_t batch_node_params(const BatchImage *const &imgs, const CUtensorMap *
     kp->func = (void *)k1_fused_batch_kernel<BAND, PATH, PERSIST>;
     kp->gridDim = dim3(grid > 0 ? grid : 1u);
     kp->blockDim = dim3(THREADS);
-    kp->sharedMemBytes = sizeof(Smem<BAND>);
+    kp->sharedMemBytes = sizeof(Smem);
     kp->kernelParams = args;
     return cudaSuccess;
 }

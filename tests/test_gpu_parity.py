@@ -66,12 +66,12 @@ def test_small_workload_bit_exact():
     assert np.array_equal(cls, oracle.classify_u8(img))
 
 
-# Sizes at the edge of the interior test: a unit (strip X0 = 224 k, band
+# Sizes at the edge of the interior test: a unit (strip X0 = 480 k, band
 # Y0 = 64 j) runs the stencil without border checks only when X0 >= 16,
-# X0 + 248 <= w, Y0 >= 4 and Y0 + 68 < h. Each size puts one strip or band
+# X0 + 496 <= w, Y0 >= 4 and Y0 + 68 <= h. Each size puts one strip or band
 # exactly on either side of that line; all must stay bit-exact.
-@pytest.mark.parametrize("h,w", [(132, 472), (133, 472), (132, 471), (133, 473), (197, 696), (196, 697),
-                                 (261, 920), (260, 919), (69, 248), (68, 247)])
+@pytest.mark.parametrize("h,w", [(132, 976), (133, 976), (132, 975), (133, 977), (197, 1456), (196, 1457),
+                                 (261, 1936), (260, 1935), (69, 496), (68, 495), (132, 472), (133, 473)])
 def test_interior_unit_boundaries(h, w):
     img = blocky_image(h * 3 + w, h, w)
     out, st = run_int(img)

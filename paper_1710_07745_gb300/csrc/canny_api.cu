@@ -197,7 +197,8 @@ canny_status ensure_hyst(canny_ctx *c, uint32_t max_tiles, uint32_t max_imgs)
     size_t off_pend = align_up(off_masks + sizeof(TileMasks) * max_tiles, 256);
     size_t off_stamp = align_up(off_pend + sizeof(uint32_t) * HT * (size_t)max_tiles, 256);
     size_t off_lists = align_up(off_stamp + sizeof(uint32_t) * (size_t)max_tiles, 256);
-    size_t off_state = align_up(off_lists + sizeof(uint32_t) * 2 * (size_t)max_tiles, 256);
+    size_t off_bits = align_up(off_lists + sizeof(uint32_t) * 2 * (size_t)max_tiles, 256);
+    size_t off_state = align_up(off_bits + sizeof(uint32_t) * 2 * HT * (size_t)max_tiles, 256);
     size_t total = align_up(off_state + sizeof(HystState), 256);
     void *mem = nullptr;
     cudaError_t e = dev_alloc(&mem, total);
@@ -212,6 +213,7 @@ canny_status ensure_hyst(canny_ctx *c, uint32_t max_tiles, uint32_t max_imgs)
     c->hs.pend_bits = (uint32_t *)(b + off_pend);
     c->hs.stamp = (uint32_t *)(b + off_stamp);
     c->hs.lists = (uint32_t *)(b + off_lists);
+    c->hs.bits = (uint32_t *)(b + off_bits);
     c->hs.state = (HystState *)(b + off_state);
     c->hs.max_tiles = max_tiles;
     c->hs.max_imgs = max_imgs;
@@ -529,7 +531,9 @@ canny_status build_batch_graph(canny_ctx *c, canny_ctx::Slot &sl, int v)
         e = k1_add_batch_node(g, d_k1, 3, c->band, v == 1, imgs, tmaps, hdr, c->it, c->hs,
                               c->ctas_per_sm > 0 ? sm_count() * c->ctas_per_sm : 0, &k1);
     sl.k1node[v] = k1;
-    if (e == cudaSuccess) e = hyst_add_loop(g, &k1, 1, c->hs, &loop);
+    cudaGraphNode_t fill;
+    if (e == cudaSuccess) e = hyst_add_fill(g, &k1, 1, c->hs, &fill);
+    if (e == cudaSuccess) e = hyst_add_loop(g, &fill, 1, c->hs, &loop);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&sl.exec[v], g, 0);
     if (e != cudaSuccess) {
         cudaGetLastError();

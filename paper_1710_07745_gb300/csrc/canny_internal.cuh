@@ -63,6 +63,8 @@ struct HystScratch {
     HystImage *imgs;          // [max_imgs]
     TileMasks *masks;         // [max_tiles]
     uint32_t *pend_bits;      // [max_tiles * 32]: weak-not-edge pixels, one word per tile row
+    uint32_t *bits;           // [max_tiles * 64]: the stencil's class bits per tile, rows 0..31
+                              // of class >= 1 (weak or strong), then rows 0..31 of class 2
     uint32_t *stamp;          // [max_tiles]: last pass a tile was queued for
     uint32_t *lists;          // [2 * max_tiles]
     HystState *state;
@@ -195,6 +197,14 @@ cudaError_t launch_k1f_nms(const void *maps, int w, int h, const FloatParams &fp
                            const HystScratch &hs, HystImage img, cudaStream_t s);
 
 // ---------------------------------------------------------------- launchers (hysteresis.cu)
+// Tile fill from the fused stencil's class bits (hs.bits): grows every tile's
+// strong pixels through its weak ones, writes 255/0 into img.map and the tile
+// state the global passes read (after hyst_reset).
+cudaError_t launch_hyst_fill_single(const HystScratch &hs, HystImage img, cudaStream_t s);
+// The same over every tile of a batch, as a graph node (tile count and images read
+// from the control block and hs.imgs when it runs).
+cudaError_t hyst_add_fill(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, const HystScratch &hs,
+                          cudaGraphNode_t *out);
 // Local fill over all tiles of one image whose class map is already in img.map.
 cudaError_t launch_hyst_local_single(const HystScratch &hs, HystImage img, cudaStream_t s);
 // Local fill over all tiles of the images already uploaded to hs.imgs.

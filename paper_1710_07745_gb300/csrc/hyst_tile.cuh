@@ -41,6 +41,47 @@ __device__ __forceinline__ uint32_t flood_tile(uint32_t e, uint32_t c, int lane)
     return e;
 }
 
+// fill_runs with the bit reversal of c computed once by the caller.
+__device__ __forceinline__ uint32_t fill_runs_r(uint32_t s, uint32_t c, uint32_t rc)
+{
+    uint32_t up = (c & ~(c + s)) | s;
+    uint32_t rs = __brev(s);
+    uint32_t dn = __brev((rc & ~(rc + rs)) | rs);
+    return up | dn;
+}
+
+// A row mask and its left and right neighbours.
+__device__ __forceinline__ uint32_t dilate(uint32_t x) { return x | (x << 1) | (x >> 1); }
+
+// Four tiles per warp: lane 8 t + s holds rows 4 s .. 4 s + 3 of tile t, as
+// e[0..3] (subsets of c[0..3]). Grows every tile's e through 8-connected pixels
+// of its c until no tile changes. A round fills each row's runs while sweeping
+// the lane's four rows down and back up, then passes the outer rows' neighbours
+// to the lanes above and below in the same tile, so a chain climbs several rows
+// per round. Every round that changes something adds a pixel, so at most
+// 4 x 1024 + 1 rounds run.
+__device__ __forceinline__ void flood4(uint32_t (&e)[4], const uint32_t (&c)[4], int sl)
+{
+    uint32_t rc[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) rc[r] = __brev(c[r]);
+    for (int it = 0; it < 4 * HT * HT + 2; ++it) {
+        const uint32_t o0 = e[0], o1 = e[1], o2 = e[2], o3 = e[3];
+        e[0] = fill_runs_r(e[0], c[0], rc[0]);
+#pragma unroll
+        for (int r = 1; r < 4; ++r) e[r] = fill_runs_r(e[r] | (c[r] & dilate(e[r - 1])), c[r], rc[r]);
+#pragma unroll
+        for (int r = 2; r >= 0; --r) e[r] = fill_runs_r(e[r] | (c[r] & dilate(e[r + 1])), c[r], rc[r]);
+        uint32_t a = __shfl_up_sync(FULL, dilate(e[3]), 1, 8);
+        uint32_t b = __shfl_down_sync(FULL, dilate(e[0]), 1, 8);
+        if (sl == 0) a = 0u;
+        if (sl == 7) b = 0u;
+        e[0] = fill_runs_r(e[0] | (c[0] & a), c[0], rc[0]);
+        e[3] = fill_runs_r(e[3] | (c[3] & b), c[3], rc[3]);
+        if (!__any_sync(FULL, ((e[0] ^ o0) | (e[1] ^ o1) | (e[2] ^ o2) | (e[3] ^ o3)) != 0u)) break;
+    }
+}
+
 // 4-bit mask of the nonzero bytes of w (bit k = byte k).
 __device__ __forceinline__ uint32_t nz_nibble(uint32_t w)
 {
@@ -128,6 +169,99 @@ __device__ __forceinline__ void store_row(const HystImage &im, int tx, int ty, i
 #pragma unroll
     for (int k = 0; k < 8; ++k) wd[k] = nibble_bytes(e >> (4 * k));
     store32(row, wd);
+}
+
+// Write image row y of tile column tx as 255 where e is set, 0 elsewhere.
+__device__ __forceinline__ void store_tile_row(const HystImage &im, int tx, int y, uint32_t e)
+{
+    const int x0 = tx * HT;
+    if (y >= im.h) return;
+    uint8_t *row = im.map + (int64_t)y * im.pitch + x0;
+    const int n = min(HT, im.w - x0);
+    if (n < HT) {
+        for (int i = 0; i < n; ++i) row[i] = ((e >> i) & 1) ? 255 : 0;
+        return;
+    }
+    uint32_t wd[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) wd[k] = nibble_bytes(e >> (4 * k));
+    store32(row, wd);
+}
+
+// Finish four tiles at once (lane 8 tt + sl holds rows 4 sl .. 4 sl + 3 of its
+// tile): grow the edges e (the strong pixels) through the candidates c, write the
+// tile's edge rows as 255/0, its border masks, pending bitmap and queue stamp.
+// valid: the lane's tile exists (tile index tid at (tx, ty) of image im); the
+// other lanes pass c = e = 0.
+// Returns, on the tile's first lane, bit 0: queue the tile for pass 0, bit 1: it
+// has pending pixels (the caller counts them and fills the worklist).
+__device__ __forceinline__ uint32_t finish4(const HystScratch &hs, const HystImage &im, int tx, int ty, uint32_t tid,
+                                            bool valid, const uint32_t (&c)[4], uint32_t (&e)[4], int lane)
+{
+    const int tt = lane >> 3, sl = lane & 7;
+    if (__any_sync(FULL, ((c[0] ^ e[0]) | (c[1] ^ e[1]) | (c[2] ^ e[2]) | (c[3] ^ e[3])) != 0u)) flood4(e, c, sl);
+    uint32_t pend[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) pend[r] = c[r] & ~e[r];
+    // border columns: each lane's four bits, gathered over the tile's eight lanes
+    uint32_t el = 0u, er = 0u, pl = 0u, pr = 0u;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        el |= (e[r] & 1u) << r;
+        er |= (e[r] >> 31) << r;
+        pl |= (pend[r] & 1u) << r;
+        pr |= (pend[r] >> 31) << r;
+    }
+    el <<= 4 * sl;
+    er <<= 4 * sl;
+    pl <<= 4 * sl;
+    pr <<= 4 * sl;
+#pragma unroll
+    for (int d = 1; d < 8; d <<= 1) {
+        el |= __shfl_xor_sync(FULL, el, d);
+        er |= __shfl_xor_sync(FULL, er, d);
+        pl |= __shfl_xor_sync(FULL, pl, d);
+        pr |= __shfl_xor_sync(FULL, pr, d);
+    }
+    TileMasks m;
+    m.edge_top = __shfl_sync(FULL, e[0], lane & ~7);
+    m.edge_bottom = __shfl_sync(FULL, e[3], lane | 7);
+    m.pend_top = __shfl_sync(FULL, pend[0], lane & ~7);
+    m.pend_bottom = __shfl_sync(FULL, pend[3], lane | 7);
+    m.edge_left = el;
+    m.edge_right = er;
+    m.pend_left = pl;
+    m.pend_right = pr;
+    const uint32_t pbal = __ballot_sync(FULL, (pend[0] | pend[1] | pend[2] | pend[3]) != 0u);
+    const bool any_pend = ((pbal >> (8 * tt)) & 0xFFu) != 0u;
+    if (!valid) return 0u;
+    const int y0 = ty * HT + 4 * sl;
+    const bool fast = ((((uintptr_t)im.map) | (uintptr_t)im.pitch) & 15) == 0 && (tx + 1) * HT <= im.w &&
+                      (ty + 1) * HT <= im.h;
+    if (fast) {
+        // whole tile in 16-byte aligned rows: two 16-byte stores a row
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            uint4 *p = reinterpret_cast<uint4 *>(im.map + (int64_t)(y0 + r) * im.pitch + tx * HT);
+            p[0] = make_uint4(nibble_bytes(e[r]), nibble_bytes(e[r] >> 4), nibble_bytes(e[r] >> 8),
+                              nibble_bytes(e[r] >> 12));
+            p[1] = make_uint4(nibble_bytes(e[r] >> 16), nibble_bytes(e[r] >> 20), nibble_bytes(e[r] >> 24),
+                              nibble_bytes(e[r] >> 28));
+        }
+    } else {
+#pragma unroll 1
+        for (int r = 0; r < 4; ++r) store_tile_row(im, tx, y0 + r, e[r]);
+    }
+    if (!CANNY_CHECK(tid < hs.max_tiles, &hs.state->error)) return 0u;
+    if (any_pend)
+        *reinterpret_cast<uint4 *>(&hs.pend_bits[(size_t)tid * HT + 4 * sl]) = make_uint4(pend[0], pend[1], pend[2], pend[3]);
+    if (sl != 0) return 0u;
+    hs.masks[tid] = m;
+    // pending pixels on the border may be reached from a neighbour: queue for
+    // pass 0 (1 = queued for pass 0, 0 = not queued; every tile writes its stamp)
+    const bool queue = (m.pend_top | m.pend_bottom | m.pend_left | m.pend_right) != 0u;
+    hs.stamp[tid] = queue ? 1u : 0u;
+    return (queue ? 1u : 0u) | (any_pend ? 2u : 0u);
 }
 
 __device__ __forceinline__ int find_image(const HystImage *imgs, int nimg, uint32_t t)

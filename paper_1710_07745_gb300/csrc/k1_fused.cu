@@ -275,44 +275,22 @@ __device__ __forceinline__ void finish_tile_row(Smem &S, const Unit &U_, const O
             }
         }
     } else {
+        // the tile row's class bits go to the tile fill: rows of class >= 1, then rows of class 2
         constexpr int TILES_Y = Band<BAND>::TILES_Y;
+        const HystImage &im = O.img;
         const int ty = U_.sy * TILES_Y + t;
-        if (ty >= O.img.nty) {
-            for (int txl = 0; txl < TILES_X; ++txl) S.cand[brow][txl] = S.strong[brow][txl] = 0u;
-            __syncwarp();
-            return;
-        }
-        // a tile row of whole tiles in 16-byte aligned output rows: empty tiles take two zero stores a row
-        const int y = ty * HT + lane;
-        const bool fast = ((((uintptr_t)O.img.map) | (uintptr_t)O.img.pitch) & 15) == 0 && (ty + 1) * HT <= O.img.h;
-        uint8_t *orow = O.img.map + (int64_t)min(y, O.img.h - 1) * O.img.pitch;
 #pragma unroll 1
         for (int txl = 0; txl < TILES_X; ++txl) {
             const int tx = U_.sx * TILES_X + txl;
-            const uint32_t cand = S.cand[brow][txl], strong = S.strong[brow][txl];
+            const uint32_t c = S.cand[brow][txl], sg = S.strong[brow][txl];
             S.cand[brow][txl] = 0u;
             S.strong[brow][txl] = 0u;
-            if (tx >= O.img.ntx) continue;                              // warp-uniform
-            const uint32_t tid = O.img.tile_base + (uint32_t)ty * (uint32_t)O.img.ntx + (uint32_t)tx;
-            if (!__any_sync(FULL, cand != 0u)) {
-                // nothing above the low threshold: zeros, empty border masks, not queued
-                if (fast && (tx + 1) * HT <= O.img.w) {
-                    uint4 *p = reinterpret_cast<uint4 *>(orow + tx * HT);
-                    p[0] = make_uint4(0u, 0u, 0u, 0u);
-                    p[1] = make_uint4(0u, 0u, 0u, 0u);
-                } else {
-                    tile::store_row(O.img, tx, ty, lane, 0u);
-                }
-                if (lane == 0 && CANNY_CHECK(tid < O.hs.max_tiles, &O.hs.state->error)) {
-                    O.hs.masks[tid] = TileMasks{};
-                    O.hs.stamp[tid] = 0u;
-                }
-                continue;
-            }
-            // every candidate strong: nothing to grow
-            const uint32_t e = __all_sync(FULL, cand == strong) ? cand : tile::flood_tile(strong, cand, lane);
-            tile::store_row(O.img, tx, ty, lane, e);
-            tile::finish_tile(O.hs, tid, e, cand, lane);
+            if (tx >= im.ntx || ty >= im.nty) continue;                 // warp-uniform
+            const uint32_t tid = im.tile_base + (uint32_t)ty * (uint32_t)im.ntx + (uint32_t)tx;
+            if (!CANNY_CHECK(tid < O.hs.max_tiles, &O.hs.state->error)) continue;
+            uint32_t *bt = O.hs.bits + (size_t)tid * 2 * HT;
+            bt[lane] = c;
+            bt[HT + lane] = sg;
         }
     }
     __syncwarp();
@@ -329,6 +307,9 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const Unit
     const int w = U_.w, h = U_.h, X0 = U_.X0, Y0 = U_.Y0;
     const int xl = X0 - LPX + LPX * lane;       // image column of the lane's first pixel
     const bool border = !INTERIOR && (xl < 0 || xl + LPX > w);
+    // some lane of the warp is at an image border: the per-lane border work runs
+    // behind this warp-uniform test, so units away from the borders skip it
+    const bool wborder = !INTERIOR && __any_sync(FULL, border);
     const bool out_lane = lane >= 1 && lane <= OUT_LANES;
     const int e_last = w - 1 - xl;               // lane pixel holding column w - 1 (if 0..15)
     const float lo2 = (float)min(t.lo2, 1 << 24), hi2 = (float)min(t.hi2, 1 << 24);
@@ -398,7 +379,7 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const Unit
             } else if (TMA) {
                 const bool above = !INTERIOR && yin < 0;
                 const int slot = above ? ROW0_CHUNK % STAGES : g % STAGES, ru = above ? ROW0_OFF : u;
-                if (!border) {
+                if (!wborder || !border) {
                     const uint4 v = *reinterpret_cast<const uint4 *>(&S.in[slot][lane >> 4][ru][(lane & 15) * LPX]);
                     wd[0] = v.x; wd[1] = v.y; wd[2] = v.z; wd[3] = v.w;
                 } else {
@@ -465,7 +446,7 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const Unit
                 SO[k] = perm(ho, H1024, 0x7351u);
             }
             // replicate border on S at the right image edge: S(w) = S(w - 1)
-            if (border && e_last >= 0 && e_last < LPX - 1) {
+            if (wborder && border && e_last >= 0 && e_last < LPX - 1) {
 #pragma unroll
                 for (int p = 0; p < LPX - 1; ++p)
                     if (p == e_last) set_px(SE, SO, p + 1, get_px(SE, SO, p));
@@ -479,7 +460,7 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const Unit
             for (int k = 0; k < 4; ++k) {
                 uint32_t SB = k ? perm(SO[k - 1], SO[k], 0x5432u) : perm(SLw, SO[0], 0x5432u);   // (S4k-1, S4k+1)
                 uint32_t SC = k < 3 ? perm(SE[k], SE[k + 1], 0x5432u) : perm(SE[3], SRw, 0x5432u); // (S4k+2, S4k+4)
-                if (!INTERIOR) {
+                if (wborder) {
                     if (k == 0 && xl == 0) SB = perm(SE[0], SO[0], 0x5410u);               // S(-1) = S(0)
                     if (k == 3 && e_last == LPX - 1) SC = perm(SE[3], SO[3], 0x7632u);     // S(w) = S(w-1)
                 }
@@ -509,7 +490,7 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const Unit
                 if (r < 0 || r >= h) {
 #pragma unroll
                     for (int j = 0; j < 8; ++j) gx[j] = gy[j] = 0u;
-                } else if (border) {
+                } else if (wborder && border) {
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const int p0 = 4 * (j & 3) + (j >> 2), p1 = p0 + 2;   // pixels of pair j
@@ -852,7 +833,10 @@ cudaError_t launch_k1_edges_u8(const uint8_t *in, int in_pitch, int w, int h, In
                                const HystScratch &hs, HystImage img, cudaStream_t s, int band)
 {
     if (w <= 0 || h <= 0) return cudaSuccess;
-    return launch_any<MODE_EDGES>(band, in, in_pitch, w, h, t, img.map, img.pitch, hs, img, &hs.state->error, s);
+    cudaError_t e = launch_any<MODE_EDGES>(band, in, in_pitch, w, h, t, img.map, img.pitch, hs, img,
+                                           &hs.state->error, s);
+    if (e == cudaSuccess) e = launch_hyst_fill_single(hs, img, s);
+    return e;
 }
 
 // Kernel node parameters of the batch kernel; grid: CTAs (persistent) or units.

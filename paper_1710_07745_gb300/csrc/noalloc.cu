@@ -18,8 +18,9 @@ constexpr size_t OFF_MASKS = align256(OFF_IMGS + sizeof(HystImage));
 constexpr size_t OFF_PEND = align256(OFF_MASKS + sizeof(TileMasks) * NOALLOC_MAX_TILES);
 constexpr size_t OFF_STAMP = align256(OFF_PEND + sizeof(uint32_t) * HT * NOALLOC_MAX_TILES);
 constexpr size_t OFF_LISTS = align256(OFF_STAMP + sizeof(uint32_t) * NOALLOC_MAX_TILES);
-constexpr size_t OFF_STATE = align256(OFF_LISTS + sizeof(uint32_t) * 2 * NOALLOC_MAX_TILES);
-constexpr size_t SCRATCH_BYTES = align256(OFF_STATE + sizeof(HystState));   // about 2.8 MB
+constexpr size_t OFF_BITS = align256(OFF_LISTS + sizeof(uint32_t) * 2 * NOALLOC_MAX_TILES);
+constexpr size_t OFF_STATE = align256(OFF_BITS + sizeof(uint32_t) * 2 * HT * NOALLOC_MAX_TILES);
+constexpr size_t SCRATCH_BYTES = align256(OFF_STATE + sizeof(HystState));   // about 7 MB
 
 // Shared by every call on a device; every device that loads the library holds it
 // until the process exits.
@@ -82,6 +83,7 @@ extern "C" canny_status canny_run_noalloc(const uint8_t *d_in, int in_pitch, uin
     hs.pend_bits = (uint32_t *)(b + OFF_PEND);
     hs.stamp = (uint32_t *)(b + OFF_STAMP);
     hs.lists = (uint32_t *)(b + OFF_LISTS);
+    hs.bits = (uint32_t *)(b + OFF_BITS);
     hs.state = (HystState *)(b + OFF_STATE);
     hs.max_tiles = NOALLOC_MAX_TILES;
     hs.max_imgs = 1;

@@ -210,8 +210,9 @@ canny_status canny_read_timing(canny_ctx *ctx, canny_timing *out);
 
 /*
  * Launch configuration of the fused integer kernel: rows per unit of work
- * (band: 64, 160 or 256; taller bands cut halo work, shorter ones balance small
- * images better) and, for batches, ctas_per_sm: 0 (the default) launches one
+ * (band: 32, 64, 160 or 256; taller bands cut halo work, shorter ones balance
+ * small images better; 0, the default: 32 or 64 rows chosen per image size for
+ * single images, 64 for batches) and, for batches, ctas_per_sm: 0 (the default) launches one
  * CTA per (image, strip, band) unit and lets the hardware schedule them, 1..32
  * launches that many persistent CTAs per SM that pop units from a device
  * counter. direct_loads = 1 reads
@@ -253,16 +254,17 @@ canny_status canny_get_stats(canny_ctx *ctx, canny_stats *out);
  * Same result as canny_run_pitched on an integer-path context with thresholds
  * low/high (integers, 0 <= low <= high < 2^15). The caller passes the device
  * input and output as for canny_run_pitched; no context is needed. The
- * hysteresis scratch is one fixed device array in the library (about 2.8 MB,
+ * hysteresis scratch is one fixed device array in the library (about 7 MB,
  * held on every GPU that loads the library until the process exits), so the
  * image may have at most 16384 tiles of 32x32 pixels (16.8 Mpixel, e.g.
  * 4096 x 4096); larger images return CANNY_EUNSUPPORTED before any work is
  * queued. Every call shares that array: calls that overlap on the GPU (other
  * streams, other threads) race and must be serialised by the caller. The first
  * call on each device looks up the array's device address (set-up, once per
- * device); make that first call before any stream capture. Returns after the
- * work has finished: the hysteresis passes are driven by the host, which
- * synchronises the stream after each pass.
+ * device). The global hysteresis passes run in one cooperative launch where
+ * the device allows, otherwise (or if the device refuses that grid) the host
+ * drives them, one pass at a time. Either way the call reads the result's
+ * status back, so it synchronises the stream before it returns.
  */
 canny_status canny_run_noalloc(const uint8_t *d_in, int in_pitch, uint8_t *d_out, int out_pitch,
                                int w, int h, int low, int high, void *stream);
@@ -329,14 +331,20 @@ canny_status canny_serve(const canny_serve_config *cfg, int n, const canny_reque
  *                       attempt);
  *   stalled_barriers    the next single-image runs start their global
  *                       hysteresis passes with a grid barrier that can never
- *                       complete: its bounded wait runs out (about a second)
- *                       and the run reports CANNY_ECUDA through
- *                       canny_get_stats; the context stays usable.
+ *                       complete: its bounded wait runs out (after a second
+ *                       of GPU time) and the run reports CANNY_ECUDA through
+ *                       canny_get_stats; the context stays usable;
+ *   host_driven_passes  the next single-image runs (canny_run,
+ *                       canny_run_pitched, canny_run_noalloc) drive their
+ *                       global hysteresis passes from the host, one launch
+ *                       and one read of the control block per pass, as when
+ *                       the device refuses the cooperative grid.
  */
 typedef struct {
     int device_allocations;
     int arena_admissions;
     int stalled_barriers;
+    int host_driven_passes;
 } canny_fault_injection;
 
 canny_status canny_inject_faults(const canny_fault_injection *f);

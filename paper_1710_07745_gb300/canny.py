@@ -74,7 +74,7 @@ class canny_serve_config(ctypes.Structure):
 
 class canny_fault_injection(ctypes.Structure):
     _fields_ = [("device_allocations", ctypes.c_int), ("arena_admissions", ctypes.c_int),
-                ("stalled_barriers", ctypes.c_int)]
+                ("stalled_barriers", ctypes.c_int), ("host_driven_passes", ctypes.c_int)]
 
 
 class canny_serve_report(ctypes.Structure):
@@ -164,10 +164,12 @@ def load_checked() -> ctypes.CDLL:
         return _checked
 
 
-def canny_inject_faults(device_allocations: int = 0, arena_admissions: int = 0, stalled_barriers: int = 0) -> None:
+def canny_inject_faults(device_allocations: int = 0, arena_admissions: int = 0, stalled_barriers: int = 0,
+                        host_driven_passes: int = 0) -> None:
     """Test hook: make the library's next allocations, serving admissions or
-    single-image hysteresis barriers fail (see include/canny.h)."""
-    f = canny_fault_injection(device_allocations, arena_admissions, stalled_barriers)
+    single-image hysteresis barriers fail, or the next single-image runs drive
+    their global passes from the host (see include/canny.h)."""
+    f = canny_fault_injection(device_allocations, arena_admissions, stalled_barriers, host_driven_passes)
     _check(load().canny_inject_faults(ctypes.byref(f)), "canny_inject_faults")
 
 

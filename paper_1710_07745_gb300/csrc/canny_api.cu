@@ -48,7 +48,7 @@ struct canny_ctx {
     int ev_runs = 0;
 
     // launch configuration of the fused kernel (canny_set_tuning / canny_autotune_batch)
-    int band = 64;                     // rows per unit of work
+    int band = 0;                      // rows per unit of work; 0: chosen per image size
     int ctas_per_sm = 0;               // batches: 0 = one CTA per unit, else persistent CTAs per SM
     int direct_loads = 0;              // 1: inputs the TMA path cannot read are not repitched
 
@@ -123,7 +123,7 @@ uint32_t tiles_of(int w, int h)
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Failures injected by canny_inject_faults (test hooks).
-std::atomic<int> g_fail_device{0}, g_fail_arena{0}, g_fail_barrier{0};
+std::atomic<int> g_fail_device{0}, g_fail_arena{0}, g_fail_barrier{0}, g_host_passes{0};
 
 bool take_failure(std::atomic<int> &n)
 {
@@ -243,7 +243,7 @@ uint32_t auto_max_passes(uint32_t ntiles)
 canny_status run_global(canny_ctx *c, cudaStream_t s)
 {
     // one cooperative launch runs every pass; else a graph while-loop; else the host loop
-    if (c->use_graph && hyst_coop_supported()) {
+    if (c->use_graph && hyst_coop_supported() && !host_passes_injected()) {
         cudaError_t e = cudaSuccess;
         if (take_failure(g_fail_barrier)) e = launch_hyst_phantom_arrival(c->hs, s);   // test hook
         if (e == cudaSuccess) e = launch_hyst_global_coop(c->hs, s);
@@ -284,12 +284,15 @@ canny_status check_image(const canny_ctx *c, const canny_image *im, bool per_dim
     return CANNY_OK;
 }
 
+int band_for(const canny_ctx *c, int w, int h);
+
 // Steps 1-3 + thresholds into im->d_out as a class map.
 canny_status run_stencil(canny_ctx *c, const canny_image *im, cudaStream_t s)
 {
     if (c->p.path == CANNY_PATH_INT)
         return from_cuda(launch_k1_classify_u8(im->d_in, im->in_pitch, im->d_out, im->out_pitch,
-                                               im->w, im->h, c->it, &c->hs.state->error, s, c->band));
+                                               im->w, im->h, c->it, &c->hs.state->error, s,
+                                               band_for(c, im->w, im->h)));
     if (!c->mag) {
         // the stored strength image is only needed for a class map of the float path
         if (dev_alloc((void **)&c->mag, sizeof(float) * (size_t)c->max_w * c->max_h) != cudaSuccess) {
@@ -413,7 +416,7 @@ canny_status run_one(canny_ctx *c, const canny_image *im, cudaStream_t s, bool s
     if (stencil && c->p.path == CANNY_PATH_INT) {
         // fused: Steps 1-3, thresholds and the tile-local fill in one kernel
         st = from_cuda(launch_k1_edges_u8(staged.d_in, staged.in_pitch, im->w, im->h, c->it, c->hs, himg, s,
-                                          c->band));
+                                          band_for(c, im->w, im->h)));
         if (st != CANNY_OK) return st;
         if (ev) {
             cudaEventRecord(ev[2], s);
@@ -499,6 +502,23 @@ int sm_count()
     return n;
 }
 
+// Band height of a single image's units: the configured one, else whichever of
+// 32 and 64 rows needs fewer rows of work per SM slot (waves x rows per unit; 12
+// one-warp CTAs fit on an SM): small images take the shorter units.
+int band_for(const canny_ctx *c, int w, int h)
+{
+    if (c->band > 0) return c->band;
+    const int64_t slots = (int64_t)sm_count() * 12;
+    auto cost = [&](int band) {
+        const int64_t units = k1_units(w, h, band);
+        return (units + slots - 1) / slots * k1_band_rows(band);
+    };
+    return cost(32) < cost(64) ? 32 : 64;
+}
+
+// Band height of batch units: the configured one, else 64.
+int batch_band(const canny_ctx *c) { return c->band > 0 ? c->band : 64; }
+
 // The batch graph: upload descriptors -> reset, repitch inputs the TMA path
 // cannot read -> fused kernel (persistent, pops units) -> while (work) global pass.
 // Variant 1 holds the TMA-only fused kernel (every input TMA-readable).
@@ -528,7 +548,7 @@ canny_status build_batch_graph(canny_ctx *c, canny_ctx::Slot &sl, int v)
         e = add_repitch_list_node(g, &up1, 1, (const Repitch *)(c->d_blob + L.stage), hdr, &stage);
     cudaGraphNode_t d_k1[3] = {up2, init, stage};
     if (e == cudaSuccess)
-        e = k1_add_batch_node(g, d_k1, 3, c->band, v == 1, imgs, tmaps, hdr, c->it, c->hs,
+        e = k1_add_batch_node(g, d_k1, 3, batch_band(c), v == 1, imgs, tmaps, hdr, c->it, c->hs,
                               c->ctas_per_sm > 0 ? sm_count() * c->ctas_per_sm : 0, &k1);
     sl.k1node[v] = k1;
     cudaGraphNode_t fill;
@@ -616,7 +636,7 @@ canny_status run_batch_int(canny_ctx *c, int n, const canny_image *imgs, uint32_
         all_tma = all_tma && b.tma;
         bi[k] = b;
         tile_base += tiles_of(im->w, im->h);
-        unit_base += (uint32_t)k1_units(im->w, im->h, c->band);
+        unit_base += (uint32_t)k1_units(im->w, im->h, batch_band(c));
         ++k;
     }
     BatchHeader hh = {};
@@ -635,7 +655,7 @@ canny_status run_batch_int(canny_ctx *c, int n, const canny_image *imgs, uint32_
     }
     cudaError_t e = cudaSuccess;
     if (c->ctas_per_sm <= 0)
-        e = k1_set_batch_units(sl.exec[v], sl.k1node[v], c->band, v == 1, (const BatchImage *)(c->d_blob + L.imgs),
+        e = k1_set_batch_units(sl.exec[v], sl.k1node[v], batch_band(c), v == 1, (const BatchImage *)(c->d_blob + L.imgs),
                                (const CUtensorMap *)(c->d_blob + L.tmaps), (BatchHeader *)c->d_blob, c->it, c->hs,
                                unit_base);
     if (e == cudaSuccess) e = cudaGraphLaunch(sl.exec[v], s);
@@ -667,16 +687,21 @@ cudaError_t pinned_alloc(void **p, size_t bytes)
 
 bool arena_failure_injected() { return take_failure(g_fail_arena); }
 
+bool host_passes_injected() { return take_failure(g_host_passes); }
+
 }  // namespace canny
 
 extern "C" {
 
 canny_status canny_inject_faults(const canny_fault_injection *f)
 {
-    if (!f || f->device_allocations < 0 || f->arena_admissions < 0 || f->stalled_barriers < 0) return CANNY_EINVAL;
+    if (!f || f->device_allocations < 0 || f->arena_admissions < 0 || f->stalled_barriers < 0 ||
+        f->host_driven_passes < 0)
+        return CANNY_EINVAL;
     g_fail_device.store(f->device_allocations);
     g_fail_arena.store(f->arena_admissions);
     g_fail_barrier.store(f->stalled_barriers);
+    g_host_passes.store(f->host_driven_passes);
     return CANNY_OK;
 }
 
@@ -946,7 +971,8 @@ canny_status canny_read_timing(canny_ctx *c, canny_timing *out)
 canny_status canny_set_tuning(canny_ctx *c, const canny_tuning *t)
 {
     if (!c || !t) return CANNY_EINVAL;
-    if (!k1_band_supported(t->band) || t->ctas_per_sm < 0 || t->ctas_per_sm > 32) return CANNY_EINVAL;
+    if ((t->band != 0 && !k1_band_supported(t->band)) || t->ctas_per_sm < 0 || t->ctas_per_sm > 32)
+        return CANNY_EINVAL;
     if (t->direct_loads != 0 && t->direct_loads != 1) return CANNY_EINVAL;
     c->direct_loads = t->direct_loads;
     if (t->band != c->band || t->ctas_per_sm != c->ctas_per_sm) {
@@ -1011,7 +1037,7 @@ canny_status canny_autotune_batch(canny_ctx *c, int n, const canny_image *imgs, 
     }
     if (!best.from_cache) {
         // time every candidate on this batch: warm-up run, then two timed runs
-        const int bands[3] = {64, 160, 256};
+        const int bands[3] = {32, 64, 160};
         const int ctas[3] = {0, 12, 16};
         cudaEvent_t e0, e1;
         if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return CANNY_ECUDA;
@@ -1095,7 +1121,8 @@ canny_status build_frame_graph(canny_ctx *c, canny_ctx::FrameSlot &f)
     canny_status st = from_cuda(hyst_reset(c->hs, ntiles, 1, max_passes_for(c, ntiles), c->s_cap, &himg));
     if (st == CANNY_OK) {
         if (c->p.path == CANNY_PATH_INT)
-            st = from_cuda(launch_k1_edges_u8(im.d_in, im.in_pitch, im.w, im.h, c->it, c->hs, himg, c->s_cap, c->band));
+            st = from_cuda(launch_k1_edges_u8(im.d_in, im.in_pitch, im.w, im.h, c->it, c->hs, himg, c->s_cap,
+                                              band_for(c, im.w, im.h)));
         else
             st = run_float_fused(c, &im, himg, c->s_cap);
     }

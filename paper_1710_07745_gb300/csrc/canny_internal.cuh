@@ -43,6 +43,16 @@ struct TileMasks {
 #define CANNY_CHECK(cond, errp) true
 #endif
 
+// Nanoseconds of the GPU's global timer: bounds the waits of device-side spins by
+// time, not by an iteration count whose duration depends on the clock and load.
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+constexpr uint64_t WAIT_TIMEOUT_NS = 1000000000ull;   // a device-side wait gives up after a second
+
 struct HystState {
     uint32_t list_count[2];   // sizes of the two worklists
     uint32_t done_ctas;       // CTAs finished in the current global pass
@@ -107,6 +117,8 @@ struct BatchHeader {
 // ---------------------------------------------------------------- launchers (k1_fused.cu)
 // Band heights the fused kernel is built for (rows per unit of work).
 bool k1_band_supported(int band);
+// Input rows a unit of the given band height processes (its band plus halos).
+int k1_band_rows(int band);
 int k1_units(int w, int h, int band);
 int k1_strip_width();
 bool encode_k1_map(void *tmap_out, const uint8_t *in, int w, int h, int in_pitch);
@@ -217,6 +229,10 @@ cudaError_t launch_hyst_global_pass(const HystScratch &hs, int grid, bool in_gra
 // Every global pass in one cooperative launch (passes separated by a bounded
 // grid barrier): cudaErrorNotSupported when the device cannot hold the grid.
 bool hyst_coop_supported();
+// Test hook (canny_inject_faults): true, and one count used up, if the next
+// single-image global passes are to be driven from the host as when the device
+// refuses the cooperative grid.
+bool host_passes_injected();
 cudaError_t launch_hyst_global_coop(const HystScratch &hs, cudaStream_t s);
 // Test hook: barrier arrivals that no CTA makes, so the next cooperative
 // launch's barrier never completes and its bounded wait runs out.

@@ -417,7 +417,6 @@ hyst_global_kernel(HystScratch hs, int in_graph, cudaGraphConditionalHandle cond
 // Grid-wide barrier of a cooperative launch (every CTA is resident): the last
 // CTA to arrive advances the generation. The wait is bounded; if it runs out,
 // error bit 1 is set and false returned in every thread of the CTA.
-constexpr uint32_t BARRIER_SPIN_LIMIT = 1u << 21;   // about a second
 
 __device__ __forceinline__ bool grid_barrier(HystState *st)
 {
@@ -432,9 +431,11 @@ __device__ __forceinline__ bool grid_barrier(HystState *st)
             __threadfence();
             atomicAdd(&st->bar_gen, 1u);
         } else {
-            uint32_t n = 0;
+            // bounded by time: a legitimate pass of the largest image ends within
+            // milliseconds, so a second without the last arrival is a failure
+            const uint64_t t0 = globaltimer_ns();
             while (atomicAdd(&st->bar_gen, 0u) == gen) {
-                if (++n > BARRIER_SPIN_LIMIT) {
+                if (globaltimer_ns() - t0 > WAIT_TIMEOUT_NS) {
                     atomicOr(&st->error, 2u);
                     ok = 0;
                     break;
@@ -494,17 +495,29 @@ __global__ void hyst_error_or_kernel(const HystState *st, uint32_t *acc)
 
 }  // namespace
 
+// Per device (cached): CTAs of a global pass, and whether one cooperative launch
+// of that grid fits.
+namespace {
+constexpr int MAX_DEVICES = 64;
+int g_grid[MAX_DEVICES] = {};
+int g_coop[MAX_DEVICES] = {};       // 0: not yet known, 1: no, 2: yes
+int current_device()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) dev = 0;
+    return dev;
+}
+}  // namespace
+
 int hyst_pass_grid()
 {
-    static int grid = 0;
-    if (!grid) {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
-            sms = 152;
-        grid = 2 * sms;
+    const int dev = current_device();
+    if (!g_grid[dev]) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+        g_grid[dev] = 2 * sms;
     }
-    return grid;
+    return g_grid[dev];
 }
 
 cudaError_t hyst_reset(const HystScratch &hs, uint32_t ntiles, uint32_t nimg, uint32_t max_passes,
@@ -544,18 +557,18 @@ cudaError_t launch_hyst_global_pass(const HystScratch &hs, int grid, bool in_gra
 
 bool hyst_coop_supported()
 {
-    static int ok = -1;
-    if (ok < 0) {
-        int dev = 0, coop = 0, per_sm = 0, sms = 0;
-        cudaGetDevice(&dev);
-        ok = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
-             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
-             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hyst_global_coop_kernel, THREADS, 0) ==
-                 cudaSuccess &&
-             (int64_t)per_sm * sms >= hyst_pass_grid();
+    const int dev = current_device();
+    if (g_coop[dev] == 0) {
+        int coop = 0, per_sm = 0, sms = 0;
+        const bool ok = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
+                        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+                        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hyst_global_coop_kernel, THREADS,
+                                                                      0) == cudaSuccess &&
+                        (int64_t)per_sm * sms >= hyst_pass_grid();
         cudaGetLastError();
+        g_coop[dev] = ok ? 2 : 1;
     }
-    return ok == 1;
+    return g_coop[dev] == 2;
 }
 
 namespace {

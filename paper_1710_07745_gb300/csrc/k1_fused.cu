@@ -65,10 +65,11 @@ constexpr int GROW = 4 * GHALF;         // one gradient row: Gx E, Gx O, Gy E, G
 constexpr uint32_t CHUNK_BYTES = ROWB * CH;
 static_assert(OUT_W % HT == 0, "strips hold whole tiles");
 
-// Rows per unit: input rows Y0-4 .. Y0+BAND+3 in groups of U.
+// Rows per unit: input rows Y0-4 .. Y0+BAND+3 in groups of U (rounded up to a
+// whole group; the extra rows' results are not used).
 template <int BAND>
 struct Band {
-    static constexpr int ITERS = BAND + 8;
+    static constexpr int ITERS = (BAND + 8 + U - 1) / U * U;
     static constexpr int GROUPS = ITERS / U;
     static constexpr int TILES_Y = BAND / HT;
     static_assert(BAND % HT == 0 && ITERS % U == 0 && GROUPS % STAGES == 0, "bad band height");
@@ -78,7 +79,6 @@ constexpr uint32_t BIAS = 0x00800080u;              // +128 in both 16-bit lanes
 constexpr uint32_t H1024 = 0x64006400u;             // fp16 1024 in both halves (exponent byte 0x64)
 constexpr uint32_t HTWO = 0x40004000u;              // fp16 2.0
 constexpr uint32_t HM3072 = 0xEA00EA00u;            // fp16 -3072
-constexpr uint32_t WAIT_LIMIT = 1u << 22;           // bounded mbarrier waits
 
 enum { MODE_CLASSMAP = 0, MODE_EDGES = 1 };
 
@@ -345,10 +345,12 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const Unit
     bool failed = false;
     auto wait_chunk = [&](int c) {
         if (failed) return;
-        uint32_t n = 0;
         const uint32_t parity = ((uint32_t)(c / STAGES) + pbase) & 1u;
+        if (mbar_try_wait(&S.full[c % STAGES], parity)) return;
+        // bounded by time: a TMA load that has not landed in a second has failed
+        const uint64_t t0 = globaltimer_ns();
         while (!mbar_try_wait(&S.full[c % STAGES], parity))
-            if (++n > WAIT_LIMIT) { failed = true; break; }
+            if (globaltimer_ns() - t0 > WAIT_TIMEOUT_NS) { failed = true; break; }
         if (failed && lane == 0) atomicOr(err, 2u);
     };
     if (TMA && lane == 0)
@@ -605,12 +607,12 @@ __device__ __forceinline__ void stencil_band(const CUtensorMap *tmap, const Unit
     }
 }
 
-// A unit away from every image border: input rows Y0 - 4 .. Y0 + BAND + 3 and
+// A unit away from every image border: input rows Y0 - 4 .. Y0 + ITERS - 5 and
 // the columns of all 32 lanes (X0 - 16 .. X0 + 495) in the image.
 template <int BAND>
 __device__ __forceinline__ bool interior_unit(const Unit &U_)
 {
-    return U_.X0 >= LPX && U_.X0 + OUT_W + LPX <= U_.w && U_.Y0 >= 4 && U_.Y0 + BAND + 4 <= U_.h;
+    return U_.X0 >= LPX && U_.X0 + OUT_W + LPX <= U_.w && U_.Y0 >= 4 && U_.Y0 + Band<BAND>::ITERS - 4 <= U_.h;
 }
 
 // PATH: 0 = per unit (U.tma), 1 = TMA only, 2 = direct loads only. A kernel that
@@ -802,6 +804,7 @@ cudaError_t launch_any(int band, const uint8_t *in, int in_pitch, int w, int h, 
     memset(&tmap, 0, sizeof(tmap));
     const bool tma = encode_u8_map(&tmap, in, w, h, in_pitch, BOX, CH);
     switch (band) {
+    case 32: return launch_single<32, MODE>(tmap, tma, in, in_pitch, w, h, t, out, out_pitch, hs, img, err, s);
     case 160: return launch_single<160, MODE>(tmap, tma, in, in_pitch, w, h, t, out, out_pitch, hs, img, err, s);
     case 256: return launch_single<256, MODE>(tmap, tma, in, in_pitch, w, h, t, out, out_pitch, hs, img, err, s);
     default: return launch_single<64, MODE>(tmap, tma, in, in_pitch, w, h, t, out, out_pitch, hs, img, err, s);
@@ -810,7 +813,17 @@ cudaError_t launch_any(int band, const uint8_t *in, int in_pitch, int w, int h, 
 
 }  // namespace
 
-bool k1_band_supported(int band) { return band == 64 || band == 160 || band == 256; }
+bool k1_band_supported(int band) { return band == 32 || band == 64 || band == 160 || band == 256; }
+
+int k1_band_rows(int band)
+{
+    switch (band) {
+    case 32: return Band<32>::ITERS;
+    case 160: return Band<160>::ITERS;
+    case 256: return Band<256>::ITERS;
+    default: return Band<64>::ITERS;
+    }
+}
 
 int k1_units(int w, int h, int band)
 {
@@ -879,6 +892,7 @@ cudaError_t batch_params(int band, bool tma_only, bool persist, const BatchImage
                          const HystScratch &hs, unsigned grid, void **args, cudaKernelNodeParams *kp)
 {
     switch (band) {
+    case 32: return batch_params_band<32>(tma_only, persist, imgs, tmaps, hdr, t, hs, grid, args, kp);
     case 160: return batch_params_band<160>(tma_only, persist, imgs, tmaps, hdr, t, hs, grid, args, kp);
     case 256: return batch_params_band<256>(tma_only, persist, imgs, tmaps, hdr, t, hs, grid, args, kp);
     default: return batch_params_band<64>(tma_only, persist, imgs, tmaps, hdr, t, hs, grid, args, kp);

@@ -9,7 +9,9 @@
 namespace canny {
 namespace {
 
-// Largest image: 16384 tiles of 32x32 pixels (16.8 Mpixel, e.g. 4096 x 4096).
+// Largest image: 16384 tiles of 32x32 pixels (16.8 Mpixel, e.g. 4096 x 4096);
+// the scratch holds per tile its masks, pending bitmap, stamp, worklist slots
+// and the stencil's class bits (428 bytes), about 7 MB in all.
 constexpr uint32_t NOALLOC_MAX_TILES = 16384;
 
 constexpr size_t align256(size_t v) { return (v + 255) / 256 * 256; }
@@ -98,21 +100,27 @@ extern "C" canny_status canny_run_noalloc(const uint8_t *d_in, int in_pitch, uin
     im.ntx = (w + HT - 1) / HT;
     im.nty = (h + HT - 1) / HT;
     im.tile_base = 0;
-    // the control block and the queue stamps must start at zero on every call
+    // hyst_reset clears the control block; the tile fill rewrites the pending
+    // bitmaps, masks and queue stamp of every tile of this image, and the fused
+    // stencil its class bits, so a previous call's leftovers are never read
     const uint32_t cap = (uint32_t)(64 + (uint64_t)(4 * HT - 4) * ntiles);
     e = hyst_reset(hs, (uint32_t)ntiles, 1, cap, s, &im);
     if (e != cudaSuccess) return status_of(e);
     e = launch_k1_edges_u8(d_in, in_pitch, w, h, t, hs, im, s);
     if (e != cudaSuccess) return status_of(e);
-    // global passes: one cooperative launch runs them all where the device allows,
-    // else they are driven from the host (one pass, read the control block, repeat)
+    // global passes: one cooperative launch runs them all where the device allows;
+    // if it refuses the grid (a device shared with other work), the host drives
+    // them: one pass, read the control block, repeat
     HystState st = {};
-    if (hyst_coop_supported()) {
+    if (hyst_coop_supported() && !host_passes_injected()) {
         e = launch_hyst_global_coop(hs, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&st, hs.state, sizeof(st), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) return status_of(e);
-        return (st.error & 10u) ? CANNY_ECUDA : (st.error & 1u) ? CANNY_ENOCONVERGE : CANNY_OK;
+        if (e != cudaErrorCooperativeLaunchTooLarge) {
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&st, hs.state, sizeof(st), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return status_of(e);
+            return (st.error & 10u) ? CANNY_ECUDA : (st.error & 1u) ? CANNY_ENOCONVERGE : CANNY_OK;
+        }
+        cudaGetLastError();   // the refusal is not left pending for the caller's next CUDA call
     }
     for (;;) {
         e = launch_hyst_global_pass(hs, hyst_pass_grid(), false, 0, s);

@@ -97,9 +97,9 @@ def test_create_rejects_bad_sizes_and_nulls(lib):
 def test_inject_faults_rejects_negative_counts(lib):
     import ctypes
     from paper_1710_07745_gb300 import canny
-    for bad in [(-1, 0, 0), (0, -2, 0), (0, 0, -3)]:
+    for bad in [(-1, 0, 0, 0), (0, -2, 0, 0), (0, 0, -3, 0), (0, 0, 0, -4)]:
         f = canny.canny_fault_injection(*bad)
         assert lib.canny_inject_faults(ctypes.byref(f)) == canny.CANNY_EINVAL
     assert lib.canny_inject_faults(None) == canny.CANNY_EINVAL
-    ok = canny.canny_fault_injection(0, 0, 0)
+    ok = canny.canny_fault_injection(0, 0, 0, 0)
     assert lib.canny_inject_faults(ctypes.byref(ok)) == canny.CANNY_OK

@@ -117,3 +117,29 @@ def test_stalled_grid_barrier_times_out_and_is_reported():
         assert c.stats()["status"] == canny.CANNY_OK
         assert np.array_equal(out.cpu().numpy(), oracle.canny_u8(img))
 
+
+
+def test_host_driven_passes_give_the_oracle_edges():
+    """The path taken when the device refuses the cooperative grid (forced by the
+    host-side hook): one global pass per launch, driven from the host, on a weak
+    serpentine through every tile with a strong pixel at its start (more passes
+    than one: the chase budget per worklist entry runs out)."""
+    n, gap = 1024, 32
+    cls = np.zeros((n, n), np.uint8)
+    rows = list(range(gap // 2, n, gap))
+    for j, r in enumerate(rows):
+        cls[r, :] = 1
+        if j + 1 < len(rows):
+            col = n - 1 if j % 2 == 0 else 0
+            cls[r:rows[j + 1] + 1, col] = 1
+    cls[rows[0], 0] = 2
+    with canny.Canny(n, n) as c:
+        out = torch.full((n, n), 7, dtype=torch.uint8, device="cuda")
+        canny.canny_inject_faults(host_driven_passes=1)
+        c.hysteresis(dev(cls), out)
+        torch.cuda.synchronize()
+        st = c.stats()
+        assert st["status"] == canny.CANNY_OK and st["hyst_passes"] >= 1
+        got = out.cpu().numpy()
+        assert np.array_equal(got, oracle.hysteresis(cls))
+        assert (got == 255).sum() == (cls > 0).sum()

@@ -38,16 +38,22 @@ LOW, HIGH = 40, 100
 METRIC = "Canny Mpixel/s & % of HBM roofline; batched vs plain loop; p50/p99 latency"
 UNIT = "Mpixel/s"
 WORKLOAD = "canny_int_16384x16384"
-# algorithmic bytes per pixel of the fused kernel: read the image byte, write the edge byte
+# algorithmic bytes per pixel of the stencil stage (fused stencil + tile fill): read the
+# image byte, write the edge byte
 K1_BYTES_PER_PX = 2
-# ncu DRAM traffic of the fused kernel per 16384^2 launch, valid only for the kernel
-# source it was measured on (profiles/k1_fused_16384x8192.md: capture at half size, x2)
-K1_TRAFFIC = {"sha256_prefix": "e9deaa80b2807105", "bytes": 467_559_424}
-# whole pipeline floor: stencil 2 B/px + tile-local hysteresis read + write 2 B/px
-PIPE_BYTES_PER_PX = 4
-# ncu smsp__inst_executed.sum of the fused kernel per pixel (same capture and source
-# as K1_TRAFFIC: 278,582,223 warp instructions on 16384 x 8192 pixels)
-K1_INST = {"sha256_prefix": "e9deaa80b2807105", "warp_inst_per_px": 202_902_579 / (16384 * 8192)}
+# the design's own traffic per pixel: the 2-bit class masks per pixel go from the
+# stencil to the tile fill and back (0.25 B/px each way)
+K1_DESIGN_BYTES_PER_PX = 2.5
+# ncu DRAM traffic of the two stencil-stage kernels per 16384^2 image, valid only for
+# the kernel sources it was measured on (a 16384 x 8192 capture, x2)
+K1_TRAFFIC = {"sha256_prefix": None, "bytes": None}
+# whole pipeline floor (the spec minimum): read the image, write the edge map
+PIPE_BYTES_PER_PX = 2
+# ncu smsp__inst_executed.sum of the two stencil-stage kernels per pixel (same
+# capture and sources as K1_TRAFFIC)
+K1_INST = {"sha256_prefix": None, "warp_inst_per_px": None}
+# ncu DRAM traffic of the global hysteresis passes per 16384^2 image (same sources)
+K3_TRAFFIC = {"sha256_prefix": None, "bytes": None}
 # warp instructions an SM can issue per clock (4 schedulers, one each)
 ISSUE_PER_SM_CLK = 4
 
@@ -61,21 +67,40 @@ def measured_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-def k1_digest() -> str:
-    """sha256 over the fused kernel's source and the tile header it inlines."""
+def src_digest(names) -> str:
+    """sha256 over the named kernel sources."""
     import hashlib
     h = hashlib.sha256()
-    for name in ("k1_fused.cu", "hyst_tile.cuh"):
+    for name in names:
         with open(os.path.join(ROOT, "paper_1710_07745_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
 
 
+def k1_digest() -> str:
+    """The stencil stage's sources: fused stencil, tile fill, the tile header."""
+    return src_digest(("k1_fused.cu", "tile_fill.cu", "hyst_tile.cuh", "canny_internal.cuh"))
+
+
+def k3_digest() -> str:
+    """The global passes' sources."""
+    return src_digest(("hysteresis.cu", "hyst_tile.cuh", "canny_internal.cuh"))
+
+
 def k1_traffic(w: int, h: int):
     """Recorded ncu DRAM bytes per launch, if the kernel source is unchanged since."""
-    if not k1_digest().startswith(K1_TRAFFIC["sha256_prefix"]) or (w, h) != (16384, 16384):
+    if not K1_TRAFFIC["sha256_prefix"] or not k1_digest().startswith(K1_TRAFFIC["sha256_prefix"]) or \
+            (w, h) != (16384, 16384):
         return None
     return K1_TRAFFIC["bytes"]
+
+
+def k3_traffic(w: int, h: int):
+    """Recorded ncu DRAM bytes of the global passes, if the sources are unchanged since."""
+    if not K3_TRAFFIC["sha256_prefix"] or not k3_digest().startswith(K3_TRAFFIC["sha256_prefix"]) or \
+            (w, h) != (16384, 16384):
+        return None
+    return K3_TRAFFIC["bytes"]
 
 
 def alu_roofline(px: int, k1_ms: float, hbm_gbs: float, clk: dict | None) -> dict | None:
@@ -83,7 +108,7 @@ def alu_roofline(px: int, k1_ms: float, hbm_gbs: float, clk: dict | None) -> dic
     launch over the CUDA-event launch time, against SMs x 4 issue slots x the SM clock.
     None once the kernel source differs from the one the count was taken on."""
     import torch
-    if not k1_digest().startswith(K1_INST["sha256_prefix"]):
+    if not K1_INST["sha256_prefix"] or not k1_digest().startswith(K1_INST["sha256_prefix"]):
         return None
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     mhz = (clk or {}).get("sm_max_mhz") or 2070.0
@@ -203,6 +228,99 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CPU legs (oracle)
+def cpu_info() -> dict:
+    """The host the oracle baselines ran on: core count and CPU model."""
+    import platform
+    import re
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            txt = f.read()
+        m = re.search(r"^model name\s*:\s*(.+)$", txt, re.M)
+        if m:
+            model = m.group(1).strip()
+        else:
+            impl = re.search(r"^CPU implementer\s*:\s*(\S+)", txt, re.M)
+            part = re.search(r"^CPU part\s*:\s*(\S+)", txt, re.M)
+            if impl and part:
+                known = {("0x41", "0xd4f"): "Arm Neoverse V2", ("0x41", "0xd40"): "Arm Neoverse V1",
+                         ("0x41", "0xd0c"): "Arm Neoverse N1"}
+                model = known.get((impl.group(1).lower(), part.group(1).lower()),
+                                  f"CPU implementer {impl.group(1)} part {part.group(1)}")
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model, "machine": platform.machine()}
+
+
+def oracle_median(fn, runs: int = 3) -> float:
+    """Median wall time of `runs` single-thread oracle calls."""
+    ts = []
+    for _ in range(runs):
+        t0 = time.perf_counter()
+        fn()
+        ts.append(time.perf_counter() - t0)
+    return statistics.median(ts)
+
+
+def float_ambiguous(gx, gy, M, lo=0.1, hi=0.3, tol=1e-3):
+    """Pixels where one of the oracle's float decisions (a threshold, the sector
+    boundary, a suppression neighbour) lies within tol (relative): the only
+    pixels, with those connected to them, where the float variant's edge map may
+    differ from the oracle's."""
+    mmax = np.float32(M.max())
+    lo_t, hi_t = np.float32(lo) * mmax, np.float32(hi) * mmax
+
+    def near(a, b):
+        return np.abs(a - b) <= tol * np.maximum(np.abs(a), np.abs(b))
+
+    amb = near(M, lo_t) | near(M, hi_t)
+    ax, ay = np.abs(gx), np.abs(gy)
+    t = np.float32(0.41421356)
+    amb |= near(ay, ax * t) | near(ax, ay * t)
+    P = np.pad(M, 1)
+    h, w = M.shape
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            if dy or dx:
+                amb |= near(M, P[1 + dy:1 + dy + h, 1 + dx:1 + dx + w]) & (M > 0)
+    return amb
+
+
+def float_error(img: np.ndarray, d_in, d_out, ctx, rows: int | None = None) -> dict:
+    """The float variant against the fp32 oracle (run here, single thread): the
+    largest relative strength error of the production kernel's strengths
+    (canny_magnitude_f32 runs the pipeline's own first pass), and, on a whole
+    image, the pixels whose edge bytes differ and the ambiguous pixels. rows:
+    compare strengths on rows 0 .. rows - 1 only (the oracle runs on rows 0 ..
+    rows + 7, so every compared row has its true neighbours)."""
+    import torch
+
+    import oracle
+    from paper_1710_07745_gb300 import canny
+    h, w = img.shape
+    mag = torch.empty((h, w), dtype=torch.float32, device="cuda")
+    mx = torch.zeros(1, dtype=torch.float32, device="cuda")
+    canny.canny_magnitude_f32(ctx.ctx, canny.image_of(d_in, d_out), mag.data_ptr(), w, mx.data_ptr(),
+                              torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    crop = img if rows is None else np.ascontiguousarray(img[:min(h, rows + 8)])
+    t0 = time.perf_counter()
+    e, M, cls = oracle.canny_f32(crop, want_stages=True)
+    dt = time.perf_counter() - t0
+    n = crop.shape[0] if rows is None else min(h, rows)
+    got = mag[:n].cpu().numpy()
+    ref = M[:n]
+    rel = float(np.max(np.abs(got.astype(np.float64) - ref) / np.maximum(np.abs(ref), 1.0)))
+    out = {"max_rel_strength_error": rel, "strength_rows_compared": int(n), "tolerance": 1e-5,
+           "oracle_s": round(dt, 2)}
+    if rows is None:
+        gx, gy = oracle.sobel_f32(oracle.gauss_f32(crop))
+        amb = float_ambiguous(gx, gy, M)
+        got_e = d_out.cpu().numpy()
+        out.update({"pixels_differing": int((got_e != e).sum()), "pixels_ambiguous": int(amb.sum()),
+                    "pixels": int(e.size)})
+    return out
+
 def oracle_sample(img: np.ndarray, rows: int) -> tuple[float, str]:
     """Time the oracle on the first `rows` rows of the image; returns (Mpixel/s, description)."""
     import oracle
@@ -213,7 +331,7 @@ def oracle_sample(img: np.ndarray, rows: int) -> tuple[float, str]:
     return sample.size / dt / 1e6, f"rows 0..{rows} of the {W}x{H} image ({sample.size / 1e6:.1f} Mpixel), 1 thread"
 
 
-def oracle_images_parallel(imgs: list) -> dict:
+def oracle_images_parallel(imgs: list) -> tuple:
     """The oracle once per image, one image per thread on every host core (the
     images are independent; the ctypes call releases the GIL)."""
     import concurrent.futures as cf
@@ -223,11 +341,12 @@ def oracle_images_parallel(imgs: list) -> dict:
     oracle.lib()
     t0 = time.perf_counter()
     with cf.ThreadPoolExecutor(max_workers=cores) as ex:
-        list(ex.map(lambda im: oracle.canny_u8(im, LOW, HIGH), imgs))
+        outs = list(ex.map(lambda im: oracle.canny_u8(im, LOW, HIGH), imgs))
     dt = time.perf_counter() - t0
     px = sum(im.size for im in imgs)
     return {"value": round(px / dt / 1e6, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"all {len(imgs)} images ({px / 1e6:.1f} Mpixel), one image per thread"}
+            "sample": f"all {len(imgs)} images ({px / 1e6:.1f} Mpixel), one image per thread",
+            **cpu_info()}, outs
 
 
 def run_reference(args, rank: int, world: int) -> None:
@@ -322,11 +441,15 @@ def measure_batched(steps: int, cpu: bool = False) -> dict:
     same = all(torch.equal(a, b) for a, b in zip(outs_b, outs_l))
     ctx.close()
     loop_ctx.close()
-    cpu_line = oracle_images_parallel(imgs) if cpu else None
+    cpu_line, matches = None, None
+    if cpu:
+        cpu_line, want = oracle_images_parallel(imgs)
+        matches = all(np.array_equal(o.cpu().numpy(), wnt) for o, wnt in zip(outs_b, want))
     return {"images": BATCH_N, "sides": [BATCH_LO, BATCH_HI], "pixels": total,
             "batch_ms": round(res["batch"], 4), "loop_ms": round(res["loop"], 4),
             "batch_mpx_s": round(total / res["batch"] / 1e3, 1), "loop_mpx_s": round(total / res["loop"] / 1e3, 1),
             "speedup": round(res["loop"] / res["batch"], 2), "outputs_identical": bool(same),
+            "matches_oracle": matches,
             "tuning": {"band": tune["band"], "ctas_per_sm": tune["ctas_per_sm"]},
             "cpu_baseline": cpu_line}
 
@@ -373,10 +496,12 @@ def host_link_bound(h_in, h_out, d_a, d_b, px: int) -> dict:
 
 
 # ------------------------------------------------------------------ the other image sizes
-def measure_configs() -> list:
+def measure_configs(cpu: bool = False) -> list:
     """Per-image pipeline times on the smaller synthetic workloads: each run timed
     alone with CUDA events (median), stage averages from the library's own events.
-    These images fit in the 129 MB L2 except 7680 x 4320 (66 MB in + out: mostly)."""
+    These images fit in the 129 MB L2 except 7680 x 4320 (66 MB in + out: mostly).
+    cpu: also the oracle on each image (single thread, median of 3) and, for the
+    float variant, its error against the oracle."""
     import torch
 
     from paper_1710_07745_gb300 import canny, synth
@@ -412,21 +537,33 @@ def measure_configs() -> list:
         st = ctx.stats()
         ms = statistics.median(e0.elapsed_time(e1) for e0, e1 in ev)
         runs = max(1, tm["runs"])
-        out.append({"workload": name, "w": w, "h": h, "runs": n, "median_ms": round(ms, 4),
-                    "mpx_s": round(w * h / ms / 1e3, 1),
-                    "stencil_ms": round(tm["stencil_ms"] / runs, 4),
-                    "local_ms": round(tm["local_ms"] / runs, 4),
-                    "global_ms": round(tm["global_ms"] / runs, 4),
-                    "hyst_passes": int(st["hyst_passes"]), "pending_tiles": int(st["pending_tiles"]),
-                    "tiles_visited": int(st["hyst_tiles_visited"])})
+        entry = {"workload": name, "w": w, "h": h, "runs": n, "median_ms": round(ms, 4),
+                 "mpx_s": round(w * h / ms / 1e3, 1),
+                 "stencil_ms": round(tm["stencil_ms"] / runs, 4),
+                 "local_ms": round(tm["local_ms"] / runs, 4),
+                 "global_ms": round(tm["global_ms"] / runs, 4),
+                 "hyst_passes": int(st["hyst_passes"]), "pending_tiles": int(st["pending_tiles"]),
+                 "tiles_visited": int(st["hyst_tiles_visited"])}
+        if cpu:
+            import oracle
+            if path == canny.CANNY_PATH_INT:
+                t = oracle_median(lambda: oracle.canny_u8(img, LOW, HIGH))
+            else:
+                t = oracle_median(lambda: oracle.canny_f32(img))
+                entry["vs_oracle"] = float_error(img, d_in, d_out, ctx)
+            entry["cpu_baseline"] = {"value": round(w * h / t / 1e6, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                                     "sample": "the whole image, median of 3 single-thread runs", **cpu_info()}
+        out.append(entry)
         ctx.close()
         del d_in, d_out
     return out
 
 
-def measure_float_on(d_in, d_out, name: str, n: int) -> dict:
+def measure_float_on(d_in, d_out, name: str, n: int, img: np.ndarray | None = None) -> dict:
     """The float32 variant (sigma 1.4, 7 taps, thresholds 0.1 / 0.3 of the largest
-    strength) on an image already on the device: n runs timed with CUDA events."""
+    strength) on an image already on the device: n runs timed with CUDA events.
+    img: also the production kernel's strength error against the oracle on its
+    first 1024 rows."""
     import torch
 
     from paper_1710_07745_gb300 import canny
@@ -450,12 +587,15 @@ def measure_float_on(d_in, d_out, name: str, n: int) -> dict:
     tm = canny.canny_read_timing(ctx.ctx).as_dict()
     canny.canny_enable_timing(ctx.ctx, False)
     st = ctx.stats()
-    ctx.close()
     runs = max(1, tm["runs"])
-    return {"workload": name, "w": w, "h": h, "runs": n, "mean_ms": round(ms, 4),
-            "mpx_s": round(w * h / ms / 1e3, 1), "stencil_ms": round(tm["stencil_ms"] / runs, 4),
-            "global_ms": round(tm["global_ms"] / runs, 4), "hyst_passes": int(st["hyst_passes"]),
-            "pending_tiles": int(st["pending_tiles"]), "tiles_visited": int(st["hyst_tiles_visited"])}
+    entry = {"workload": name, "w": w, "h": h, "runs": n, "mean_ms": round(ms, 4),
+             "mpx_s": round(w * h / ms / 1e3, 1), "stencil_ms": round(tm["stencil_ms"] / runs, 4),
+             "global_ms": round(tm["global_ms"] / runs, 4), "hyst_passes": int(st["hyst_passes"]),
+             "pending_tiles": int(st["pending_tiles"]), "tiles_visited": int(st["hyst_tiles_visited"])}
+    if img is not None:
+        entry["vs_oracle"] = float_error(img, d_in, d_out, ctx, rows=1024)
+    ctx.close()
+    return entry
 
 
 # ------------------------------------------------------------------ serving
@@ -590,7 +730,9 @@ def run_ours(args, rank: int, world: int) -> None:
     value = job_value(world, args.steps, px, ms_max)
     k1_ms = tm["stencil_ms"] / max(1, tm["runs"])
     k1_gbs = K1_BYTES_PER_PX * px / (k1_ms / 1e3) / 1e9
-    pipe_gbs = PIPE_BYTES_PER_PX * px / (ms / args.steps / 1e3) / 1e9
+    k3_bytes = k3_traffic(W, H) if args.path == "int" else None
+    pipe_bytes = PIPE_BYTES_PER_PX * px + (k3_bytes or 0)
+    pipe_gbs = pipe_bytes / (ms / args.steps / 1e3) / 1e9
     stages = {"runs": tm["runs"], "reset_ms": round(tm["reset_ms"] / max(1, tm["runs"]), 4),
               "stencil_ms": round(k1_ms, 4),
               "local_ms": round(tm["local_ms"] / max(1, tm["runs"]), 4),
@@ -635,11 +777,11 @@ def run_ours(args, rank: int, world: int) -> None:
                                "api": "canny_run_host", "steps": single_steps},
                "link_bound": host_link_bound(h_in[0], h_out[0], d_in, d_out, px)}
 
-    configs = None if args.no_configs else measure_configs()
+    do_cpu = rank == 0 and not args.no_cpu
+    configs = None if args.no_configs else measure_configs(cpu=do_cpu)
     if configs is not None:
-        configs.append(measure_float_on(d_in, d_out, f"canny_f32_{W}x{H}", 10))
-    batched = None if args.no_batch else measure_batched(max(3, min(args.steps, 10)),
-                                                          cpu=rank == 0 and not args.no_cpu)
+        configs.append(measure_float_on(d_in, d_out, f"canny_f32_{W}x{H}", 10, img if do_cpu else None))
+    batched = None if args.no_batch else measure_batched(max(3, min(args.steps, 10)), cpu=do_cpu)
     serving = None if args.no_serve else measure_serving(args.serve_requests)
     if rank != 0:
         ctx.close()
@@ -649,14 +791,15 @@ def run_ours(args, rank: int, world: int) -> None:
         rows = min(H, int(os.environ.get("CANNY_CPU_ROWS", "4096")))
         cpu_v, cpu_sample = oracle_sample(img, rows)
         cpu = {"value": round(cpu_v, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": cpu_sample}
+               "sample": cpu_sample, **cpu_info()}
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int32" if args.path == "int" else "f32",
         "data": "synthetic", "config": config({"path": "integer" if args.path == "int" else "float32"}),
-        "roofline": {"kernel": "k1_fused_kernel (Gauss/Sobel/NMS/threshold + tile-local hysteresis)"
+        "roofline": {"kernel": "stencil stage: k1_fused_kernel (Gauss/Sobel/NMS/thresholds -> 2-bit class masks) "
+                               "+ hyst_fill_kernel (tile-local hysteresis -> edge bytes); 2 B/px algorithmic"
                      if args.path == "int" else
                      "k1f_strength_kernel + k1f_nms_kernel (both stencil passes of the float variant)",
                      "bound": "hbm", "achieved": round(k1_gbs, 1), "peak": peaks["hbm_gbs"],
@@ -666,7 +809,9 @@ def run_ours(args, rank: int, world: int) -> None:
                      "bytes_per_launch": K1_BYTES_PER_PX * px},
         "alu_roofline": alu_roofline(px, k1_ms, peaks["hbm_gbs"], clk) if args.path == "int" else None,
         "pipeline_roofline": {"achieved": round(pipe_gbs, 1), "unit": "GB/s",
-                              "bytes_per_px": PIPE_BYTES_PER_PX,
+                              "bytes": pipe_bytes, "basis": f"{PIPE_BYTES_PER_PX} B/px (read the image, write the edge "
+                              "map) + the global passes' measured DRAM bytes" + ("" if k3_bytes else
+                                                                             " (not recorded for this source: 0)"),
                               "frac": round(pipe_gbs / peaks["hbm_gbs"], 4)},
         "stages": stages, "dominant_stage": dominant,
         "configs": configs,
@@ -674,8 +819,9 @@ def run_ours(args, rank: int, world: int) -> None:
         "serving": serving,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        # per step: the control-block reset, the fused kernel, one kernel per global pass
-        "gpu_launches": int(args.steps * (2 + passes)),
+        # per step: the control-block reset, the fused stencil, the tile fill and one
+        # cooperative launch that runs every global pass
+        "gpu_launches": int(args.steps * 4),
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)

@@ -181,9 +181,11 @@ canny_status canny_classify(canny_ctx *ctx, const canny_image *img, void *stream
 canny_status canny_hysteresis(canny_ctx *ctx, const canny_image *img, void *stream);
 
 /*
- * Float path, Steps 1-2 only: the gradient strength M (float32, row stride
- * d_mag_pitch floats) of img into d_mag, and the image's largest strength into
- * *d_max (device float). The context must use CANNY_PATH_F32.
+ * Float path, Steps 1-2 only (Sec. 2.2.1 Step 2, "gradient strength"): the
+ * strength M (float32, row stride d_mag_pitch floats) of img into d_mag, and the
+ * image's largest strength into *d_max (device float), as computed by the
+ * float pipeline's own first pass (M = sqrt_rn(Gx^2 + Gy^2) per pixel). The
+ * context must use CANNY_PATH_F32.
  */
 canny_status canny_magnitude_f32(canny_ctx *ctx, const canny_image *img, float *d_mag,
                                  int d_mag_pitch, float *d_max, void *stream);

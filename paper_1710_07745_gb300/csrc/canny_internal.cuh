@@ -202,6 +202,10 @@ size_t k1f_map_bytes(int w, int h);
 // into *d_smax (as float bits; the caller zeroes it first).
 cudaError_t launch_k1f_strength(const uint8_t *in, int in_pitch, int w, int h, const FloatParams &fp,
                                 float *d_smax, void *maps, cudaStream_t s);
+// The strengths of pass 1's maps: M = sqrt_rn(s) per pixel into mag (mag_pitch
+// floats a row), Mmax = sqrt_rn(*d_smax) into *d_max.
+cudaError_t launch_k1f_strength_out(const void *maps, int w, int h, float *mag, int mag_pitch, const float *d_smax,
+                                    float *d_max, cudaStream_t s);
 // Float path pass 2: Step 3 and the thresholds relative to sqrt(*d_smax) from the
 // maps, then the tile-local hysteresis: edges into img.map, tile state into hs
 // (after hyst_reset).

@@ -499,6 +499,28 @@ cudaError_t launch_k1f_strength(const uint8_t *in, int in_pitch, int w, int h, c
     }
 }
 
+namespace {
+// Strength M = sqrt_rn(s) of every pixel from pass 1's map, and Mmax = sqrt_rn(smax).
+__global__ void k1f_strength_out_kernel(const float *__restrict__ smap, int mp, int w, int h, float *__restrict__ mag,
+                                        int mag_pitch, const float *d_smax, float *d_max)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x == 0 && y == 0) *d_max = __fsqrt_rn(*d_smax);
+    if (x < w && y < h) mag[(int64_t)y * mag_pitch + x] = __fsqrt_rn(smap[(int64_t)y * mp + x]);
+}
+}  // namespace
+
+cudaError_t launch_k1f_strength_out(const void *maps, int w, int h, float *mag, int mag_pitch, const float *d_smax,
+                                    float *d_max, cudaStream_t s)
+{
+    if (w <= 0 || h <= 0) return cudaSuccess;
+    const MapLayout L = map_layout(w, h);
+    const dim3 grid((w + 255) / 256, h);
+    k1f_strength_out_kernel<<<grid, 256, 0, s>>>(static_cast<const float *>(maps), L.mp, w, h, mag, mag_pitch, d_smax,
+                                                 d_max);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_k1f_nms(const void *maps, int w, int h, const FloatParams &fp, const float *d_smax,
                            const HystScratch &hs, HystImage img, cudaStream_t s)
 {

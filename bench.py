@@ -598,6 +598,54 @@ def measure_float_on(d_in, d_out, name: str, n: int, img: np.ndarray | None = No
     return entry
 
 
+# ------------------------------------------------------------------ long weak chains
+def serpentine(n: int, gap: int = 32) -> np.ndarray:
+    """Class map of one weak path through every 32 x 32 tile of an n x n image:
+    horizontal runs every `gap` rows joined at alternate ends, strong only at its
+    start (the adversarial case for hysteresis)."""
+    cls = np.zeros((n, n), np.uint8)
+    rows = list(range(gap // 2, n, gap))
+    for j, r in enumerate(rows):
+        cls[r, :] = 1
+        if j + 1 < len(rows):
+            c = n - 1 if j % 2 == 0 else 0
+            cls[r:rows[j + 1] + 1, c] = 1
+    cls[rows[0], 0] = 2
+    return cls
+
+
+def measure_chains(tile_counts=(256, 1024, 4096, 16384), runs: int = 5) -> list:
+    """Global hysteresis time and passes against the length of one weak chain
+    (a serpentine through every tile), through canny_hysteresis on a class map."""
+    import torch
+
+    from paper_1710_07745_gb300 import canny
+    out = []
+    sp = torch.cuda.current_stream().cuda_stream
+    for tiles in tile_counts:
+        n = 32 * int(round(tiles ** 0.5))
+        cls = serpentine(n)
+        d_in = torch.from_numpy(cls).cuda()
+        d_out = torch.empty_like(d_in)
+        with canny.Canny(n, n) as c:
+            img = canny.image_of(d_in, d_out)
+            for _ in range(2):
+                canny.canny_hysteresis(c.ctx, img, sp)
+            torch.cuda.synchronize()
+            canny.canny_enable_timing(c.ctx, True)
+            for _ in range(runs):
+                canny.canny_hysteresis(c.ctx, img, sp)
+            torch.cuda.synchronize()
+            tm = canny.canny_read_timing(c.ctx).as_dict()
+            canny.canny_enable_timing(c.ctx, False)
+            st = c.stats()
+            reached = int((d_out == 255).sum().item())
+        out.append({"tiles": tiles, "chain_pixels": int((cls > 0).sum()), "reached": reached,
+                    "global_ms": round(tm["global_ms"] / max(1, tm["runs"]), 4),
+                    "hyst_passes": int(st["hyst_passes"]), "tiles_visited": int(st["hyst_tiles_visited"])})
+    return out
+
+
 # ------------------------------------------------------------------ serving
 SERVE_POOL, SERVE_LO, SERVE_HI, SERVE_SEED = 256, 128, 4096, 5000
 
@@ -783,6 +831,7 @@ def run_ours(args, rank: int, world: int) -> None:
         configs.append(measure_float_on(d_in, d_out, f"canny_f32_{W}x{H}", 10, img if do_cpu else None))
     batched = None if args.no_batch else measure_batched(max(3, min(args.steps, 10)), cpu=do_cpu)
     serving = None if args.no_serve else measure_serving(args.serve_requests)
+    chains = None if args.no_configs else measure_chains()
     if rank != 0:
         ctx.close()
         return
@@ -817,6 +866,7 @@ def run_ours(args, rank: int, world: int) -> None:
         "configs": configs,
         "batched": batched,
         "serving": serving,
+        "hysteresis_chains": chains,
         "cpu_baseline": cpu,
         "e2e": e2e,
         # per step: the control-block reset, the fused stencil, the tile fill and one

@@ -198,7 +198,10 @@ canny_status ensure_hyst(canny_ctx *c, uint32_t max_tiles, uint32_t max_imgs)
     size_t off_stamp = align_up(off_pend + sizeof(uint32_t) * HT * (size_t)max_tiles, 256);
     size_t off_lists = align_up(off_stamp + sizeof(uint32_t) * (size_t)max_tiles, 256);
     size_t off_bits = align_up(off_lists + sizeof(uint32_t) * 2 * (size_t)max_tiles, 256);
-    size_t off_state = align_up(off_bits + sizeof(uint32_t) * 2 * HT * (size_t)max_tiles, 256);
+    size_t off_uf_label = align_up(off_bits + sizeof(uint32_t) * 2 * HT * (size_t)max_tiles, 256);
+    size_t off_uf_parent = align_up(off_uf_label + 128 * (size_t)max_tiles, 256);
+    size_t off_uf_seeded = align_up(off_uf_parent + sizeof(uint32_t) * 64 * (size_t)max_tiles, 256);
+    size_t off_state = align_up(off_uf_seeded + 64 * (size_t)max_tiles, 256);
     size_t total = align_up(off_state + sizeof(HystState), 256);
     void *mem = nullptr;
     cudaError_t e = dev_alloc(&mem, total);
@@ -214,6 +217,9 @@ canny_status ensure_hyst(canny_ctx *c, uint32_t max_tiles, uint32_t max_imgs)
     c->hs.stamp = (uint32_t *)(b + off_stamp);
     c->hs.lists = (uint32_t *)(b + off_lists);
     c->hs.bits = (uint32_t *)(b + off_bits);
+    c->hs.uf_label = (uint8_t *)(b + off_uf_label);
+    c->hs.uf_parent = (uint32_t *)(b + off_uf_parent);
+    c->hs.uf_seeded = (uint8_t *)(b + off_uf_seeded);
     c->hs.state = (HystState *)(b + off_state);
     c->hs.max_tiles = max_tiles;
     c->hs.max_imgs = max_imgs;

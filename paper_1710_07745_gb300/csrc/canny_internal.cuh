@@ -80,6 +80,11 @@ struct HystScratch {
     HystState *state;
     uint32_t max_tiles;
     uint32_t max_imgs;
+    // union-find over the border components of pending pixels (the global passes'
+    // stage for long chains; null: passes only)
+    uint8_t *uf_label;        // [max_tiles * 128]: component of each of the 124 border pixels, count at 127
+    uint32_t *uf_parent;      // [max_tiles * 64]: parent of component 64 t + j
+    uint8_t *uf_seeded;       // [max_tiles * 64]: component touches an edge of a neighbouring tile
 };
 
 // ---------------------------------------------------------------- stencil launch data

@@ -57,7 +57,7 @@ enum { NB_U, NB_UL, NB_UR, NB_D, NB_DL, NB_DR, NB_L, NB_R };
 
 // Tiles one worklist entry may chase into within a pass before the rest is
 // queued for the next pass, and the depth of the per-warp chase stack.
-constexpr int CHASE_BUDGET = 512;
+constexpr int CHASE_BUDGET = 64;
 constexpr int CHASE_STACK = 32;
 
 // Border masks as other warps last wrote them: loads that bypass L1, since
@@ -396,9 +396,279 @@ __device__ __forceinline__ bool grid_barrier(HystState *st)
     return ok_s != 0;
 }
 
+// ---------------------------------------------------------------- long chains: union-find
+// When the first pass leaves work for a second one (a chain longer than one
+// warp's chase budget, or more chains than the chase stacks hold), the rest is
+// resolved at once instead of pass after pass. Every pending pixel is, by then,
+// a weak pixel not connected inside its tile to an edge, so a pending pixel
+// becomes an edge exactly when it is connected, through pending pixels across
+// tile borders, to a pending border pixel next to an edge of a neighbouring tile.
+//   label   each tile with pending border pixels splits them into the components
+//           of its pending pixels (one flood per component) and lists itself;
+//   union   each listed tile joins its components with those of its right,
+//           lower and two lower diagonal neighbours wherever pending border
+//           pixels touch (lock-free union-find, links by atomicCAS, finds with
+//           path halving), and marks components next to a neighbour's edge;
+//   roots   a marked component marks its root;
+//   apply   each listed tile floods its pending pixels from the border pixels
+//           whose component's root is marked and writes the new edges.
+// The phases are separated by grid barriers, whatever the chain length; between
+// union and roots, rounds of pointer jumping (each halves every path) make the
+// trees flat, so at most log2(components) rounds run.
+constexpr int UF_LSTRIDE = 128;         // label bytes a tile: 124 border pixels, count at byte 127
+constexpr int UF_COUNT = 127;
+constexpr uint32_t UF_MAXC = 64;        // components a tile (at most 62 can touch its border)
+
+// Border pixel (x, y) of a tile as a position: 0..31 top row, 32..63 bottom row,
+// 64..93 left column rows 1..30, 94..123 right column rows 1..30.
+__device__ __forceinline__ int border_pos(int x, int y)
+{
+    return y == 0 ? x : (y == HT - 1 ? HT + x : (x == 0 ? 2 * HT + y - 1 : 3 * HT - 2 + y - 1));
+}
+
+__device__ __forceinline__ bool pending_border(const TileMasks &m)
+{
+    return (m.pend_top | m.pend_bottom | m.pend_left | m.pend_right) != 0u;
+}
+
+__device__ __forceinline__ uint32_t uf_find(uint32_t *parent, uint32_t x)
+{
+    for (;;) {
+        const uint32_t p = __ldcg(parent + x);
+        if (p == x) return x;
+        const uint32_t gp = __ldcg(parent + p);
+        if (gp != p) parent[x] = gp;          // path halving: gp is an ancestor of x
+        x = gp;
+    }
+}
+
+__device__ __forceinline__ void uf_union(uint32_t *parent, uint32_t a, uint32_t b)
+{
+    for (;;) {
+        a = uf_find(parent, a);
+        b = uf_find(parent, b);
+        if (a == b) return;
+        if (a < b) { const uint32_t t = a; a = b; b = t; }
+        if (atomicCAS(parent + a, a, b) == a) return;   // link the larger root under the smaller
+    }
+}
+
+__device__ __forceinline__ uint32_t uf_comp(const HystScratch &hs, uint32_t t, int pos)
+{
+    return t * UF_MAXC + __ldcg(hs.uf_label + (size_t)t * UF_LSTRIDE + pos);
+}
+
+// label: every tile of the run with pending border pixels (lanes test 32 tiles at
+// once; the warp labels those that have some)
+__device__ __forceinline__ void uf_label_phase(const HystScratch &hs, int lane, uint32_t warp, uint32_t nwarps)
+{
+    HystState *st = hs.state;
+    const uint32_t ntiles = min(st->ntiles, hs.max_tiles);
+    for (uint32_t base = warp * 32u; base < ntiles; base += nwarps * 32u) {
+        const uint32_t i = base + (uint32_t)lane;
+        const bool act = i < ntiles && pending_border(masks_cg(&hs.masks[i]));
+        uint32_t todo = __ballot_sync(FULL, act);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const uint32_t t = base + (uint32_t)src;
+            const TileMasks m = masks_cg(&hs.masks[t]);
+            const uint32_t P = __ldcg(&hs.pend_bits[(size_t)t * HT + lane]);
+            uint8_t *lab = hs.uf_label + (size_t)t * UF_LSTRIDE;
+            uint32_t rt = m.pend_top, rb = m.pend_bottom;
+            uint32_t rl = m.pend_left & 0x7FFFFFFEu, rr = m.pend_right & 0x7FFFFFFEu;   // rows 1..30
+            uint32_t k = 0;
+            while ((rt | rb | rl | rr) != 0u && k < UF_MAXC) {
+                int sy, sx;
+                if (rt) { sy = 0; sx = __ffs(rt) - 1; }
+                else if (rb) { sy = HT - 1; sx = __ffs(rb) - 1; }
+                else if (rl) { sy = __ffs(rl) - 1; sx = 0; }
+                else { sy = __ffs(rr) - 1; sx = HT - 1; }
+                const uint32_t C = flood_tile(lane == sy ? (1u << sx) : 0u, P, lane);
+                const uint32_t ct = __shfl_sync(FULL, C, 0), cb = __shfl_sync(FULL, C, HT - 1);
+                const uint32_t cl = __ballot_sync(FULL, C & 1u), cr = __ballot_sync(FULL, C >> 31);
+                if (((ct & rt) >> lane) & 1u) lab[lane] = (uint8_t)k;
+                if (((cb & rb) >> lane) & 1u) lab[HT + lane] = (uint8_t)k;
+                if (((cl & rl) >> lane) & 1u) lab[2 * HT + lane - 1] = (uint8_t)k;
+                if (((cr & rr) >> lane) & 1u) lab[3 * HT - 2 + lane - 1] = (uint8_t)k;
+                rt &= ~ct;
+                rb &= ~cb;
+                rl &= ~cl;
+                rr &= ~cr;
+                if (lane == 0) {
+                    hs.uf_parent[(size_t)t * UF_MAXC + k] = t * UF_MAXC + k;
+                    hs.uf_seeded[(size_t)t * UF_MAXC + k] = 0;
+                }
+                ++k;
+            }
+            if (lane == 0) {
+                lab[UF_COUNT] = (uint8_t)k;
+                const uint32_t slot = atomicAdd(&st->pad[0], 1u);
+                if (CANNY_CHECK(slot < hs.max_tiles, &st->error)) hs.lists[slot] = t;
+            }
+        }
+    }
+}
+
+// union: a listed tile with its right, lower, lower-right and lower-left neighbours;
+// components next to a neighbour's edge are marked
+__device__ __forceinline__ void uf_union_phase(const HystScratch &hs, int lane, uint32_t warp, uint32_t nwarps)
+{
+    HystState *st = hs.state;
+    const uint32_t n = min(*(volatile uint32_t *)&st->pad[0], hs.max_tiles);
+    const int nimg = (int)st->nimg;
+    for (uint32_t i = warp; i < n; i += nwarps) {
+        const uint32_t t = __ldcg(&hs.lists[i]);
+        TileSeeds sd;
+        find_seeds(hs, t, nimg, sd);
+        const HystImage &im = sd.im;
+        const int tx = sd.tx, ty = sd.ty;
+        const uint32_t ntx = (uint32_t)im.ntx;
+        const bool hasL = tx > 0, hasR = tx < im.ntx - 1, hasD = ty < im.nty - 1;
+        const TileMasks m = masks_cg(&hs.masks[t]);
+        const int y = lane, x = lane;
+        // marks: pending border pixels next to an edge of a neighbouring tile
+        if ((sd.top >> x) & 1u) hs.uf_seeded[uf_comp(hs, t, x)] = 1;
+        if ((sd.bot >> x) & 1u) hs.uf_seeded[uf_comp(hs, t, HT + x)] = 1;
+        if ((sd.left >> y) & 1u) hs.uf_seeded[uf_comp(hs, t, border_pos(0, y))] = 1;
+        if ((sd.right >> y) & 1u) hs.uf_seeded[uf_comp(hs, t, border_pos(HT - 1, y))] = 1;
+        if (hasR && ((m.pend_right >> y) & 1u)) {
+            const uint32_t nb = t + 1;
+            const uint32_t pl = __ldcg(&hs.masks[nb].pend_left);
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int y2 = y + dy;
+                if (y2 >= 0 && y2 < HT && ((pl >> y2) & 1u))
+                    uf_union(hs.uf_parent, uf_comp(hs, t, border_pos(HT - 1, y)), uf_comp(hs, nb, border_pos(0, y2)));
+            }
+        }
+        if (hasD && ((m.pend_bottom >> x) & 1u)) {
+            const uint32_t nb = t + ntx;
+            const uint32_t pt = __ldcg(&hs.masks[nb].pend_top);
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int x2 = x + dx;
+                if (x2 >= 0 && x2 < HT && ((pt >> x2) & 1u))
+                    uf_union(hs.uf_parent, uf_comp(hs, t, HT + x), uf_comp(hs, nb, x2));
+            }
+        }
+        if (lane == 0 && hasD && hasR && (m.pend_bottom >> 31) && (__ldcg(&hs.masks[t + ntx + 1].pend_top) & 1u))
+            uf_union(hs.uf_parent, uf_comp(hs, t, 2 * HT - 1), uf_comp(hs, t + ntx + 1, 0));
+        if (lane == 1 && hasD && hasL && (m.pend_bottom & 1u) && (__ldcg(&hs.masks[t + ntx - 1].pend_top) >> 31))
+            uf_union(hs.uf_parent, uf_comp(hs, t, HT), uf_comp(hs, t + ntx - 1, HT - 1));
+    }
+}
+
+// jump: every component's parent becomes its grandparent; a round that changes
+// nothing ends the jumping (the forest is final once the unions are done, so
+// after r rounds paths are 2^r times shorter)
+__device__ __forceinline__ bool uf_jump_phase(const HystScratch &hs, int lane, uint32_t warp, uint32_t nwarps)
+{
+    HystState *st = hs.state;
+    const uint32_t n = min(*(volatile uint32_t *)&st->pad[0], hs.max_tiles);
+    bool changed = false;
+    for (uint32_t i = warp; i < n; i += nwarps) {
+        const uint32_t t = __ldcg(&hs.lists[i]);
+        const uint32_t k = __ldcg(hs.uf_label + (size_t)t * UF_LSTRIDE + UF_COUNT);
+        for (uint32_t j = (uint32_t)lane; j < k; j += 32u) {
+            const uint32_t c = t * UF_MAXC + j;
+            const uint32_t p = __ldcg(hs.uf_parent + c), gp = __ldcg(hs.uf_parent + p);
+            if (gp != p) {
+                hs.uf_parent[c] = gp;
+                changed = true;
+            }
+        }
+    }
+    return changed;
+}
+
+// roots: a marked component marks its root
+__device__ __forceinline__ void uf_roots_phase(const HystScratch &hs, int lane, uint32_t warp, uint32_t nwarps)
+{
+    HystState *st = hs.state;
+    const uint32_t n = min(*(volatile uint32_t *)&st->pad[0], hs.max_tiles);
+    for (uint32_t i = warp; i < n; i += nwarps) {
+        const uint32_t t = __ldcg(&hs.lists[i]);
+        const uint32_t k = __ldcg(hs.uf_label + (size_t)t * UF_LSTRIDE + UF_COUNT);
+        for (uint32_t j = (uint32_t)lane; j < k; j += 32u) {
+            const uint32_t c = t * UF_MAXC + j;
+            if (__ldcg(hs.uf_seeded + c)) hs.uf_seeded[uf_find(hs.uf_parent, c)] = 1;
+        }
+    }
+}
+
+// apply: a listed tile floods its pending pixels from the border pixels of marked
+// components and writes the new edges
+__device__ __forceinline__ void uf_apply_phase(const HystScratch &hs, int lane, uint32_t warp, uint32_t nwarps)
+{
+    HystState *st = hs.state;
+    const uint32_t n = min(*(volatile uint32_t *)&st->pad[0], hs.max_tiles);
+    const int nimg = (int)st->nimg;
+    for (uint32_t i = warp; i < n; i += nwarps) {
+        const uint32_t t = __ldcg(&hs.lists[i]);
+        const TileMasks m = masks_cg(&hs.masks[t]);
+        const int y = lane, x = lane;
+        auto marked = [&](int pos) { return __ldcg(hs.uf_seeded + uf_find(hs.uf_parent, uf_comp(hs, t, pos))) != 0; };
+        const bool st_top = ((m.pend_top >> x) & 1u) && marked(x);
+        const bool st_bot = ((m.pend_bottom >> x) & 1u) && marked(HT + x);
+        const bool st_l = y > 0 && y < HT - 1 && ((m.pend_left >> y) & 1u) && marked(border_pos(0, y));
+        const bool st_r = y > 0 && y < HT - 1 && ((m.pend_right >> y) & 1u) && marked(border_pos(HT - 1, y));
+        const uint32_t top = __ballot_sync(FULL, st_top), bot = __ballot_sync(FULL, st_bot);
+        uint32_t e0 = (st_l ? 1u : 0u) | (st_r ? 0x80000000u : 0u);
+        if (lane == 0) e0 |= top;
+        if (lane == HT - 1) e0 |= bot;
+        if (!__any_sync(FULL, e0 != 0u)) continue;
+        const uint32_t p = __ldcg(&hs.pend_bits[(size_t)t * HT + lane]);
+        const uint32_t e = flood_tile(e0 & p, p, lane);
+        const HystImage im = hs.imgs[find_image(hs.imgs, nimg, t)];
+        const uint32_t local = t - im.tile_base;
+        const int tx = (int)(local % (uint32_t)im.ntx), ty = (int)(local / (uint32_t)im.ntx);
+        if (e) {
+            uint8_t *row = im.map + (int64_t)(ty * HT + lane) * im.pitch + tx * HT;
+            uint32_t bits = e;
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                row[b] = 255;
+                bits &= bits - 1;
+            }
+        }
+        hs.pend_bits[(size_t)t * HT + lane] = p & ~e;
+    }
+}
+
+// The four phases in one cooperative launch (every CTA resident); false if a
+// barrier's bounded wait ran out.
+__device__ __forceinline__ bool uf_resolve(const HystScratch &hs)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * THREADS + threadIdx.x) >> 5, nwarps = gridDim.x * WARPS;
+    if (blockIdx.x == 0 && threadIdx.x == 0) hs.state->pad[0] = hs.state->pad[1] = 0u;
+    if (!grid_barrier(hs.state)) return false;
+    uf_label_phase(hs, lane, warp, nwarps);
+    if (!grid_barrier(hs.state)) return false;
+    uf_union_phase(hs, lane, warp, nwarps);
+    if (!grid_barrier(hs.state)) return false;
+    // pad[1]: the last jump round (counted from 1) that changed a parent
+    for (uint32_t r = 1; r <= 32; ++r) {
+        if (uf_jump_phase(hs, lane, warp, nwarps)) atomicMax(&hs.state->pad[1], r);
+        if (!grid_barrier(hs.state)) return false;
+        if (*(volatile uint32_t *)&hs.state->pad[1] < r) break;
+    }
+    uf_roots_phase(hs, lane, warp, nwarps);
+    if (!grid_barrier(hs.state)) return false;
+    uf_apply_phase(hs, lane, warp, nwarps);
+    if (!grid_barrier(hs.state)) return false;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        HystState *st = hs.state;
+        st->visited += st->pad[0];
+        st->pass += 1;                          // the union-find stage counts as one pass
+        st->keep_going = 0;
+        st->list_count[0] = st->list_count[1] = 0;
+    }
+    return true;
+}
+
 // All passes in one cooperative launch: pass, barrier, stop when the last CTA
 // of the pass found nothing more to do (or the pass cap was reached).
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, 2)
 hyst_global_coop_kernel(HystScratch hs)
 {
     __shared__ uint32_t stack[WARPS][CHASE_STACK];
@@ -407,6 +677,11 @@ hyst_global_coop_kernel(HystScratch hs)
         global_pass(hs, 0, cudaGraphConditionalHandle{}, stack, visits);
         if (!grid_barrier(hs.state)) break;
         if (!*(volatile uint32_t *)&hs.state->keep_going) break;
+        // work left after a pass: resolve every long chain at once
+        if (hs.uf_parent) {
+            uf_resolve(hs);
+            break;
+        }
     }
 }
 

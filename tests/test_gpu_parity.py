@@ -304,6 +304,36 @@ def test_hysteresis_chain_longer_than_the_chase_budget():
     assert st["hyst_passes"] > 1                          # the budget per entry spills to later passes
 
 
+@pytest.mark.parametrize("tiles", [256, 1024, 4096, 16384])
+def test_hysteresis_long_serpentines_resolve_in_two_passes(tiles):
+    """One weak chain through every tile (strong only at its start): the first
+    pass chases it for a budget of tiles, the union-find stage resolves the rest
+    at once, so the pass count stays at two whatever the length."""
+    n = 32 * int(round(tiles ** 0.5))
+    cls = serpentine_map(n)
+    out, st = run_hyst(cls)
+    assert st["status"] == canny.CANNY_OK
+    assert np.array_equal(out, oracle.hysteresis(cls))
+    assert (out == 255).sum() == (cls > 0).sum()
+    assert st["hyst_passes"] <= 2
+
+
+def test_hysteresis_union_find_keeps_unreached_components_weak():
+    """Long chains, one seeded at its start and one never seeded, plus pending
+    blobs that touch tile borders without any edge: only the seeded chain's
+    pixels become edges."""
+    n = 1024
+    cls = serpentine_map(n)
+    cls[n // 2 + 7, :] = 0                              # cut the chain once: its far part stays weak
+    rng = np.random.default_rng(5)
+    for _ in range(40):
+        y, x = (int(v) for v in rng.integers(0, n - 8, 2))
+        cls[y:y + 6, x:x + 6] = np.maximum(cls[y:y + 6, x:x + 6], 1)
+    out, st = run_hyst(cls)
+    assert st["status"] == canny.CANNY_OK
+    assert np.array_equal(out, oracle.hysteresis(cls))
+
+
 def test_hysteresis_pass_cap_reports_no_convergence():
     cls = serpentine_map(2048)
     out, st = run_hyst(cls, max_passes=1)

@@ -450,7 +450,8 @@ def measure_batched(steps: int, cpu: bool = False) -> dict:
             "batch_mpx_s": round(total / res["batch"] / 1e3, 1), "loop_mpx_s": round(total / res["loop"] / 1e3, 1),
             "speedup": round(res["loop"] / res["batch"], 2), "outputs_identical": bool(same),
             "matches_oracle": matches,
-            "tuning": {"band": tune["band"], "ctas_per_sm": tune["ctas_per_sm"]},
+            "tuning": {k: tune[k] for k in ("band", "ctas_per_sm", "direct_loads", "chase_budget", "batch_passes",
+                                            "from_cache")},
             "cpu_baseline": cpu_line}
 
 

@@ -220,6 +220,16 @@ canny_status canny_read_timing(canny_ctx *ctx, canny_timing *out);
  * counter. direct_loads = 1 reads
  * inputs whose base or pitch is not a multiple of 16 bytes directly instead of
  * repitching them into staging first (slower; no staging memory); 0 or 1.
+ *
+ * Schedule of the global hysteresis passes (Section 3's connectivity step):
+ * chase_budget is how many further tiles one worklist entry may follow a weak
+ * chain into within a pass before it leaves the rest to the next pass (0, the
+ * default: 64; else 1..4096); batch_passes picks how a batch graph runs the
+ * passes: 0 (the default) a graph while-loop of one launch per pass, 1 one
+ * cooperative kernel node that runs every pass behind a grid barrier (and
+ * resolves chains still unfinished after a pass by union-find over tile-border
+ * components); 1 falls back to 0 where the device cannot hold that grid.
+ * Every setting gives the same edge map.
  */
 typedef struct {
     int band;
@@ -227,6 +237,8 @@ typedef struct {
     double ms;        /* canny_autotune_batch: measured time of one batch run */
     int from_cache;   /* canny_autotune_batch: 1 if read from the cache file */
     int direct_loads;
+    int chase_budget;
+    int batch_passes;
 } canny_tuning;
 
 /* Apply a configuration; CANNY_EINVAL for an unsupported band or CTA count. */
@@ -236,9 +248,13 @@ canny_status canny_get_tuning(const canny_ctx *ctx, canny_tuning *out);
 /*
  * Pick the configuration for batches like `imgs` (integer path): look up the
  * size class (device, image count and mean area in octaves) in cache_path
- * (JSON lines; NULL for none); if absent, time every candidate on this batch
- * (each runs the batch three times; outputs are overwritten with the same
- * edge maps), append the winner to cache_path, and apply it. Synchronous.
+ * (JSON lines; NULL for none); if absent, time candidates on this batch in
+ * three stages, each keeping the best of the one before: tile shape (band x
+ * ctas_per_sm), then the halo layout of unaligned inputs (direct_loads 0/1,
+ * only when the batch has such an input), then the pass schedule
+ * (chase_budget x batch_passes). Each candidate runs the batch three times
+ * (outputs are overwritten with the same edge maps). The winner is appended to
+ * cache_path and applied. Synchronous.
  */
 canny_status canny_autotune_batch(canny_ctx *ctx, int n, const canny_image *imgs, void *stream,
                                   const char *cache_path, canny_tuning *out);

@@ -54,7 +54,8 @@ class canny_timing(ctypes.Structure):
 
 class canny_tuning(ctypes.Structure):
     _fields_ = [("band", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("ms", ctypes.c_double),
-                ("from_cache", ctypes.c_int), ("direct_loads", ctypes.c_int)]
+                ("from_cache", ctypes.c_int), ("direct_loads", ctypes.c_int), ("chase_budget", ctypes.c_int),
+                ("batch_passes", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -266,8 +267,9 @@ def canny_run_noalloc(d_in: int, in_pitch: int, d_out: int, out_pitch: int, w: i
            "canny_run_noalloc")
 
 
-def canny_set_tuning(ctx: int, band: int, ctas_per_sm: int, direct_loads: int = 0) -> None:
-    t = canny_tuning(band, ctas_per_sm, 0.0, 0, direct_loads)
+def canny_set_tuning(ctx: int, band: int, ctas_per_sm: int, direct_loads: int = 0, chase_budget: int = 0,
+                     batch_passes: int = 0) -> None:
+    t = canny_tuning(band, ctas_per_sm, 0.0, 0, direct_loads, chase_budget, batch_passes)
     _check(load().canny_set_tuning(ctx, ctypes.byref(t)), "canny_set_tuning")
 
 
@@ -372,8 +374,9 @@ class Canny:
         return canny_autotune_batch(self.ctx, [image_of(a, b) for a, b in pairs], _stream_ptr(stream),
                                     cache_path).as_dict()
 
-    def set_tuning(self, band: int, ctas_per_sm: int, direct_loads: int = 0) -> None:
-        canny_set_tuning(self.ctx, band, ctas_per_sm, direct_loads)
+    def set_tuning(self, band: int, ctas_per_sm: int, direct_loads: int = 0, chase_budget: int = 0,
+                   batch_passes: int = 0) -> None:
+        canny_set_tuning(self.ctx, band, ctas_per_sm, direct_loads, chase_budget, batch_passes)
 
     def stats(self) -> dict:
         return canny_get_stats(self.ctx).as_dict()

@@ -51,6 +51,8 @@ struct canny_ctx {
     int band = 0;                      // rows per unit of work; 0: chosen per image size
     int ctas_per_sm = 0;               // batches: 0 = one CTA per unit, else persistent CTAs per SM
     int direct_loads = 0;              // 1: inputs the TMA path cannot read are not repitched
+    int chase_budget = 0;              // global passes: tiles one worklist entry may chase (0: default)
+    int batch_passes = 0;              // batch graphs: 0 = while-loop of passes, 1 = one cooperative node
 
     // integer-path batches: per staging slot one graph per fused-kernel variant
     // ([0] TMA or direct loads per image, [1] TMA only), descriptors uploaded
@@ -411,7 +413,7 @@ canny_status run_one(canny_ctx *c, const canny_image *im, cudaStream_t s, bool s
     cudaEvent_t *ev = slot >= 0 ? &c->ev[EV_PER_RUN * slot] : nullptr;
     if (ev) cudaEventRecord(ev[0], s);
     const HystImage himg = hyst_image(im, 0);
-    st = from_cuda(hyst_reset(c->hs, ntiles, 1, max_passes_for(c, ntiles), s, &himg));
+    st = from_cuda(hyst_reset(c->hs, ntiles, 1, max_passes_for(c, ntiles), s, &himg, (uint32_t)c->chase_budget));
     if (st != CANNY_OK) return st;
     if (ev) cudaEventRecord(ev[1], s);
     canny_image staged = *im;
@@ -561,7 +563,15 @@ canny_status build_batch_graph(canny_ctx *c, canny_ctx::Slot &sl, int v)
     sl.k1node[v] = k1;
     cudaGraphNode_t fill;
     if (e == cudaSuccess) e = hyst_add_fill(g, &k1, 1, c->hs, &fill);
-    if (e == cudaSuccess) e = hyst_add_loop(g, &fill, 1, c->hs, &loop);
+    if (e == cudaSuccess && c->batch_passes == 1) {
+        e = hyst_add_coop(g, &fill, 1, c->hs, &loop);
+        if (e == cudaErrorNotSupported) {   // the device cannot hold the cooperative grid
+            cudaGetLastError();
+            e = hyst_add_loop(g, &fill, 1, c->hs, &loop);
+        }
+    } else if (e == cudaSuccess) {
+        e = hyst_add_loop(g, &fill, 1, c->hs, &loop);
+    }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&sl.exec[v], g, 0);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -655,6 +665,7 @@ canny_status run_batch_int(canny_ctx *c, int n, const canny_image *imgs, uint32_
     hh.max_passes = max_passes_for(c, ntiles);
     hh.nstage = nstage;
     hh.stage_tasks = stage_tasks;
+    hh.chase_budget = (uint32_t)c->chase_budget;
     *hdr = hh;
     const int v = all_tma ? 1 : 0;
     if (!sl.valid[v]) {
@@ -867,7 +878,7 @@ canny_status canny_run_batch(canny_ctx *c, int n, const canny_image *imgs, void 
     e = cudaMemcpyAsync(c->hs.imgs, c->h_imgs, sizeof(HystImage) * nimg, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaEventRecord(c->staging_free, s);
     if (e != cudaSuccess) return from_cuda(e);
-    st = from_cuda(hyst_reset(c->hs, ntiles, nimg, max_passes_for(c, ntiles), s));
+    st = from_cuda(hyst_reset(c->hs, ntiles, nimg, max_passes_for(c, ntiles), s, nullptr, (uint32_t)c->chase_budget));
     if (st != CANNY_OK) return st;
     base = 0;
     for (int i = 0; i < n; ++i) {
@@ -986,12 +997,18 @@ canny_status canny_set_tuning(canny_ctx *c, const canny_tuning *t)
     if ((t->band != 0 && !k1_band_supported(t->band)) || t->ctas_per_sm < 0 || t->ctas_per_sm > 32)
         return CANNY_EINVAL;
     if (t->direct_loads != 0 && t->direct_loads != 1) return CANNY_EINVAL;
+    if (t->chase_budget < 0 || t->chase_budget > 4096) return CANNY_EINVAL;
+    if (t->batch_passes != 0 && t->batch_passes != 1) return CANNY_EINVAL;
     c->direct_loads = t->direct_loads;
-    if (t->band != c->band || t->ctas_per_sm != c->ctas_per_sm) {
+    // frame graphs hold the chase budget of their reset node; batch graphs hold the rest
+    if (t->band != c->band || t->ctas_per_sm != c->ctas_per_sm || t->batch_passes != c->batch_passes ||
+        t->chase_budget != c->chase_budget) {
         cudaDeviceSynchronize();
         drop_batch_graphs(c);
         c->band = t->band;
         c->ctas_per_sm = t->ctas_per_sm;
+        c->batch_passes = t->batch_passes;
+        c->chase_budget = t->chase_budget;
     }
     return CANNY_OK;
 }
@@ -1003,6 +1020,8 @@ canny_status canny_get_tuning(const canny_ctx *c, canny_tuning *out)
     out->band = c->band;
     out->ctas_per_sm = c->ctas_per_sm;
     out->direct_loads = c->direct_loads;
+    out->chase_budget = c->chase_budget;
+    out->batch_passes = c->batch_passes;
     return CANNY_OK;
 }
 
@@ -1015,8 +1034,13 @@ canny_status canny_autotune_batch(canny_ctx *c, int n, const canny_image *imgs, 
     // size class of the batch: image count and mean image area, in octaves
     int64_t px = 0;
     int nimg = 0;
+    bool unaligned = false;
     for (int i = 0; i < n; ++i) {
-        if (imgs[i].w > 0 && imgs[i].h > 0) { px += (int64_t)imgs[i].w * imgs[i].h; ++nimg; }
+        if (imgs[i].w > 0 && imgs[i].h > 0) {
+            px += (int64_t)imgs[i].w * imgs[i].h;
+            ++nimg;
+            unaligned = unaligned || !tma_usable(imgs[i].d_in, imgs[i].in_pitch);
+        }
     }
     if (nimg == 0) return CANNY_EINVAL;
     int dev = 0;
@@ -1024,23 +1048,24 @@ canny_status canny_autotune_batch(canny_ctx *c, int n, const canny_image *imgs, 
     cudaGetDevice(&dev);
     if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return CANNY_ECUDA;
     char key[320];   // device name (at most 256) + the size classes
-    snprintf(key, sizeof(key), "%s|int|n%d|a%d", prop.name, (int)log2((double)nimg), (int)log2((double)px / nimg));
+    snprintf(key, sizeof(key), "%s|int|n%d|a%d|u%d|v2", prop.name, (int)log2((double)nimg),
+             (int)log2((double)px / nimg), unaligned ? 1 : 0);
     canny_tuning best = {};
     best.direct_loads = c->direct_loads;
     if (cache_path && *cache_path) {
         FILE *f = fopen(cache_path, "r");
         if (f) {
-            char line[512];
+            char line[640];
             while (fgets(line, sizeof(line), f)) {
-                char k[256];
-                int b = 0, q = 0;
-                double ms = 0;
-                if (sscanf(line, "{\"key\": \"%255[^\"]\", \"band\": %d, \"ctas_per_sm\": %d, \"ms\": %lf}", k, &b, &q,
-                           &ms) == 4 &&
+                char k[320];
+                canny_tuning t = {};
+                if (sscanf(line,
+                           "{\"key\": \"%319[^\"]\", \"band\": %d, \"ctas_per_sm\": %d, \"direct_loads\": %d, "
+                           "\"chase_budget\": %d, \"batch_passes\": %d, \"ms\": %lf}",
+                           k, &t.band, &t.ctas_per_sm, &t.direct_loads, &t.chase_budget, &t.batch_passes,
+                           &t.ms) == 7 &&
                     strcmp(k, key) == 0) {
-                    best.band = b;
-                    best.ctas_per_sm = q;
-                    best.ms = ms;
+                    best = t;
                     best.from_cache = 1;
                 }
             }
@@ -1048,44 +1073,72 @@ canny_status canny_autotune_batch(canny_ctx *c, int n, const canny_image *imgs, 
         }
     }
     if (!best.from_cache) {
-        // time every candidate on this batch: warm-up run, then two timed runs
+        cudaEvent_t e0, e1;
+        if (cudaEventCreate(&e0) != cudaSuccess) return CANNY_ECUDA;
+        if (cudaEventCreate(&e1) != cudaSuccess) {
+            cudaEventDestroy(e0);
+            return CANNY_ECUDA;
+        }
+        // one candidate: a warm-up run, then two timed runs; best is replaced if faster
+        auto trial = [&](canny_tuning cand) -> canny_status {
+            canny_status st = canny_set_tuning(c, &cand);
+            if (st == CANNY_OK) st = canny_run_batch(c, n, imgs, stream);
+            if (st == CANNY_OK && cudaEventRecord(e0, s) != cudaSuccess) st = CANNY_ECUDA;
+            for (int r = 0; r < 2 && st == CANNY_OK; ++r) st = canny_run_batch(c, n, imgs, stream);
+            if (st == CANNY_OK && cudaEventRecord(e1, s) != cudaSuccess) st = CANNY_ECUDA;
+            if (st == CANNY_OK && cudaEventSynchronize(e1) != cudaSuccess) st = CANNY_ECUDA;
+            if (st != CANNY_OK) return st;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms / 2 < best.ms) {
+                best = cand;
+                best.ms = ms / 2;
+            }
+            return CANNY_OK;
+        };
+        canny_status st = CANNY_OK;
+        best.ms = 1e30;
+        // stage 1, tile shape: rows per unit x persistent CTAs per SM
         const int bands[3] = {32, 64, 160};
         const int ctas[3] = {0, 12, 16};
-        cudaEvent_t e0, e1;
-        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return CANNY_ECUDA;
-        best.ms = 1e30;
-        for (int bi = 0; bi < 3; ++bi) {
-            for (int ci = 0; ci < 3; ++ci) {
-                canny_tuning cand = {};
+        const canny_tuning base = best;
+        for (int bi = 0; bi < 3 && st == CANNY_OK; ++bi)
+            for (int ci = 0; ci < 3 && st == CANNY_OK; ++ci) {
+                canny_tuning cand = base;
                 cand.band = bands[bi];
                 cand.ctas_per_sm = ctas[ci];
-                cand.direct_loads = c->direct_loads;
-                canny_status st = canny_set_tuning(c, &cand);
-                if (st == CANNY_OK) st = canny_run_batch(c, n, imgs, stream);
-                if (st == CANNY_OK && cudaEventRecord(e0, s) != cudaSuccess) st = CANNY_ECUDA;
-                for (int r = 0; r < 2 && st == CANNY_OK; ++r) st = canny_run_batch(c, n, imgs, stream);
-                if (st == CANNY_OK && cudaEventRecord(e1, s) != cudaSuccess) st = CANNY_ECUDA;
-                if (st == CANNY_OK && cudaEventSynchronize(e1) != cudaSuccess) st = CANNY_ECUDA;
-                if (st != CANNY_OK) {
-                    cudaEventDestroy(e0);
-                    cudaEventDestroy(e1);
-                    return st;
-                }
-                float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms / 2 < best.ms) {
-                    best = cand;
-                    best.ms = ms / 2;
-                }
+                st = trial(cand);
             }
+        // stage 2, halo layout of inputs the TMA path cannot read: repitched or direct loads
+        if (unaligned && st == CANNY_OK) {
+            canny_tuning cand = best;
+            cand.direct_loads = 1 - best.direct_loads;
+            st = trial(cand);
         }
+        // stage 3, pass schedule: chase budget x while-loop or one cooperative node
+        const int budgets[3] = {16, 64, 256};
+        const canny_tuning shape = best;
+        for (int bi = 0; bi < 3 && st == CANNY_OK; ++bi)
+            for (int p = 0; p < 2 && st == CANNY_OK; ++p) {
+                canny_tuning cand = shape;
+                cand.chase_budget = budgets[bi];
+                cand.batch_passes = p;
+                if (cand.chase_budget == 64 && p == 0 && shape.chase_budget == 0 && shape.batch_passes == 0)
+                    continue;   // the defaults, timed in stage 1
+                st = trial(cand);
+            }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        if (st != CANNY_OK) return st;
+        best.from_cache = 0;
         if (cache_path && *cache_path) {
             FILE *f = fopen(cache_path, "a");
             if (f) {
-                fprintf(f, "{\"key\": \"%s\", \"band\": %d, \"ctas_per_sm\": %d, \"ms\": %.6f}\n", key, best.band,
-                        best.ctas_per_sm, best.ms);
+                fprintf(f,
+                        "{\"key\": \"%s\", \"band\": %d, \"ctas_per_sm\": %d, \"direct_loads\": %d, "
+                        "\"chase_budget\": %d, \"batch_passes\": %d, \"ms\": %.6f}\n",
+                        key, best.band, best.ctas_per_sm, best.direct_loads, best.chase_budget, best.batch_passes,
+                        best.ms);
                 fclose(f);
             }
         }
@@ -1130,7 +1183,8 @@ canny_status build_frame_graph(canny_ctx *c, canny_ctx::FrameSlot &f)
     cudaGraph_t body = nullptr, g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(c->s_cap, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) return from_cuda(e);
-    canny_status st = from_cuda(hyst_reset(c->hs, ntiles, 1, max_passes_for(c, ntiles), c->s_cap, &himg));
+    canny_status st = from_cuda(hyst_reset(c->hs, ntiles, 1, max_passes_for(c, ntiles), c->s_cap, &himg,
+                                           (uint32_t)c->chase_budget));
     if (st == CANNY_OK) {
         if (c->p.path == CANNY_PATH_INT)
             st = from_cuda(launch_k1_edges_u8(im.d_in, im.in_pitch, im.w, im.h, c->it, c->hs, himg, c->s_cap,

@@ -66,7 +66,9 @@ struct HystState {
     uint32_t nimg;            // images in this run
     uint32_t keep_going;      // 1 if another pass is needed
     uint32_t bar_count, bar_gen;   // grid barrier of the cooperative multi-pass kernel
-    uint32_t pad[3];
+    uint32_t uf_count;        // union-find stage: tiles listed
+    uint32_t uf_round;        // union-find stage: last pointer-jumping round that changed a parent
+    uint32_t chase_budget;    // tiles one worklist entry may chase into within a pass
 };
 
 struct HystScratch {
@@ -116,7 +118,7 @@ struct BatchImage {
 struct BatchHeader {
     uint32_t nimg, total_units, next_unit, ntiles, max_passes;
     uint32_t nstage, stage_tasks;   // inputs repitched into staging first (Repitch list), their tasks
-    uint32_t pad;
+    uint32_t chase_budget;          // the global passes' chase budget (0: the default)
 };
 
 // ---------------------------------------------------------------- launchers (k1_fused.cu)
@@ -249,12 +251,17 @@ cudaError_t launch_hyst_phantom_arrival(const HystScratch &hs, cudaStream_t s);
 // Clear the worklist stamps and the control block before a run; for a single
 // image, also store its descriptor as image 0 (the global passes read it).
 cudaError_t hyst_reset(const HystScratch &hs, uint32_t ntiles, uint32_t nimg,
-                       uint32_t max_passes, cudaStream_t s, const HystImage *single = nullptr);
+                       uint32_t max_passes, cudaStream_t s, const HystImage *single = nullptr,
+                       uint32_t chase_budget = 0);
 int hyst_pass_grid();
 // Executable graph { while (cond) global pass } bound to this scratch.
 cudaError_t hyst_build_graph(const HystScratch &hs, cudaGraph_t *graph_out, cudaGraphExec_t *exec_out);
 // Graph pieces for the batch graph.
 cudaError_t hyst_add_loop(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, const HystScratch &hs,
+                          cudaGraphNode_t *out);
+// Every global pass as one cooperative kernel node (long chains resolved by the
+// union-find stage); cudaErrorNotSupported where the device cannot hold the grid.
+cudaError_t hyst_add_coop(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, const HystScratch &hs,
                           cudaGraphNode_t *out);
 // Append { *acc |= state->error } after the given nodes (errors of one run of a
 // sequence survive the next run's reset).

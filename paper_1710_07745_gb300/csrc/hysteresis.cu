@@ -277,6 +277,7 @@ __device__ __forceinline__ void global_pass(const HystScratch &hs, int in_graph,
     const uint32_t warp = (blockIdx.x * THREADS + threadIdx.x) >> 5;
     const uint32_t nwarps = gridDim.x * WARPS;
     const uint32_t *list = hs.lists + (size_t)cur * hs.max_tiles;
+    const int chase_budget = st->chase_budget ? (int)st->chase_budget : CHASE_BUDGET;
     if (threadIdx.x == 0) visits = 0;
     __syncthreads();
     uint32_t my_visits = 0;
@@ -297,7 +298,7 @@ __device__ __forceinline__ void global_pass(const HystScratch &hs, int in_graph,
             const int src = __ffs(todo) - 1;
             todo &= todo - 1;
             uint32_t t = __shfl_sync(FULL, mine, src);
-            int sp = 0, budget = CHASE_BUDGET;
+            int sp = 0, budget = chase_budget;
             for (;;) {
                 TileSeeds sd;
                 Facing fp;
@@ -503,7 +504,7 @@ __device__ __forceinline__ void uf_label_phase(const HystScratch &hs, int lane, 
             }
             if (lane == 0) {
                 lab[UF_COUNT] = (uint8_t)k;
-                const uint32_t slot = atomicAdd(&st->pad[0], 1u);
+                const uint32_t slot = atomicAdd(&st->uf_count, 1u);
                 if (CANNY_CHECK(slot < hs.max_tiles, &st->error)) hs.lists[slot] = t;
             }
         }
@@ -515,7 +516,7 @@ __device__ __forceinline__ void uf_label_phase(const HystScratch &hs, int lane, 
 __device__ __forceinline__ void uf_union_phase(const HystScratch &hs, int lane, uint32_t warp, uint32_t nwarps)
 {
     HystState *st = hs.state;
-    const uint32_t n = min(*(volatile uint32_t *)&st->pad[0], hs.max_tiles);
+    const uint32_t n = min(*(volatile uint32_t *)&st->uf_count, hs.max_tiles);
     const int nimg = (int)st->nimg;
     for (uint32_t i = warp; i < n; i += nwarps) {
         const uint32_t t = __ldcg(&hs.lists[i]);
@@ -563,7 +564,7 @@ __device__ __forceinline__ void uf_union_phase(const HystScratch &hs, int lane, 
 __device__ __forceinline__ bool uf_jump_phase(const HystScratch &hs, int lane, uint32_t warp, uint32_t nwarps)
 {
     HystState *st = hs.state;
-    const uint32_t n = min(*(volatile uint32_t *)&st->pad[0], hs.max_tiles);
+    const uint32_t n = min(*(volatile uint32_t *)&st->uf_count, hs.max_tiles);
     bool changed = false;
     for (uint32_t i = warp; i < n; i += nwarps) {
         const uint32_t t = __ldcg(&hs.lists[i]);
@@ -584,7 +585,7 @@ __device__ __forceinline__ bool uf_jump_phase(const HystScratch &hs, int lane, u
 __device__ __forceinline__ void uf_roots_phase(const HystScratch &hs, int lane, uint32_t warp, uint32_t nwarps)
 {
     HystState *st = hs.state;
-    const uint32_t n = min(*(volatile uint32_t *)&st->pad[0], hs.max_tiles);
+    const uint32_t n = min(*(volatile uint32_t *)&st->uf_count, hs.max_tiles);
     for (uint32_t i = warp; i < n; i += nwarps) {
         const uint32_t t = __ldcg(&hs.lists[i]);
         const uint32_t k = __ldcg(hs.uf_label + (size_t)t * UF_LSTRIDE + UF_COUNT);
@@ -600,7 +601,7 @@ __device__ __forceinline__ void uf_roots_phase(const HystScratch &hs, int lane, 
 __device__ __forceinline__ void uf_apply_phase(const HystScratch &hs, int lane, uint32_t warp, uint32_t nwarps)
 {
     HystState *st = hs.state;
-    const uint32_t n = min(*(volatile uint32_t *)&st->pad[0], hs.max_tiles);
+    const uint32_t n = min(*(volatile uint32_t *)&st->uf_count, hs.max_tiles);
     const int nimg = (int)st->nimg;
     for (uint32_t i = warp; i < n; i += nwarps) {
         const uint32_t t = __ldcg(&hs.lists[i]);
@@ -640,17 +641,17 @@ __device__ __forceinline__ bool uf_resolve(const HystScratch &hs)
 {
     const int lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * THREADS + threadIdx.x) >> 5, nwarps = gridDim.x * WARPS;
-    if (blockIdx.x == 0 && threadIdx.x == 0) hs.state->pad[0] = hs.state->pad[1] = 0u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) hs.state->uf_count = hs.state->uf_round = 0u;
     if (!grid_barrier(hs.state)) return false;
     uf_label_phase(hs, lane, warp, nwarps);
     if (!grid_barrier(hs.state)) return false;
     uf_union_phase(hs, lane, warp, nwarps);
     if (!grid_barrier(hs.state)) return false;
-    // pad[1]: the last jump round (counted from 1) that changed a parent
+    // uf_round: the last jump round (counted from 1) that changed a parent
     for (uint32_t r = 1; r <= 32; ++r) {
-        if (uf_jump_phase(hs, lane, warp, nwarps)) atomicMax(&hs.state->pad[1], r);
+        if (uf_jump_phase(hs, lane, warp, nwarps)) atomicMax(&hs.state->uf_round, r);
         if (!grid_barrier(hs.state)) return false;
-        if (*(volatile uint32_t *)&hs.state->pad[1] < r) break;
+        if (*(volatile uint32_t *)&hs.state->uf_round < r) break;
     }
     uf_roots_phase(hs, lane, warp, nwarps);
     if (!grid_barrier(hs.state)) return false;
@@ -658,7 +659,7 @@ __device__ __forceinline__ bool uf_resolve(const HystScratch &hs)
     if (!grid_barrier(hs.state)) return false;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         HystState *st = hs.state;
-        st->visited += st->pad[0];
+        st->visited += st->uf_count;
         st->pass += 1;                          // the union-find stage counts as one pass
         st->keep_going = 0;
         st->list_count[0] = st->list_count[1] = 0;
@@ -686,13 +687,14 @@ hyst_global_coop_kernel(HystScratch hs)
 }
 
 __global__ void hyst_init_kernel(HystState *st, uint32_t ntiles, uint32_t nimg, uint32_t max_passes,
-                                 HystImage *imgs, HystImage single, int write_single)
+                                 HystImage *imgs, HystImage single, int write_single, uint32_t chase_budget)
 {
     if (write_single) imgs[0] = single;
     HystState s = {};
     s.ntiles = ntiles;
     s.nimg = nimg;
     s.max_passes = max_passes;
+    s.chase_budget = chase_budget;
     s.keep_going = 1;
     *st = s;
 }
@@ -703,6 +705,7 @@ __global__ void hyst_init_from_header_kernel(HystState *st, const BatchHeader *h
     s.ntiles = hdr->ntiles;
     s.nimg = hdr->nimg;
     s.max_passes = hdr->max_passes;
+    s.chase_budget = hdr->chase_budget;
     s.keep_going = 1;
     *st = s;
 }
@@ -742,11 +745,12 @@ int hyst_pass_grid()
 }
 
 cudaError_t hyst_reset(const HystScratch &hs, uint32_t ntiles, uint32_t nimg, uint32_t max_passes,
-                       cudaStream_t s, const HystImage *single)
+                       cudaStream_t s, const HystImage *single, uint32_t chase_budget)
 {
     // the worklist stamps need no clearing: the local fill writes every tile's stamp
     HystImage one = single ? *single : HystImage{};
-    hyst_init_kernel<<<1, 1, 0, s>>>(hs.state, ntiles, nimg, max_passes, hs.imgs, one, single ? 1 : 0);
+    hyst_init_kernel<<<1, 1, 0, s>>>(hs.state, ntiles, nimg, max_passes, hs.imgs, one, single ? 1 : 0,
+                                     chase_budget);
     return cudaGetLastError();
 }
 
@@ -839,6 +843,24 @@ cudaError_t hyst_add_loop(cudaGraph_t g, const cudaGraphNode_t *deps, size_t nde
     kp.kernelParams = args;
     cudaGraphNode_t knode;
     return cudaGraphAddKernelNode(&knode, body, nullptr, 0, &kp);
+}
+
+cudaError_t hyst_add_coop(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, const HystScratch &hs,
+                          cudaGraphNode_t *out)
+{
+    if (!hyst_coop_supported()) return cudaErrorNotSupported;
+    HystScratch hs_copy = hs;
+    void *args[] = {&hs_copy};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void *)hyst_global_coop_kernel;
+    kp.gridDim = dim3(hyst_pass_grid());
+    kp.blockDim = dim3(THREADS);
+    kp.kernelParams = args;
+    cudaError_t err = cudaGraphAddKernelNode(out, g, deps, ndeps, &kp);
+    if (err != cudaSuccess) return err;
+    cudaKernelNodeAttrValue v = {};
+    v.cooperative = 1;
+    return cudaGraphKernelNodeSetAttribute(*out, cudaLaunchAttributeCooperative, &v);
 }
 
 // Append { *acc |= state->error } to graph g after the given nodes.

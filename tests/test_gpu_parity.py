@@ -250,14 +250,17 @@ def spiral_map(n, gap=1):
     return cls
 
 
-def run_hyst(cls, max_passes=0):
+def run_hyst(cls, max_passes=0, ctx=None):
     h, w = cls.shape
-    with canny.Canny(w, h, max_passes=max_passes) as c:
-        d_in = dev(cls)
-        d_out = torch.empty_like(d_in)
-        c.hysteresis(d_in, d_out)
-        torch.cuda.synchronize()
-        return d_out.cpu().numpy(), c.stats()
+    c = ctx or canny.Canny(w, h, max_passes=max_passes)
+    d_in = dev(cls)
+    d_out = torch.empty_like(d_in)
+    c.hysteresis(d_in, d_out)
+    torch.cuda.synchronize()
+    out, st = d_out.cpu().numpy(), c.stats()
+    if ctx is None:
+        c.close()
+    return out, st
 
 
 @pytest.mark.parametrize("seed", range(8))
@@ -668,6 +671,67 @@ def test_every_tuning_gives_identical_edges(band, ctas, direct):
             assert np.array_equal(out, oracle.canny_u8(im))
 
 
+def serpentine_u8(n, gap=32):
+    """A 3-pixel bar of grey 32 on black through every 32 x 32 tile of an n x n
+    image (runs every `gap` rows joined at alternate ends), its first 8 pixels
+    at grey 80: with thresholds 40/100 the bar's edges are one weak chain whose
+    only strong pixels sit at its start."""
+    img = np.zeros((n, n), np.uint8)
+    rows = list(range(gap // 2, n, gap))
+    for j, r in enumerate(rows):
+        img[r - 1:r + 2, 2:n - 2] = 32
+        if j + 1 < len(rows):
+            c = n - 3 if j % 2 == 0 else 2
+            img[r:rows[j + 1] + 1, c - 1:c + 2] = 32
+    img[rows[0] - 1:rows[0] + 2, 2:10] = 80
+    return img
+
+
+def test_serpentine_u8_is_one_long_weak_chain():
+    img = serpentine_u8(256)
+    cls = oracle.classify_u8(img, 40, 100)
+    out = oracle.canny_u8(img, 40, 100)
+    assert (cls == 2).sum() < 32 and (cls == 1).sum() > 4000
+    assert (out == 255).sum() == (cls > 0).sum()          # every weak pixel is reached
+
+
+@pytest.mark.parametrize("budget,passes", [(1, 0), (1, 1), (16, 0), (16, 1), (64, 1), (256, 0), (4096, 1)])
+def test_every_pass_schedule_gives_identical_edges(budget, passes):
+    """Chase budget x while-loop or cooperative node: batches holding a chain
+    through 1024 tiles, images that end inside a tile and an empty-edged one,
+    and single images through the same context."""
+    imgs = [serpentine_u8(1024), synth.image(950, 300, 500, 8, 8, 10), serpentine_u8(320)[:, :301],
+            synth.image(951, 70, 1, 8, 8, 10), np.zeros((33, 65), np.uint8)]
+    total = sum(im.size for im in imgs)
+    with canny.Canny(total, 1) as c:
+        c.set_tuning(64, 0, 0, budget, passes)
+        t = canny.canny_get_tuning(c.ctx)
+        assert (t.chase_budget, t.batch_passes) == (budget, passes)
+        for rep in range(2):
+            outs, st = _batch_run(c, imgs)
+            assert st["status"] == canny.CANNY_OK
+            for im, o in zip(imgs, outs):
+                assert np.array_equal(o, oracle.canny_u8(im))
+    with canny.Canny(1024, 1024) as c:
+        c.set_tuning(0, 0, 0, budget, passes)
+        out, st = run_int(imgs[0], ctx=c)
+        assert np.array_equal(out, oracle.canny_u8(imgs[0]))
+        cls = serpentine_map(1024)
+        h, _ = run_hyst(cls, ctx=c)
+        assert np.array_equal(h, oracle.hysteresis(cls))
+
+
+def test_tuning_rejects_out_of_range_schedules():
+    with canny.Canny(64, 64) as c:
+        for band, ctas, direct, budget, passes in [(64, 0, 0, -1, 0), (64, 0, 0, 4097, 0), (64, 0, 0, 0, 2),
+                                                   (48, 0, 0, 0, 0), (64, 33, 0, 0, 0), (64, 0, 2, 0, 0)]:
+            with pytest.raises(canny.CannyError):
+                c.set_tuning(band, ctas, direct, budget, passes)
+        c.set_tuning(32, 4, 1, 4096, 1)
+        t = canny.canny_get_tuning(c.ctx)
+        assert (t.band, t.ctas_per_sm, t.direct_loads, t.chase_budget, t.batch_passes) == (32, 4, 1, 4096, 1)
+
+
 def test_autotune_picks_a_supported_config_and_caches_it(tmp_path):
     rng = np.random.default_rng(5)
     sizes = [(int(h), int(w)) for h, w in rng.integers(64, 300, (40, 2))]
@@ -679,8 +743,12 @@ def test_autotune_picks_a_supported_config_and_caches_it(tmp_path):
     with canny.Canny(total, 1) as c:
         t1 = c.autotune_batch(list(zip(ins, outs)), cache_path=cache)
         assert t1["band"] in (32, 64, 160) and t1["ctas_per_sm"] in (0, 12, 16) and t1["from_cache"] == 0
+        assert t1["chase_budget"] in (0, 16, 64, 256) and t1["batch_passes"] in (0, 1)
+        assert t1["direct_loads"] in (0, 1)                 # widths not multiples of 16: both layouts timed
         t2 = c.autotune_batch(list(zip(ins, outs)), cache_path=cache)
-        assert t2["from_cache"] == 1 and (t2["band"], t2["ctas_per_sm"]) == (t1["band"], t1["ctas_per_sm"])
+        keys = ("band", "ctas_per_sm", "direct_loads", "chase_budget", "batch_passes")
+        assert t2["from_cache"] == 1 and all(t2[k] == t1[k] for k in keys)
+        assert all(getattr(canny.canny_get_tuning(c.ctx), k) == t1[k] for k in keys)
         c.run_batch(list(zip(ins, outs)))
         torch.cuda.synchronize()
     for im, o in zip(imgs, outs):

@@ -103,7 +103,7 @@ typedef struct canny_ctx canny_ctx;
 canny_status canny_params_default(canny_params *p);
 
 /*
- * Create a context for images of at most max_w x max_h pixels (the pixel
+ * Set-up for Steps 1-4 (Sec. 2.2.1): create a context for images of at most max_w x max_h pixels (the pixel
  * budget max_w * max_h also bounds the total pixels of one canny_run_batch
  * call). Allocates the scratch on the current device. Returns CANNY_EINVAL for
  * non-positive sizes or invalid params, CANNY_ENOMEM if allocation fails.
@@ -114,15 +114,18 @@ canny_status canny_create(int max_w, int max_h, const canny_params *p, canny_ctx
 void canny_destroy(canny_ctx *ctx);
 
 /*
- * Edge map of one max_w x max_h image with tight rows (pitch = max_w): d_in and
- * d_out are device buffers of max_w * max_h bytes. d_out doubles as the class
- * map between the stencil and the hysteresis, so no other image-sized scratch
- * is used on the integer path. Asynchronous on stream.
+ * Steps 1-4 (Sec. 2.2.1, Algorithm 1): edge map of one max_w x max_h image with
+ * tight rows (pitch = max_w); d_in and d_out are device buffers of
+ * max_w * max_h bytes. On the integer path the classes of Steps 1-3 and the
+ * double threshold pass from the stencil to the hysteresis as two bits per
+ * pixel in the context's tile scratch (0.25 byte per pixel); d_out is written
+ * once, with the final edge map. Asynchronous on stream.
  */
 canny_status canny_run(canny_ctx *ctx, const uint8_t *d_in, uint8_t *d_out, void *stream);
 
 /*
- * Edge map of one image of any size up to the context's, with its own pitches.
+ * Steps 1-4 (Sec. 2.2.1): edge map of one image of any size up to the
+ * context's, with its own pitches.
  * An input whose base address or pitch is not a multiple of 16 bytes is first
  * copied on the device into a 16-byte pitched staging buffer of the context
  * (allocated on first need, which synchronises the device once, and kept until
@@ -132,16 +135,17 @@ canny_status canny_run(canny_ctx *ctx, const uint8_t *d_in, uint8_t *d_out, void
 canny_status canny_run_pitched(canny_ctx *ctx, const canny_image *img, void *stream);
 
 /*
- * Edge maps of n images of any sizes (total pixels at most max_w * max_h, the
- * context's pixel budget) in one launch sequence: every stage runs
- * once over the tiles of all images. The image descriptors are read from host
+ * Steps 1-4 over many images at once (Sec. 2.2.2: the work of all images
+ * shared out to the cores as one pool of tasks): edge maps of n images of any
+ * sizes (total pixels at most max_w * max_h, the context's pixel budget) in
+ * one launch sequence: every stage runs once over the tiles of all images. The image descriptors are read from host
  * memory before the call returns. Outputs equal n separate canny_run_pitched
  * calls byte for byte.
  */
 canny_status canny_run_batch(canny_ctx *ctx, int n, const canny_image *imgs, void *stream);
 
 /*
- * End-to-end call on host buffers: copies h_in (host, h rows of in_pitch bytes)
+ * Steps 1-4 (Sec. 2.2.1) end to end on host buffers: copies h_in (host, h rows of in_pitch bytes)
  * to the device, runs the pipeline and copies the edge map back to h_out (host,
  * h rows of out_pitch bytes); returns after the stream has been synchronised.
  * Pinned (page-locked) host buffers give the fastest copies. Device buffers for
@@ -169,13 +173,15 @@ canny_status canny_run_frames(canny_ctx *ctx, int n, const uint8_t *const *h_in,
                               uint8_t *const *h_out, int out_pitch, int w, int h, void *stream);
 
 /*
- * Steps 1-3 and the double threshold only: the class map before hysteresis,
+ * Steps 1-3 and the double threshold of Step 4 (Sec. 2.2.1) only: the class
+ * map before the connectivity search,
  * 0 (none), 1 (weak) or 2 (strong) per pixel, into img->d_out.
  */
 canny_status canny_classify(canny_ctx *ctx, const canny_image *img, void *stream);
 
 /*
- * Step 4 only: img->d_in holds a class map (0 none, 1 weak, 2 strong; other
+ * Step 4's connectivity search only (Sec. 2.2.1; weak pixels kept when
+ * 8-connected to a strong one): img->d_in holds a class map (0 none, 1 weak, 2 strong; other
  * values count as strong); the 0/255 edge map goes to img->d_out.
  */
 canny_status canny_hysteresis(canny_ctx *ctx, const canny_image *img, void *stream);
@@ -194,8 +200,10 @@ canny_status canny_magnitude_f32(canny_ctx *ctx, const canny_image *img, float *
 typedef struct {
     int64_t runs;          /* runs timed */
     double reset_ms;       /* clearing the hysteresis worklist state */
-    double stencil_ms;     /* Steps 1-3 + thresholds (integer path: fused with the per-tile fill) */
-    double local_ms;       /* hysteresis: per-tile fill, when it runs as its own kernel */
+    double stencil_ms;     /* Steps 1-3 + thresholds and the per-tile fill (integer path: the fused
+                              stencil and the tile-fill kernel; float path: both passes, the second
+                              fused with the fill) */
+    double local_ms;       /* hysteresis: per-tile fill of canny_hysteresis (a class map input) */
     double global_ms;      /* hysteresis: global passes */
     double total_ms;       /* first stage start to last stage end, summed over runs */
 } canny_timing;
@@ -246,7 +254,8 @@ canny_status canny_set_tuning(canny_ctx *ctx, const canny_tuning *t);
 canny_status canny_get_tuning(const canny_ctx *ctx, canny_tuning *out);
 
 /*
- * Pick the configuration for batches like `imgs` (integer path): look up the
+ * How the work is split (Sec. 2.2.2: the split of tasks over cores decides the
+ * load balance): pick the configuration for batches like `imgs` (integer path): look up the
  * size class (device, image count and mean area in octaves) in cache_path
  * (JSON lines; NULL for none); if absent, time candidates on this batch in
  * three stages, each keeping the best of the one before: tile shape (band x
@@ -263,7 +272,8 @@ canny_status canny_autotune_batch(canny_ctx *ctx, int n, const canny_image *imgs
 canny_status canny_get_stats(canny_ctx *ctx, canny_stats *out);
 
 /*
- * Integer pipeline without any device allocation. The paper has no counterpart:
+ * Steps 1-4 (Sec. 2.2.1), integer pipeline without any device allocation. The
+ * paper has no counterpart for the allocation rule:
  * this entry point exists for callers that cannot call cudaMalloc -- code that
  * runs under a device-memory budget held entirely by another allocator (a
  * framework's caching allocator, a fixed arena), or a frame loop in which the
@@ -321,7 +331,8 @@ typedef struct {
 } canny_serve_report;
 
 /*
- * Serve a request trace in real time with continuous batching (integer path).
+ * Steps 1-4 (Sec. 2.2.1) as a service: serve a request trace in real time with
+ * continuous batching (integer path).
  * Requests arriving while earlier ones run are admitted in arrival order as
  * soon as the memory budget has room for their input and output buffers;
  * every idle stream takes all admitted, not-yet-running requests as one
@@ -336,7 +347,6 @@ typedef struct {
 canny_status canny_serve(const canny_serve_config *cfg, int n, const canny_request *reqs, double *latency_ms,
                          canny_serve_report *out);
 
-/* Static, human-readable message for a status. */
 /*
  * Test hooks for failure detection, with no GPU fault involved. Counts of
  * events that go wrong from now on (process-wide; each call replaces the
@@ -367,6 +377,7 @@ typedef struct {
 
 canny_status canny_inject_faults(const canny_fault_injection *f);
 
+/* Static, human-readable message for a status. */
 const char *canny_strerror(canny_status s);
 
 #ifdef __cplusplus

@@ -203,7 +203,8 @@ canny_status ensure_hyst(canny_ctx *c, uint32_t max_tiles, uint32_t max_imgs)
     size_t off_uf_label = align_up(off_bits + sizeof(uint32_t) * 2 * HT * (size_t)max_tiles, 256);
     size_t off_uf_parent = align_up(off_uf_label + 128 * (size_t)max_tiles, 256);
     size_t off_uf_seeded = align_up(off_uf_parent + sizeof(uint32_t) * 64 * (size_t)max_tiles, 256);
-    size_t off_state = align_up(off_uf_seeded + 64 * (size_t)max_tiles, 256);
+    size_t off_queue = align_up(off_uf_seeded + 64 * (size_t)max_tiles, 256);
+    size_t off_state = align_up(off_queue + sizeof(unsigned long long) * (size_t)max_tiles, 256);
     size_t total = align_up(off_state + sizeof(HystState), 256);
     void *mem = nullptr;
     cudaError_t e = dev_alloc(&mem, total);
@@ -222,10 +223,12 @@ canny_status ensure_hyst(canny_ctx *c, uint32_t max_tiles, uint32_t max_imgs)
     c->hs.uf_label = (uint8_t *)(b + off_uf_label);
     c->hs.uf_parent = (uint32_t *)(b + off_uf_parent);
     c->hs.uf_seeded = (uint8_t *)(b + off_uf_seeded);
+    c->hs.queue = (unsigned long long *)(b + off_queue);
     c->hs.state = (HystState *)(b + off_state);
     c->hs.max_tiles = max_tiles;
     c->hs.max_imgs = max_imgs;
     if (cudaMemset(c->hs.state, 0, sizeof(HystState)) != cudaSuccess) return CANNY_ECUDA;
+    if (cudaMemset(c->hs.queue, 0, sizeof(unsigned long long) * max_tiles) != cudaSuccess) return CANNY_ECUDA;
     // (single images run their passes in one cooperative launch where the device
     // allows; the graph while-loop is the fallback)
     if (c->use_graph && !hyst_coop_supported()) {

@@ -68,7 +68,13 @@ struct HystState {
     uint32_t bar_count, bar_gen;   // grid barrier of the cooperative multi-pass kernel
     uint32_t uf_count;        // union-find stage: tiles listed
     uint32_t uf_round;        // union-find stage: last pointer-jumping round that changed a parent
-    uint32_t chase_budget;    // tiles one worklist entry may chase into within a pass
+    uint32_t chase_budget;    // tiles a chain may be followed into within a pass (0: the default)
+    // the in-pass queue of a global pass (zero between passes)
+    uint32_t list_head;       // worklist entries claimed so far
+    uint32_t q_head, q_tail;  // queue slots claimed by consumers / reserved by producers
+    uint32_t q_open;          // queued items not yet finished, plus worklist chunks in hand
+    uint32_t q_waiters;       // warps that stay for queued items
+    uint32_t run_tag;         // 1..65535, new for every run: tags queue items of this run
 };
 
 struct HystScratch {
@@ -87,6 +93,9 @@ struct HystScratch {
     uint8_t *uf_label;        // [max_tiles * 128]: component of each of the 124 border pixels, count at 127
     uint32_t *uf_parent;      // [max_tiles * 64]: parent of component 64 t + j
     uint8_t *uf_seeded;       // [max_tiles * 64]: component touches an edge of a neighbouring tile
+    // in-pass queue of the global passes: (run tag << 48) | (budget << 32) | tile,
+    // 0 when empty; zeroed once at allocation, each slot re-zeroed by its consumer
+    unsigned long long *queue;   // [max_tiles]
 };
 
 // ---------------------------------------------------------------- stencil launch data

@@ -10,11 +10,12 @@
 //                are edges or pending;
 //   global pass  a tile on the worklist takes the edges on its neighbours'
 //                borders as seeds for its pending border pixels and grows them
-//                (the lanes of a warp first check 32 entries for seeds at once;
-//                the warp grows the few that have some). A neighbour whose
-//                facing border gained edges next to its pending pixels is
-//                followed at once by the same warp, or queued for the next pass
-//                when the warp's budget runs out. Passes repeat until the
+//                (the lanes of a warp first check a chunk of entries for seeds
+//                at once). A neighbour whose facing border gained edges next
+//                to its pending pixels is followed at once by the same warp;
+//                further seeded entries and branches go to an in-pass queue
+//                that idle warps drain, and what the chain's budget cannot
+//                take is listed for the next pass. Passes repeat until the
 //                worklist is empty, decided by the last CTA of each pass: for a
 //                single image all passes run in one cooperative launch (a
 //                bounded grid barrier between them); inside the batch and
@@ -55,10 +56,9 @@ hyst_local_kernel(HystScratch hs, HystImage single, uint32_t ntiles, uint32_t ni
 // Neighbour directions of a tile, as bits of the "affected" mask.
 enum { NB_U, NB_UL, NB_UR, NB_D, NB_DL, NB_DR, NB_L, NB_R };
 
-// Tiles one worklist entry may chase into within a pass before the rest is
-// queued for the next pass, and the depth of the per-warp chase stack.
+// Tiles a chain may be followed into within a pass before the rest is listed
+// for the next pass (the default of the chase budget).
 constexpr int CHASE_BUDGET = 64;
-constexpr int CHASE_STACK = 32;
 
 // Border masks as other warps last wrote them: loads that bypass L1, since
 // tiles are revisited within one pass and L1 is not coherent across SMs.
@@ -254,18 +254,78 @@ __device__ __forceinline__ uint32_t grow_tile(const HystScratch &hs, uint32_t t,
     return __shfl_sync(FULL, aff, 0);
 }
 
-// One pass over the current worklist. A warp that adds edges next to a
-// neighbour's pending pixels follows them into that neighbour at once (depth
-// first, up to CHASE_BUDGET tiles per worklist entry), so a chain of weak pixels
-// across many tiles costs one pass, not one pass per tile; what the budget or
-// the stack cannot take is queued for the next pass. A tile may be visited by
-// two warps at a time: both only add edges, and each re-reads the masks, so the
-// result is the same.
-// One pass (all CTAs of the grid). The last CTA to finish swaps the worklists,
-// counts the pass and sets keep_going (and, in a graph, the while-node's
-// condition).
+// ---------------------------------------------------------------- the in-pass queue
+// Work of one pass that any warp may take: a worklist entry found seeded while
+// its warp was busy with another, or a branch of a chain (the neighbours a
+// visit affected beyond the one its warp follows). Each item carries what is
+// left of its chain's budget. q_open counts items queued but not yet finished
+// plus worklist chunks in hand: a waiting warp leaves the pass only when the
+// worklist is exhausted and q_open is 0, so no item is left behind, and idle
+// warps keep taking branches while long chains run.
+__device__ __forceinline__ unsigned long long make_item(uint32_t tag, uint32_t budget, uint32_t tile)
+{
+    return ((unsigned long long)tag << 48) | ((unsigned long long)budget << 32) | tile;
+}
+
+// Queue tile with budget (one thread). The caller has made its edges visible
+// (a fence in every lane). A full queue hands the tile to the next pass instead.
+__device__ __forceinline__ void queue_push(const HystScratch &hs, uint32_t tag, uint32_t budget, uint32_t tile,
+                                           uint32_t nxt, uint32_t stamp)
+{
+    HystState *st = hs.state;
+    atomicAdd(&st->q_open, 1u);
+    const uint32_t slot = atomicAdd(&st->q_tail, 1u);
+    if (slot < hs.max_tiles) {
+        atomicExch(&hs.queue[slot], make_item(tag, budget, tile));
+    } else {
+        push(hs, nxt, tile, stamp);
+        atomicSub(&st->q_open, 1u);
+    }
+}
+
+// Take an item (lane 0): 0 if none is queued now. A claimed slot whose producer
+// has not yet written it is waited for (bounded); on a timeout error bit 1 is
+// set and the item is dropped (the run then reports the error).
+__device__ __forceinline__ unsigned long long queue_pop(const HystScratch &hs, uint32_t tag)
+{
+    HystState *st = hs.state;
+    for (;;) {
+        const uint32_t h = *(volatile uint32_t *)&st->q_head;
+        const uint32_t t = min(*(volatile uint32_t *)&st->q_tail, hs.max_tiles);
+        if (h >= t) return 0ull;
+        if (atomicCAS(&st->q_head, h, h + 1u) != h) continue;
+        const uint64_t t0 = globaltimer_ns();
+        for (;;) {
+            const unsigned long long v = atomicExch(&hs.queue[h], 0ull);
+            if ((uint32_t)(v >> 48) == tag) {
+                __threadfence();                // the producer's edges before this warp reads masks
+                return v;
+            }
+            // (v nonzero here is a leftover of a run that stopped on an error: dropped)
+            if (globaltimer_ns() - t0 > WAIT_TIMEOUT_NS) {
+                atomicOr(&st->error, 2u);
+                atomicSub(&st->q_open, 1u);
+                return 0ull;
+            }
+            __nanosleep(32);
+        }
+    }
+}
+
+// One pass over the current worklist, all CTAs of the grid. Warps claim chunks
+// of entries (32, or fewer when the list is short so that every warp gets
+// some); the lanes check a chunk's entries for seeds at once. A warp grows one
+// seeded tile and follows the chain it starts (depth first: it visits next a
+// neighbour whose facing pending pixels touch the edges it added, while the
+// chain's budget lasts); further seeded entries and further affected
+// neighbours go to the in-pass queue for idle warps, and what a spent budget
+// or a full queue cannot take is listed for the next pass. A tile may be
+// visited by two warps at a time: both only add edges, and each re-reads the
+// masks, so the result is the same. The last CTA to finish swaps the
+// worklists, counts the pass and sets keep_going (and, in a graph, the
+// while-node's condition).
 __device__ __forceinline__ void global_pass(const HystScratch &hs, int in_graph, cudaGraphConditionalHandle cond,
-                                            uint32_t (&stack)[WARPS][CHASE_STACK], uint32_t &visits)
+                                            uint32_t &visits)
 {
     HystState *st = hs.state;
     const uint32_t k = *(volatile uint32_t *)&st->pass;
@@ -273,60 +333,118 @@ __device__ __forceinline__ void global_pass(const HystScratch &hs, int in_graph,
     uint32_t count = *(volatile uint32_t *)&st->list_count[cur];
     if (!CANNY_CHECK(count <= hs.max_tiles, &st->error)) count = hs.max_tiles;
     const int nimg = (int)st->nimg;
-    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const uint32_t warp = (blockIdx.x * THREADS + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     const uint32_t nwarps = gridDim.x * WARPS;
     const uint32_t *list = hs.lists + (size_t)cur * hs.max_tiles;
-    const int chase_budget = st->chase_budget ? (int)st->chase_budget : CHASE_BUDGET;
+    const uint32_t budget0 = st->chase_budget ? st->chase_budget : (uint32_t)CHASE_BUDGET;
+    const uint32_t tag = st->run_tag;
+    const uint32_t chunk = count >= nwarps * 32u ? 32u : max(1u, (count + nwarps - 1u) / nwarps);
     if (threadIdx.x == 0) visits = 0;
     __syncthreads();
     uint32_t my_visits = 0;
-    // each lane checks one worklist entry for seeds; the warp then grows the
-    // tiles that have some, one after the other, and follows their chains
-    for (uint32_t base = warp * 32u; base < count; base += nwarps * 32u) {
-        const uint32_t i = base + (uint32_t)lane;
-        uint32_t mine = 0;
-        bool has = false;
-        if (i < count) {
+
+    // follow the chain from tile t with budget b (whole warp)
+    auto chase = [&](uint32_t t, uint32_t b) {
+        for (;;) {
             TileSeeds sd;
-            mine = __ldcg(&list[i]);      // (a cooperative launch reuses L1 across passes)
-            has = CANNY_CHECK(mine < hs.max_tiles, &st->error) && find_seeds(hs, mine, nimg, sd);
-        }
-        my_visits += (lane == 0) ? min(32u, count - base) : 0u;   // entries examined
-        uint32_t todo = __ballot_sync(FULL, has);
-        while (todo) {
-            const int src = __ffs(todo) - 1;
-            todo &= todo - 1;
-            uint32_t t = __shfl_sync(FULL, mine, src);
-            int sp = 0, budget = chase_budget;
-            for (;;) {
-                TileSeeds sd;
-                Facing fp;
-                uint32_t aff = 0, ntx = 0;
-                if (!CANNY_CHECK(t < hs.max_tiles, &st->error)) break;
-                const uint32_t p_row = __ldcg(&hs.pend_bits[(size_t)t * HT + lane]);   // issued with the masks
-                if (chase_seeds(hs, t, nimg, sd, lane, fp)) {
-                    aff = grow_tile(hs, t, sd, lane, p_row, fp);
-                    ntx = (uint32_t)sd.im.ntx;
-                }
-                ++my_visits;
+            Facing fp;
+            uint32_t aff = 0, ntx = 0;
+            if (!CANNY_CHECK(t < hs.max_tiles, &st->error)) return;
+            const uint32_t p_row = __ldcg(&hs.pend_bits[(size_t)t * HT + lane]);   // issued with the masks
+            if (chase_seeds(hs, t, nimg, sd, lane, fp)) {
+                aff = grow_tile(hs, t, sd, lane, p_row, fp);
+                ntx = (uint32_t)sd.im.ntx;
+            }
+            ++my_visits;
+            if (!aff) return;
+            // the first affected neighbour is followed by this warp (lane 0 made
+            // the mask updates it reads back); the others are handed on
+            const int d0 = __ffs(aff) - 1;
+            aff &= aff - 1;
+            const uint32_t next = neighbour(t, d0, ntx);
+            if (aff && b > 0) {
+                __threadfence();                    // this visit's edges, before another warp looks
+                __syncwarp();
+            }
+            if (lane == 0) {
                 while (aff) {
                     const int d = __ffs(aff) - 1;
                     aff &= aff - 1;
                     const uint32_t n = neighbour(t, d, ntx);
-                    if (sp < CHASE_STACK && budget > 0) {
-                        if (lane == 0) stack[wl][sp] = n;
-                        ++sp;
-                        --budget;
-                    } else if (lane == 0) {
-                        push(hs, nxt, n, k + 2);
-                    }
+                    if (b > 0) queue_push(hs, tag, b - 1u, n, nxt, k + 2);
+                    else push(hs, nxt, n, k + 2);
                 }
-                __syncwarp();
-                if (sp == 0) break;
-                t = stack[wl][--sp];
-                __syncwarp();
             }
+            __syncwarp();
+            if (b == 0) {
+                if (lane == 0) push(hs, nxt, next, k + 2);
+                return;
+            }
+            t = next;
+            --b;
+        }
+    };
+
+    // worklist chunks
+    for (;;) {
+        uint32_t base = 0;
+        if (lane == 0) {
+            atomicAdd(&st->q_open, 1u);            // keep the pass open while the chunk is in hand
+            base = atomicAdd(&st->list_head, chunk);
+            if (base >= count) atomicSub(&st->q_open, 1u);
+        }
+        base = __shfl_sync(FULL, base, 0);
+        if (base >= count) break;
+        const uint32_t i = base + (uint32_t)lane;
+        uint32_t mine = 0;
+        bool has = false;
+        if ((uint32_t)lane < chunk && i < count) {
+            TileSeeds sd;
+            mine = __ldcg(&list[i]);      // (a cooperative launch reuses L1 across passes)
+            has = CANNY_CHECK(mine < hs.max_tiles, &st->error) && find_seeds(hs, mine, nimg, sd);
+        }
+        my_visits += (lane == 0) ? min(chunk, count - base) : 0u;   // entries examined
+        const uint32_t todo = __ballot_sync(FULL, has);
+        if (todo) {
+            const int src = __ffs(todo) - 1;
+            // the other seeded entries go to idle warps (nothing of this warp's to publish)
+            if (has && lane != src) queue_push(hs, tag, budget0, mine, nxt, k + 2);
+            chase(__shfl_sync(FULL, mine, src), budget0);
+        }
+        if (lane == 0) atomicSub(&st->q_open, 1u);
+    }
+
+    // queued items until every chunk and item of the pass is finished. At most
+    // as many warps wait as the grid has CTAs (the others leave); a waiting warp
+    // stays until the pass is done, so nothing queued is left behind.
+    bool waiter = false;
+    if (lane == 0) waiter = atomicAdd(&st->q_waiters, 1u) < gridDim.x;
+    if (__shfl_sync(FULL, waiter, 0)) {
+        const uint64_t t0 = globaltimer_ns();
+        uint32_t nap = 32;
+        for (;;) {
+            unsigned long long item = 0;
+            bool done = false;
+            if (lane == 0) {
+                item = queue_pop(hs, tag);
+                if (!item) {
+                    const bool late = globaltimer_ns() - t0 > WAIT_TIMEOUT_NS;
+                    done = *(volatile uint32_t *)&st->q_open == 0u || (*(volatile uint32_t *)&st->error & 2u) ||
+                           late;
+                    if (late && *(volatile uint32_t *)&st->q_open != 0u) atomicOr(&st->error, 2u);
+                }
+            }
+            item = __shfl_sync(FULL, item, 0);
+            if (item) {
+                __threadfence();
+                chase((uint32_t)item, (uint32_t)(item >> 32) & 0xffffu);
+                if (lane == 0) atomicSub(&st->q_open, 1u);
+                nap = 32;
+                continue;
+            }
+            if (__shfl_sync(FULL, done, 0)) break;
+            __nanosleep(nap);
+            nap = min(nap * 2u, 1024u);
         }
     }
     if (lane == 0) atomicAdd(&visits, my_visits);
@@ -339,6 +457,9 @@ __device__ __forceinline__ void global_pass(const HystScratch &hs, int in_graph,
             __threadfence();
             const uint32_t next = atomicAdd(&st->list_count[nxt], 0u);
             st->list_count[cur] = 0;
+            st->list_head = 0;
+            st->q_head = st->q_tail = 0;
+            st->q_open = st->q_waiters = 0;
             st->pass = k + 1;
             st->done_ctas = 0;
             bool more = next > 0;
@@ -346,6 +467,7 @@ __device__ __forceinline__ void global_pass(const HystScratch &hs, int in_graph,
                 st->error |= 1u;
                 more = false;
             }
+            if (st->error & 2u) more = false;
             st->keep_going = more ? 1u : 0u;
             __threadfence();
             if (in_graph) cudaGraphSetConditional(cond, more ? 1u : 0u);
@@ -356,9 +478,8 @@ __device__ __forceinline__ void global_pass(const HystScratch &hs, int in_graph,
 __global__ void __launch_bounds__(THREADS)
 hyst_global_kernel(HystScratch hs, int in_graph, cudaGraphConditionalHandle cond)
 {
-    __shared__ uint32_t stack[WARPS][CHASE_STACK];
     __shared__ uint32_t visits;
-    global_pass(hs, in_graph, cond, stack, visits);
+    global_pass(hs, in_graph, cond, visits);
 }
 
 // Grid-wide barrier of a cooperative launch (every CTA is resident): the last
@@ -672,10 +793,9 @@ __device__ __forceinline__ bool uf_resolve(const HystScratch &hs)
 __global__ void __launch_bounds__(THREADS, 2)
 hyst_global_coop_kernel(HystScratch hs)
 {
-    __shared__ uint32_t stack[WARPS][CHASE_STACK];
     __shared__ uint32_t visits;
     for (;;) {
-        global_pass(hs, 0, cudaGraphConditionalHandle{}, stack, visits);
+        global_pass(hs, 0, cudaGraphConditionalHandle{}, visits);
         if (!grid_barrier(hs.state)) break;
         if (!*(volatile uint32_t *)&hs.state->keep_going) break;
         // work left after a pass: resolve every long chain at once
@@ -691,6 +811,7 @@ __global__ void hyst_init_kernel(HystState *st, uint32_t ntiles, uint32_t nimg, 
 {
     if (write_single) imgs[0] = single;
     HystState s = {};
+    s.run_tag = st->run_tag % 65535u + 1u;
     s.ntiles = ntiles;
     s.nimg = nimg;
     s.max_passes = max_passes;
@@ -702,6 +823,7 @@ __global__ void hyst_init_kernel(HystState *st, uint32_t ntiles, uint32_t nimg, 
 __global__ void hyst_init_from_header_kernel(HystState *st, const BatchHeader *hdr)
 {
     HystState s = {};
+    s.run_tag = st->run_tag % 65535u + 1u;
     s.ntiles = hdr->ntiles;
     s.nimg = hdr->nimg;
     s.max_passes = hdr->max_passes;

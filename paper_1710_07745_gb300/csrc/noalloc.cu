@@ -10,8 +10,8 @@ namespace canny {
 namespace {
 
 // Largest image: 16384 tiles of 32x32 pixels (16.8 Mpixel, e.g. 4096 x 4096);
-// the scratch holds per tile its masks, pending bitmap, stamp, worklist slots
-// and the stencil's class bits (428 bytes), about 7 MB in all.
+// the scratch holds per tile its masks, pending bitmap, stamp, worklist slots,
+// in-pass queue slot and the stencil's class bits (436 bytes), about 7 MB in all.
 constexpr uint32_t NOALLOC_MAX_TILES = 16384;
 
 constexpr size_t align256(size_t v) { return (v + 255) / 256 * 256; }
@@ -21,7 +21,8 @@ constexpr size_t OFF_PEND = align256(OFF_MASKS + sizeof(TileMasks) * NOALLOC_MAX
 constexpr size_t OFF_STAMP = align256(OFF_PEND + sizeof(uint32_t) * HT * NOALLOC_MAX_TILES);
 constexpr size_t OFF_LISTS = align256(OFF_STAMP + sizeof(uint32_t) * NOALLOC_MAX_TILES);
 constexpr size_t OFF_BITS = align256(OFF_LISTS + sizeof(uint32_t) * 2 * NOALLOC_MAX_TILES);
-constexpr size_t OFF_STATE = align256(OFF_BITS + sizeof(uint32_t) * 2 * HT * NOALLOC_MAX_TILES);
+constexpr size_t OFF_QUEUE = align256(OFF_BITS + sizeof(uint32_t) * 2 * HT * NOALLOC_MAX_TILES);
+constexpr size_t OFF_STATE = align256(OFF_QUEUE + sizeof(unsigned long long) * NOALLOC_MAX_TILES);
 constexpr size_t SCRATCH_BYTES = align256(OFF_STATE + sizeof(HystState));   // about 7 MB
 
 // Shared by every call on a device; every device that loads the library holds it
@@ -86,6 +87,7 @@ extern "C" canny_status canny_run_noalloc(const uint8_t *d_in, int in_pitch, uin
     hs.stamp = (uint32_t *)(b + OFF_STAMP);
     hs.lists = (uint32_t *)(b + OFF_LISTS);
     hs.bits = (uint32_t *)(b + OFF_BITS);
+    hs.queue = (unsigned long long *)(b + OFF_QUEUE);   // zero-initialised with the array
     hs.state = (HystState *)(b + OFF_STATE);
     hs.max_tiles = NOALLOC_MAX_TILES;
     hs.max_imgs = 1;

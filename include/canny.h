@@ -229,15 +229,16 @@ canny_status canny_read_timing(canny_ctx *ctx, canny_timing *out);
  * inputs whose base or pitch is not a multiple of 16 bytes directly instead of
  * repitching them into staging first (slower; no staging memory); 0 or 1.
  *
- * Schedule of the global hysteresis passes (Section 3's connectivity step):
- * chase_budget is how many further tiles one worklist entry may follow a weak
- * chain into within a pass before it leaves the rest to the next pass (0, the
- * default: 64; else 1..4096); batch_passes picks how a batch graph runs the
- * passes: 0 (the default) a graph while-loop of one launch per pass, 1 one
- * cooperative kernel node that runs every pass behind a grid barrier (and
- * resolves chains still unfinished after a pass by union-find over tile-border
- * components); 1 falls back to 0 where the device cannot hold that grid.
- * Every setting gives the same edge map.
+ * Schedule of the global hysteresis passes (Step 4's connectivity search):
+ * chase_budget is how many further tiles a weak chain may be followed into
+ * within a pass before the rest is left to the next one (0, the default: 16;
+ * else 1..4096). Where the passes run in one cooperative launch (single images;
+ * batches with batch_passes = 1), work left after the first pass is resolved at
+ * once by union-find over tile-border components when that pass's worklist held
+ * at most 32768 tiles, and by further passes otherwise. batch_passes picks how
+ * a batch graph runs the passes: 0 (the default) a graph while-loop of one
+ * launch per pass, 1 one cooperative kernel node; 1 falls back to 0 where the
+ * device cannot hold that grid. Every setting gives the same edge map.
  */
 typedef struct {
     int band;

@@ -1119,14 +1119,14 @@ canny_status canny_autotune_batch(canny_ctx *c, int n, const canny_image *imgs, 
             st = trial(cand);
         }
         // stage 3, pass schedule: chase budget x while-loop or one cooperative node
-        const int budgets[3] = {16, 64, 256};
+        const int budgets[3] = {4, 16, 64};
         const canny_tuning shape = best;
         for (int bi = 0; bi < 3 && st == CANNY_OK; ++bi)
             for (int p = 0; p < 2 && st == CANNY_OK; ++p) {
                 canny_tuning cand = shape;
                 cand.chase_budget = budgets[bi];
                 cand.batch_passes = p;
-                if (cand.chase_budget == 64 && p == 0 && shape.chase_budget == 0 && shape.batch_passes == 0)
+                if (cand.chase_budget == 16 && p == 0 && shape.chase_budget == 0 && shape.batch_passes == 0)
                     continue;   // the defaults, timed in stage 1
                 st = trial(cand);
             }

@@ -66,8 +66,8 @@ struct HystState {
     uint32_t nimg;            // images in this run
     uint32_t keep_going;      // 1 if another pass is needed
     uint32_t bar_count, bar_gen;   // grid barrier of the cooperative multi-pass kernel
-    uint32_t uf_count;        // union-find stage: tiles listed
-    uint32_t uf_round;        // union-find stage: last pointer-jumping round that changed a parent
+    uint32_t uf_entries;      // union-find stage: entries of the pass before it (list of that pass)
+    uint32_t uf_count;        // union-find stage: tiles listed (in list 1)
     uint32_t chase_budget;    // tiles a chain may be followed into within a pass (0: the default)
     // the in-pass queue of a global pass (zero between passes)
     uint32_t list_head;       // worklist entries claimed so far

@@ -21,26 +21,6 @@ __device__ __forceinline__ uint32_t fill_runs(uint32_t s, uint32_t c)
     return up | dn;
 }
 
-// Grow e (subset of c) through 8-connected pixels of c inside the tile until
-// stable. Every round that changes something adds at least one pixel, so at
-// most 1024 + 1 rounds run.
-__device__ __forceinline__ uint32_t flood_tile(uint32_t e, uint32_t c, int lane)
-{
-    for (int it = 0; it < HT * HT + 2; ++it) {
-        uint32_t f = fill_runs(e, c);
-        uint32_t d = f | (f << 1) | (f >> 1);
-        uint32_t up = __shfl_up_sync(FULL, d, 1);
-        uint32_t dn = __shfl_down_sync(FULL, d, 1);
-        if (lane == 0) up = 0;
-        if (lane == HT - 1) dn = 0;
-        uint32_t ne = f | (c & (up | dn));
-        bool changed = __any_sync(FULL, ne != e);
-        e = ne;
-        if (!changed) break;
-    }
-    return e;
-}
-
 // fill_runs with the bit reversal of c computed once by the caller.
 __device__ __forceinline__ uint32_t fill_runs_r(uint32_t s, uint32_t c, uint32_t rc)
 {
@@ -52,6 +32,47 @@ __device__ __forceinline__ uint32_t fill_runs_r(uint32_t s, uint32_t c, uint32_t
 
 // A row mask and its left and right neighbours.
 __device__ __forceinline__ uint32_t dilate(uint32_t x) { return x | (x << 1) | (x >> 1); }
+
+// Grow e (subset of c) through 8-connected pixels of c inside the tile until
+// stable (lane = row). A round pulls the masks of the four rows above and the
+// four below and grows them in order towards the lane's own row (each row's
+// runs filled, then the next row seeded from its dilation), so a chain climbs
+// up to four rows per round instead of one. Every round that changes something
+// adds at least one pixel, so at most 1024 + 1 rounds run.
+__device__ __forceinline__ uint32_t flood_tile(uint32_t e, uint32_t c, int lane)
+{
+    const uint32_t rc = __brev(c);
+    uint32_t ca[4], cb[4], rca[4], rcb[4];     // c of rows lane-1-k and lane+1+k (0 outside)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        ca[k] = __shfl_up_sync(FULL, c, k + 1);
+        cb[k] = __shfl_down_sync(FULL, c, k + 1);
+        if (lane < k + 1) ca[k] = 0u;
+        if (lane + k + 1 > HT - 1) cb[k] = 0u;
+        rca[k] = __brev(ca[k]);
+        rcb[k] = __brev(cb[k]);
+    }
+    e = fill_runs_r(e, c, rc);
+    for (int it = 0; it < HT * HT + 2; ++it) {
+        uint32_t a[4], b[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            a[k] = __shfl_up_sync(FULL, e, k + 1) & ca[k];
+            b[k] = __shfl_down_sync(FULL, e, k + 1) & cb[k];
+        }
+        uint32_t x = a[3], y = b[3];
+#pragma unroll
+        for (int k = 2; k >= 0; --k) {
+            x = fill_runs_r(a[k] | (ca[k] & dilate(x)), ca[k], rca[k]);
+            y = fill_runs_r(b[k] | (cb[k] & dilate(y)), cb[k], rcb[k]);
+        }
+        const uint32_t ne = fill_runs_r(e | (c & (dilate(x) | dilate(y))), c, rc);
+        const bool changed = __any_sync(FULL, ne != e);
+        e = ne;
+        if (!changed) break;
+    }
+    return e;
+}
 
 // Four tiles per warp: lane 8 t + s holds rows 4 s .. 4 s + 3 of tile t, as
 // e[0..3] (subsets of c[0..3]). Grows every tile's e through 8-connected pixels

@@ -58,7 +58,12 @@ enum { NB_U, NB_UL, NB_UR, NB_D, NB_DL, NB_DR, NB_L, NB_R };
 
 // Tiles a chain may be followed into within a pass before the rest is listed
 // for the next pass (the default of the chase budget).
-constexpr int CHASE_BUDGET = 64;
+constexpr int CHASE_BUDGET = 16;
+// The union-find stage follows the first pass only when that pass's worklist
+// held at most this many tiles: its cost grows with the tiles it labels, a
+// pass's with the length of the chains it follows, so images with many short
+// chains (a large list) keep to passes.
+constexpr uint32_t UF_MAX_ENTRIES = 32768;
 
 // Border masks as other warps last wrote them: loads that bypass L1, since
 // tiles are revisited within one pass and L1 is not coherent across SMs.
@@ -76,6 +81,27 @@ __device__ __forceinline__ uint32_t edge_bottom_cg(const TileMasks *m) { return 
 __device__ __forceinline__ uint32_t edge_top_cg(const TileMasks *m) { return __ldcg(&m->edge_top); }
 __device__ __forceinline__ uint32_t edge_left_cg(const TileMasks *m) { return __ldcg(&m->edge_left); }
 __device__ __forceinline__ uint32_t edge_right_cg(const TileMasks *m) { return __ldcg(&m->edge_right); }
+
+// Write 255 at the pixels of e (row `lane` of tile (tx, ty); whole warp). The
+// other bytes of the rows may be edges already, so only e's bytes are stored:
+// lane by lane (as many rounds as the fullest row has bits) or row by row (one
+// coalesced store per row that has any), whichever takes fewer rounds.
+__device__ __forceinline__ void store_new_edges(const HystImage &im, int tx, int ty, int lane, uint32_t e)
+{
+    const uint32_t rows = __ballot_sync(FULL, e != 0u);
+    if (!rows) return;
+    const int most = (int)__reduce_max_sync(FULL, (unsigned)__popc(e));
+    if (__popc(rows) < most) {
+        uint8_t *col = im.map + (int64_t)ty * HT * im.pitch + tx * HT + lane;
+        for (uint32_t m = rows; m; m &= m - 1) {
+            const int r = __ffs(m) - 1;
+            if ((__shfl_sync(FULL, e, r) >> lane) & 1u) col[(int64_t)r * im.pitch] = 255;
+        }
+    } else {
+        uint8_t *row = im.map + (int64_t)(ty * HT + lane) * im.pitch + tx * HT;
+        for (uint32_t bits = e; bits; bits &= bits - 1) row[__ffs(bits) - 1] = 255;
+    }
+}
 
 // Neighbour of tile t in direction d (NB_*) for an image ntx tiles wide:
 // t + dy * ntx + dx, with dx + 1 and dy + 1 packed two bits per direction.
@@ -194,17 +220,8 @@ __device__ __forceinline__ uint32_t grow_tile(const HystScratch &hs, uint32_t t,
     e0 &= p;
     const uint32_t e = flood_tile(e0, p, lane);
 
-    // write the new edges (sparse byte stores) and the shrunken pending set
-    if (e) {
-        int y = ty * HT + lane;
-        uint8_t *row = im.map + (int64_t)y * im.pitch + tx * HT;
-        uint32_t bits = e;
-        while (bits) {
-            int b = __ffs(bits) - 1;
-            row[b] = 255;
-            bits &= bits - 1;
-        }
-    }
+    // write the new edges and the shrunken pending set
+    store_new_edges(im, tx, ty, lane, e);
     p &= ~e;
     hs.pend_bits[(size_t)t * HT + lane] = p;
 
@@ -415,8 +432,9 @@ __device__ __forceinline__ void global_pass(const HystScratch &hs, int in_graph,
     }
 
     // queued items until every chunk and item of the pass is finished. At most
-    // as many warps wait as the grid has CTAs (the others leave); a waiting warp
-    // stays until the pass is done, so nothing queued is left behind.
+    // as many warps wait as the grid has CTAs (the others leave: more pollers
+    // of the control block slow the warps that work); a waiting warp stays
+    // until the pass is done, so nothing queued is left behind.
     bool waiter = false;
     if (lane == 0) waiter = atomicAdd(&st->q_waiters, 1u) < gridDim.x;
     if (__shfl_sync(FULL, waiter, 0)) {
@@ -457,6 +475,8 @@ __device__ __forceinline__ void global_pass(const HystScratch &hs, int in_graph,
             __threadfence();
             const uint32_t next = atomicAdd(&st->list_count[nxt], 0u);
             st->list_count[cur] = 0;
+            st->uf_entries = count;           // a union-find stage after this pass labels these tiles
+            st->uf_count = 0;
             st->list_head = 0;
             st->q_head = st->q_tail = 0;
             st->q_open = st->q_waiters = 0;
@@ -519,9 +539,9 @@ __device__ __forceinline__ bool grid_barrier(HystState *st)
 }
 
 // ---------------------------------------------------------------- long chains: union-find
-// When the first pass leaves work for a second one (a chain longer than one
-// warp's chase budget, or more chains than the chase stacks hold), the rest is
-// resolved at once instead of pass after pass. Every pending pixel is, by then,
+// When the first pass leaves work for a second one (a chain longer than the
+// chase budget, or a full in-pass queue), the rest is resolved at once instead
+// of pass after pass. Every pending pixel is, by then,
 // a weak pixel not connected inside its tile to an edge, so a pending pixel
 // becomes an edge exactly when it is connected, through pending pixels across
 // tile borders, to a pending border pixel next to an edge of a neighbouring tile.
@@ -531,12 +551,13 @@ __device__ __forceinline__ bool grid_barrier(HystState *st)
 //           lower and two lower diagonal neighbours wherever pending border
 //           pixels touch (lock-free union-find, links by atomicCAS, finds with
 //           path halving), and marks components next to a neighbour's edge;
-//   roots   a marked component marks its root;
+//   roots   a marked component marks its root (a find with path halving);
 //   apply   each listed tile floods its pending pixels from the border pixels
 //           whose component's root is marked and writes the new edges.
-// The phases are separated by grid barriers, whatever the chain length; between
-// union and roots, rounds of pointer jumping (each halves every path) make the
-// trees flat, so at most log2(components) rounds run.
+// Four phases separated by grid barriers, whatever the chain length. Links go
+// from the larger root to the smaller and every find halves the path it walks,
+// so the trees stay shallow (the finds of the roots phase shorten them again
+// for the apply phase).
 constexpr int UF_LSTRIDE = 128;         // label bytes a tile: 124 border pixels, count at byte 127
 constexpr int UF_COUNT = 127;
 constexpr uint32_t UF_MAXC = 64;        // components a tile (at most 62 can touch its border)
@@ -580,21 +601,23 @@ __device__ __forceinline__ uint32_t uf_comp(const HystScratch &hs, uint32_t t, i
     return t * UF_MAXC + __ldcg(hs.uf_label + (size_t)t * UF_LSTRIDE + pos);
 }
 
-// label: every tile of the run with pending border pixels (lanes test 32 tiles at
-// once; the warp labels those that have some)
+// label: every tile with pending border pixels, one warp a tile. The stage runs
+// right after the first pass, whose worklist (list 0) holds every tile the local
+// fill left with pending border pixels (pending pixels only ever become edges),
+// so that list is the one to scan; the labelled tiles are listed in list 1.
 __device__ __forceinline__ void uf_label_phase(const HystScratch &hs, int lane, uint32_t warp, uint32_t nwarps)
 {
     HystState *st = hs.state;
-    const uint32_t ntiles = min(st->ntiles, hs.max_tiles);
-    for (uint32_t base = warp * 32u; base < ntiles; base += nwarps * 32u) {
-        const uint32_t i = base + (uint32_t)lane;
-        const bool act = i < ntiles && pending_border(masks_cg(&hs.masks[i]));
-        uint32_t todo = __ballot_sync(FULL, act);
-        while (todo) {
-            const int src = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const uint32_t t = base + (uint32_t)src;
-            const TileMasks m = masks_cg(&hs.masks[t]);
+    // every tile with pending border pixels now was on the first pass's worklist
+    // (list 0: the tiles the local fill left with pending border pixels)
+    const uint32_t n0 = min(*(volatile uint32_t *)&st->uf_entries, hs.max_tiles);
+    uint32_t *uf_list = hs.lists + hs.max_tiles;
+    for (uint32_t i = warp; i < n0; i += nwarps) {
+        const uint32_t t = __ldcg(&hs.lists[i]);
+        if (!CANNY_CHECK(t < hs.max_tiles, &st->error)) continue;
+        const TileMasks m = masks_cg(&hs.masks[t]);
+        if (!pending_border(m)) continue;
+        {
             const uint32_t P = __ldcg(&hs.pend_bits[(size_t)t * HT + lane]);
             uint8_t *lab = hs.uf_label + (size_t)t * UF_LSTRIDE;
             uint32_t rt = m.pend_top, rb = m.pend_bottom;
@@ -626,7 +649,7 @@ __device__ __forceinline__ void uf_label_phase(const HystScratch &hs, int lane, 
             if (lane == 0) {
                 lab[UF_COUNT] = (uint8_t)k;
                 const uint32_t slot = atomicAdd(&st->uf_count, 1u);
-                if (CANNY_CHECK(slot < hs.max_tiles, &st->error)) hs.lists[slot] = t;
+                if (CANNY_CHECK(slot < hs.max_tiles, &st->error)) uf_list[slot] = t;
             }
         }
     }
@@ -640,7 +663,7 @@ __device__ __forceinline__ void uf_union_phase(const HystScratch &hs, int lane, 
     const uint32_t n = min(*(volatile uint32_t *)&st->uf_count, hs.max_tiles);
     const int nimg = (int)st->nimg;
     for (uint32_t i = warp; i < n; i += nwarps) {
-        const uint32_t t = __ldcg(&hs.lists[i]);
+        const uint32_t t = __ldcg(&hs.lists[hs.max_tiles + i]);
         TileSeeds sd;
         find_seeds(hs, t, nimg, sd);
         const HystImage &im = sd.im;
@@ -679,36 +702,13 @@ __device__ __forceinline__ void uf_union_phase(const HystScratch &hs, int lane, 
     }
 }
 
-// jump: every component's parent becomes its grandparent; a round that changes
-// nothing ends the jumping (the forest is final once the unions are done, so
-// after r rounds paths are 2^r times shorter)
-__device__ __forceinline__ bool uf_jump_phase(const HystScratch &hs, int lane, uint32_t warp, uint32_t nwarps)
-{
-    HystState *st = hs.state;
-    const uint32_t n = min(*(volatile uint32_t *)&st->uf_count, hs.max_tiles);
-    bool changed = false;
-    for (uint32_t i = warp; i < n; i += nwarps) {
-        const uint32_t t = __ldcg(&hs.lists[i]);
-        const uint32_t k = __ldcg(hs.uf_label + (size_t)t * UF_LSTRIDE + UF_COUNT);
-        for (uint32_t j = (uint32_t)lane; j < k; j += 32u) {
-            const uint32_t c = t * UF_MAXC + j;
-            const uint32_t p = __ldcg(hs.uf_parent + c), gp = __ldcg(hs.uf_parent + p);
-            if (gp != p) {
-                hs.uf_parent[c] = gp;
-                changed = true;
-            }
-        }
-    }
-    return changed;
-}
-
 // roots: a marked component marks its root
 __device__ __forceinline__ void uf_roots_phase(const HystScratch &hs, int lane, uint32_t warp, uint32_t nwarps)
 {
     HystState *st = hs.state;
     const uint32_t n = min(*(volatile uint32_t *)&st->uf_count, hs.max_tiles);
     for (uint32_t i = warp; i < n; i += nwarps) {
-        const uint32_t t = __ldcg(&hs.lists[i]);
+        const uint32_t t = __ldcg(&hs.lists[hs.max_tiles + i]);
         const uint32_t k = __ldcg(hs.uf_label + (size_t)t * UF_LSTRIDE + UF_COUNT);
         for (uint32_t j = (uint32_t)lane; j < k; j += 32u) {
             const uint32_t c = t * UF_MAXC + j;
@@ -725,7 +725,7 @@ __device__ __forceinline__ void uf_apply_phase(const HystScratch &hs, int lane, 
     const uint32_t n = min(*(volatile uint32_t *)&st->uf_count, hs.max_tiles);
     const int nimg = (int)st->nimg;
     for (uint32_t i = warp; i < n; i += nwarps) {
-        const uint32_t t = __ldcg(&hs.lists[i]);
+        const uint32_t t = __ldcg(&hs.lists[hs.max_tiles + i]);
         const TileMasks m = masks_cg(&hs.masks[t]);
         const int y = lane, x = lane;
         auto marked = [&](int pos) { return __ldcg(hs.uf_seeded + uf_find(hs.uf_parent, uf_comp(hs, t, pos))) != 0; };
@@ -743,15 +743,7 @@ __device__ __forceinline__ void uf_apply_phase(const HystScratch &hs, int lane, 
         const HystImage im = hs.imgs[find_image(hs.imgs, nimg, t)];
         const uint32_t local = t - im.tile_base;
         const int tx = (int)(local % (uint32_t)im.ntx), ty = (int)(local / (uint32_t)im.ntx);
-        if (e) {
-            uint8_t *row = im.map + (int64_t)(ty * HT + lane) * im.pitch + tx * HT;
-            uint32_t bits = e;
-            while (bits) {
-                const int b = __ffs(bits) - 1;
-                row[b] = 255;
-                bits &= bits - 1;
-            }
-        }
+        store_new_edges(im, tx, ty, lane, e);
         hs.pend_bits[(size_t)t * HT + lane] = p & ~e;
     }
 }
@@ -762,18 +754,11 @@ __device__ __forceinline__ bool uf_resolve(const HystScratch &hs)
 {
     const int lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * THREADS + threadIdx.x) >> 5, nwarps = gridDim.x * WARPS;
-    if (blockIdx.x == 0 && threadIdx.x == 0) hs.state->uf_count = hs.state->uf_round = 0u;
-    if (!grid_barrier(hs.state)) return false;
+    // (uf_count and uf_entries were set by the last CTA of the pass)
     uf_label_phase(hs, lane, warp, nwarps);
     if (!grid_barrier(hs.state)) return false;
     uf_union_phase(hs, lane, warp, nwarps);
     if (!grid_barrier(hs.state)) return false;
-    // uf_round: the last jump round (counted from 1) that changed a parent
-    for (uint32_t r = 1; r <= 32; ++r) {
-        if (uf_jump_phase(hs, lane, warp, nwarps)) atomicMax(&hs.state->uf_round, r);
-        if (!grid_barrier(hs.state)) return false;
-        if (*(volatile uint32_t *)&hs.state->uf_round < r) break;
-    }
     uf_roots_phase(hs, lane, warp, nwarps);
     if (!grid_barrier(hs.state)) return false;
     uf_apply_phase(hs, lane, warp, nwarps);
@@ -798,8 +783,9 @@ hyst_global_coop_kernel(HystScratch hs)
         global_pass(hs, 0, cudaGraphConditionalHandle{}, visits);
         if (!grid_barrier(hs.state)) break;
         if (!*(volatile uint32_t *)&hs.state->keep_going) break;
-        // work left after a pass: resolve every long chain at once
-        if (hs.uf_parent) {
+        // work left after the first pass: resolve every long chain at once
+        if (hs.uf_parent && *(volatile uint32_t *)&hs.state->pass == 1u &&
+            *(volatile uint32_t *)&hs.state->uf_entries <= UF_MAX_ENTRIES) {
             uf_resolve(hs);
             break;
         }

@@ -32,7 +32,11 @@
 // shared-memory loads (the horizontal pass pairs two rows, the vertical pass
 // and Sobel pair two columns); the arithmetic itself is scalar and correctly
 // rounded per operation (__fmul_rn / __fadd_rn, and __fmaf_rn only where the
-// product by 2 is exact).
+// product by 2 is exact). The Gaussian's products of a pair of independent
+// sums come from one two-wide multiply (mul.rn.f32x2, each half rounded like
+// __fmul_rn); the sums stay scalar __fadd_rn. A two-wide multiply feeding a
+// two-wide add was found to round once, like a fused multiply-add, whatever
+// the contraction settings, so the adds are never two-wide.
 #include "hyst_tile.cuh"
 
 namespace canny {
@@ -78,29 +82,32 @@ __device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b)
 __device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 tap2(const FloatParams &fp, int k) { return f2(fp.taps[k], fp.taps[k]); }
+
+// a * b on both halves, each correctly rounded
+__device__ __forceinline__ float2 mul2_rn(float2 a, float2 b)
+{
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;"
+        : "=l"(r)
+        : "l"(*reinterpret_cast<const unsigned long long *>(&a)), "l"(*reinterpret_cast<const unsigned long long *>(&b)));
+    return *reinterpret_cast<const float2 *>(&r);
+}
+// a + b on both halves as two scalar correctly rounded adds
+__device__ __forceinline__ float2 add2_rn(float2 a, float2 b) { return f2(fadd(a.x, b.x), fadd(a.y, b.y)); }
 
 // One Gaussian tap sum on a pair of independent sums:
-// taps[0]*v(0) + taps[1]*v(1) + ..., each product and each sum rounded. The
-// pair shares its loads; the arithmetic is scalar __fmul_rn / __fadd_rn per
-// lane, which are never merged into a fused multiply-add (a paired multiply
-// followed by a paired add was observed to round once, like an FMA).
-// KS = 0: run-time ksize (taps read by index).
+// taps[0]*v(0) + taps[1]*v(1) + ..., each product and each sum rounded, both
+// sums at once with the two-wide operations. KS = 0: run-time ksize.
 template <int KS, typename Load>
 __device__ __forceinline__ float2 tap_sum2(const FloatParams &fp, Load v)
 {
-    float2 x = v(0);
-    float2 acc = f2(fmul(fp.taps[0], x.x), fmul(fp.taps[0], x.y));
+    float2 acc = mul2_rn(tap2(fp, 0), v(0));
     if constexpr (KS > 0) {
 #pragma unroll
-        for (int k = 1; k < KS; ++k) {
-            x = v(k);
-            acc = f2(fadd(acc.x, fmul(fp.taps[k], x.x)), fadd(acc.y, fmul(fp.taps[k], x.y)));
-        }
+        for (int k = 1; k < KS; ++k) acc = add2_rn(acc, mul2_rn(tap2(fp, k), v(k)));
     } else {
-        for (int k = 1; k < fp.ksize; ++k) {
-            x = v(k);
-            acc = f2(fadd(acc.x, fmul(fp.taps[k], x.x)), fadd(acc.y, fmul(fp.taps[k], x.y)));
-        }
+        for (int k = 1; k < fp.ksize; ++k) acc = add2_rn(acc, mul2_rn(tap2(fp, k), v(k)));
     }
     return acc;
 }
@@ -126,20 +133,29 @@ __device__ __forceinline__ void hrow_regs(const uint8_t *row, int x0, int c0, co
     const uint32_t wd[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
     // window index of image column x0 - 2 + c0 + q - R + k is 14 + q - R + k
     constexpr int LO = 14 - R, N = NOUT + 2 * R;
-    float v[N];
+    static_assert(N % 2 == 0 && NOUT % 4 == 0, "outputs in pairs, stores in fours");
+    // the inputs as pairs from even offsets, (v[2j], v[2j+1]), and from odd
+    // ones, (v[2j+1], v[2j+2]), so that outputs q, q + 1 take both operands of
+    // every tap as one pair
+    auto raw = [&](int i) { return __uint_as_float(__byte_perm(wd[(LO + i) >> 2], 0x4B000000u, 0x7640u | ((LO + i) & 3))); };
+    const float2 bias = f2(-8388608.f, -8388608.f);
+    float2 pe[N / 2], po[N / 2 - 1];
 #pragma unroll
-    for (int i = 0; i < N; ++i) v[i] = byte_f(wd[(LO + i) >> 2], (LO + i) & 3);
-    float out[NOUT];
+    for (int j = 0; j < N / 2; ++j) pe[j] = add2_rn(f2(raw(2 * j), raw(2 * j + 1)), bias);
 #pragma unroll
-    for (int q = 0; q < NOUT; ++q) {
-        float acc = fmul(fp.taps[0], v[q]);
+    for (int j = 0; j < N / 2 - 1; ++j) po[j] = add2_rn(f2(raw(2 * j + 1), raw(2 * j + 2)), bias);
+    float2 out[NOUT / 2];
 #pragma unroll
-        for (int k = 1; k < KS; ++k) acc = fadd(acc, fmul(fp.taps[k], v[q + k]));
-        out[q] = acc;
+    for (int qp = 0; qp < NOUT / 2; ++qp) {
+        float2 acc = mul2_rn(tap2(fp, 0), pe[qp]);
+#pragma unroll
+        for (int k = 1; k < KS; ++k)
+            acc = add2_rn(acc, mul2_rn(tap2(fp, k), (k & 1) ? po[qp + (k >> 1)] : pe[qp + (k >> 1)]));
+        out[qp] = acc;
     }
 #pragma unroll
     for (int q = 0; q < NOUT; q += 4)
-        *reinterpret_cast<float4 *>(dst + q) = make_float4(out[q], out[q + 1], out[q + 2], out[q + 3]);
+        *reinterpret_cast<float4 *>(dst + q) = make_float4(out[q / 2].x, out[q / 2].y, out[q / 2 + 1].x, out[q / 2 + 1].y);
 }
 
 // Step 1's horizontal pass through a staged copy of the input (blocks at the
@@ -246,11 +262,9 @@ __device__ __forceinline__ void smooth_block(const uint8_t *__restrict__ in, int
                     for (int i = 0; i < KS + RB - 1; ++i) win[i] = *reinterpret_cast<const float2 *>(src + i * g.SX);
 #pragma unroll
                     for (int o = 0; o < RB; ++o) {
-                        float2 acc = f2(fmul(fp.taps[0], win[o].x), fmul(fp.taps[0], win[o].y));
+                        float2 acc = mul2_rn(tap2(fp, 0), win[o]);
 #pragma unroll
-                        for (int k = 1; k < KS; ++k)
-                            acc = f2(fadd(acc.x, fmul(fp.taps[k], win[o + k].x)),
-                                     fadd(acc.y, fmul(fp.taps[k], win[o + k].y)));
+                        for (int k = 1; k < KS; ++k) acc = add2_rn(acc, mul2_rn(tap2(fp, k), win[o + k]));
                         *reinterpret_cast<float2 *>(S_s + (rb + o) * g.SX + 2 * q) = acc;
                     }
                     continue;
@@ -268,10 +282,12 @@ __device__ __forceinline__ void smooth_block(const uint8_t *__restrict__ in, int
 __device__ __forceinline__ uint32_t sector_of(float gx, float gy)
 {
     const float t = 0.41421356f, ax = fabsf(gx), ay = fabsf(gy);
-    if (ay < fmul(ax, t)) return 0u;
-    if (ax < fmul(ay, t)) return 1u;
-    if ((gx > 0.f && gy > 0.f) || (gx < 0.f && gy < 0.f)) return 2u;
-    return 3u;
+    // the first test that holds decides, as selects rather than branches
+    const bool same_sign = (gx > 0.f && gy > 0.f) || (gx < 0.f && gy < 0.f);
+    uint32_t code = same_sign ? 2u : 3u;
+    code = (ax < fmul(ay, t)) ? 1u : code;
+    code = (ay < fmul(ax, t)) ? 0u : code;
+    return code;
 }
 
 // Sobel (in the definition's order: columns summed top to bottom; a + 2 b

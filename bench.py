@@ -45,15 +45,17 @@ K1_BYTES_PER_PX = 2
 # stencil to the tile fill and back (0.25 B/px each way)
 K1_DESIGN_BYTES_PER_PX = 2.5
 # ncu DRAM traffic of the two stencil-stage kernels per 16384^2 image, valid only for
-# the kernel sources it was measured on (a 16384 x 8192 capture, x2)
-K1_TRAFFIC = {"sha256_prefix": None, "bytes": None}
+# the kernel sources it was measured on (a 16384 x 8192 capture, x2: both kernels'
+# traffic is proportional to the pixels)
+K1_TRAFFIC = {"sha256_prefix": "123c42479c581de3", "bytes": 563.6e6}
 # whole pipeline floor (the spec minimum): read the image, write the edge map
 PIPE_BYTES_PER_PX = 2
 # ncu smsp__inst_executed.sum of the two stencil-stage kernels per pixel (same
 # capture and sources as K1_TRAFFIC)
-K1_INST = {"sha256_prefix": None, "warp_inst_per_px": None}
-# ncu DRAM traffic of the global hysteresis passes per 16384^2 image (same sources)
-K3_TRAFFIC = {"sha256_prefix": None, "bytes": None}
+K1_INST = {"sha256_prefix": "123c42479c581de3", "warp_inst_per_px": 0.9737}
+# ncu DRAM traffic of the global hysteresis passes per 16384^2 image (same capture,
+# x2: an estimate, since the passes' work follows the image's chains, not its area)
+K3_TRAFFIC = {"sha256_prefix": "3b040c6d0a504184", "bytes": 8.8e6}
 # warp instructions an SM can issue per clock (4 schedulers, one each)
 ISSUE_PER_SM_CLK = 4
 

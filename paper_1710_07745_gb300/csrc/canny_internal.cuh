@@ -70,9 +70,8 @@ struct HystState {
     uint32_t uf_count;        // union-find stage: tiles listed (in list 1)
     uint32_t chase_budget;    // tiles a chain may be followed into within a pass (0: the default)
     // the in-pass queue of a global pass (zero between passes)
-    uint32_t list_head;       // worklist entries claimed so far
     uint32_t q_head, q_tail;  // queue slots claimed by consumers / reserved by producers
-    uint32_t q_open;          // queued items not yet finished, plus worklist chunks in hand
+    uint32_t q_open;          // queued items not yet finished, plus CTAs still on their worklist entries
     uint32_t q_waiters;       // warps that stay for queued items
     uint32_t run_tag;         // 1..65535, new for every run: tags queue items of this run
 };

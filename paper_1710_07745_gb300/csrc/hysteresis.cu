@@ -276,9 +276,10 @@ __device__ __forceinline__ uint32_t grow_tile(const HystScratch &hs, uint32_t t,
 // its warp was busy with another, or a branch of a chain (the neighbours a
 // visit affected beyond the one its warp follows). Each item carries what is
 // left of its chain's budget. q_open counts items queued but not yet finished
-// plus worklist chunks in hand: a waiting warp leaves the pass only when the
-// worklist is exhausted and q_open is 0, so no item is left behind, and idle
-// warps keep taking branches while long chains run.
+// plus CTAs whose warps are still on their worklist entries. A warp that queued
+// an item stays until q_open is 0, so no item is left behind even if a CTA
+// starts late (after others have left); the waiting warps keep taking branches
+// while long chains run.
 __device__ __forceinline__ unsigned long long make_item(uint32_t tag, uint32_t budget, uint32_t tile)
 {
     return ((unsigned long long)tag << 48) | ((unsigned long long)budget << 32) | tile;
@@ -329,20 +330,20 @@ __device__ __forceinline__ unsigned long long queue_pop(const HystScratch &hs, u
     }
 }
 
-// One pass over the current worklist, all CTAs of the grid. Warps claim chunks
-// of entries (32, or fewer when the list is short so that every warp gets
-// some); the lanes check a chunk's entries for seeds at once. A warp grows one
-// seeded tile and follows the chain it starts (depth first: it visits next a
+// One pass over the current worklist, all CTAs of the grid. Warps take chunks
+// of entries in order (32, or fewer when the list is short so that every warp
+// gets some); the lanes check a chunk's entries for seeds at once. A warp grows
+// a seeded tile and follows the chain it starts (depth first: it visits next a
 // neighbour whose facing pending pixels touch the edges it added, while the
-// chain's budget lasts); further seeded entries and further affected
-// neighbours go to the in-pass queue for idle warps, and what a spent budget
-// or a full queue cannot take is listed for the next pass. A tile may be
+// chain's budget lasts); further affected neighbours, and on a short list the
+// chunk's other seeded entries, go to the in-pass queue for idle warps, and
+// what a spent budget or a full queue cannot take is listed for the next pass. A tile may be
 // visited by two warps at a time: both only add edges, and each re-reads the
 // masks, so the result is the same. The last CTA to finish swaps the
 // worklists, counts the pass and sets keep_going (and, in a graph, the
 // while-node's condition).
 __device__ __forceinline__ void global_pass(const HystScratch &hs, int in_graph, cudaGraphConditionalHandle cond,
-                                            uint32_t &visits)
+                                            uint32_t &visits, uint32_t &warps_on_list)
 {
     HystState *st = hs.state;
     const uint32_t k = *(volatile uint32_t *)&st->pass;
@@ -351,14 +352,20 @@ __device__ __forceinline__ void global_pass(const HystScratch &hs, int in_graph,
     if (!CANNY_CHECK(count <= hs.max_tiles, &st->error)) count = hs.max_tiles;
     const int nimg = (int)st->nimg;
     const int lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * THREADS + threadIdx.x) >> 5;
     const uint32_t nwarps = gridDim.x * WARPS;
     const uint32_t *list = hs.lists + (size_t)cur * hs.max_tiles;
     const uint32_t budget0 = st->chase_budget ? st->chase_budget : (uint32_t)CHASE_BUDGET;
     const uint32_t tag = st->run_tag;
     const uint32_t chunk = count >= nwarps * 32u ? 32u : max(1u, (count + nwarps - 1u) / nwarps);
-    if (threadIdx.x == 0) visits = 0;
+    if (threadIdx.x == 0) {
+        visits = 0;
+        warps_on_list = WARPS;
+        atomicAdd(&st->q_open, 1u);            // the CTA keeps the pass open while its warps work the list
+    }
     __syncthreads();
     uint32_t my_visits = 0;
+    bool pushed = false;                       // this thread queued an item
 
     // follow the chain from tile t with budget b (whole warp)
     auto chase = [&](uint32_t t, uint32_t b) {
@@ -388,8 +395,12 @@ __device__ __forceinline__ void global_pass(const HystScratch &hs, int in_graph,
                     const int d = __ffs(aff) - 1;
                     aff &= aff - 1;
                     const uint32_t n = neighbour(t, d, ntx);
-                    if (b > 0) queue_push(hs, tag, b - 1u, n, nxt, k + 2);
-                    else push(hs, nxt, n, k + 2);
+                    if (b > 0) {
+                        queue_push(hs, tag, b - 1u, n, nxt, k + 2);
+                        pushed = true;
+                    } else {
+                        push(hs, nxt, n, k + 2);
+                    }
                 }
             }
             __syncwarp();
@@ -402,16 +413,8 @@ __device__ __forceinline__ void global_pass(const HystScratch &hs, int in_graph,
         }
     };
 
-    // worklist chunks
-    for (;;) {
-        uint32_t base = 0;
-        if (lane == 0) {
-            atomicAdd(&st->q_open, 1u);            // keep the pass open while the chunk is in hand
-            base = atomicAdd(&st->list_head, chunk);
-            if (base >= count) atomicSub(&st->q_open, 1u);
-        }
-        base = __shfl_sync(FULL, base, 0);
-        if (base >= count) break;
+    // worklist chunks, spread over the warps in order
+    for (uint32_t base = warp * chunk; base < count; base += nwarps * chunk) {
         const uint32_t i = base + (uint32_t)lane;
         uint32_t mine = 0;
         bool has = false;
@@ -421,22 +424,32 @@ __device__ __forceinline__ void global_pass(const HystScratch &hs, int in_graph,
             has = CANNY_CHECK(mine < hs.max_tiles, &st->error) && find_seeds(hs, mine, nimg, sd);
         }
         my_visits += (lane == 0) ? min(chunk, count - base) : 0u;   // entries examined
-        const uint32_t todo = __ballot_sync(FULL, has);
-        if (todo) {
+        uint32_t todo = __ballot_sync(FULL, has);
+        if (todo && chunk < 32u) {
+            // a short list leaves warps idle: the other seeded entries go to them
+            // (nothing of this warp's to publish)
             const int src = __ffs(todo) - 1;
-            // the other seeded entries go to idle warps (nothing of this warp's to publish)
-            if (has && lane != src) queue_push(hs, tag, budget0, mine, nxt, k + 2);
+            if (has && lane != src) {
+                queue_push(hs, tag, budget0, mine, nxt, k + 2);
+                pushed = true;
+            }
+            todo = 1u << src;
+        }
+        // a long list keeps every warp busy: the warp grows its seeded entries in turn
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
             chase(__shfl_sync(FULL, mine, src), budget0);
         }
-        if (lane == 0) atomicSub(&st->q_open, 1u);
     }
+    // the CTA's last warp off the list releases its hold on the pass
+    if (lane == 0 && atomicSub(&warps_on_list, 1u) == 1u) atomicSub(&st->q_open, 1u);
 
-    // queued items until every chunk and item of the pass is finished. At most
-    // as many warps wait as the grid has CTAs (the others leave: more pollers
-    // of the control block slow the warps that work); a waiting warp stays
-    // until the pass is done, so nothing queued is left behind.
-    bool waiter = false;
-    if (lane == 0) waiter = atomicAdd(&st->q_waiters, 1u) < gridDim.x;
+    // queued items until every item of the pass is finished. Warps that queued
+    // some stay; of the others at most as many wait as the grid has CTAs (more
+    // pollers of the control block slow the warps that work).
+    bool waiter = __any_sync(FULL, pushed);
+    if (lane == 0 && !waiter) waiter = atomicAdd(&st->q_waiters, 1u) < gridDim.x;
     if (__shfl_sync(FULL, waiter, 0)) {
         const uint64_t t0 = globaltimer_ns();
         uint32_t nap = 32;
@@ -477,7 +490,6 @@ __device__ __forceinline__ void global_pass(const HystScratch &hs, int in_graph,
             st->list_count[cur] = 0;
             st->uf_entries = count;           // a union-find stage after this pass labels these tiles
             st->uf_count = 0;
-            st->list_head = 0;
             st->q_head = st->q_tail = 0;
             st->q_open = st->q_waiters = 0;
             st->pass = k + 1;
@@ -498,8 +510,8 @@ __device__ __forceinline__ void global_pass(const HystScratch &hs, int in_graph,
 __global__ void __launch_bounds__(THREADS)
 hyst_global_kernel(HystScratch hs, int in_graph, cudaGraphConditionalHandle cond)
 {
-    __shared__ uint32_t visits;
-    global_pass(hs, in_graph, cond, visits);
+    __shared__ uint32_t visits, warps_on_list;
+    global_pass(hs, in_graph, cond, visits, warps_on_list);
 }
 
 // Grid-wide barrier of a cooperative launch (every CTA is resident): the last
@@ -778,9 +790,9 @@ __device__ __forceinline__ bool uf_resolve(const HystScratch &hs)
 __global__ void __launch_bounds__(THREADS, 2)
 hyst_global_coop_kernel(HystScratch hs)
 {
-    __shared__ uint32_t visits;
+    __shared__ uint32_t visits, warps_on_list;
     for (;;) {
-        global_pass(hs, 0, cudaGraphConditionalHandle{}, visits);
+        global_pass(hs, 0, cudaGraphConditionalHandle{}, visits, warps_on_list);
         if (!grid_barrier(hs.state)) break;
         if (!*(volatile uint32_t *)&hs.state->keep_going) break;
         // work left after the first pass: resolve every long chain at once

@@ -1,13 +1,16 @@
-// k1_fused.cu -- the integer path of Steps 1-4 of the paper's Sec. 2.2.1 in one
-// kernel: Gaussian -> Sobel -> strength -> direction sector -> non-maximum
-// suppression -> double threshold -> tile-local hysteresis. The image is read
-// once and the edge map written once; the class map never leaves the SM.
+// k1_fused.cu -- the integer path of Steps 1-3 and Step 4's double threshold
+// of the paper's Sec. 2.2.1 in one kernel: Gaussian -> Sobel -> strength ->
+// direction sector -> non-maximum suppression -> double threshold, written as
+// two bits per pixel (weak-or-strong, strong) into the tile scratch; the tile
+// fill kernel (tile_fill.cu), launched right after it, runs the tile-local
+// hysteresis and writes the edge map. The image is read once and the edge map
+// written once; the class map never exists as bytes.
 //
 // A CTA is one warp. Its unit of work is a strip of 480 columns x BAND rows
 // (15 x BAND/32 hysteresis tiles). Lane L owns the 16 pixels starting at
 // column X0 - 16 + 16 L; lanes 1..30 give the output, lanes 0 and 31 supply
 // the halo columns. The warp slides down the BAND rows plus a 4-row halo on
-// each side, four rows per group:
+// each side, three rows per group:
 //   - TMA stages the strip's input rows (512 bytes from X0 - 16, as two
 //     256-byte boxes) three rows per chunk into a 2-stage ring, one mbarrier
 //     per stage;
@@ -30,10 +33,9 @@
 //     for its pixel: fp32 strength (exact), the Q15 sector test, suppression
 //     against the two neighbours its sector names, and the Step 4
 //     thresholds, setting bits in the tile row's weak/strong bitmasks;
-//   - after every 32 rows the warp runs the tile flood fill of the
-//     hysteresis on the 15 tiles of that tile row and writes 255/0 edge bytes
-//     plus the tile border masks and pending bitmaps that the global passes
-//     need (or, for canny_classify, the class bytes).
+//   - after every 32 rows the warp writes the tile row's class bitmasks, 64
+//     words per tile (rows 0..31 weak-or-strong, then rows 0..31 strong), for
+//     the tile fill (or, for canny_classify, the class bytes).
 // Units away from every image border run a copy of the band loop compiled
 // without the border and row-range tests.
 #include <cuda.h>

@@ -13,9 +13,11 @@
 //                (the lanes of a warp first check a chunk of entries for seeds
 //                at once). A neighbour whose facing border gained edges next
 //                to its pending pixels is followed at once by the same warp;
-//                further seeded entries and branches go to an in-pass queue
-//                that idle warps drain, and what the chain's budget cannot
-//                take is listed for the next pass. Passes repeat until the
+//                in the cooperative launch (every CTA resident) further seeded
+//                entries and branches go to an in-pass queue that idle warps
+//                drain, in one launch per pass to the warp's own stack; what
+//                the budget cannot take is listed for the next pass. Passes
+//                repeat until the
 //                worklist is empty, decided by the last CTA of each pass: for a
 //                single image all passes run in one cooperative launch (a
 //                bounded grid barrier between them); inside the batch and
@@ -59,6 +61,10 @@ enum { NB_U, NB_UL, NB_UR, NB_D, NB_DL, NB_DR, NB_L, NB_R };
 // Tiles a chain may be followed into within a pass before the rest is listed
 // for the next pass (the default of the chase budget).
 constexpr int CHASE_BUDGET = 16;
+// The one-launch-per-pass kernel's default budget per worklist entry, and the
+// depth of its per-warp chase stack.
+constexpr int STACK_BUDGET = 64;
+constexpr int CHASE_STACK = 32;
 // The union-find stage follows the first pass only when that pass's worklist
 // held at most this many tiles: its cost grows with the tiles it labels, a
 // pass's with the length of the chains it follows, so images with many short
@@ -208,7 +214,7 @@ __device__ __forceinline__ bool chase_seeds(const HystScratch &hs, uint32_t t, i
 // facing words lane 0 read in chase_seeds (older words may hold pixels that
 // are no longer pending: that only costs a step that finds no seeds).
 __device__ __forceinline__ uint32_t grow_tile(const HystScratch &hs, uint32_t t, const TileSeeds &sd, int lane,
-                                              uint32_t p, const Facing &fp)
+                                              uint32_t p, const Facing &fp, bool rowwise = true)
 {
     const HystImage &im = sd.im;
     const int tx = sd.tx, ty = sd.ty;
@@ -221,7 +227,12 @@ __device__ __forceinline__ uint32_t grow_tile(const HystScratch &hs, uint32_t t,
     const uint32_t e = flood_tile(e0, p, lane);
 
     // write the new edges and the shrunken pending set
-    store_new_edges(im, tx, ty, lane, e);
+    if (rowwise) {
+        store_new_edges(im, tx, ty, lane, e);
+    } else if (e) {
+        uint8_t *row = im.map + (int64_t)(ty * HT + lane) * im.pitch + tx * HT;
+        for (uint32_t bits = e; bits; bits &= bits - 1) row[__ffs(bits) - 1] = 255;
+    }
     p &= ~e;
     hs.pend_bits[(size_t)t * HT + lane] = p;
 
@@ -271,7 +282,112 @@ __device__ __forceinline__ uint32_t grow_tile(const HystScratch &hs, uint32_t t,
     return __shfl_sync(FULL, aff, 0);
 }
 
+// ---------------------------------------------------------------- one launch per pass
+// The pass of the one-launch-per-pass kernel (graph while-loops, the host-driven
+// loop), whose CTAs need not all be resident at once (batches on several
+// streams share the GPU): no warp waits for another. A warp that adds edges next to a
+// neighbour's pending pixels follows them into that neighbour at once (depth
+// first, up to CHASE_BUDGET tiles per worklist entry), so a chain of weak pixels
+// across many tiles costs one pass, not one pass per tile; what the budget or
+// the stack cannot take is queued for the next pass. A tile may be visited by
+// two warps at a time: both only add edges, and each re-reads the masks, so the
+// result is the same.
+// One pass (all CTAs of the grid). The last CTA to finish swaps the worklists,
+// counts the pass and sets keep_going (and, in a graph, the while-node's
+// condition).
+__device__ __forceinline__ void global_pass_stack(const HystScratch &hs, int in_graph, cudaGraphConditionalHandle cond,
+                                            uint32_t (&stack)[WARPS][CHASE_STACK], uint32_t &visits)
+{
+    HystState *st = hs.state;
+    const uint32_t k = *(volatile uint32_t *)&st->pass;
+    const uint32_t cur = k & 1u, nxt = cur ^ 1u;
+    uint32_t count = *(volatile uint32_t *)&st->list_count[cur];
+    if (!CANNY_CHECK(count <= hs.max_tiles, &st->error)) count = hs.max_tiles;
+    const int nimg = (int)st->nimg;
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const uint32_t warp = (blockIdx.x * THREADS + threadIdx.x) >> 5;
+    const uint32_t nwarps = gridDim.x * WARPS;
+    const uint32_t *list = hs.lists + (size_t)cur * hs.max_tiles;
+    const int chase_budget = st->chase_budget ? (int)st->chase_budget : STACK_BUDGET;
+    if (threadIdx.x == 0) visits = 0;
+    __syncthreads();
+    uint32_t my_visits = 0;
+    // each lane checks one worklist entry for seeds; the warp then grows the
+    // tiles that have some, one after the other, and follows their chains
+    for (uint32_t base = warp * 32u; base < count; base += nwarps * 32u) {
+        const uint32_t i = base + (uint32_t)lane;
+        uint32_t mine = 0;
+        bool has = false;
+        if (i < count) {
+            TileSeeds sd;
+            mine = __ldcg(&list[i]);      // (a cooperative launch reuses L1 across passes)
+            has = CANNY_CHECK(mine < hs.max_tiles, &st->error) && find_seeds(hs, mine, nimg, sd);
+        }
+        my_visits += (lane == 0) ? min(32u, count - base) : 0u;   // entries examined
+        uint32_t todo = __ballot_sync(FULL, has);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            uint32_t t = __shfl_sync(FULL, mine, src);
+            int sp = 0, budget = chase_budget;
+            for (;;) {
+                TileSeeds sd;
+                Facing fp;
+                uint32_t aff = 0, ntx = 0;
+                if (!CANNY_CHECK(t < hs.max_tiles, &st->error)) break;
+                const uint32_t p_row = __ldcg(&hs.pend_bits[(size_t)t * HT + lane]);   // issued with the masks
+                if (chase_seeds(hs, t, nimg, sd, lane, fp)) {
+                    aff = grow_tile(hs, t, sd, lane, p_row, fp, false);
+                    ntx = (uint32_t)sd.im.ntx;
+                }
+                ++my_visits;
+                while (aff) {
+                    const int d = __ffs(aff) - 1;
+                    aff &= aff - 1;
+                    const uint32_t n = neighbour(t, d, ntx);
+                    if (sp < CHASE_STACK && budget > 0) {
+                        if (lane == 0) stack[wl][sp] = n;
+                        ++sp;
+                        --budget;
+                    } else if (lane == 0) {
+                        push(hs, nxt, n, k + 2);
+                    }
+                }
+                __syncwarp();
+                if (sp == 0) break;
+                t = stack[wl][--sp];
+                __syncwarp();
+            }
+        }
+    }
+    if (lane == 0) atomicAdd(&visits, my_visits);
+
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(&st->visited, visits);
+        __threadfence();
+        if (atomicAdd(&st->done_ctas, 1u) == gridDim.x - 1) {
+            __threadfence();
+            const uint32_t next = atomicAdd(&st->list_count[nxt], 0u);
+            st->list_count[cur] = 0;
+            st->pass = k + 1;
+            st->done_ctas = 0;
+            bool more = next > 0;
+            if (more && k + 1 >= st->max_passes) {
+                st->error |= 1u;
+                more = false;
+            }
+            st->keep_going = more ? 1u : 0u;
+            __threadfence();
+            if (in_graph) cudaGraphSetConditional(cond, more ? 1u : 0u);
+        }
+    }
+}
+
+
 // ---------------------------------------------------------------- the in-pass queue
+// (the cooperative kernel's passes: every CTA of its grid is resident, so a
+// warp may wait for work that another warp queues)
 // Work of one pass that any warp may take: a worklist entry found seeded while
 // its warp was busy with another, or a branch of a chain (the neighbours a
 // visit affected beyond the one its warp follows). Each item carries what is
@@ -510,8 +626,9 @@ __device__ __forceinline__ void global_pass(const HystScratch &hs, int in_graph,
 __global__ void __launch_bounds__(THREADS)
 hyst_global_kernel(HystScratch hs, int in_graph, cudaGraphConditionalHandle cond)
 {
-    __shared__ uint32_t visits, warps_on_list;
-    global_pass(hs, in_graph, cond, visits, warps_on_list);
+    __shared__ uint32_t stack[WARPS][CHASE_STACK];
+    __shared__ uint32_t visits;
+    global_pass_stack(hs, in_graph, cond, stack, visits);
 }
 
 // Grid-wide barrier of a cooperative launch (every CTA is resident): the last

@@ -711,6 +711,18 @@ bool arena_failure_injected() { return take_failure(g_fail_arena); }
 
 bool host_passes_injected() { return take_failure(g_host_passes); }
 
+canny_status batch_reserve(canny_ctx *c, uint32_t max_images, uint32_t max_tiles)
+{
+    if (!c || c->p.path != CANNY_PATH_INT) return CANNY_EINVAL;
+    canny_status st = ensure_blob(c, max_images < 1 ? 1 : max_images);
+    if (st == CANNY_OK) st = ensure_hyst(c, max_tiles, c->blob_cap);
+    // the graphs for inputs the TMA path reads, instantiated now rather than
+    // on a slot's first batch
+    for (auto &sl : c->slots)
+        if (st == CANNY_OK && !sl.valid[1]) st = build_batch_graph(c, sl, 1);
+    return st;
+}
+
 }  // namespace canny
 
 extern "C" {

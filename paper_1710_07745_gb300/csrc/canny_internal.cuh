@@ -252,6 +252,11 @@ bool hyst_coop_supported();
 // single-image global passes are to be driven from the host as when the device
 // refuses the cooperative grid.
 bool host_passes_injected();
+// Integer-path batches: size the context's descriptor blob and hysteresis
+// scratch for batches of up to max_images images and max_tiles tiles, so that
+// no later batch of that size grows them (a growth synchronises the device and
+// rebuilds the batch graphs), and instantiate the batch graphs.
+canny_status batch_reserve(canny_ctx *c, uint32_t max_images, uint32_t max_tiles);
 cudaError_t launch_hyst_global_coop(const HystScratch &hs, cudaStream_t s);
 // Test hook: barrier arrivals that no CTA makes, so the next cooperative
 // launch's barrier never completes and its bounded wait runs out.

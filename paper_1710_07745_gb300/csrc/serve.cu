@@ -179,6 +179,15 @@ extern "C" canny_status canny_serve(const canny_serve_config *cfg, int n, const 
     Arena arena;
     if (!arena.init((size_t)cfg->memory_budget_bytes)) return CANNY_ENOMEM;
 
+    // most tiles one batch can hold: its pixels in whole tiles plus a partial
+    // row and column of tiles per image, and never more than the whole trace
+    uint64_t trace_tiles = 0;
+    for (int i = 0; i < n; ++i)
+        trace_tiles += (uint64_t)((reqs[i].w + HT - 1) / HT) * (uint64_t)((reqs[i].h + HT - 1) / HT);
+    const uint64_t per_image = (uint64_t)(max_w + HT - 1) / HT + (uint64_t)(max_h + HT - 1) / HT + 1;
+    const uint64_t batch_bound = (uint64_t)cfg->max_batch_pixels / (HT * HT) +
+                                 (uint64_t)std::min(cfg->max_batch_images, n) * per_image;
+    const uint32_t batch_tiles = (uint32_t)std::min<uint64_t>({trace_tiles, batch_bound, 0x7fffffffull});
     const int nlanes = cfg->serial ? 1 : cfg->streams;
     std::vector<Lane> lanes(nlanes);
     canny_status st = CANNY_OK;
@@ -201,8 +210,15 @@ extern "C" canny_status canny_serve(const canny_serve_config *cfg, int n, const 
             break;
         }
         if (cfg->band) {
-            canny_tuning t = {cfg->band, cfg->ctas_per_sm, 0.0, 0, 0};
+            canny_tuning t = {cfg->band, cfg->ctas_per_sm, 0.0, 0, 0, 0, 0};
             st = canny_set_tuning(L.ctx, &t);
+            if (st != CANNY_OK) break;
+        }
+        // size the lane for its largest possible batch now, so that no batch
+        // grows the descriptor blob or the hysteresis scratch (each growth
+        // synchronises the whole device, stalling every lane) while requests wait
+        if (!cfg->serial) {
+            st = batch_reserve(L.ctx, (uint32_t)std::min(cfg->max_batch_images, n), batch_tiles);
             if (st != CANNY_OK) break;
         }
     }

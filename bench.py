@@ -47,15 +47,15 @@ K1_DESIGN_BYTES_PER_PX = 2.5
 # ncu DRAM traffic of the two stencil-stage kernels per 16384^2 image, valid only for
 # the kernel sources it was measured on (a 16384 x 8192 capture, x2: both kernels'
 # traffic is proportional to the pixels)
-K1_TRAFFIC = {"sha256_prefix": "123c42479c581de3", "bytes": 563.6e6}
+K1_TRAFFIC = {"sha256_prefix": "2895ae67f99649c3", "bytes": 564.5e6}
 # whole pipeline floor (the spec minimum): read the image, write the edge map
 PIPE_BYTES_PER_PX = 2
 # ncu smsp__inst_executed.sum of the two stencil-stage kernels per pixel (same
 # capture and sources as K1_TRAFFIC)
-K1_INST = {"sha256_prefix": "123c42479c581de3", "warp_inst_per_px": 0.9737}
+K1_INST = {"sha256_prefix": "2895ae67f99649c3", "warp_inst_per_px": 0.9737}
 # ncu DRAM traffic of the global hysteresis passes per 16384^2 image (same capture,
 # x2: an estimate, since the passes' work follows the image's chains, not its area)
-K3_TRAFFIC = {"sha256_prefix": "3b040c6d0a504184", "bytes": 8.8e6}
+K3_TRAFFIC = {"sha256_prefix": "577665447b4bdf0c", "bytes": 8.8e6}
 # warp instructions an SM can issue per clock (4 schedulers, one each)
 ISSUE_PER_SM_CLK = 4
 
@@ -653,7 +653,7 @@ def measure_chains(tile_counts=(256, 1024, 4096, 16384), runs: int = 5) -> list:
 SERVE_POOL, SERVE_LO, SERVE_HI, SERVE_SEED = 256, 128, 4096, 5000
 
 
-def measure_serving(n_requests: int, loads=(0.1, 0.25, 0.5, 0.9, 1.5), budget_gb: float = 16.0, streams: int = 4,
+def measure_serving(n_requests: int, loads=(0.1, 0.25, 0.5, 0.9, 1.5), budget_gb: float = 16.0, streams: int = 8,
                     max_trace_s: float = 8.0) -> dict:
     """Continuous-batching server on Poisson arrivals, sides log-uniform in [128, 4096].
 
@@ -684,9 +684,9 @@ def measure_serving(n_requests: int, loads=(0.1, 0.25, 0.5, 0.9, 1.5), budget_gb
                                     float(t[i] - t[0]) if rate else 0.0) for i in range(n)]
 
     def cfg(serial):
-        # at most 64 Mpixel a batch: with 4 streams, smaller batches overlap one
-        # batch's upload with another's stencil (all-at-once capacity 144 Gpixel/s
-        # against 123 for 3 streams of 256 Mpixel batches)
+        # at most 64 Mpixel a batch on 8 streams: smaller batches on more streams
+        # overlap one batch's upload with others' kernels (all-at-once capacity
+        # 180 Gpixel/s, against 155 on 6 streams and 140 on 4)
         return canny.canny_serve_config(budget_gb * 2 ** 30, streams, 4096, 64 << 20, serial, LOW, HIGH, 0, 0)
 
     def summary(rep, offered=None):

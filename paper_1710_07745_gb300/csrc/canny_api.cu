@@ -257,7 +257,7 @@ canny_status run_global(canny_ctx *c, cudaStream_t s)
     if (c->use_graph && hyst_coop_supported() && !host_passes_injected()) {
         cudaError_t e = cudaSuccess;
         if (take_failure(g_fail_barrier)) e = launch_hyst_phantom_arrival(c->hs, s);   // test hook
-        if (e == cudaSuccess) e = launch_hyst_global_coop(c->hs, s);
+        if (e == cudaSuccess) e = launch_hyst_global_coop(c->hs, s, (uint32_t)c->last.tiles);
         // a device shared with other work (fewer SMs than at start-up) may refuse
         // the grid: then the passes are driven from the host below
         if (e != cudaErrorCooperativeLaunchTooLarge) return from_cuda(e);

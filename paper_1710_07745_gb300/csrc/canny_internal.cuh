@@ -257,7 +257,9 @@ bool host_passes_injected();
 // no later batch of that size grows them (a growth synchronises the device and
 // rebuilds the batch graphs), and instantiate the batch graphs.
 canny_status batch_reserve(canny_ctx *c, uint32_t max_images, uint32_t max_tiles);
-cudaError_t launch_hyst_global_coop(const HystScratch &hs, cudaStream_t s);
+// All global passes of a single image in one cooperative launch: a grid of
+// 2 x SMs CTAs, or fewer for an image of ntiles tiles (0: the full grid).
+cudaError_t launch_hyst_global_coop(const HystScratch &hs, cudaStream_t s, uint32_t ntiles = 0);
 // Test hook: barrier arrivals that no CTA makes, so the next cooperative
 // launch's barrier never completes and its bounded wait runs out.
 cudaError_t launch_hyst_phantom_arrival(const HystScratch &hs, cudaStream_t s);

@@ -24,6 +24,8 @@
 //                frame graphs a CUDA-graph while-node drives the loop.
 // Pending pixels live only in a compact bitmap, so the map never holds a value
 // other than 0/255 and no clean-up sweep is needed.
+#include <algorithm>
+
 #include "hyst_tile.cuh"
 
 namespace canny {
@@ -214,7 +216,8 @@ __device__ __forceinline__ bool chase_seeds(const HystScratch &hs, uint32_t t, i
 // facing words lane 0 read in chase_seeds (older words may hold pixels that
 // are no longer pending: that only costs a step that finds no seeds).
 __device__ __forceinline__ uint32_t grow_tile(const HystScratch &hs, uint32_t t, const TileSeeds &sd, int lane,
-                                              uint32_t p, const Facing &fp, bool rowwise = true)
+                                              uint32_t p, const Facing &fp, bool rowwise = true,
+                                              TileMasks *after = nullptr)
 {
     const HystImage &im = sd.im;
     const int tx = sd.tx, ty = sd.ty;
@@ -240,6 +243,11 @@ __device__ __forceinline__ uint32_t grow_tile(const HystScratch &hs, uint32_t t,
     const uint32_t e_left = __ballot_sync(FULL, e & 1u), e_right = __ballot_sync(FULL, e >> 31);
     const uint32_t p_top = __shfl_sync(FULL, p, 0), p_bot = __shfl_sync(FULL, p, HT - 1);
     const uint32_t p_left = __ballot_sync(FULL, p & 1u), p_right = __ballot_sync(FULL, p >> 31);
+    if (after) {
+        // the border edges this step added and the border pixels left pending (every lane)
+        after->edge_top = e_top; after->edge_bottom = e_bot; after->edge_left = e_left; after->edge_right = e_right;
+        after->pend_top = p_top; after->pend_bottom = p_bot; after->pend_left = p_left; after->pend_right = p_right;
+    }
     uint32_t aff = 0;
     if (lane == 0) {
         TileMasks *mt = &hs.masks[t];
@@ -385,6 +393,76 @@ __device__ __forceinline__ void global_pass_stack(const HystScratch &hs, int in_
 }
 
 
+// ---------------------------------------------------------------- the next step, read ahead
+// Offsets (dx, dy) of the neighbour in direction d (NB_*).
+__device__ __forceinline__ int nb_dx(int d) { return (int)((0x8861u >> (2 * d)) & 3u) - 1; }
+__device__ __forceinline__ int nb_dy(int d) { return (int)((0x5A80u >> (2 * d)) & 3u) - 1; }
+
+// Issued before a step's flood, so that the loads of the next step are in flight
+// while it runs: lane k < 25 loads the masks of the tile at offset
+// (k % 5 - 2, k / 5 - 2) from t (zero outside the image), every lane its row of
+// the pending bitmap of each of t's eight neighbours (zero outside). The words
+// may be older than the next step's start; a pending word only ever loses bits
+// and an edge another warp adds next to a pending pixel is followed by that
+// warp, so an older word costs at most a wasted step, never a missed seed.
+__device__ __forceinline__ void read_ahead(const HystScratch &hs, const TileSeeds &sd, uint32_t t, int lane,
+                                           TileMasks &blk, uint32_t (&pn)[8])
+{
+    const HystImage &im = sd.im;
+    const int dx = lane % 5 - 2, dy = lane / 5 - 2;
+    const int x = sd.tx + dx, y = sd.ty + dy;
+    blk = TileMasks{0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    if (lane < 25 && x >= 0 && x < im.ntx && y >= 0 && y < im.nty)
+        blk = masks_cg(&hs.masks[(uint32_t)((int64_t)t + (int64_t)dy * im.ntx + dx)]);
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        const int nx = sd.tx + nb_dx(d), ny = sd.ty + nb_dy(d);
+        pn[d] = (nx >= 0 && nx < im.ntx && ny >= 0 && ny < im.nty)
+                    ? __ldcg(&hs.pend_bits[(size_t)neighbour(t, d, (uint32_t)im.ntx) * HT + lane]) : 0u;
+    }
+}
+
+// The seeds, facing pending words and pending row of t's neighbour in direction
+// d0, from the words read ahead (every lane). t's own words are its masks after
+// this step: the edges it had plus those the step added, and the pixels left
+// pending.
+__device__ __forceinline__ void step_ahead(TileSeeds &sd, Facing &fp, uint32_t &p_row, const TileMasks &blk,
+                                           const uint32_t (&pn)[8], const TileMasks &after, int d0)
+{
+    const int ox = nb_dx(d0), oy = nb_dy(d0);
+    enum { ET, EB, EL, ER, PT, PB, PL, PR };
+    auto get = [&](int dx, int dy, int f) -> uint32_t {
+        const int k = (dy + 2) * 5 + (dx + 2);
+        const uint32_t w = f == ET ? blk.edge_top : f == EB ? blk.edge_bottom : f == EL ? blk.edge_left :
+                           f == ER ? blk.edge_right : f == PT ? blk.pend_top : f == PB ? blk.pend_bottom :
+                           f == PL ? blk.pend_left : blk.pend_right;
+        uint32_t v = __shfl_sync(FULL, w, k);
+        if (dx == 0 && dy == 0) {
+            const uint32_t a = f == ET ? after.edge_top : f == EB ? after.edge_bottom : f == EL ? after.edge_left :
+                               f == ER ? after.edge_right : f == PT ? after.pend_top : f == PB ? after.pend_bottom :
+                               f == PL ? after.pend_left : after.pend_right;
+            v = f < PT ? (v | a) : a;
+        }
+        return v;
+    };
+    const uint32_t pt = get(ox, oy, PT), pb = get(ox, oy, PB), pl = get(ox, oy, PL), pr = get(ox, oy, PR);
+    const uint32_t eu = get(ox, oy - 1, EB), eul = get(ox - 1, oy - 1, EB), eur = get(ox + 1, oy - 1, EB);
+    const uint32_t ed = get(ox, oy + 1, ET), edl = get(ox - 1, oy + 1, ET), edr = get(ox + 1, oy + 1, ET);
+    const uint32_t el = get(ox - 1, oy, ER), er = get(ox + 1, oy, EL);
+    fp.u = get(ox, oy - 1, PB); fp.ul = get(ox - 1, oy - 1, PB); fp.ur = get(ox + 1, oy - 1, PB);
+    fp.d = get(ox, oy + 1, PT); fp.dl = get(ox - 1, oy + 1, PT); fp.dr = get(ox + 1, oy + 1, PT);
+    fp.l = get(ox - 1, oy, PR); fp.r = get(ox + 1, oy, PL);
+    sd.top = (eu | (eu << 1) | (eu >> 1) | (eul >> 31) | ((eur & 1u) << 31)) & pt;
+    sd.bot = (ed | (ed << 1) | (ed >> 1) | (edl >> 31) | ((edr & 1u) << 31)) & pb;
+    sd.left = dilate(el) & pl;
+    sd.right = dilate(er) & pr;
+    sd.tx += ox;
+    sd.ty += oy;
+#pragma unroll
+    for (int d = 0; d < 8; ++d)
+        if (d == d0) p_row = pn[d];
+}
+
 // ---------------------------------------------------------------- the in-pass queue
 // (the cooperative kernel's passes: every CTA of its grid is resident, so a
 // warp may wait for work that another warp queues)
@@ -483,16 +561,29 @@ __device__ __forceinline__ void global_pass(const HystScratch &hs, int in_graph,
     uint32_t my_visits = 0;
     bool pushed = false;                       // this thread queued an item
 
-    // follow the chain from tile t with budget b (whole warp)
+    // follow the chain from tile t with budget b (whole warp); the words of the
+    // step that follows a step are read during its flood
     auto chase = [&](uint32_t t, uint32_t b) {
+        TileSeeds sd;
+        Facing fp;
+        uint32_t p_row = 0u;
+        bool ahead = false;                    // sd, fp and p_row of t are already known
         for (;;) {
-            TileSeeds sd;
-            Facing fp;
             uint32_t aff = 0, ntx = 0;
             if (!CANNY_CHECK(t < hs.max_tiles, &st->error)) return;
-            const uint32_t p_row = __ldcg(&hs.pend_bits[(size_t)t * HT + lane]);   // issued with the masks
-            if (chase_seeds(hs, t, nimg, sd, lane, fp)) {
-                aff = grow_tile(hs, t, sd, lane, p_row, fp);
+            bool has;
+            if (ahead) {
+                has = (sd.top | sd.bot | sd.left | sd.right) != 0u;
+            } else {
+                p_row = __ldcg(&hs.pend_bits[(size_t)t * HT + lane]);   // issued with the masks
+                has = chase_seeds(hs, t, nimg, sd, lane, fp);
+            }
+            ahead = false;
+            TileMasks blk, after;
+            uint32_t pn[8];
+            if (has) {
+                read_ahead(hs, sd, t, lane, blk, pn);
+                aff = grow_tile(hs, t, sd, lane, p_row, fp, true, &after);
                 ntx = (uint32_t)sd.im.ntx;
             }
             ++my_visits;
@@ -524,6 +615,8 @@ __device__ __forceinline__ void global_pass(const HystScratch &hs, int in_graph,
                 if (lane == 0) push(hs, nxt, next, k + 2);
                 return;
             }
+            step_ahead(sd, fp, p_row, blk, pn, after, d0);
+            ahead = true;
             t = next;
             --b;
         }
@@ -1045,13 +1138,16 @@ cudaError_t launch_hyst_phantom_arrival(const HystScratch &hs, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_hyst_global_coop(const HystScratch &hs, cudaStream_t s)
+cudaError_t launch_hyst_global_coop(const HystScratch &hs, cudaStream_t s, uint32_t ntiles)
 {
     if (!hyst_coop_supported()) return cudaErrorNotSupported;
     HystScratch hs_copy = hs;
     void *args[] = {&hs_copy};
-    return cudaLaunchCooperativeKernel((void *)hyst_global_coop_kernel, dim3(hyst_pass_grid()), dim3(THREADS), args,
-                                       0, s);
+    // a small image needs fewer CTAs (a warp per tile at most), and every pass's
+    // end and grid barrier costs an arrival per CTA
+    int grid = hyst_pass_grid();
+    if (ntiles > 0) grid = (int)std::min<uint64_t>((uint64_t)grid, std::max<uint64_t>(4, ((uint64_t)ntiles + WARPS - 1) / WARPS));
+    return cudaLaunchCooperativeKernel((void *)hyst_global_coop_kernel, dim3(grid), dim3(THREADS), args, 0, s);
 }
 
 // Append { while (cond) hyst_global_kernel } to graph g after the given nodes.

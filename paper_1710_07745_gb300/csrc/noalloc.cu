@@ -115,7 +115,7 @@ extern "C" canny_status canny_run_noalloc(const uint8_t *d_in, int in_pitch, uin
     // them: one pass, read the control block, repeat
     HystState st = {};
     if (hyst_coop_supported() && !host_passes_injected()) {
-        e = launch_hyst_global_coop(hs, s);
+        e = launch_hyst_global_coop(hs, s, (uint32_t)ntiles);
         if (e != cudaErrorCooperativeLaunchTooLarge) {
             if (e == cudaSuccess) e = cudaMemcpyAsync(&st, hs.state, sizeof(st), cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);

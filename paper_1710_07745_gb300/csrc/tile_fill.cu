@@ -20,7 +20,7 @@ constexpr int FILL_WARPS = 8;
 constexpr int FILL_THREADS = FILL_WARPS * 32;
 
 template <bool SINGLE>
-__global__ void __launch_bounds__(FILL_THREADS)
+__global__ void __launch_bounds__(FILL_THREADS, 6)
 hyst_fill_kernel(HystScratch hs, HystImage single, uint32_t ntiles_single)
 {
     __shared__ uint32_t s_queued, s_pending, s_base;

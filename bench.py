@@ -47,15 +47,15 @@ K1_DESIGN_BYTES_PER_PX = 2.5
 # ncu DRAM traffic of the two stencil-stage kernels per 16384^2 image, valid only for
 # the kernel sources it was measured on (a 16384 x 8192 capture, x2: both kernels'
 # traffic is proportional to the pixels)
-K1_TRAFFIC = {"sha256_prefix": "2895ae67f99649c3", "bytes": 564.5e6}
+K1_TRAFFIC = {"sha256_prefix": "f8399db8212309d6", "bytes": 568.5e6}
 # whole pipeline floor (the spec minimum): read the image, write the edge map
 PIPE_BYTES_PER_PX = 2
 # ncu smsp__inst_executed.sum of the two stencil-stage kernels per pixel (same
 # capture and sources as K1_TRAFFIC)
-K1_INST = {"sha256_prefix": "2895ae67f99649c3", "warp_inst_per_px": 0.9737}
+K1_INST = {"sha256_prefix": "f8399db8212309d6", "warp_inst_per_px": 0.9740}
 # ncu DRAM traffic of the global hysteresis passes per 16384^2 image (same capture,
 # x2: an estimate, since the passes' work follows the image's chains, not its area)
-K3_TRAFFIC = {"sha256_prefix": "577665447b4bdf0c", "bytes": 8.8e6}
+K3_TRAFFIC = {"sha256_prefix": "ecd40c592ae66c79", "bytes": 9.46e6}
 # warp instructions an SM can issue per clock (4 schedulers, one each)
 ISSUE_PER_SM_CLK = 4
 

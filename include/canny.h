@@ -231,8 +231,10 @@ canny_status canny_read_timing(canny_ctx *ctx, canny_timing *out);
  *
  * Schedule of the global hysteresis passes (Step 4's connectivity search):
  * chase_budget is how many further tiles a weak chain may be followed into
- * within a pass before the rest is left to the next one (0, the default: 16;
- * else 1..4096). Where the passes run in one cooperative launch (single images;
+ * within a pass before the rest is left to the next one (1..4096; 0, the
+ * default, takes 16 in a cooperative launch, 64 in a loop of one launch per
+ * pass, and 4 for single images on the float path, whose long weak chains the
+ * union-find stage below resolves sooner than longer chases). Where the passes run in one cooperative launch (single images;
  * batches with batch_passes = 1), work left after the first pass is resolved at
  * once by union-find over tile-border components when that pass's worklist held
  * at most 32768 tiles, and by further passes otherwise. batch_passes picks how

@@ -654,7 +654,7 @@ SERVE_POOL, SERVE_LO, SERVE_HI, SERVE_SEED = 256, 128, 4096, 5000
 
 
 def measure_serving(n_requests: int, loads=(0.1, 0.25, 0.5, 0.9, 1.5), budget_gb: float = 16.0, streams: int = 8,
-                    max_trace_s: float = 8.0) -> dict:
+                    max_trace_s: float = 10.0) -> dict:
     """Continuous-batching server on Poisson arrivals, sides log-uniform in [128, 4096].
 
     Request i carries image i mod 256 of a seeded pool (the sizes follow the stated

@@ -338,9 +338,11 @@ typedef struct {
  * continuous batching (integer path).
  * Requests arriving while earlier ones run are admitted in arrival order as
  * soon as the memory budget has room for their input and output buffers;
- * every idle stream takes all admitted, not-yet-running requests as one
- * canny_run_batch, so batches of later arrivals overlap earlier ones on the
- * GPU. Each result equals the request's canny_run_pitched result. Writes the
+ * the idle streams share the admitted, not-yet-running requests in arrival
+ * order, each taking about an equal part of their pixels as one
+ * canny_run_batch (a lone idle stream takes them all, up to the batch
+ * limits), so batches of later arrivals overlap earlier ones on the GPU.
+ * Each result equals the request's canny_run_pitched result. Writes the
  * per-request latencies (ms) to latency_ms if not NULL. Synchronous: returns
  * when every request has completed. The budget is allocated once per call.
  * CANNY_EINVAL if a request's input and output buffers (16-byte pitched rows)

@@ -2,8 +2,9 @@
 //
 // Requests (host images with arrival times) are admitted in arrival order as
 // device memory frees up: each admitted request gets its input and output
-// buffers from a device arena of a fixed byte budget, and every stream that is
-// idle takes all admitted, not-yet-running requests as one batch: one gather
+// buffers from a device arena of a fixed byte budget, and the idle streams
+// share the admitted, not-yet-running requests, each taking its part as one
+// batch (a lone idle stream takes them all, up to the batch limits): one gather
 // launch uploads their pinned host images (a copy-engine copy serves any other
 // host buffer), one canny_run_batch runs them, one scatter launch writes the
 // edge maps back. Several streams keep batches in flight at once, so new
@@ -20,6 +21,7 @@
 #include <vector>
 
 #include "canny_internal.cuh"
+#include "serve_policy.h"
 
 namespace canny {
 namespace {
@@ -264,19 +266,21 @@ extern "C" canny_status canny_serve(const canny_serve_config *cfg, int n, const 
             admitted.push_back({waiting.front(), in, o, pitch, bytes});
             waiting.pop_front();
         }
-        // every idle stream takes the admitted requests as one batch
+        // the idle streams share the admitted requests (serve_policy.h)
         bool launched = false;
+        int idle = 0;
+        int64_t admitted_px = 0;
+        for (const Lane &L : lanes) idle += L.running.empty() ? 1 : 0;
+        auto px_of = [&](size_t i) { return (int64_t)reqs[admitted[i].req].w * reqs[admitted[i].req].h; };
+        if (idle > 0)
+            for (size_t i = 0; i < admitted.size(); ++i) admitted_px += px_of(i);
         for (auto &L : lanes) {
             if (!L.running.empty() || admitted.empty()) continue;
             std::vector<canny_image> imgs;
-            int64_t px = 0;
-            size_t k = 0;
-            for (; k < admitted.size(); ++k) {
-                const canny_request &r = reqs[admitted[k].req];
-                const int64_t a = (int64_t)r.w * r.h;
-                if ((int)k >= cfg->max_batch_images || px + a > cfg->max_batch_pixels || (cfg->serial && k >= 1)) break;
-                px += a;
-            }
+            const size_t k = batch_take(px_of, admitted.size(), cfg->max_batch_images, cfg->max_batch_pixels,
+                                        batch_share(admitted_px, idle), cfg->serial != 0);
+            for (size_t i = 0; i < k; ++i) admitted_px -= px_of(i);
+            --idle;
             L.running.assign(admitted.begin(), admitted.begin() + (long)k);
             admitted.erase(admitted.begin(), admitted.begin() + (long)k);
             for (const Admitted &a : L.running) {

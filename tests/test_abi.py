@@ -103,3 +103,41 @@ def test_inject_faults_rejects_negative_counts(lib):
     assert lib.canny_inject_faults(None) == canny.CANNY_EINVAL
     ok = canny.canny_fault_injection(0, 0, 0, 0)
     assert lib.canny_inject_faults(ctypes.byref(ok)) == canny.CANNY_OK
+
+
+def test_serve_rejects_bad_configs_and_requests_without_cuda(lib):
+    # canny_serve checks its configuration and the whole trace before it
+    # allocates anything; an empty trace completes at once
+    import numpy as np
+    from paper_1710_07745_gb300 import canny
+    img = np.zeros((40, 64), np.uint8)
+    ptr = img.ctypes.data
+
+    def serve(cfg, reqs):
+        arr = (canny.canny_request * max(len(reqs), 1))(*reqs)
+        rep = canny.canny_serve_report()
+        return lib.canny_serve(ctypes.byref(cfg) if cfg is not None else None, len(reqs), arr, None,
+                               ctypes.byref(rep)), rep
+
+    def cfg(**kw):
+        c = canny.canny_serve_config(float(1 << 24), 2, 64, 1 << 20, 0, 40, 100, 0, 0)
+        for k, v in kw.items():
+            setattr(c, k, v)
+        return c
+
+    good = canny.canny_request(64, 40, ptr, 64, None, 0, 0.0)
+    assert serve(None, [good])[0] == canny.CANNY_EINVAL
+    for bad in [dict(streams=0), dict(max_batch_images=0), dict(max_batch_images=65536),
+                dict(max_batch_pixels=0), dict(memory_budget_bytes=0.0)]:
+        assert serve(cfg(**bad), [good])[0] == canny.CANNY_EINVAL, bad
+    for bad in [canny.canny_request(0, 40, ptr, 64, None, 0, 0.0),     # empty image
+                canny.canny_request(64, 40, None, 64, None, 0, 0.0),   # no input
+                canny.canny_request(64, 40, ptr, 63, None, 0, 0.0),    # pitch below the width
+                canny.canny_request(64, 40, ptr, 64, ptr, 32, 0.0)]:   # output pitch below the width
+        assert serve(cfg(), [bad])[0] == canny.CANNY_EINVAL
+    late_first = [canny.canny_request(64, 40, ptr, 64, None, 0, 1.0), canny.canny_request(64, 40, ptr, 64, None, 0, 0.5)]
+    assert serve(cfg(), late_first)[0] == canny.CANNY_EINVAL              # arrivals out of order
+    assert serve(cfg(memory_budget_bytes=4096.0), [good])[0] == canny.CANNY_EINVAL   # buffers beyond the budget
+    assert serve(cfg(max_batch_pixels=64 * 40 - 1), [good])[0] == canny.CANNY_EINVAL  # beyond one batch
+    st, rep = serve(cfg(), [])
+    assert st == canny.CANNY_OK and rep.completed == 0
